@@ -133,6 +133,30 @@ double orc_store(double w, int dtype) {
 
 static inline double clampd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
 
+/* Integer decisions taken from coordinates (which bin holds a cell centre,
+ * whether a cell overlaps a macro) are made in FP32, the precision the
+ * coordinates are stored in, with one stated sequence of IEEE single
+ * operations; the coordinate is first rounded to FP32.  Bin of a point:
+ * clamp(floor((x - xl) * (nb / (xh - xl))), 0, nb - 1) with xl and the scale
+ * each rounded to FP32. */
+static int32_t bin_of(double x, double xl, double xh, int32_t nb) {
+  float xf = (float)x;
+  float xlf = (float)xl;
+  float sc = (float)((double)nb / (xh - xl));
+  float t = (xf - xlf) * sc;
+  double f = floor((double)t);
+  if (!(f >= 0.0)) return 0;
+  if (f > (double)(nb - 1)) return nb - 1;
+  return (int32_t)f;
+}
+
+/* Positive-area overlap of a cell (centre x, y; size w, h) with a macro
+ * (centre xm, ym; size wm, hm): |x - xm| < (w + wm)/2 on both axes, in FP32. */
+static int overlaps(double x, double y, float w, float h, float xm, float ym, float wm, float hm) {
+  float dx = fabsf((float)x - xm), dy = fabsf((float)y - ym);
+  return dx < 0.5f * (w + wm) && dy < 0.5f * (h + hm);
+}
+
 /* ------------------------------------------------------ A1: static graph */
 
 /* Instance graph of the netlist hypergraph with macro pin expansion
@@ -434,9 +458,9 @@ static int cmp_pair(const void *a, const void *b) {
 }
 
 /* Every (movable cell with baseWeight > 0, macro) pair whose rectangles
- * overlap with positive area: |dx| < (w_i + w_m)/2 and |dy| < (h_i + h_m)/2.
- * Cells are bucketed by centre on a uniform grid only to skip pairs that
- * cannot overlap; the test itself is the one above.  Sorted by (cell, macro). */
+ * overlap with positive area (the FP32 test of overlaps()).  Cells are
+ * bucketed by centre on a uniform grid only to skip pairs that cannot
+ * overlap.  Sorted by (cell, macro). */
 static mpair_t *macro_pairs(const orc_graph *g, const double *gx, const double *gy,
                             int64_t *npairs) {
   const int32_t C = g->C;
@@ -472,18 +496,18 @@ static mpair_t *macro_pairs(const orc_graph *g, const double *gx, const double *
     int32_t c = g->macro_cell[m];
     double xm = g->fx[g->Nst + m], ym = g->fy[g->Nst + m];
     double ex = 0.5 * ((double)g->cw[c] + wmax), ey = 0.5 * ((double)g->ch[c] + hmax);
-    int32_t kx0 = (int32_t)clampd(floor((xm - ex - g->xl) / G), 0.0, gnx - 1.0);
-    int32_t kx1 = (int32_t)clampd(floor((xm + ex - g->xl) / G), 0.0, gnx - 1.0);
-    int32_t ky0 = (int32_t)clampd(floor((ym - ey - g->yl) / G), 0.0, gny - 1.0);
-    int32_t ky1 = (int32_t)clampd(floor((ym + ey - g->yl) / G), 0.0, gny - 1.0);
+    /* one extra bucket each side covers the FP32 rounding of the test */
+    int32_t kx0 = (int32_t)clampd(floor((xm - ex - g->xl) / G) - 1.0, 0.0, gnx - 1.0);
+    int32_t kx1 = (int32_t)clampd(floor((xm + ex - g->xl) / G) + 1.0, 0.0, gnx - 1.0);
+    int32_t ky0 = (int32_t)clampd(floor((ym - ey - g->yl) / G) - 1.0, 0.0, gny - 1.0);
+    int32_t ky1 = (int32_t)clampd(floor((ym + ey - g->yl) / G) + 1.0, 0.0, gny - 1.0);
     for (int32_t ky = ky0; ky <= ky1; ++ky)
       for (int32_t kx = kx0; kx <= kx1; ++kx) {
         int64_t k = (int64_t)ky * gnx + kx;
         for (int64_t t = bptr[k]; t < bptr[k + 1]; ++t) {
           int32_t i = bcell[t];
-          double dx = fabs(gx[i] - xm), dy = fabs(gy[i] - ym);
-          if (!(dx < 0.5 * ((double)g->cw[i] + (double)g->cw[c]) &&
-                dy < 0.5 * ((double)g->ch[i] + (double)g->ch[c])))
+          if (!overlaps(gx[i], gy[i], g->cw[i], g->ch[i], (float)xm, (float)ym, g->cw[c],
+                        g->ch[c]))
             continue;
           if (n == cap) {
             cap *= 2;
@@ -508,9 +532,9 @@ static mpair_t *macro_pairs(const orc_graph *g, const double *gx, const double *
  * Readings:
  *  - only movable cells with baseWeight > 0 get hint edges;
  *  - "overlaps macro m": the cell rectangle (centre, w, h) and the macro
- *    rectangle intersect with positive area;
+ *    rectangle intersect with positive area (decided in FP32, overlaps());
  *  - D_b = (sum of w*h of movable cells whose centre lies in b, ascending cell
- *    id) / bin area; bin of a point = clamp(floor((x - xl) / w_b), 0, nb-1);
+ *    id) / bin area; the bin of a centre is decided in FP32 (bin_of());
  *  - capacity of b = C * (A_bin - macro area in b) / A_bin;
  *  - phi_b = 2 / (1 + exp(-mu (D_b - C_b))) - 1  (= 2 sigmoid(.) - 1);
  *  - cell i is in N(b) when its centre bin lies in the n_x x n_y window of b,
@@ -532,9 +556,8 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
   for (int32_t i = 0; i < C; ++i) {
     g->cell_bin[i] = -1;
     if (g->ckind[i] != 0) continue;
-    double fxb = floor((gx[i] - g->xl) / g->wb), fyb = floor((gy[i] - g->yl) / g->hb);
-    int32_t bx = (int32_t)clampd(fxb, 0.0, (double)(g->nbx - 1));
-    int32_t by = (int32_t)clampd(fyb, 0.0, (double)(g->nby - 1));
+    int32_t bx = bin_of(gx[i], g->xl, g->xh, g->nbx);
+    int32_t by = bin_of(gy[i], g->yl, g->yh, g->nby);
     int32_t b = by * g->nbx + bx;
     g->cell_bin[i] = b;
     g->Db[b] += (double)g->cw[i] * (double)g->ch[i];

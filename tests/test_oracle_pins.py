@@ -328,8 +328,10 @@ def test_hint_structure_matches_numpy_statement():
     m = o.merged()
     bw = o.static_csr()["base_w"]
     wb, hb = (xh - xl) / nb, (yh - yl) / nb
-    bxs = np.clip(np.floor((gx[:o.C] - xl) / wb), 0, nb - 1).astype(int)
-    bys = np.clip(np.floor((gy[:o.C] - yl) / hb), 0, nb - 1).astype(int)
+    # integer decisions in FP32: bin = floor((x - xl) * (nb / (xh - xl)))
+    f32 = np.float32
+    bxs = np.clip(np.floor((gx[:o.C].astype(f32) - f32(xl)) * f32(nb / (xh - xl))), 0, nb - 1).astype(int)
+    bys = np.clip(np.floor((gy[:o.C].astype(f32) - f32(yl)) * f32(nb / (yh - yl))), 0, nb - 1).astype(int)
     area = nl.cell_w.astype(np.float64) * nl.cell_h
     Db = np.zeros(nb * nb)
     for i in np.where(mov)[0]:
@@ -345,8 +347,11 @@ def test_hint_structure_matches_numpy_statement():
         want_c, want_w = [], []
         if bw[i] > 0:
             for k, c in enumerate(macros):
-                dx, dy = abs(gx[i] - nl.fixed_x[c]), abs(gy[i] - nl.fixed_y[c])
-                if dx < 0.5 * (nl.cell_w[i] + nl.cell_w[c]) and dy < 0.5 * (nl.cell_h[i] + nl.cell_h[c]):
+                dxf = abs(f32(gx[i]) - nl.fixed_x[c])
+                dyf = abs(f32(gy[i]) - nl.fixed_y[c])
+                if dxf < f32(0.5) * (nl.cell_w[i] + nl.cell_w[c]) and \
+                        dyf < f32(0.5) * (nl.cell_h[i] + nl.cell_h[c]):
+                    dx, dy = abs(gx[i] - float(nl.fixed_x[c])), abs(gy[i] - float(nl.fixed_y[c]))
                     want_c.append(o.Nst + k)
                     r = max(dx / (nl.cell_w[c] * 0.5), dy / (nl.cell_h[c] * 0.5))
                     want_w.append(-(np.exp(-r) * bw[i]))
