@@ -1,0 +1,198 @@
+/* libpl: GB300 (sm_103a) area-hint refinement placement initializer.
+ *
+ * C ABI of the data-parallel hot path of "Bridging the Initialization Gap: A
+ * Co-Optimization Framework for Mixed-Size Global Placement" (arXiv
+ * 2511.10073):
+ *   A1  netlist hypergraph -> static instance graph with macro pin expansion
+ *       (Sec. V "Macro pin expansion"; the graph G = (V, E) of Sec. IV);
+ *   A0  GSP-based initialization: multi-band normalized-adjacency filter
+ *       (Sec. IV, multi-band filter H and its three-step procedure);
+ *   A2  area hints: macro virtual nodes with repulsive edges and bin virtual
+ *       nodes with density-aware signed edges (Sec. V);
+ *   A3  signed Laplacian L_hint and its Gershgorin bound lambda_up (Sec. V,
+ *       refinement filter H_r);
+ *   A4  refinement filter H_r = ((lambda_up I - L_hint)/lambda_up)^k applied
+ *       in the relaxed fixed-point iteration of Algorithm 1;
+ *   A5  half-perimeter wirelength, the paper's quality metric (Sec. VII-VIII).
+ *
+ * Conventions
+ *   - Every pointer in pl_netlist and every coordinate buffer is a DEVICE
+ *     pointer owned by the caller, unless a parameter says "host".
+ *   - Coordinates are interleaved FP32 pairs (x0, y0, x1, y1, ...).  "cells"
+ *     buffers hold num_cells pairs; "nodes" buffers hold pl_graph_info()'s N
+ *     pairs in node order: [cells][macro pins][star nodes][macro virtual
+ *     nodes][bin nodes, row-major, x fastest].
+ *   - Calls are issued on the given stream.  Calls that must learn sizes from
+ *     the device (graph builds) synchronize that stream; pl_filter_init reads
+ *     the device status once at its end.  No call aborts, traps or spins
+ *     without bound; failures come back as a pl_status and pl_last_error().
+ *   - The library owns the pl_graph object and the device memory inside it
+ *     (allocated with cudaMalloc, freed by pl_graph_destroy).
+ *   - One pl_graph must not be used from two host threads at once.
+ */
+#ifndef PL_H
+#define PL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pl_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  PL_OK = 0,
+  PL_ERR_INVALID_ARG = 1, /* bad pointer, size, index, parameter or netlist content */
+  PL_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in pl_last_error) */
+  PL_ERR_WORKSPACE = 3,   /* caller workspace too small */
+  PL_ERR_OOM = 4,         /* device allocation failed */
+  PL_ERR_SPECTRUM = 5,    /* lambda_up <= 0 or not finite: no refinement filter */
+  PL_ERR_NONFINITE = 6,   /* a coordinate given to the library is NaN or infinite */
+  PL_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+  PL_ERR_UNSUPPORTED = 8  /* input beyond a documented size limit */
+} pl_status;
+
+typedef enum { PL_W_FP32 = 1, PL_W_BF16 = 2 } pl_wdtype;
+
+/* The placement instance (Sec. IV problem statement): objects V = I/Os,
+ * macros, standard cells; nets E as a pin -> net incidence. */
+typedef struct {
+  int32_t num_cells;         /* cells = movable std cells + fixed macros + fixed I/Os */
+  int32_t num_nets;
+  int64_t num_pins;          /* = net_ptr[num_nets] */
+  const int64_t *net_ptr;    /* [num_nets+1] pin ranges, net_ptr[0] = 0, nondecreasing */
+  const int32_t *pin_cell;   /* [num_pins] cell of each pin, in [0, num_cells) */
+  const float *pin_dx;       /* [num_pins] pin offset from its cell centre, or NULL (0) */
+  const float *pin_dy;
+  const float *cell_w;       /* [num_cells] width, height (>= 0; > 0 for macros) */
+  const float *cell_h;
+  const uint8_t *cell_kind;  /* [num_cells] 0 movable, 1 fixed macro, 2 fixed I/O */
+  const float *fixed_x;      /* [num_cells] centre, read for kind != 0 */
+  const float *fixed_y;
+  double xl, yl, xh, yh;     /* placement region, xh > xl, yh > yl */
+} pl_netlist;
+
+/* Table I parameters plus the readings the paper leaves open. */
+typedef struct {
+  int32_t clique_max;        /* nets with <= clique_max distinct nodes are cliques, 2..16 */
+  int32_t wdtype;            /* pl_wdtype: storage type of edge weights */
+  int32_t gift_enable;       /* run the GSP initialization filter (A0) */
+  int32_t gift_center;       /* filter coordinates relative to the region centre */
+  int32_t gift_k[3];         /* low, mid, high band: exponent k (Table I *_filter_k) */
+  double gift_sigma[3];      /* self-loop sigma > 0 (Table I *_filter_sigma) */
+  double gift_alpha[3];      /* band weights (Table I *_filter_effect) */
+  int32_t t_hint;            /* refinement iterations T_hint (Table I refine_iteration) */
+  int32_t nbx, nby;          /* refinement bins (Table I refine_num_bin_xy) */
+  double gamma;              /* relaxation in [0, 1] (Algorithm 1) */
+  double det_ratio;          /* detection window ratio (Table I detection_ratio) */
+  double capacity;           /* bin capacity C (Table I bin_capacity) */
+  double mu;                 /* logistic slope of phi_b (Sec. V) */
+  int32_t ntaps;             /* 1..4 filter taps: g~ = sum_t alpha_t H_r^{k_t} g */
+  int32_t tap_k[4];          /* strictly increasing orders, 1..64 */
+  double tap_alpha[4];
+  int32_t pin_every_step;    /* re-pin fixed nodes after every power of H_r */
+  int32_t clamp;             /* clamp movable centres into the region */
+} pl_params;
+
+typedef struct pl_graph pl_graph;
+
+/* Defaults: clique_max 16, FP32 weights, GiFt bands (k, sigma, alpha) =
+ * (4, 4, 0.7), (2, 4, 0.2), (2, 2, 0.1), T_hint 3, 32 x 32 bins, gamma 0.5,
+ * detection ratio 0.1, capacity 1, mu 4, one tap of order 8, clamping on. */
+void pl_params_default(pl_params *p);
+
+/* A1 (+ A2/A3 when xy_nodes != NULL).  Builds the static instance graph of
+ * `nl` into *g: creates the graph when *g == NULL, otherwise rebuilds it in
+ * place (buffers are reused when large enough; the netlist may differ).
+ * With xy_nodes (device, N pairs) it also builds the area-hint graph for that
+ * placement (as pl_build_hints).  Synchronizes `stream`.
+ * Errors: INVALID_ARG (netlist or params), UNSUPPORTED (a net with more than
+ * 32768 pins, a graph row beyond 2^31 entries), OOM, CUDA, NONFINITE. */
+pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *xy_nodes,
+                         pl_stream stream, pl_graph **g);
+
+/* Sizes of a built graph, written to host out[16]:
+ *   0 num_cells  1 macro pin nodes  2 star nodes  3 macros  4 bins
+ *   5 static nodes  6 N (all nodes)  7 static nnz  8 augmented nnz (0 before
+ *   the first hint build)  9 window half-width x  10 half-width y
+ *   11 long (hub-path) rows  12 movable cells */
+pl_status pl_graph_info(const pl_graph *g, int64_t *out);
+
+/* A2 + A3 for the node placement xy_nodes (device, N pairs): bin densities
+ * and phi_b, macro and bin hint edges, the augmented signed graph, degrees and
+ * lambda_up.  Synchronizes `stream`.  Errors: NONFINITE (a movable cell
+ * coordinate), SPECTRUM (lambda_up <= 0), OOM, CUDA. */
+pl_status pl_build_hints(pl_graph *g, const pl_params *p, const float *xy_nodes,
+                         pl_stream stream);
+
+/* A4, one round of Algorithm 1 on the current augmented graph:
+ * g~ = sum_t alpha_t H_r^{k_t} g, fixed nodes re-pinned, then
+ * g' = (1 - gamma) g + gamma g~, re-pinned, movable centres clamped.
+ * xy_in, xy_out: device, N pairs each, distinct buffers. */
+pl_status pl_filter_apply(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
+                          pl_stream stream);
+
+/* A0 steps 2-3: g' = sum_b alpha_b A~_{sigma_b}^{k_b} g on the static graph,
+ * fixed nodes re-pinned, movable centres clamped.  Device, N pairs each. */
+pl_status pl_gift(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
+                  pl_stream stream);
+
+/* A0 step 1: movable cells from xy0_cells (device, num_cells pairs) or, when
+ * NULL, uniform in the region from splitmix64(seed, counter 2i + axis); fixed
+ * objects at their positions; star nodes at the mean of their net's nodes. */
+pl_status pl_init_signal(pl_graph *g, uint64_t seed, const float *xy0_cells, float *xy_nodes,
+                         pl_stream stream);
+
+/* The whole initializer: A0 (pl_init_signal, then pl_gift when gift_enable)
+ * followed by T_hint rounds of A2-A4.  xy_out_cells: device, num_cells pairs.
+ * Reads the device status once at the end (synchronizes `stream`). */
+pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const float *xy0_cells,
+                         float *xy_out_cells, pl_stream stream);
+
+/* A5: writes sum over nets of (max - min) pin x + (max - min) pin y, pin =
+ * cell centre (xy_cells, device) + offset, as one double to *hpwl (device).
+ * ws: device scratch of at least pl_hpwl_workspace_size(num_nets) bytes, 256-
+ * byte aligned; its contents need no initialisation and are left zeroed for
+ * the next call.  Does not synchronize.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+size_t pl_hpwl_workspace_size(int32_t num_nets);
+pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, void *ws,
+                  size_t ws_bytes, pl_stream stream);
+
+/* Copies of the graph for exact comparison (all HOST buffers):
+ * static CSR: rp[static nodes + 1], col[static nnz], w[static nnz] (stored
+ * weight as double), base_w[num_cells] (baseWeight_i, FP64).
+ * Synchronizes the graph's last stream. */
+pl_status pl_graph_export_static(const pl_graph *g, int64_t *rp, int32_t *col, double *w,
+                                 double *base_w);
+/* augmented CSR in canonical row order: rp[N+1], col[nnz], w[nnz], deg[N]
+ * (signed degree D_ii), *lam_up, Db/Cb/phi[bins], cell_bin[num_cells] (-1 for
+ * non-movable cells).  Any pointer may be NULL to skip that array. */
+pl_status pl_graph_export(const pl_graph *g, int64_t *rp, int32_t *col, double *w, double *deg,
+                          double *lam_up, double *Db, double *Cb, double *phi,
+                          int32_t *cell_bin);
+
+void pl_graph_destroy(pl_graph *g);
+
+/* Benchmark hooks (no counterpart in the paper; for measuring this library).
+ * pl_prof_enable(1) clears the records and starts counting: every kernel the
+ * library launches is counted, and each sparse-product launch (A0, A4) is
+ * bracketed by a CUDA event pair on its own stream.  pl_prof_enable(0) stops
+ * recording.  pl_prof_read writes host out[8]:
+ *   0 kernel launches since enable
+ *   1 refinement-filter (A4) launches  2 their summed time, ms
+ *   3 their algorithmic bytes (indices + weights once, row pointers, x read,
+ *     y written, one coefficient per row)
+ *   4 GiFt (A0) launches  5 ms  6 algorithmic bytes
+ * It synchronizes on the recorded events.  Process-wide, not per graph. */
+void pl_prof_enable(int on);
+pl_status pl_prof_read(double *out);
+
+/* Message of the last failed call on this host thread ("" when none). */
+const char *pl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

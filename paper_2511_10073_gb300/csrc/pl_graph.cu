@@ -1,0 +1,616 @@
+// A1: the static instance graph of a netlist hypergraph, GPU-side.
+//
+// Sec. V "Macro pin expansion": every pin on a macro is its own fixed node at
+// macro centre + pin offset; other pins map to their cell.  Net model (a
+// reading; the paper gives none): a net with p distinct nodes is a clique of
+// weight 1/(p-1) when 2 <= p <= clique_max, else a star of weight p/(p-1) to
+// a new movable star node.  Parallel edges add exactly on the integer lattice
+// 1/360360 = 1/lcm(1..15) and are divided once (IEEE correctly rounded).
+#include <cmath>
+#include <cstring>
+
+#include "pl_internal.h"
+
+namespace pl {
+
+constexpr long long kLattice = 360360;
+constexpr long long kMaxNetPins = 32768;
+
+#define TRY(x)                                   \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+// ----------------------------------------------------------- validation
+__global__ void k_validate_cells(const float *w, const float *h, const uint8_t *kind,
+                                 const float *fx, const float *fy, int32_t C, int *status,
+                                 uint8_t *is_macro, unsigned *maxdims) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+    uint8_t k = kind[i];
+    float wi = w[i], hi = h[i];
+    bool ok = k <= 2 && isfinite(wi) && isfinite(hi) && wi >= 0.f && hi >= 0.f;
+    if (k == 1) ok = ok && wi > 0.f && hi > 0.f;
+    if (k != 0) ok = ok && isfinite(fx[i]) && isfinite(fy[i]);
+    if (!ok) flag(status, ST_BAD_CELL);
+    is_macro[i] = k == 1;
+    if (k == 0) atomicAdd(&status[12], 1);
+    if (ok) {
+      if (k == 0) {
+        atomicMax(&maxdims[0], __float_as_uint(wi));
+        atomicMax(&maxdims[1], __float_as_uint(hi));
+      } else if (k == 1) {
+        atomicMax(&maxdims[2], __float_as_uint(wi));
+        atomicMax(&maxdims[3], __float_as_uint(hi));
+      }
+    }
+  }
+}
+
+__global__ void k_validate_nets(const int64_t *ptr, int32_t M, int64_t P, int *status) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= M; e += gridDim.x * blockDim.x) {
+    if (e == 0 && ptr[0] != 0) flag(status, ST_BAD_NET);
+    if (e == M && ptr[M] != P) flag(status, ST_BAD_NET);
+    if (e < M) {
+      long long d = ptr[e + 1] - ptr[e];
+      if (d < 0) flag(status, ST_BAD_NET);
+      if (d > kMaxNetPins) flag(status, ST_TOO_BIG);
+    }
+  }
+}
+
+__global__ void k_validate_pins(const int32_t *pin_cell, const float *dx, const float *dy,
+                                int64_t P, int32_t C, int *status) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int32_t c = pin_cell[p];
+    if (c < 0 || c >= C) flag(status, ST_BAD_INDEX);
+    if ((dx && !isfinite(dx[p])) || (dy && !isfinite(dy[p]))) flag(status, ST_BAD_CELL);
+  }
+}
+
+// ------------------------------------------------------- node numbering
+__global__ void k_macro_list(const uint8_t *is_macro, const int32_t *scan, int32_t C,
+                             int32_t *macro_cell) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x)
+    if (is_macro[i]) macro_cell[scan[i]] = i;
+}
+
+__global__ void k_pin_macro_flag(const int32_t *pin_cell, const uint8_t *is_macro, int64_t P,
+                                 uint8_t *f) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x)
+    f[p] = is_macro[pin_cell[p]];
+}
+
+__global__ void k_pin_node(const int32_t *pin_cell, const uint8_t *f, const int32_t *scan,
+                           int64_t P, int32_t C, int32_t *pin_node, uint32_t *keys) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int32_t v = f[p] ? C + scan[p] : pin_cell[p];
+    pin_node[p] = v;
+    keys[p] = (uint32_t)v;
+  }
+}
+
+__global__ void k_star_flag(const int32_t *net_p, int32_t M, int32_t cmax, uint8_t *f) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x)
+    f[e] = net_p[e] > cmax;
+}
+
+__global__ void k_star_list(const uint8_t *f, const int32_t *scan, int32_t M, int32_t *star_net) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x)
+    if (f[e]) star_net[scan[e]] = e;
+}
+
+// ---------------------------------------------------- edge expansion
+// Row counts of the unmerged edge list: warp per net.
+__global__ void k_row_count(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
+                            const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
+                            int32_t *cnt) {
+  const int lane = threadIdx.x & 31;
+  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < M;
+       e += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int p = net_p[e];
+    if (p < 2) continue;
+    long long b = ptr[e];
+    int add = p <= cmax ? p - 1 : 1;
+    for (int k = lane; k < p; k += 32) atomicAdd(&cnt[nd[b + k]], add);
+    if (p > cmax && lane == 0) cnt[star0 + star_of[e]] = p;
+  }
+}
+
+// Unmerged entries as (col << 32 | value): value = 360360/(p-1) for a clique
+// pair, -p for a star edge.  Star rows are written in node order directly.
+__global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
+                          const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
+                          const int64_t *row_off, unsigned long long *cursor, uint64_t *keys) {
+  const int lane = threadIdx.x & 31;
+  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < M;
+       e += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int p = net_p[e];
+    if (p < 2) continue;
+    long long b = ptr[e];
+    if (p <= cmax) {
+      uint32_t lat = (uint32_t)(kLattice / (p - 1));
+      int npair = p * (p - 1);
+      for (int q = lane; q < npair; q += 32) {
+        int a = q / (p - 1), c = q % (p - 1);
+        c += c >= a;
+        uint32_t ra = nd[b + a], rc = nd[b + c];
+        unsigned long long slot = atomicAdd(&cursor[ra], 1ull);
+        keys[slot] = ((uint64_t)rc << 32) | lat;
+      }
+    } else {
+      long long s = star0 + star_of[e];
+      uint32_t code = (uint32_t)(-p);
+      long long so = row_off[s];
+      for (int k = lane; k < p; k += 32) {
+        uint32_t v = nd[b + k];
+        unsigned long long slot = atomicAdd(&cursor[v], 1ull);
+        keys[slot] = ((uint64_t)(uint32_t)s << 32) | code;
+        keys[so + k] = ((uint64_t)v << 32) | code;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double lattice_weight(long long val) {
+  if (val > 0) return __ddiv_rn((double)val, (double)kLattice);
+  long long p = -val;
+  return __ddiv_rn((double)p, (double)(p - 1));
+}
+
+__device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
+  if (wdtype == PL_W_BF16) {
+    uint16_t h = d2bf16(w);
+    *bits = h;
+    return bf16_to_f(h);
+  }
+  return __double2float_rn(w);
+}
+
+// Final static CSR: warp per row copies merged (col, value) and converts the
+// exact lattice values into stored weights; lane 0 forms baseWeight (FP64 mean
+// of the exact weights in column order) and the static degree.
+__global__ void k_static_compact(const int64_t *row_off, const int32_t *mcol, const int64_t *mval,
+                                 const int64_t *srp, int64_t Nst, int32_t C, int wdtype,
+                                 const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
+                                 uint8_t *hflag, double *sdeg) {
+  const int lane = threadIdx.x & 31;
+  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < Nst;
+       v += ((long long)gridDim.x * blockDim.x) >> 5) {
+    long long src = row_off[v], dst = srp[v];
+    int m = (int)(srp[v + 1] - dst);
+    for (int k = lane; k < m; k += 32) {
+      double w = lattice_weight(mval[src + k]);
+      scol[dst + k] = mcol[src + k];
+      uint16_t hb = 0;
+      float f = stored(w, wdtype, &hb);
+      if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dst + k] = hb;
+      else reinterpret_cast<float *>(sw)[dst + k] = f;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double s = 0.0, d = 0.0;
+      for (int k = 0; k < m; ++k) {
+        double w = lattice_weight(mval[src + k]);
+        s = __dadd_rn(s, w);
+        uint16_t hb;
+        d = __dadd_rn(d, (double)stored(w, wdtype, &hb));
+      }
+      sdeg[v] = d;
+      if (v < C) {
+        double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
+        base_w[v] = bw;
+        hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------- node tables
+__global__ void k_nodes(int64_t N, int32_t C, int32_t Pm, int32_t S, int32_t Mm, int32_t nbx,
+                        const uint8_t *ckind, const float *cw, const float *ch, const float *fx,
+                        const float *fy, const int32_t *macro_cell, double xl, double yl,
+                        double xh, double yh, double wb, double hb, uint8_t *nkind,
+                        float2 *fixedp, float4 *bounds) {
+  const int64_t st0 = (int64_t)C + Pm, mv0 = st0 + S, bn0 = mv0 + Mm;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    uint8_t k = 2;
+    float2 f = make_float2(0.f, 0.f);
+    float4 bd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v < C) {
+      if (ckind[v] == 0) {
+        k = 0;
+        double hw = (double)cw[v] * 0.5, hh = (double)ch[v] * 0.5;
+        bd = make_float4(__double2float_rn(xl + hw), __double2float_rn(yl + hh),
+                         __double2float_rn(xh - hw), __double2float_rn(yh - hh));
+      } else {
+        f = make_float2(fx[v], fy[v]);
+      }
+    } else if (v < st0) {
+      // macro pins: filled by k_pin_fixed
+    } else if (v < mv0) {
+      k = 1;
+      bd = make_float4(__double2float_rn(xl), __double2float_rn(yl), __double2float_rn(xh),
+                       __double2float_rn(yh));
+    } else if (v < bn0) {
+      int32_t c = macro_cell[v - mv0];
+      f = make_float2(fx[c], fy[c]);
+    } else {
+      long long b = v - bn0;
+      int bx = (int)(b % nbx), by = (int)(b / nbx);
+      f = make_float2(__double2float_rn(xl + ((double)bx + 0.5) * wb),
+                      __double2float_rn(yl + ((double)by + 0.5) * hb));
+    }
+    nkind[v] = k;
+    if (v < C || v >= st0) fixedp[v] = f;
+    bounds[v] = bd;
+  }
+}
+
+__global__ void k_pin_fixed(const int32_t *pin_node, const int32_t *pin_cell, const float *dx,
+                            const float *dy, const float *fx, const float *fy, int64_t P,
+                            int32_t C, float2 *fixedp) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int32_t v = pin_node[p];
+    if (v < C) continue;
+    int32_t c = pin_cell[p];
+    double x = (double)fx[c] + (dx ? (double)dx[p] : 0.0);
+    double y = (double)fy[c] + (dy ? (double)dy[p] : 0.0);
+    fixedp[v] = make_float2(__double2float_rn(x), __double2float_rn(y));
+  }
+}
+
+// Macro area inside each bin, summed over macros in macro order (FP64).
+__global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const int32_t *macro_cell,
+                                 const float *cw, const float *ch, const float *fx,
+                                 const float *fy, double xl, double yl, double wb, double hb,
+                                 double *amac) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
+    int bx = b % nbx, by = b / nbx;
+    double bxl = xl + (double)bx * wb, bxh = xl + (double)(bx + 1) * wb;
+    double byl = yl + (double)by * hb, byh = yl + (double)(by + 1) * hb;
+    float fxl = (float)bxl, fxh = (float)bxh, fyl = (float)byl, fyh = (float)byh;
+    double a = 0.0;
+    for (int m = 0; m < Mm; ++m) {
+      int c = macro_cell[m];
+      float hwf = cw[c] * 0.5f, hhf = ch[c] * 0.5f;
+      // cheap reject: FP32 boxes separated by more than rounding
+      if (fx[c] - hwf > fxh + 1.f || fx[c] + hwf < fxl - 1.f || fy[c] - hhf > fyh + 1.f ||
+          fy[c] + hhf < fyl - 1.f)
+        continue;
+      double hwm = __dmul_rn((double)cw[c], 0.5), hhm = __dmul_rn((double)ch[c], 0.5);
+      double ox = __dadd_rn(fmin(bxh, __dadd_rn((double)fx[c], hwm)),
+                            -fmax(bxl, __dadd_rn((double)fx[c], -hwm)));
+      double oy = __dadd_rn(fmin(byh, __dadd_rn((double)fy[c], hhm)),
+                            -fmax(byl, __dadd_rn((double)fy[c], -hhm)));
+      if (ox > 0.0 && oy > 0.0) a = __dadd_rn(a, __dmul_rn(ox, oy));
+    }
+    amac[b] = a;
+  }
+}
+
+// Macro lookup grid: every macro is listed in the grid buckets its rectangle,
+// grown by half the largest movable cell and one bucket of margin, touches.
+__device__ __forceinline__ void macro_bucket_range(int m, const int32_t *macro_cell,
+                                                   const float *cw, const float *ch,
+                                                   const float *fx, const float *fy, float wmax,
+                                                   float hmax, double xl, double yl, double sx,
+                                                   double sy, int gnx, int gny, int *k) {
+  int c = macro_cell[m];
+  double ex = 0.5 * ((double)cw[c] + (double)wmax) * (1.0 + 1e-6) + 1e-6;
+  double ey = 0.5 * ((double)ch[c] + (double)hmax) * (1.0 + 1e-6) + 1e-6;
+  double a0 = floor(((double)fx[c] - ex - xl) * sx) - 1.0, a1 = floor(((double)fx[c] + ex - xl) * sx) + 1.0;
+  double b0 = floor(((double)fy[c] - ey - yl) * sy) - 1.0, b1 = floor(((double)fy[c] + ey - yl) * sy) + 1.0;
+  k[0] = (int)fmin(fmax(a0, 0.0), (double)(gnx - 1));
+  k[1] = (int)fmin(fmax(a1, 0.0), (double)(gnx - 1));
+  k[2] = (int)fmin(fmax(b0, 0.0), (double)(gny - 1));
+  k[3] = (int)fmin(fmax(b1, 0.0), (double)(gny - 1));
+}
+
+__global__ void k_grid_count(int32_t Mm, const int32_t *macro_cell, const float *cw,
+                             const float *ch, const float *fx, const float *fy, float wmax,
+                             float hmax, double xl, double yl, double sx, double sy, int gnx,
+                             int gny, int32_t *cnt) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mm; m += gridDim.x * blockDim.x) {
+    int k[4];
+    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, gnx, gny, k);
+    for (int y = k[2]; y <= k[3]; ++y)
+      for (int x = k[0]; x <= k[1]; ++x) atomicAdd(&cnt[(long long)y * gnx + x], 1);
+  }
+}
+
+__global__ void k_grid_fill(int32_t Mm, const int32_t *macro_cell, const float *cw,
+                            const float *ch, const float *fx, const float *fy, float wmax,
+                            float hmax, double xl, double yl, double sx, double sy, int gnx,
+                            int gny, int32_t *cur, uint32_t *list) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mm; m += gridDim.x * blockDim.x) {
+    int k[4];
+    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, gnx, gny, k);
+    for (int y = k[2]; y <= k[3]; ++y)
+      for (int x = k[0]; x <= k[1]; ++x) list[atomicAdd(&cur[(long long)y * gnx + x], 1)] = m;
+  }
+}
+
+__global__ void k_i32_to_i64(const int32_t *a, int64_t *b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+__global__ void k_i64_to_i32(const int64_t *a, int32_t *b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (int32_t)a[i];
+}
+
+// ------------------------------------------------------------- driver
+template <typename T>
+static cudaError_t d2h(T *h, const void *d, size_t n, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+static cudaError_t scan_tmp(pl_graph *g, long long n, void **t) {
+  cudaError_t e = ensure(g->tmp[7], scan_tmp_bytes(n) + 4096);
+  *t = g->tmp[7].p;
+  return e;
+}
+
+pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cudaStream_t s) {
+  const int32_t C = nl->num_cells, M = nl->num_nets;
+  const int64_t NP = nl->num_pins;
+  g->C = C;
+  g->M = M;
+  g->P = NP;
+  g->xl = nl->xl; g->yl = nl->yl; g->xh = nl->xh; g->yh = nl->yh;
+  g->wdtype = p->wdtype;
+  g->clique_max = p->clique_max;
+  g->det_ratio = p->det_ratio;
+  g->nbx = p->nbx;
+  g->nby = p->nby;
+  g->NB = p->nbx * p->nby;
+  g->have_hints = false;
+  g->stream = s;
+
+  // copies of the netlist arrays
+  TRY(ensure(g->cw, (size_t)C * 4 + 16));
+  TRY(ensure(g->ch, (size_t)C * 4 + 16));
+  TRY(ensure(g->ckind, (size_t)C + 16));
+  TRY(ensure(g->cfx, (size_t)C * 4 + 16));
+  TRY(ensure(g->cfy, (size_t)C * 4 + 16));
+  TRY(ensure(g->net_ptr, (size_t)(M + 1) * 8));
+  if (C) {
+    TRY(cudaMemcpyAsync(g->cw.p, nl->cell_w, (size_t)C * 4, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemcpyAsync(g->ch.p, nl->cell_h, (size_t)C * 4, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemcpyAsync(g->ckind.p, nl->cell_kind, (size_t)C, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemcpyAsync(g->cfx.p, nl->fixed_x, (size_t)C * 4, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemcpyAsync(g->cfy.p, nl->fixed_y, (size_t)C * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  TRY(cudaMemcpyAsync(g->net_ptr.p, nl->net_ptr, (size_t)(M + 1) * 8, cudaMemcpyDeviceToDevice, s));
+
+  TRY(ensure(g->status, 64));
+  TRY(cudaMemsetAsync(g->status.p, 0, 64, s));
+  int *status = P<int>(g->status);
+  unsigned *maxdims = reinterpret_cast<unsigned *>(status + 8);
+  uint8_t *is_macro;
+  TRY(ensure(g->tmp[0], (size_t)C + 256));
+  is_macro = P<uint8_t>(g->tmp[0]);
+  k_validate_cells<<<grid_for(C, 256), 256, 0, s>>>(P<float>(g->cw), P<float>(g->ch),
+                                                    P<uint8_t>(g->ckind), P<float>(g->cfx),
+                                                    P<float>(g->cfy), C, status, is_macro, maxdims);
+  note_launch();
+  k_validate_nets<<<grid_for(M + 1, 256), 256, 0, s>>>(P<int64_t>(g->net_ptr), M, NP, status);
+  note_launch();
+  if (NP) {
+    k_validate_pins<<<grid_for(NP, 256), 256, 0, s>>>(nl->pin_cell, nl->pin_dx, nl->pin_dy, NP, C,
+                                                     status);
+    note_launch();
+  }
+  TRY(cudaGetLastError());
+  int hst[16];
+  TRY(d2h(hst, g->status.p, 16, s));
+  if (hst[0] & (ST_BAD_CELL | ST_BAD_NET | ST_BAD_INDEX)) {
+    set_error("invalid netlist:%s%s%s", (hst[0] & ST_BAD_CELL) ? " cell size/kind/position" : "",
+              (hst[0] & ST_BAD_NET) ? " net_ptr" : "",
+              (hst[0] & ST_BAD_INDEX) ? " pin_cell out of range" : "");
+    return PL_ERR_INVALID_ARG;
+  }
+  if (hst[0] & ST_TOO_BIG) {
+    set_error("a net has more than %lld pins", (long long)kMaxNetPins);
+    return PL_ERR_UNSUPPORTED;
+  }
+  g->nmov = hst[12];
+  float wmax, hmax, mwmax, mhmax;
+  memcpy(&wmax, &hst[8], 4);
+  memcpy(&hmax, &hst[9], 4);
+  memcpy(&mwmax, &hst[10], 4);
+  memcpy(&mhmax, &hst[11], 4);
+
+  // macros and macro pin nodes
+  void *stmp;
+  TRY(ensure(g->cell_macro, (size_t)(C + 1) * 4));
+  TRY(scan_tmp(g, C > NP ? C : NP, &stmp));
+  TRY((exclusive_scan<uint8_t, int32_t>(is_macro, P<int32_t>(g->cell_macro), C, stmp, s)));
+  TRY(ensure(g->tmp[1], (size_t)NP + 256));
+  uint8_t *pflag = P<uint8_t>(g->tmp[1]);
+  TRY(ensure(g->tmp[2], (size_t)(NP + 1) * 4 + 256));
+  int32_t *pscan = P<int32_t>(g->tmp[2]);
+  if (NP) {
+    k_pin_macro_flag<<<grid_for(NP, 256), 256, 0, s>>>(nl->pin_cell, is_macro, NP, pflag);
+    note_launch();
+  }
+  TRY((exclusive_scan<uint8_t, int32_t>(pflag, pscan, NP, stmp, s)));
+  int32_t sizes2[2];
+  TRY(d2h(&sizes2[0], P<int32_t>(g->cell_macro) + C, 1, s));
+  TRY(d2h(&sizes2[1], pscan + NP, 1, s));
+  g->Mm = sizes2[0];
+  g->Pm = sizes2[1];
+  TRY(ensure(g->macro_cell, (size_t)g->Mm * 4 + 16));
+  k_macro_list<<<grid_for(C, 256), 256, 0, s>>>(is_macro, P<int32_t>(g->cell_macro), C,
+                                                P<int32_t>(g->macro_cell));
+  note_launch();
+  TRY(ensure(g->pin_node, (size_t)NP * 4 + 16));
+  TRY(ensure(g->nd, (size_t)NP * 4 + 16));
+  if (NP) {
+    k_pin_node<<<grid_for(NP, 256), 256, 0, s>>>(nl->pin_cell, pflag, pscan, NP, C,
+                                                P<int32_t>(g->pin_node), P<uint32_t>(g->nd));
+    note_launch();
+  }
+
+  // distinct nodes of each net
+  TRY(ensure(g->net_p, (size_t)M * 4 + 16));
+  TRY(ensure(g->tmp[3], segsort_tmp_bytes(M, NP, 4)));
+  TRY((segmented_sort<uint32_t, MODE_UNIQUE>(P<uint32_t>(g->nd), P<int64_t>(g->net_ptr), M, NP,
+                                             P<int32_t>(g->net_p), nullptr, nullptr,
+                                             g->tmp[3].p, s)));
+  // star nodes
+  TRY(ensure(g->star_of, (size_t)(M + 1) * 4));
+  k_star_flag<<<grid_for(M, 256), 256, 0, s>>>(P<int32_t>(g->net_p), M, p->clique_max, pflag);
+  note_launch();
+  TRY(scan_tmp(g, M, &stmp));
+  TRY((exclusive_scan<uint8_t, int32_t>(pflag, P<int32_t>(g->star_of), M, stmp, s)));
+  int32_t S;
+  TRY(d2h(&S, P<int32_t>(g->star_of) + M, 1, s));
+  g->S = S;
+  TRY(ensure(g->star_net, (size_t)S * 4 + 16));
+  k_star_list<<<grid_for(M, 256), 256, 0, s>>>(pflag, P<int32_t>(g->star_of), M,
+                                               P<int32_t>(g->star_net));
+  note_launch();
+  g->Nst = (int64_t)C + g->Pm + S;
+  g->N = g->Nst + g->Mm + g->NB;
+  if (g->N >= (1LL << 31) - 1) {
+    set_error("too many nodes (%lld)", (long long)g->N);
+    return PL_ERR_UNSUPPORTED;
+  }
+  const int64_t Nst = g->Nst, star0 = (int64_t)C + g->Pm;
+
+  // unmerged row counts and offsets
+  TRY(ensure(g->tmp[4], (size_t)(Nst + 1) * 4 + 256));
+  int32_t *cnt = P<int32_t>(g->tmp[4]);
+  TRY(cudaMemsetAsync(cnt, 0, (size_t)(Nst + 1) * 4, s));
+  k_row_count<<<grid_for((long long)M * 32, 256), 256, 0, s>>>(
+      P<int64_t>(g->net_ptr), P<uint32_t>(g->nd), P<int32_t>(g->net_p), P<int32_t>(g->star_of),
+      M, p->clique_max, star0, cnt);
+  note_launch();
+  TRY(ensure(g->tmp[5], (size_t)(Nst + 1) * 8 + 256));
+  int64_t *row_off = P<int64_t>(g->tmp[5]);
+  TRY(scan_tmp(g, Nst, &stmp));
+  TRY((exclusive_scan<int32_t, int64_t>(cnt, row_off, Nst, stmp, s)));
+  int64_t npre;
+  TRY(d2h(&npre, row_off + Nst, 1, s));
+
+  // scatter, sort, merge
+  TRY(ensure(g->tmp[6], (size_t)npre * 8 + (size_t)(Nst + 1) * 8 + 512));
+  uint64_t *keys = P<uint64_t>(g->tmp[6]);
+  unsigned long long *cursor = reinterpret_cast<unsigned long long *>(keys + npre + 1);
+  TRY(cudaMemcpyAsync(cursor, row_off, (size_t)Nst * 8, cudaMemcpyDeviceToDevice, s));
+  k_scatter<<<grid_for((long long)M * 32, 256), 256, 0, s>>>(
+      P<int64_t>(g->net_ptr), P<uint32_t>(g->nd), P<int32_t>(g->net_p), P<int32_t>(g->star_of),
+      M, p->clique_max, star0, row_off, cursor, keys);
+  note_launch();
+  TRY(ensure(g->tmp[1], (size_t)npre * 12 + 512));  // merged col (int32) + value (int64)
+  int64_t *mval = P<int64_t>(g->tmp[1]);
+  int32_t *mcol = reinterpret_cast<int32_t *>(mval + npre + 1);
+  TRY(ensure(g->tmp[3], segsort_tmp_bytes(Nst, npre, 8)));
+  TRY((segmented_sort<uint64_t, MODE_MERGE>(keys, row_off, Nst, npre, cnt, mcol, mval,
+                                            g->tmp[3].p, s)));
+  TRY(ensure(g->srp, (size_t)(Nst + 1) * 8));
+  TRY((exclusive_scan<int32_t, int64_t>(cnt, P<int64_t>(g->srp), Nst, stmp, s)));
+  int64_t nnz;
+  TRY(d2h(&nnz, P<int64_t>(g->srp) + Nst, 1, s));
+  g->nnz_static = (uint64_t)nnz;
+  TRY(ensure(g->scol, (size_t)nnz * 4 + 64));
+  TRY(ensure(g->sw, (size_t)nnz * 4 + 64));
+  TRY(ensure(g->base_w, (size_t)C * 8 + 16));
+  TRY(ensure(g->hflag, (size_t)C + 16));
+  TRY(ensure(g->sdeg, (size_t)Nst * 8 + 16));
+  k_static_compact<<<grid_for(Nst * 32, 256), 256, 0, s>>>(
+      row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
+      P<int32_t>(g->scol), g->sw.p, P<double>(g->base_w), P<uint8_t>(g->hflag), P<double>(g->sdeg));
+  note_launch();
+  TRY(cudaGetLastError());
+
+  // node tables
+  const int64_t N = g->N;
+  g->wb = (g->xh - g->xl) / (double)g->nbx;
+  g->hb = (g->yh - g->yl) / (double)g->nby;
+  g->abin = g->wb * g->hb;
+  int nx = (int)floor(p->det_ratio * (double)g->nbx), ny = (int)floor(p->det_ratio * (double)g->nby);
+  if (nx < 1) nx = 1;
+  if (ny < 1) ny = 1;
+  g->hx = (nx - 1) / 2;
+  g->hy = (ny - 1) / 2;
+  TRY(ensure(g->nkind, (size_t)N + 16));
+  TRY(ensure(g->fixedp, (size_t)N * 8 + 16));
+  TRY(ensure(g->bounds, (size_t)N * 16 + 16));
+  k_nodes<<<grid_for(N, 256), 256, 0, s>>>(N, C, g->Pm, S, g->Mm, g->nbx, P<uint8_t>(g->ckind),
+                                           P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
+                                           P<float>(g->cfy), P<int32_t>(g->macro_cell), g->xl,
+                                           g->yl, g->xh, g->yh, g->wb, g->hb, P<uint8_t>(g->nkind),
+                                           P<float2>(g->fixedp), P<float4>(g->bounds));
+  note_launch();
+  if (NP) {
+    k_pin_fixed<<<grid_for(NP, 256), 256, 0, s>>>(P<int32_t>(g->pin_node), nl->pin_cell, nl->pin_dx,
+                                                 nl->pin_dy, P<float>(g->cfx), P<float>(g->cfy), NP,
+                                                 C, P<float2>(g->fixedp));
+    note_launch();
+  }
+  TRY(ensure(g->amac, (size_t)g->NB * 8 + 16));
+  TRY(ensure(g->Cb, (size_t)g->NB * 8 + 16));
+  k_bin_macro_area<<<grid_for(g->NB, 128), 128, 0, s>>>(
+      g->NB, g->nbx, g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch),
+      P<float>(g->cfx), P<float>(g->cfy), g->xl, g->yl, g->wb, g->hb, P<double>(g->amac));
+  note_launch();
+
+  // macro lookup grid
+  double gs = fmax(1.0, fmax((double)mwmax, (double)mhmax));
+  g->gnx = (int)fmin(2048.0, fmax(1.0, ceil((g->xh - g->xl) / gs)));
+  g->gny = (int)fmin(2048.0, fmax(1.0, ceil((g->yh - g->yl) / gs)));
+  const long long ng = (long long)g->gnx * g->gny;
+  const double sx = (double)g->gnx / (g->xh - g->xl), sy = (double)g->gny / (g->yh - g->yl);
+  TRY(ensure(g->gptr, (size_t)(ng + 1) * 8 + 16));
+  TRY(ensure(g->tmp[4], (size_t)(ng + 1) * 4 + 256));
+  int32_t *gcnt = P<int32_t>(g->tmp[4]);
+  TRY(cudaMemsetAsync(gcnt, 0, (size_t)(ng + 1) * 4, s));
+  k_grid_count<<<grid_for(g->Mm, 128), 128, 0, s>>>(
+      g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
+      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, g->gnx, g->gny, gcnt);
+  note_launch();
+  int64_t *gptr = P<int64_t>(g->gptr);
+  TRY(scan_tmp(g, ng, &stmp));
+  TRY((exclusive_scan<int32_t, int64_t>(gcnt, gptr, ng, stmp, s)));
+  int64_t nreg;
+  TRY(d2h(&nreg, gptr + ng, 1, s));
+  TRY(ensure(g->glist, (size_t)nreg * 4 + 16));
+  if (nreg >= (1LL << 31)) {
+    set_error("macro lookup grid too large");
+    return PL_ERR_UNSUPPORTED;
+  }
+  TRY(ensure(g->tmp[2], (size_t)(ng + 1) * 4 + 256));
+  int32_t *gcur = P<int32_t>(g->tmp[2]);
+  k_i64_to_i32<<<grid_for(ng, 256), 256, 0, s>>>(gptr, gcur, ng);
+  note_launch();
+  k_grid_fill<<<grid_for(g->Mm, 128), 128, 0, s>>>(
+      g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
+      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, g->gnx, g->gny, gcur,
+      P<uint32_t>(g->glist));
+  note_launch();
+  TRY(ensure(g->tmp[3], segsort_tmp_bytes(ng, nreg, 4)));
+  TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->glist), gptr, ng, nreg, nullptr,
+                                           nullptr, nullptr, g->tmp[3].p, s)));
+  g->gsz = gs;
+  g->gsx = sx;
+  g->gsy = sy;
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(s));
+  (void)kMaxNetPins;
+  return PL_OK;
+}
+
+}  // namespace pl

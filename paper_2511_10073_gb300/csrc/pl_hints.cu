@@ -1,0 +1,758 @@
+// A2 + A3: area hints and the signed Laplacian, GPU-side (Sec. V).
+//
+//  * macro virtual node v_m joined to every movable cell overlapping macro m
+//    by w = -exp(-maxRatio_{i,m}) * baseWeight_i;
+//  * bin virtual node v_b joined to every movable cell whose centre bin lies
+//    in the detection window of b by w = -exp(-maxRatio_{i,b}) phi_b
+//    baseWeight_i, phi_b = 2 sigmoid(mu (D_b - C_b)) - 1;
+//  * L_hint = D - A with signed D_ii; lambda_up = max_i (D_ii + sum_j |w_ij|)
+//    (Gershgorin), which equals max_i 2 * (sum of positive w_ij).
+// Decisions (bin of a centre, overlap) are FP32 with one stated operation
+// sequence; D_b and phi_b are FP64; edge weights are FP32 with the exponent
+// argument carried in FP64; degree sums are double-float.
+#include <cmath>
+#include <cstring>
+
+#include "pl_internal.h"
+
+namespace pl {
+
+#define TRY(x)                                       \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+struct HintGeo {
+  float xlf, ylf, sxf, syf;      // bin decision: floor((x - xl) * sx)
+  float gxf, gyf, gsxf, gsyf;    // macro grid bucket of a centre
+  double xl, yl, wb, hb, iwb2, ihb2;  // bin centres; 2 / w_b, 2 / h_b
+  int nbx, nby, hx, hy, gnx, gny;
+  int32_t C, Pm, S, Mm;
+  int64_t Nst, mv0, bn0, N;
+};
+
+__device__ __forceinline__ int bin_of(float x, float xl, float sc, int nb) {
+  float t = __fmul_rn(__fadd_rn(x, -xl), sc);
+  float f = floorf(t);
+  if (!(f >= 0.f)) return 0;
+  if (f > (float)(nb - 1)) return nb - 1;
+  return (int)f;
+}
+__device__ __forceinline__ bool overlaps(float x, float y, float w, float h, float xm, float ym,
+                                         float wm, float hm) {
+  float dx = fabsf(__fadd_rn(x, -xm)), dy = fabsf(__fadd_rn(y, -ym));
+  return dx < __fmul_rn(0.5f, __fadd_rn(w, wm)) && dy < __fmul_rn(0.5f, __fadd_rn(h, hm));
+}
+__device__ __forceinline__ int grid_of(float x, float x0, float sc, int n) { return bin_of(x, x0, sc, n); }
+
+// e^{-r} for r >= 0 carried in FP64: FP32 exp of the rounded argument times
+// the first-order correction for the rounding residue.
+__device__ __forceinline__ float exp_neg(double r) {
+  float rh = __double2float_rn(r);
+  float rl = __double2float_rn(r - (double)rh);
+  return expf(-rh) * (1.0f - rl);
+}
+
+// Writes the stored form of v and returns the value it stores.
+__device__ __forceinline__ float store_w(void *wbuf, int wdtype, uint64_t k, float v) {
+  if (wdtype == PL_W_BF16) {
+    uint16_t h = f2bf16(v);
+    reinterpret_cast<uint16_t *>(wbuf)[k] = h;
+    return bf16_to_f(h);
+  }
+  reinterpret_cast<float *>(wbuf)[k] = v;
+  return v;
+}
+__device__ __forceinline__ float load_w(const void *wbuf, int wdtype, uint64_t k) {
+  if (wdtype == PL_W_BF16) return bf16_to_f(reinterpret_cast<const uint16_t *>(wbuf)[k]);
+  return reinterpret_cast<const float *>(wbuf)[k];
+}
+__device__ __forceinline__ void copy_w(void *dst, const void *src, int wdtype, uint64_t kd,
+                                       uint64_t ks) {
+  if (wdtype == PL_W_BF16)
+    reinterpret_cast<uint16_t *>(dst)[kd] = reinterpret_cast<const uint16_t *>(src)[ks];
+  else
+    reinterpret_cast<float *>(dst)[kd] = reinterpret_cast<const float *>(src)[ks];
+}
+
+// --------------------------------------------------------- H1: cells
+__global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
+                             const uint8_t *hflag, const float *cw, const float *ch,
+                             const float *fx, const float *fy, const int32_t *macro_cell,
+                             const int64_t *gptr, const uint32_t *glist, int32_t *cell_bin,
+                             int32_t *n_ovl, int32_t *bcnt, int32_t *mcnt, int *status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
+    if (ckind[i] != 0) {
+      cell_bin[i] = -1;
+      n_ovl[i] = 0;
+      continue;
+    }
+    float2 p = xy[i];
+    if (!isfinite(p.x) || !isfinite(p.y)) {
+      flag(status, ST_NONFINITE);
+      p = make_float2(0.f, 0.f);
+    }
+    int bx = bin_of(p.x, G.xlf, G.sxf, G.nbx), by = bin_of(p.y, G.ylf, G.syf, G.nby);
+    int b = by * G.nbx + bx;
+    cell_bin[i] = b;
+    bool hint = hflag[i] != 0;
+    atomicAdd(&bcnt[2 * b + (hint ? 0 : 1)], 1);
+    int n = 0;
+    if (hint) {
+      int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
+      long long k = (long long)ky * G.gnx + kx;
+      for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
+        int m = (int)glist[q];
+        int c = macro_cell[m];
+        if (overlaps(p.x, p.y, cw[i], ch[i], fx[c], fy[c], cw[c], ch[c])) {
+          ++n;
+          atomicAdd(&mcnt[m], 1);
+        }
+      }
+    }
+    n_ovl[i] = n;
+  }
+}
+
+__global__ void k_hint_scatter(HintGeo G, const float2 *xy, const uint8_t *ckind,
+                               const uint8_t *hflag, const float *cw, const float *ch,
+                               const float *fx, const float *fy, const int32_t *macro_cell,
+                               const int64_t *gptr, const uint32_t *glist,
+                               const int32_t *cell_bin, int32_t *bcur, uint32_t *blist,
+                               int32_t *mcur, uint32_t *mlist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
+    if (ckind[i] != 0) continue;
+    int b = cell_bin[i];
+    bool hint = hflag[i] != 0;
+    blist[atomicAdd(&bcur[2 * b + (hint ? 0 : 1)], 1)] = (uint32_t)i;
+    if (!hint) continue;
+    float2 p = xy[i];
+    if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
+    int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
+    long long k = (long long)ky * G.gnx + kx;
+    for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
+      int m = (int)glist[q];
+      int c = macro_cell[m];
+      if (overlaps(p.x, p.y, cw[i], ch[i], fx[c], fy[c], cw[c], ch[c]))
+        mlist[atomicAdd(&mcur[m], 1)] = (uint32_t)i;
+    }
+  }
+}
+
+// ------------------------------------------------ H5: bin density and phi
+// D_b: FP64 sum of w*h over the movable cells of b in ascending cell id (the
+// two sorted buckets of b, hint and non-hint cells, merged on the fly).
+__global__ void k_bin_phi(HintGeo G, const int64_t *boff, const uint32_t *blist, const float *cw,
+                          const float *ch, const double *amac, double abin, double cap, double mu,
+                          double *Db, double *Cb, double *phi, float *phif, int64_t *hub_len) {
+  const int NB = G.nbx * G.nby;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
+    long long a0 = boff[2 * b], a1 = boff[2 * b + 1], c1 = boff[2 * b + 2];
+    long long ia = a0, ic = a1;
+    double s = 0.0;
+    while (ia < a1 || ic < c1) {
+      uint32_t i;
+      if (ic >= c1 || (ia < a1 && blist[ia] < blist[ic])) i = blist[ia++];
+      else i = blist[ic++];
+      s = __dadd_rn(s, __dmul_rn((double)cw[i], (double)ch[i]));
+    }
+    double d = __ddiv_rn(s, abin);
+    double c = __ddiv_rn(__dmul_rn(cap, __dadd_rn(abin, -amac[b])), abin);
+    double t = __dmul_rn(mu, __dadd_rn(d, -c));
+    double ph = __dadd_rn(__ddiv_rn(2.0, __dadd_rn(1.0, exp_cw(-t))), -1.0);
+    Db[b] = d;
+    Cb[b] = c;
+    phi[b] = ph;
+    phif[b] = __double2float_rn(ph);
+    // hub row length: hint cells of the window bins
+    int bx = b % G.nbx, by = b / G.nbx;
+    long long hl = 0;
+    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
+      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
+        int bb = yy * G.nbx + xx;
+        hl += boff[2 * bb + 1] - boff[2 * bb];
+      }
+    hub_len[b] = hl;
+  }
+}
+
+// ------------------------------------------------------- H6: row lengths
+__device__ __forceinline__ int win_count(int bx, int by, const HintGeo &G) {
+  int nx = min(G.nbx - 1, bx + G.hx) - max(0, bx - G.hx) + 1;
+  int ny = min(G.nby - 1, by + G.hy) - max(0, by - G.hy) + 1;
+  return nx * ny;
+}
+
+__global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const uint8_t *hflag,
+                          const int32_t *cell_bin, const int32_t *n_ovl, const int64_t *moff,
+                          const int64_t *hub_len, uint32_t *slen, uint64_t *llen,
+                          uint8_t *lflag) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.N;
+       v += (long long)gridDim.x * blockDim.x) {
+    long long len = v < G.Nst ? srp[v + 1] - srp[v] : 0;
+    bool hub = false;
+    if (with_hints) {
+      if (v < G.C && hflag[v]) {
+        int b = cell_bin[v];
+        len += n_ovl[v] + win_count(b % G.nbx, b / G.nbx, G);
+      } else if (v >= G.mv0 && v < G.bn0) {
+        len += moff[v - G.mv0 + 1] - moff[v - G.mv0];
+        hub = true;
+      } else if (v >= G.bn0) {
+        len += hub_len[v - G.bn0];
+        hub = true;
+      }
+    }
+    if (len > kLong) hub = true;
+    slen[v] = hub ? 0u : (uint32_t)len;
+    llen[v] = hub ? (uint64_t)len : 0ull;
+    lflag[v] = hub ? 1 : 0;
+  }
+}
+
+__global__ void k_layout_long(int64_t N, const uint8_t *lflag, const int32_t *lscan,
+                              const uint64_t *lpos, uint64_t nnz_s, int32_t *lrow, uint64_t *lptr,
+                              int32_t *longidx, int32_t *nchunk_of) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (lflag[v]) {
+      int li = lscan[v];
+      lrow[li] = (int32_t)v;
+      lptr[li] = nnz_s + lpos[v];
+      longidx[v] = li;
+      uint64_t len = lpos[v + 1] - lpos[v];
+      nchunk_of[li] = len == 0 ? 1 : (int32_t)((len + kChunk - 1) / kChunk);
+    } else {
+      longidx[v] = -1;
+    }
+    if (v == N - 1) {
+      int nl = lscan[N];
+      lptr[nl] = nnz_s + lpos[N];
+    }
+  }
+}
+
+__global__ void k_chunk_owner(int32_t nlong, const int32_t *lchunk, int32_t *chunk_lr) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlong; l += gridDim.x * blockDim.x)
+    for (int c = lchunk[l]; c < lchunk[l + 1]; ++c) chunk_lr[c] = l;
+}
+
+__global__ void k_u64_to_u32(const uint64_t *a, uint32_t *b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (uint32_t)a[i];
+}
+
+// First row owned by each tile: rows whose first short entry lies in
+// [t * kTile, (t+1) * kTile); the last tile owns every row to the end.
+__global__ void k_tiles(const uint32_t *rp_s, int64_t N, int32_t ntiles, int32_t *tile_row) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
+    if (t == 0) { tile_row[0] = 0; continue; }
+    if (t == ntiles) { tile_row[t] = (int32_t)N; continue; }
+    uint64_t target = (uint64_t)t * kTile;
+    long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] >= target
+    while (lo < hi) {
+      long long mid = (lo + hi) >> 1;
+      if ((uint64_t)rp_s[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    tile_row[t] = (int32_t)lo;
+  }
+}
+
+// ------------------------------------------------------- H9: row assembly
+__device__ __forceinline__ void acc_deg(dfl &D, dfl &Pp, float w) {
+  df_add(D, w);
+  if (w > 0.f) df_add(Pp, w);
+}
+
+// Rows of the static node range (cells, macro pins, stars): static part, then
+// for hint cells their macro entries (ascending macro) and window bin entries
+// (row-major).  Warp per row.
+__global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int64_t *srp,
+                                const int32_t *scol, const void *sw, const uint32_t *rp_s,
+                                const int32_t *longidx, const uint64_t *lptr, const uint8_t *hflag,
+                                const int32_t *cell_bin, const int32_t *n_ovl, const float2 *xy,
+                                const float *cw, const float *ch, const float *fx, const float *fy,
+                                const int32_t *macro_cell, const int64_t *gptr,
+                                const uint32_t *glist, const double *base_w, const float *phif,
+                                int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
+                                uint64_t *bin_base) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nrows = with_hints ? G.Nst : G.N;
+  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < nrows;
+       v += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int li = longidx[v];
+    uint64_t dst = li >= 0 ? lptr[li] : (uint64_t)rp_s[v];
+    long long s0 = v < G.Nst ? srp[v] : 0, sl = v < G.Nst ? srp[v + 1] - s0 : 0;
+    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
+    for (long long k = lane; k < sl; k += 32) {
+      col[dst + k] = scol[s0 + k];
+      copy_w(w, sw, wdtype, dst + k, s0 + k);
+      acc_deg(D, Pp, load_w(sw, wdtype, s0 + k));
+    }
+    if (with_hints && v < G.C && hflag[v]) {
+      float2 p = xy[v];
+      if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
+      const float bwf = __double2float_rn(base_w[v]);
+      uint64_t mb = dst + sl;
+      // macro entries, ascending macro id (grid bucket lists are sorted)
+      int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
+      long long gk = (long long)ky * G.gnx + kx;
+      long long q0 = gptr[gk], q1 = gptr[gk + 1];
+      int written = 0;
+      for (long long qb = q0; qb < q1; qb += 32) {
+        long long q = qb + lane;
+        bool hit = false;
+        int m = 0, c = 0;
+        if (q < q1) {
+          m = (int)glist[q];
+          c = macro_cell[m];
+          hit = overlaps(p.x, p.y, cw[v], ch[v], fx[c], fy[c], cw[c], ch[c]);
+        }
+        unsigned hm = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          uint64_t k = mb + written + __popc(hm & ((1u << lane) - 1u));
+          double rx = fabs((double)p.x - (double)fx[c]) / ((double)cw[c] * 0.5);
+          double ry = fabs((double)p.y - (double)fy[c]) / ((double)ch[c] * 0.5);
+          float wv = -(exp_neg(fmax(rx, ry)) * bwf);
+          col[k] = (int32_t)(G.mv0 + m);
+          acc_deg(D, Pp, store_w(w, wdtype, k, wv));
+        }
+        written += __popc(hm);
+      }
+      uint64_t bb0 = mb + n_ovl[v];
+      int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
+      int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
+      int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
+      int wx = x1 - x0 + 1, nwin = wx * (y1 - y0 + 1);
+      for (int j = lane; j < nwin; j += 32) {
+        int xx = x0 + j % wx, yy = y0 + j / wx;
+        double xb = G.xl + ((double)xx + 0.5) * G.wb, yb = G.yl + ((double)yy + 0.5) * G.hb;
+        double rx = fabs((double)p.x - xb) * G.iwb2, ry = fabs((double)p.y - yb) * G.ihb2;
+        int bb = yy * G.nbx + xx;
+        float wv = -((exp_neg(fmax(rx, ry)) * phif[bb]) * bwf);
+        uint64_t k = bb0 + j;
+        col[k] = (int32_t)(G.bn0 + bb);
+        acc_deg(D, Pp, store_w(w, wdtype, k, wv));
+      }
+      if (lane == 0) {
+        mac_base[v] = mb;
+        bin_base[v] = bb0;
+      }
+    }
+    D = warp_sum_df(D);
+    Pp = warp_sum_df(Pp);
+    if (lane == 0) {
+      dsum[v] = D;
+      psum[v] = Pp;
+    }
+  }
+}
+
+// Virtual rows: CTA per row.  Macro rows copy their sorted cell list; bin rows
+// gather the window bins' hint lists and merge the sorted runs.  Weights are
+// read back from the cells' own entries, so the matrix is exactly symmetric.
+__global__ void __launch_bounds__(256) k_assemble_hubs(
+    HintGeo G, int wdtype, const int32_t *longidx, const uint64_t *lptr, uint64_t nnz_s,
+    const int64_t *moff, const uint32_t *mlist, const int64_t *boff, const uint32_t *blist,
+    const int32_t *cell_bin, const int32_t *n_ovl, const uint64_t *mac_base,
+    const uint64_t *bin_base, int32_t *col, void *w, int32_t *hubtmp, dfl *dsum, dfl *psum) {
+  __shared__ long long run_off[1032];
+  __shared__ dfl red[2][8];
+  const int64_t nvirt = (int64_t)G.Mm + (int64_t)G.nbx * G.nby;
+  for (long long r = blockIdx.x; r < nvirt; r += gridDim.x) {
+    const int64_t v = G.mv0 + r;
+    const int li = longidx[v];
+    const uint64_t base = lptr[li];
+    const long long len = (long long)(lptr[li + 1] - base);
+    if (r < G.Mm) {
+      const int m = (int)r;
+      for (long long k = threadIdx.x; k < len; k += blockDim.x) col[base + k] = (int32_t)mlist[moff[m] + k];
+    } else {
+      const int b = (int)(r - G.Mm), bx = b % G.nbx, by = b / G.nbx;
+      const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
+      const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
+      int nr = 0;
+      long long o = 0;
+      for (int yy = y0; yy <= y1; ++yy)
+        for (int xx = x0; xx <= x1; ++xx) {
+          int bb = yy * G.nbx + xx;
+          long long a = boff[2 * bb], n = boff[2 * bb + 1] - a;
+          if (threadIdx.x == 0) run_off[nr] = o;
+          for (long long k = threadIdx.x; k < n; k += blockDim.x) col[base + o + k] = (int32_t)blist[a + k];
+          o += n;
+          ++nr;
+        }
+      if (threadIdx.x == 0) run_off[nr] = o;
+      __syncthreads();
+      cta_merge_runs<int32_t>(col + base, hubtmp + (base - nnz_s), run_off, nr);
+    }
+    __syncthreads();
+    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
+    for (long long k = threadIdx.x; k < len; k += blockDim.x) {
+      int i = col[base + k];
+      uint64_t src;
+      if (r < G.Mm) {
+        uint64_t mb = mac_base[i];
+        int n = n_ovl[i];
+        int j = 0;
+        while (j < n - 1 && col[mb + j] != (int32_t)v) ++j;
+        src = mb + j;
+      } else {
+        const int b = (int)(r - G.Mm), bxb = b % G.nbx, byb = b / G.nbx;
+        int ci = cell_bin[i], bxi = ci % G.nbx, byi = ci / G.nbx;
+        int x0 = max(0, bxi - G.hx), x1 = min(G.nbx - 1, bxi + G.hx);
+        int y0 = max(0, byi - G.hy);
+        src = bin_base[i] + (uint64_t)((byb - y0) * (x1 - x0 + 1) + (bxb - x0));
+      }
+      copy_w(w, w, wdtype, base + k, src);
+      acc_deg(D, Pp, load_w(w, wdtype, src));
+    }
+    D = warp_sum_df(D);
+    Pp = warp_sum_df(Pp);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][wid] = D;
+      red[1][wid] = Pp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      dfl a = red[0][0], c = red[1][0];
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+        df_add_df(a, red[0][k]);
+        df_add_df(c, red[1][k]);
+      }
+      dsum[v] = df_norm(a);
+      psum[v] = df_norm(c);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------- H11: lambda_up, c_i
+__global__ void k_lambda_max(int64_t N, const dfl *psum, unsigned long long *key) {
+  unsigned long long best = 0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    dfl p = psum[v];
+    dfl two = df_norm(dfl{__fmul_rn(2.f, p.hi), __fmul_rn(2.f, p.lo)});
+    unsigned long long k = df_maxkey(two);
+    if (k > best) best = k;
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, best, m);
+    best = o > best ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(key, best);
+}
+
+__global__ void k_lambda_final(double *lam, const unsigned long long *key, int *status) {
+  double l = df_from_maxkey(*key);
+  if (!(l > 0.0) || isinf(l)) {
+    flag(status, ST_SPECTRUM);
+    lam[0] = l;
+    lam[1] = 0.0;
+  } else {
+    lam[0] = l;
+    lam[1] = __ddiv_rn(1.0, l);
+  }
+}
+
+__global__ void k_coef(int64_t N, const dfl *dsum, const double *lam, float *c32) {
+  const float il = __double2float_rn(lam[1]);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    dfl d = dsum[v];
+    c32[v] = __fadd_rn(1.f, -__fmaf_rn(d.hi, il, __fmul_rn(d.lo, il)));
+  }
+}
+
+__global__ void k_coef_long(int32_t nlong, const int32_t *lrow, const dfl *dsum,
+                            const double *lam, double *c64) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlong; l += gridDim.x * blockDim.x) {
+    double d = df_to_d(dsum[lrow[l]]);
+    c64[l] = 1.0 - d * lam[1];
+  }
+}
+
+// --------------------------------------------------------------- driver
+template <typename T>
+static cudaError_t d2h(T *h, const void *d, size_t n, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+static HintGeo make_geo(const pl_graph *g) {
+  HintGeo G;
+  G.xlf = (float)g->xl;
+  G.ylf = (float)g->yl;
+  G.sxf = (float)((double)g->nbx / (g->xh - g->xl));
+  G.syf = (float)((double)g->nby / (g->yh - g->yl));
+  G.gxf = (float)g->xl;
+  G.gyf = (float)g->yl;
+  G.gsxf = (float)g->gsx;
+  G.gsyf = (float)g->gsy;
+  G.xl = g->xl;
+  G.yl = g->yl;
+  G.wb = g->wb;
+  G.hb = g->hb;
+  G.iwb2 = 2.0 / g->wb;
+  G.ihb2 = 2.0 / g->hb;
+  G.nbx = g->nbx;
+  G.nby = g->nby;
+  G.hx = g->hx;
+  G.hy = g->hy;
+  G.gnx = g->gnx;
+  G.gny = g->gny;
+  G.C = g->C;
+  G.Pm = g->Pm;
+  G.S = g->S;
+  G.Mm = g->Mm;
+  G.Nst = g->Nst;
+  G.mv0 = g->Nst;
+  G.bn0 = g->Nst + g->Mm;
+  G.N = g->N;
+  return G;
+}
+
+// Layout of a split matrix from per-row lengths already in g->slen/llen/lflag.
+static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
+  const int64_t N = g->N;
+  m.N = N;
+  void *stmp;
+  TRY(ensure(g->tmp[7], scan_tmp_bytes(N + 1) + 4096));
+  stmp = g->tmp[7].p;
+  TRY(ensure(g->tmp[0], (size_t)(N + 1) * 8 + 256));
+  uint64_t *s64 = P<uint64_t>(g->tmp[0]);
+  TRY((exclusive_scan<uint32_t, uint64_t>(P<uint32_t>(g->slen), s64, N, stmp, s)));
+  TRY(ensure(g->tmp[1], (size_t)(N + 1) * 8 + 256));
+  uint64_t *lpos = P<uint64_t>(g->tmp[1]);
+  TRY((exclusive_scan<uint64_t, uint64_t>(P<uint64_t>(g->llen), lpos, N, stmp, s)));
+  TRY(ensure(g->lflag, (size_t)(N + 1) * 4 + 256));
+  int32_t *lscan = P<int32_t>(g->lflag);
+  TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->tmp[2]), lscan, N, stmp, s)));
+  uint64_t tot[2];
+  int32_t nl;
+  TRY(d2h(&tot[0], s64 + N, 1, s));
+  TRY(d2h(&tot[1], lpos + N, 1, s));
+  TRY(d2h(&nl, lscan + N, 1, s));
+  if (tot[0] >= (1ull << 32) - kTile || tot[0] + tot[1] >= (1ull << 40)) {
+    set_error("graph too large for the 32-bit short-row layout (%llu entries)",
+              (unsigned long long)tot[0]);
+    return PL_ERR_UNSUPPORTED;
+  }
+  m.nnz_s = tot[0];
+  m.nnz_l = tot[1];
+  m.nlong = nl;
+  m.wbytes = g->wdtype == PL_W_BF16 ? 2 : 4;
+  TRY(ensure(m.rp_s, (size_t)(N + 1) * 4));
+  k_u64_to_u32<<<grid_for(N + 1, 256), 256, 0, s>>>(s64, P<uint32_t>(m.rp_s), N + 1);
+  note_launch();
+  const uint64_t cap = m.nnz_s + m.nnz_l + kPad;
+  TRY(ensure(m.col, cap * 4));
+  TRY(ensure(m.w, cap * m.wbytes));
+  TRY(ensure(m.lrow, (size_t)nl * 4 + 16));
+  TRY(ensure(m.lptr, (size_t)(nl + 1) * 8));
+  TRY(ensure(m.longidx, (size_t)N * 4 + 16));
+  TRY(ensure(m.lchunk, (size_t)(nl + 1) * 4));
+  TRY(ensure(g->tmp[3], (size_t)(nl + 1) * 4 + 256));
+  int32_t *nch = P<int32_t>(g->tmp[3]);
+  k_layout_long<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->tmp[2]), lscan, lpos, m.nnz_s,
+                                                 P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
+                                                 P<int32_t>(m.longidx), nch);
+  note_launch();
+  if (nl == 0) {
+    TRY(cudaMemsetAsync(m.lchunk.p, 0, 4, s));
+    m.nchunks = 0;
+  } else {
+    TRY((exclusive_scan<int32_t, int32_t>(nch, P<int32_t>(m.lchunk), nl, stmp, s)));
+    int32_t nc;
+    TRY(d2h(&nc, P<int32_t>(m.lchunk) + nl, 1, s));
+    m.nchunks = nc;
+  }
+  TRY(ensure(m.chunk_lr, (size_t)m.nchunks * 4 + 16));
+  if (nl) {
+    k_chunk_owner<<<grid_for(nl, 256), 256, 0, s>>>(nl, P<int32_t>(m.lchunk), P<int32_t>(m.chunk_lr));
+    note_launch();
+  }
+  m.ntiles = (int32_t)((m.nnz_s + kTile - 1) / kTile);
+  if (m.ntiles < 1) m.ntiles = 1;
+  TRY(ensure(m.tile_row, (size_t)(m.ntiles + 1) * 4));
+  k_tiles<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(P<uint32_t>(m.rp_s), N, m.ntiles,
+                                                     P<int32_t>(m.tile_row));
+  note_launch();
+  TRY(ensure(m.dsum, (size_t)N * 8 + 16));
+  TRY(ensure(m.psum, (size_t)N * 8 + 16));
+  TRY(ensure(m.c32, (size_t)N * 4 + 16));
+  TRY(ensure(m.c64l, (size_t)nl * 8 + 16));
+  TRY(ensure(m.lam, 64));
+  size_t pbytes = (size_t)(m.nchunks + 1) * 6 * 8;
+  TRY(ensure(m.part, pbytes));
+  TRY(ensure(m.tick, (size_t)nl * 4 + 16));
+  TRY(cudaMemsetAsync(m.tick.p, 0, (size_t)nl * 4 + 16, s));
+  TRY(cudaMemsetAsync(P<char>(m.col) + (m.nnz_s + m.nnz_l) * 4, 0, kPad * 4, s));
+  TRY(cudaMemsetAsync(P<char>(m.w) + (m.nnz_s + m.nnz_l) * m.wbytes, 0, kPad * m.wbytes, s));
+  return PL_OK;
+}
+
+pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s) {
+  const int64_t N = g->N;
+  HintGeo G = make_geo(g);
+  TRY(ensure(g->slen, (size_t)N * 4 + 16));
+  TRY(ensure(g->llen, (size_t)N * 8 + 16));
+  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 0, P<int64_t>(g->srp), nullptr, nullptr, nullptr,
+                                             nullptr, nullptr, P<uint32_t>(g->slen),
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]));
+  note_launch();
+  pl_status st = layout(g, g->st, s);
+  if (st != PL_OK) return st;
+  SpMat &m = g->st;
+  k_assemble_rows<<<grid_for(N * 32, 256), 256, 0, s>>>(
+      G, 0, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
+      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), nullptr, nullptr, nullptr, nullptr, nullptr,
+      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P<int32_t>(m.col),
+      m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum), nullptr, nullptr);
+  note_launch();
+  TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaStream_t s) {
+  const int64_t N = g->N;
+  const int32_t C = g->C, NB = g->NB, Mm = g->Mm;
+  const float2 *xy = reinterpret_cast<const float2 *>(xy_in);
+  HintGeo G = make_geo(g);
+  g->have_hints = false;
+  TRY(cudaMemsetAsync(g->status.p, 0, 32, s));
+  int *status = P<int>(g->status);
+  void *stmp;
+  TRY(ensure(g->tmp[7], scan_tmp_bytes(N + 1) + 4096));
+  stmp = g->tmp[7].p;
+
+  // H1: bins and macro overlaps of movable cells
+  TRY(ensure(g->cell_bin, (size_t)C * 4 + 16));
+  TRY(ensure(g->n_ovl, (size_t)C * 4 + 16));
+  TRY(ensure(g->bcnt, (size_t)(2 * NB + 1) * 4));
+  TRY(ensure(g->mcnt, (size_t)(Mm + 1) * 4));
+  TRY(cudaMemsetAsync(g->bcnt.p, 0, (size_t)(2 * NB + 1) * 4, s));
+  TRY(cudaMemsetAsync(g->mcnt.p, 0, (size_t)(Mm + 1) * 4, s));
+  k_hint_cells<<<grid_for(C, 256), 256, 0, s>>>(
+      G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
+      P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
+      P<uint32_t>(g->glist), P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl), P<int32_t>(g->bcnt),
+      P<int32_t>(g->mcnt), status);
+  note_launch();
+  // H2: bucket offsets
+  TRY(ensure(g->boff, (size_t)(2 * NB + 1) * 8));
+  TRY(ensure(g->moff, (size_t)(Mm + 1) * 8));
+  TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->bcnt), P<int64_t>(g->boff), 2 * NB, stmp, s)));
+  TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->mcnt), P<int64_t>(g->moff), Mm, stmp, s)));
+  int hst[8];
+  TRY(d2h(hst, g->status.p, 8, s));
+  if (hst[0] & ST_NONFINITE) {
+    set_error("non-finite movable cell coordinate");
+    return PL_ERR_NONFINITE;
+  }
+  int64_t nbl, nml;
+  TRY(d2h(&nbl, P<int64_t>(g->boff) + 2 * NB, 1, s));
+  TRY(d2h(&nml, P<int64_t>(g->moff) + Mm, 1, s));
+  // H3: scatter into buckets
+  TRY(ensure(g->bcur, (size_t)(2 * NB + 1) * 4));
+  TRY(ensure(g->mcur, (size_t)(Mm + 1) * 4));
+  TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
+  TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
+  k_u64_to_u32<<<grid_for(2 * NB, 256), 256, 0, s>>>(P<uint64_t>(g->boff), P<uint32_t>(g->bcur), 2 * NB);
+  note_launch();
+  if (Mm) {
+    k_u64_to_u32<<<grid_for(Mm, 256), 256, 0, s>>>(P<uint64_t>(g->moff), P<uint32_t>(g->mcur), Mm);
+    note_launch();
+  }
+  k_hint_scatter<<<grid_for(C, 256), 256, 0, s>>>(
+      G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
+      P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
+      P<uint32_t>(g->glist), P<int32_t>(g->cell_bin), P<int32_t>(g->bcur), P<uint32_t>(g->blist),
+      P<int32_t>(g->mcur), P<uint32_t>(g->mlist));
+  note_launch();
+  // H4: sort every bucket by cell id
+  TRY(ensure(g->tmp[3], segsort_tmp_bytes(2 * NB + Mm, nbl + nml, 4)));
+  TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->blist), P<int64_t>(g->boff), 2 * NB,
+                                           nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
+  if (Mm)
+    TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->mlist), P<int64_t>(g->moff), Mm, nml,
+                                             nullptr, nullptr, nullptr, g->tmp[3].p, s)));
+  // H5: densities, phi, hub lengths
+  TRY(ensure(g->Db, (size_t)NB * 8 + 16));
+  TRY(ensure(g->phi, (size_t)NB * 8 + 16));
+  const size_t phib = ((size_t)NB * 4 + 255) & ~size_t(255);
+  TRY(ensure(g->tmp[4], phib + (size_t)NB * 8 + 256));
+  float *phif = P<float>(g->tmp[4]);
+  int64_t *hub_len = reinterpret_cast<int64_t *>(P<char>(g->tmp[4]) + phib);
+  k_bin_phi<<<grid_for(NB, 64), 64, 0, s>>>(G, P<int64_t>(g->boff), P<uint32_t>(g->blist),
+                                            P<float>(g->cw), P<float>(g->ch), P<double>(g->amac),
+                                            g->abin, p->capacity, p->mu, P<double>(g->Db),
+                                            P<double>(g->Cb), P<double>(g->phi), phif, hub_len);
+  note_launch();
+  // H6-H7: row lengths and layout
+  TRY(ensure(g->slen, (size_t)N * 4 + 16));
+  TRY(ensure(g->llen, (size_t)N * 8 + 16));
+  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 1, P<int64_t>(g->srp), P<uint8_t>(g->hflag),
+                                             P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
+                                             P<int64_t>(g->moff), hub_len, P<uint32_t>(g->slen),
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]));
+  note_launch();
+  pl_status st = layout(g, g->hm, s);
+  if (st != PL_OK) return st;
+  SpMat &m = g->hm;
+  // H9: rows of cells, macro pins and stars
+  TRY(ensure(g->mac_base, (size_t)C * 8 + 16));
+  TRY(ensure(g->bin_base, (size_t)C * 8 + 16));
+  k_assemble_rows<<<grid_for(g->Nst * 32, 256), 256, 0, s>>>(
+      G, 1, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
+      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
+      P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
+      P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr), P<uint32_t>(g->glist),
+      P<double>(g->base_w), phif, P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum),
+      P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
+  note_launch();
+  // H10: virtual rows
+  TRY(ensure(g->hubtmp, (size_t)m.nnz_l * 4 + 64));
+  if (g->hx * 2 + 1 > 32 || g->hy * 2 + 1 > 32) {
+    set_error("detection window larger than 31 x 31 bins");
+    return PL_ERR_UNSUPPORTED;
+  }
+  k_assemble_hubs<<<152 * 4, 256, 0, s>>>(
+      G, g->wdtype, P<int32_t>(m.longidx), P<uint64_t>(m.lptr), m.nnz_s, P<int64_t>(g->moff),
+      P<uint32_t>(g->mlist), P<int64_t>(g->boff), P<uint32_t>(g->blist), P<int32_t>(g->cell_bin),
+      P<int32_t>(g->n_ovl), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), P<int32_t>(m.col),
+      m.w.p, P<int32_t>(g->hubtmp), P<dfl>(m.dsum), P<dfl>(m.psum));
+  note_launch();
+  // H11: lambda_up and coefficients
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 2);
+  TRY(cudaMemsetAsync(key, 0, 8, s));
+  k_lambda_max<<<grid_for(N, 256, 152 * 8), 256, 0, s>>>(N, P<dfl>(m.psum), key);
+  note_launch();
+  k_lambda_final<<<1, 1, 0, s>>>(P<double>(m.lam), key, status);
+  note_launch();
+  k_coef<<<grid_for(N, 256), 256, 0, s>>>(N, P<dfl>(m.dsum), P<double>(m.lam), P<float>(m.c32));
+  note_launch();
+  if (m.nlong) {
+    k_coef_long<<<grid_for(m.nlong, 256), 256, 0, s>>>(m.nlong, P<int32_t>(m.lrow), P<dfl>(m.dsum),
+                                                        P<double>(m.lam), P<double>(m.c64l));
+    note_launch();
+  }
+  TRY(cudaGetLastError());
+  TRY(d2h(hst, g->status.p, 8, s));
+  g->have_hints = true;
+  if (hst[0] & ST_SPECTRUM) {
+    set_error("lambda_up <= 0 or not finite: the refinement filter is undefined");
+    return PL_ERR_SPECTRUM;
+  }
+  return PL_OK;
+}
+
+}  // namespace pl

@@ -1,0 +1,111 @@
+// A5: half-perimeter wirelength (the quality metric of Sec. VII-VIII):
+// sum over nets of (max - min) pin x + (max - min) pin y, pin = cell centre +
+// offset.  A thread takes a net of up to 32 pins; larger nets are taken by the
+// whole warp.  Pin positions and extrema are FP32 (min/max are exact), each
+// net's span is formed and summed in FP64.  Per-block FP64 sums go to the
+// caller's workspace; the last block to finish (ticket) adds them in block
+// order, so the result does not depend on scheduling.
+#include "pl_internal.h"
+
+namespace pl {
+
+constexpr int kHpwlThreads = 256;
+constexpr int kHpwlBlocks = 152 * 8;
+
+__device__ __forceinline__ float2 pin_pos(const float2 *xy, const int32_t *pin_cell,
+                                          const float *dx, const float *dy, long long k) {
+  float2 c = xy[pin_cell[k]];
+  if (dx) c.x += dx[k];
+  if (dy) c.y += dy[k];
+  return c;
+}
+
+__global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
+                                                       const int32_t *pin_cell, const float *dx,
+                                                       const float *dy, const float2 *xy,
+                                                       int32_t M, double *part, int *ticket,
+                                                       double *out) {
+  __shared__ double red[kHpwlThreads / 32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  // each warp takes batches of 32 consecutive nets (warp-uniform loop)
+  const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = wg * 32; base < M; base += nwarp * 32) {
+    const long long e = base + lane;
+    bool big = false;
+    if (e < M) {
+      long long b = net_ptr[e], n = net_ptr[e + 1] - b;
+      if (n > 32) {
+        big = true;
+      } else if (n > 0) {
+        float2 p = pin_pos(xy, pin_cell, dx, dy, b);
+        float x0 = p.x, x1 = p.x, y0 = p.y, y1 = p.y;
+        for (long long k = b + 1; k < b + n; ++k) {
+          p = pin_pos(xy, pin_cell, dx, dy, k);
+          x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
+          y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
+        }
+        acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+      }
+    }
+    unsigned bm = __ballot_sync(0xffffffffu, big);
+    while (bm) {
+      int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      long long ee = base + src;
+      long long b = net_ptr[ee], n = net_ptr[ee + 1] - b;
+      float x0 = 3.4e38f, x1 = -3.4e38f, y0 = 3.4e38f, y1 = -3.4e38f;
+      for (long long k = b + lane; k < b + n; k += 32) {
+        float2 p = pin_pos(xy, pin_cell, dx, dy, k);
+        x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
+        y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
+      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, m));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, m));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, m));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, m));
+      }
+      if (lane == src) acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kHpwlThreads / 32; ++k) s += red[k];
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) s += __ldcg(&part[k]);
+    *out = s;
+    *ticket = 0;
+  }
+}
+
+int hpwl_blocks(int32_t M) { return grid_for((long long)M, kHpwlThreads, kHpwlBlocks); }
+
+size_t hpwl_ws_bytes(int32_t M) { return 256 + (size_t)hpwl_blocks(M) * sizeof(double); }
+
+cudaError_t launch_hpwl(const pl_netlist *nl, const float *xy, double *out, void *ws,
+                        cudaStream_t s) {
+  int nb = hpwl_blocks(nl->num_nets);
+  int *ticket = reinterpret_cast<int *>(ws);
+  double *part = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
+  k_hpwl<<<nb, kHpwlThreads, 0, s>>>(nl->net_ptr, nl->pin_cell, nl->pin_dx, nl->pin_dy,
+                                     reinterpret_cast<const float2 *>(xy), nl->num_nets, part,
+                                     ticket, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace pl

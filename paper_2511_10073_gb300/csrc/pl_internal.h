@@ -1,0 +1,124 @@
+// Internal state of a libpl graph (host struct holding device buffers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pl.h"
+#include "pl_common.cuh"
+
+namespace pl {
+
+// SpMM tiling: short rows (<= kLong entries) are cut into tiles owning the rows
+// whose first entry falls in an nnz window of kTile; long rows and every
+// virtual-node row go to the hub path in chunks of kChunk entries.
+constexpr int kTile = 2048;
+constexpr int kLong = 1024;
+constexpr int kChunk = 2048;
+constexpr int kPad = 16;  // spare entries after the last one (vector over-reads)
+
+// A split CSR matrix as the SpMM kernels read it.  Entries of short rows come
+// first (row pointers rp_s; long rows have zero length there), entries of hub
+// rows follow at absolute offsets lptr.
+struct SpMat {
+  int64_t N = 0;
+  uint64_t nnz_s = 0, nnz_l = 0;
+  int32_t nlong = 0, ntiles = 0, nchunks = 0;
+  Buf rp_s;     // uint32 [N+1]
+  Buf col;      // int32 [nnz_s + nnz_l + kPad]
+  Buf w;        // float or uint16 (bf16) [same]
+  Buf lrow;     // int32 [nlong] node of each hub row
+  Buf lptr;     // uint64 [nlong+1] absolute entry offsets
+  Buf lchunk;   // int32 [nlong+1] first chunk of each hub row
+  Buf chunk_lr; // int32 [nchunks] hub row of each chunk
+  Buf tile_row; // int32 [ntiles+1] first row owned by each tile
+  Buf longidx;  // int32 [N] hub index or -1
+  Buf dsum;     // dfl [N] signed degree D_ii
+  Buf psum;     // dfl [N] sum of positive weights
+  Buf c32;      // float [N] 1 - D_ii / lambda_up
+  Buf c64l;     // double [nlong] same, FP64, hub rows
+  Buf lam;      // double [4]: lambda_up, 1/lambda_up, and the raw max key
+  Buf part;     // double [nchunks * 6] hub partial sums
+  Buf tick;     // int32 [nlong] arrival tickets, zero between launches
+  int wbytes = 4;
+};
+
+}  // namespace pl
+
+struct pl_graph {
+  // sizes
+  int32_t C = 0, M = 0;
+  int64_t P = 0;
+  int32_t Pm = 0, S = 0, Mm = 0, NB = 0, nbx = 0, nby = 0, hx = 0, hy = 0, nmov = 0;
+  int64_t Nst = 0, N = 0;
+  uint64_t nnz_static = 0;
+  double xl = 0, yl = 0, xh = 0, yh = 0, wb = 0, hb = 0, abin = 0;
+  int wdtype = PL_W_FP32, clique_max = 16;
+  double det_ratio = 0.1;
+  cudaStream_t stream = nullptr;
+  bool have_hints = false;
+
+  // copies of the netlist
+  pl::Buf cw, ch, ckind, cfx, cfy, net_ptr;
+  pl::Buf pin_node;    // int32 [P]
+  pl::Buf nd;          // int32 [P] distinct nodes of each net at its pin range start
+  pl::Buf net_p;       // int32 [M] distinct node count
+  pl::Buf star_of;     // int32 [M+1] scan of star flags
+  pl::Buf star_net;    // int32 [S]
+  pl::Buf macro_cell;  // int32 [Mm]
+  pl::Buf cell_macro;  // int32 [C+1] scan of macro flags
+  pl::Buf srp;         // int64 [Nst+1]
+  pl::Buf scol;        // int32 [nnz_static]
+  pl::Buf sw;          // float / uint16 [nnz_static]
+  pl::Buf base_w;      // double [C]
+  pl::Buf hflag;       // uint8 [C] movable with baseWeight > 0
+  pl::Buf sdeg;        // double [Nst] static degree (stored weights)
+  pl::Buf nkind;       // uint8 [N] 0 movable cell, 1 star, 2 fixed
+  pl::Buf fixedp;      // float2 [N]
+  pl::Buf bounds;      // float4 [N] clamp box of the centre
+  pl::Buf amac, Cb;    // double [NB]
+  // macro lookup grid
+  int32_t gnx = 1, gny = 1;
+  double gsz = 1.0, gsx = 1.0, gsy = 1.0;
+  pl::Buf gptr, glist; // int32 [gnx*gny+1], [..]
+  // per refinement round
+  pl::Buf cell_bin;    // int32 [C]
+  pl::Buf n_ovl;       // int32 [C]
+  pl::Buf bcnt, boff, blist, bcur;  // bucket sort of movable cells by (bin, hint)
+  pl::Buf mcnt, moff, mlist, mcur;  // cells overlapping each macro
+  pl::Buf Db, phi;     // double [NB]
+  pl::Buf hlen;        // int64 [N] augmented row length
+  pl::Buf slen;        // uint32 [N] short-row length (0 for hub rows)
+  pl::Buf llen;        // uint64 [N] hub length per node (0 for short rows)
+  pl::Buf lflag;       // int32 [N+1] hub flag scan
+  pl::Buf mac_base;    // uint64 [C] entry offset of a cell's first macro entry
+  pl::Buf bin_base;    // uint64 [C] entry offset of a cell's first bin entry
+  pl::Buf hubtmp;      // int32 scratch for merging bin rows
+  pl::SpMat st;        // static matrix (A0)
+  pl::SpMat hm;        // augmented matrix (A2-A4)
+  // filter state
+  pl::Buf xa, xb, xc, g0; // float2 [N]
+  pl::Buf ua, ub;         // float [N * 2 * nchain]
+  pl::Buf acc;            // double2 [N]
+  pl::Buf gsc;            // float [3 * N] GiFt scales (1/sqrt(D+sigma))
+  pl::Buf status;         // int32 [8]
+  pl::Scratch scr;
+  pl::Buf tmp[8];
+};
+
+namespace pl {
+
+void set_error(const char *fmt, ...);
+pl_status cuda_fail(cudaError_t e, const char *what);
+
+pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cudaStream_t s);
+pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy, cudaStream_t s);
+pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s);
+pl_status run_init_signal(pl_graph *g, uint64_t seed, const float *xy0, float *xy, cudaStream_t s);
+pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
+pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
+pl_status read_status(pl_graph *g, cudaStream_t s);
+
+}  // namespace pl

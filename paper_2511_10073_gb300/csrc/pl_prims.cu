@@ -1,0 +1,415 @@
+// Device-wide primitives: exclusive scan and segmented sort (+ unique / merge).
+#include <cstring>
+
+#include "pl_common.cuh"
+
+namespace pl {
+
+cudaError_t ensure(Buf &b, size_t bytes) {
+  if (bytes <= b.bytes && b.p) return cudaSuccess;
+  size_t nb = bytes + bytes / 4 + 1024;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.bytes = nb;
+  return cudaSuccess;
+}
+
+void release(Buf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+void *Scratch::take(size_t bytes) {
+  size_t off = (used + 255) & ~size_t(255);
+  if (off + bytes > buf.bytes) return nullptr;
+  used = off + bytes;
+  return static_cast<char *>(buf.p) + off;
+}
+
+// ------------------------------------------------------------------- scan
+constexpr int SCAN_T = 256, SCAN_V = 8, SCAN_B = SCAN_T * SCAN_V;
+
+template <typename Tout>
+__device__ Tout block_excl_scan(Tout v, Tout *total) {
+  __shared__ Tout wsum[SCAN_T / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  Tout x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Tout y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    Tout t = lane < SCAN_T / 32 ? wsum[lane] : Tout(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Tout y = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= d) t += y;
+    }
+    if (lane < SCAN_T / 32) wsum[lane] = t;
+  }
+  __syncthreads();
+  Tout before = w ? wsum[w - 1] : Tout(0);
+  *total = wsum[SCAN_T / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_reduce(const Tin *in, Tout *bsum, long long n) {
+  long long base = (long long)blockIdx.x * SCAN_B;
+  Tout s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) {
+    long long i = base + k * SCAN_T + threadIdx.x;
+    if (i < n) s += (Tout)in[i];
+  }
+  Tout tot;
+  block_excl_scan<Tout>(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_apply(const Tin *in, Tout *out, long long n, const Tout *boff) {
+  __shared__ Tout sm[SCAN_B];
+  long long base = (long long)blockIdx.x * SCAN_B;
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) {
+    long long i = base + k * SCAN_T + threadIdx.x;
+    sm[k * SCAN_T + threadIdx.x] = i < n ? (Tout)in[i] : Tout(0);
+  }
+  __syncthreads();
+  Tout v[SCAN_V];
+  Tout s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) {
+    v[k] = s;
+    s += sm[threadIdx.x * SCAN_V + k];
+  }
+  Tout tot;
+  Tout pre = block_excl_scan<Tout>(s, &tot);
+  Tout off = boff ? boff[blockIdx.x] : Tout(0);
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) sm[threadIdx.x * SCAN_V + k] = v[k] + pre + off;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) {
+    long long i = base + k * SCAN_T + threadIdx.x;
+    if (i < n) out[i] = sm[k * SCAN_T + threadIdx.x];
+  }
+  if (threadIdx.x == 0 && base + SCAN_B >= n) out[n] = off + tot;
+}
+
+size_t scan_tmp_bytes(long long n) {
+  size_t b = 0;
+  while (n > SCAN_B) {
+    long long nb = (n + SCAN_B - 1) / SCAN_B;
+    b += (size_t)(2 * nb + 2) * sizeof(int64_t) + 512;
+    n = nb;
+  }
+  return b + 512;
+}
+
+template <typename Tin, typename Tout>
+cudaError_t exclusive_scan(const Tin *in, Tout *out, long long n, void *tmp, cudaStream_t s) {
+  if (n <= 0) {
+    return cudaMemsetAsync(out, 0, sizeof(Tout), s);
+  }
+  long long nb = (n + SCAN_B - 1) / SCAN_B;
+  if (nb == 1) {
+    k_scan_apply<Tin, Tout><<<1, SCAN_T, 0, s>>>(in, out, n, nullptr);
+    note_launch();
+    return cudaGetLastError();
+  }
+  char *t = static_cast<char *>(tmp);
+  Tout *bsum = reinterpret_cast<Tout *>(t);
+  Tout *boff = reinterpret_cast<Tout *>(t + (((size_t)nb * sizeof(Tout) + 255) & ~size_t(255)));
+  char *rest = reinterpret_cast<char *>(boff) + (((size_t)(nb + 1) * sizeof(Tout) + 255) & ~size_t(255));
+  k_scan_reduce<Tin, Tout><<<(unsigned)nb, SCAN_T, 0, s>>>(in, bsum, n);
+  note_launch();
+  cudaError_t e = exclusive_scan<Tout, Tout>(bsum, boff, nb, rest, s);
+  if (e != cudaSuccess) return e;
+  k_scan_apply<Tin, Tout><<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, n, boff);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t exclusive_scan<int32_t, int32_t>(const int32_t *, int32_t *, long long, void *, cudaStream_t);
+template cudaError_t exclusive_scan<int32_t, int64_t>(const int32_t *, int64_t *, long long, void *, cudaStream_t);
+template cudaError_t exclusive_scan<int64_t, int64_t>(const int64_t *, int64_t *, long long, void *, cudaStream_t);
+template cudaError_t exclusive_scan<uint32_t, uint64_t>(const uint32_t *, uint64_t *, long long, void *, cudaStream_t);
+template cudaError_t exclusive_scan<uint64_t, uint64_t>(const uint64_t *, uint64_t *, long long, void *, cudaStream_t);
+template cudaError_t exclusive_scan<uint8_t, int32_t>(const uint8_t *, int32_t *, long long, void *, cudaStream_t);
+
+// --------------------------------------------------------- segmented sort
+constexpr int SEG_T = 256;
+constexpr int SEG_CAP = 4096;  // keys sorted in shared memory at once
+
+template <typename K>
+__device__ __forceinline__ K key_max() { return ~K(0); }
+// Column half of a (col << 32 | value) key; 32-bit keys have none.
+template <typename K>
+__device__ __forceinline__ int32_t key_col(K k) { return (int32_t)((uint64_t)k >> 32); }
+
+struct SegLists {
+  int32_t n_med, n_big;
+};
+
+template <typename K, int MODE>
+__device__ __forceinline__ void write_single(K key, long long o, int32_t *cnt, long long s,
+                                             int32_t *mcol, int64_t *mval) {
+  if (MODE == MODE_MERGE) {
+    mcol[o] = key_col<K>(key);
+    mval[o] = (int64_t)(int32_t)(uint32_t)((uint64_t)key & 0xffffffffu);
+  }
+  if (MODE != MODE_SORT) cnt[s] = 1;
+}
+
+template <typename K, int MODE>
+__global__ void k_seg_classify(K *keys, const int64_t *off, long long nseg, int32_t *cnt,
+                               int32_t *mcol, int64_t *mval, int32_t *med, int32_t *big,
+                               SegLists *lists) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nseg;
+       s += (long long)gridDim.x * blockDim.x) {
+    long long o = off[s], n = off[s + 1] - o;
+    if (n <= 0) {
+      if (MODE != MODE_SORT) cnt[s] = 0;
+    } else if (n == 1) {
+      write_single<K, MODE>(keys[o], o, cnt, s, mcol, mval);
+    } else if (n <= 32) {
+      // warp kernel
+    } else if (n <= SEG_CAP) {
+      med[atomicAdd(&lists->n_med, 1)] = (int32_t)s;
+    } else {
+      big[atomicAdd(&lists->n_big, 1)] = (int32_t)s;
+    }
+  }
+}
+
+template <typename K, int MODE>
+__global__ void k_seg_warp(K *keys, const int64_t *off, long long nseg, int32_t *cnt,
+                           int32_t *mcol, int64_t *mval) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < nseg;
+       s += ((long long)gridDim.x * blockDim.x) >> 5) {
+    long long o = off[s];
+    int n = (int)(off[s + 1] - o);
+    if (n < 2 || n > 32) continue;
+    K key = lane < n ? keys[o + lane] : key_max<K>();
+    key = warp_bitonic<K>(key, lane);
+    if (MODE == MODE_SORT) {
+      if (lane < n) keys[o + lane] = key;
+      continue;
+    }
+    if (MODE == MODE_UNIQUE) {
+      K prev = __shfl_up_sync(0xffffffffu, key, 1);
+      bool head = lane < n && (lane == 0 || prev != key);
+      unsigned hm = __ballot_sync(0xffffffffu, head);
+      if (head) keys[o + __popc(hm & lt)] = key;
+      if (lane == 0) cnt[s] = __popc(hm);
+      continue;
+    }
+    // MODE_MERGE
+    int32_t col = key_col<K>(key);
+    long long val = (long long)(int32_t)(uint32_t)((uint64_t)key & 0xffffffffu);
+    int32_t pcol = __shfl_up_sync(0xffffffffu, col, 1);
+    bool head = lane < n && (lane == 0 || pcol != col);
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    int seg = 31 - __clz(hm & (lt | (1u << lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long ov = __shfl_up_sync(0xffffffffu, val, d);
+      int os = __shfl_up_sync(0xffffffffu, seg, d);
+      if (lane >= d && os == seg) val += ov;
+    }
+    bool nexthead = lane + 1 >= n || ((hm >> (lane + 1)) & 1u);
+    if (lane < n && nexthead) {
+      int idx = __popc(hm & (lt | (1u << lane))) - 1;
+      mcol[o + idx] = col;
+      mval[o + idx] = val;
+    }
+    if (lane == 0) cnt[s] = __popc(hm);
+  }
+}
+
+// After a segment of n keys (at `a`, shared or global) is sorted: compaction
+// for the UNIQUE / MERGE modes by a CTA.  Each thread owns a contiguous
+// sub-range; heads are counted, block-scanned and written.
+template <typename K, int MODE>
+__device__ void cta_compact(K *a, long long n, long long o, long long s, int32_t *cnt,
+                            int32_t *mcol, int64_t *mval, K *gkeys) {
+  __shared__ long long s_base;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const long long chunk = (long long)SEG_T * 16;
+  for (long long c0 = 0; c0 < n; c0 += chunk) {
+    long long c1 = c0 + chunk < n ? c0 + chunk : n;
+    long long per = (c1 - c0 + SEG_T - 1) / SEG_T;
+    long long b = c0 + threadIdx.x * per, e = b + per < c1 ? b + per : c1;
+    int nh = 0;
+    for (long long q = b; q < e; ++q) {
+      bool head;
+      if (MODE == MODE_MERGE) head = q == 0 || key_col<K>(a[q]) != key_col<K>(a[q - 1]);
+      else head = q == 0 || a[q] != a[q - 1];
+      nh += head;
+    }
+    int64_t tot;
+    int64_t pre = block_excl_scan<int64_t>((int64_t)nh, &tot);
+    long long w = s_base + pre;
+    // all threads must read a[] before anyone writes the compacted output when
+    // a aliases the output (UNIQUE mode in global memory): collect first.
+    for (long long q = b; q < e; ++q) {
+      bool head;
+      if (MODE == MODE_MERGE) head = q == 0 || key_col<K>(a[q]) != key_col<K>(a[q - 1]);
+      else head = q == 0 || a[q] != a[q - 1];
+      if (!head) continue;
+      if (MODE == MODE_MERGE) {
+        int32_t col = key_col<K>(a[q]);
+        long long v = 0;
+        for (long long r = q; r < n && key_col<K>(a[r]) == col; ++r)
+          v += (long long)(int32_t)(uint32_t)((uint64_t)a[r] & 0xffffffffu);
+        mcol[o + w] = col;
+        mval[o + w] = v;
+      } else {
+        gkeys[o + w] = a[q];
+      }
+      ++w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt[s] = (int32_t)s_base;
+  __syncthreads();
+}
+
+template <typename K, int MODE>
+__global__ void __launch_bounds__(SEG_T) k_seg_cta(K *keys, const int64_t *off, int32_t *cnt,
+                                                   int32_t *mcol, int64_t *mval,
+                                                   const int32_t *med, const SegLists *lists) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  K *a = reinterpret_cast<K *>(smraw);
+  const int nmed = lists->n_med;
+  for (int it = blockIdx.x; it < nmed; it += gridDim.x) {
+    long long s = med[it];
+    long long o = off[s];
+    int n = (int)(off[s + 1] - o);
+    int p2 = 64;
+    while (p2 < n) p2 <<= 1;
+    for (int q = threadIdx.x; q < p2; q += SEG_T) a[q] = q < n ? keys[o + q] : key_max<K>();
+    __syncthreads();
+    cta_bitonic<K>(a, p2);
+    if (MODE == MODE_SORT) {
+      for (int q = threadIdx.x; q < n; q += SEG_T) keys[o + q] = a[q];
+      __syncthreads();
+    } else {
+      cta_compact<K, MODE>(a, n, o, s, cnt, mcol, mval, keys);
+    }
+  }
+}
+
+// Segments longer than SEG_CAP: sort SEG_CAP chunks in shared memory, then
+// merge runs of doubling size between the key array and a scratch copy.
+template <typename K, int MODE>
+__global__ void __launch_bounds__(SEG_T) k_seg_big(K *keys, K *scratch, const int64_t *off,
+                                                   int32_t *cnt, int32_t *mcol, int64_t *mval,
+                                                   const int32_t *big, const SegLists *lists) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  K *a = reinterpret_cast<K *>(smraw);
+  const int nbig = lists->n_big;
+  for (int it = blockIdx.x; it < nbig; it += gridDim.x) {
+    long long s = big[it];
+    long long o = off[s];
+    long long n = off[s + 1] - o;
+    for (long long c0 = 0; c0 < n; c0 += SEG_CAP) {
+      int m = (int)(n - c0 < SEG_CAP ? n - c0 : SEG_CAP);
+      for (int q = threadIdx.x; q < SEG_CAP; q += SEG_T) a[q] = q < m ? keys[o + c0 + q] : key_max<K>();
+      __syncthreads();
+      cta_bitonic<K>(a, SEG_CAP);
+      for (int q = threadIdx.x; q < m; q += SEG_T) keys[o + c0 + q] = a[q];
+      __syncthreads();
+    }
+    K *src = keys + o, *dst = scratch + o;
+    for (long long R = SEG_CAP; R < n; R <<= 1) {
+      for (long long r0 = 0; r0 < n; r0 += 2 * R) {
+        long long na = n - r0 < R ? n - r0 : R;
+        long long nb = n - r0 - na < R ? n - r0 - na : R;
+        if (nb > 0) cta_merge<K>(src + r0, na, src + r0 + na, nb, dst + r0);
+        else
+          for (long long q = threadIdx.x; q < na; q += SEG_T) dst[r0 + q] = src[r0 + q];
+      }
+      __syncthreads();
+      K *t = src; src = dst; dst = t;
+    }
+    if (src != keys + o) {
+      for (long long q = threadIdx.x; q < n; q += SEG_T) keys[o + q] = src[q];
+      __syncthreads();
+    }
+    if (MODE != MODE_SORT) {
+      // compaction reads from the sorted keys; UNIQUE output goes to scratch
+      // first (the input would be overwritten while read), then back.
+      if (MODE == MODE_UNIQUE) {
+        cta_compact<K, MODE>(keys + o, n, 0, s, cnt, mcol, mval, scratch + o);
+        int m = cnt[s];
+        __syncthreads();
+        for (long long q = threadIdx.x; q < m; q += SEG_T) keys[o + q] = scratch[o + q];
+        __syncthreads();
+      } else {
+        cta_compact<K, MODE>(keys + o, n, o, s, cnt, mcol, mval, keys);
+      }
+    }
+  }
+}
+
+size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes) {
+  return 1024 + 2 * (size_t)(nseg + 1) * sizeof(int32_t) + (size_t)nkeys * key_bytes + 512;
+}
+
+template <typename K, int MODE>
+cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long long nkeys,
+                           int32_t *cnt, int32_t *mcol, int64_t *mval, void *tmp,
+                           cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  char *t = static_cast<char *>(tmp);
+  SegLists *lists = reinterpret_cast<SegLists *>(t);
+  int32_t *med = reinterpret_cast<int32_t *>(t + 256);
+  int32_t *big = med + nseg;
+  size_t kb = ((256 + 2 * (size_t)(nseg + 1) * sizeof(int32_t)) + 255) & ~size_t(255);
+  K *scratch = reinterpret_cast<K *>(t + kb);
+  cudaError_t e = cudaMemsetAsync(lists, 0, sizeof(SegLists), s);
+  if (e != cudaSuccess) return e;
+  k_seg_classify<K, MODE><<<grid_for(nseg, 256), 256, 0, s>>>(keys, off, nseg, cnt, mcol, mval,
+                                                              med, big, lists);
+  note_launch();
+  k_seg_warp<K, MODE><<<grid_for(nseg * 32, 256), 256, 0, s>>>(keys, off, nseg, cnt, mcol, mval);
+  note_launch();
+  size_t sm = SEG_CAP * sizeof(K);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_seg_cta<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_seg_big<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr_done = true;
+  }
+  k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, med, lists);
+  note_launch();
+  k_seg_big<K, MODE><<<152, SEG_T, sm, s>>>(keys, scratch, off, cnt, mcol, mval, big, lists);
+  note_launch();
+  (void)nkeys;
+  return cudaGetLastError();
+}
+
+template cudaError_t segmented_sort<uint32_t, MODE_SORT>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
+template cudaError_t segmented_sort<uint32_t, MODE_UNIQUE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
+template cudaError_t segmented_sort<uint64_t, MODE_MERGE>(uint64_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
+
+}  // namespace pl

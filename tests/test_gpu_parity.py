@@ -1,0 +1,292 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle.
+
+Inputs are the seeded synthetic netlists of netgen.  Where a step consumes
+coordinates, both sides get the same FP32 node coordinates (produced by the
+GPU path itself), so each step is checked on its own:
+  * static graph (A1): CSR bit-exact (columns, stored weights, baseWeight);
+  * area hints (A2/A3): topology bit-exact (row pointers, columns, bins),
+    D_b / C_b / phi_b bit-exact (FP64), hint weights within 8 FP32 ulps
+    (FP32 storage) or 1 bf16 ulp (BF16 storage), degrees and lambda_up within
+    the resulting weight tolerance;
+  * filters (A0, A4) and the whole initializer: coordinates within 1e-4 of the
+    die width;
+  * HPWL (A5): within 1e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_10073_gb300 import netgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_ULP_TOL = 8
+
+
+def pl():
+    import paper_2511_10073_gb300 as m
+    return m
+
+
+def cfg_params(name, **kw):
+    base = dict(tiny=dict(nbx=16, nby=16), micro=dict(nbx=4, nby=4), small=dict(nbx=8, nby=8, det_ratio=0.4),
+                medium=dict(nbx=32, nby=32), large=dict(nbx=32, nby=32))[name]
+    base.update(kw)
+    return base
+
+
+class Side:
+    """One netlist on both sides."""
+
+    def __init__(self, nl, **kw):
+        self.nl = nl
+        self.kw = kw
+        self.prm = pl().params(**kw)
+        self.dnl = pl().DeviceNetlist(nl)
+        self.g = pl().pl_build_graph(self.dnl, self.prm)
+        self.info = self.g.info()
+        self.o = oracle.Oracle(nl, **kw)
+        self.N = self.info["N"]
+        self.die = nl.region[2] - nl.region[0]
+
+    def gpu_signal(self, seed):
+        x0 = torch.empty(self.N * 2, dtype=torch.float32, device="cuda")
+        pl().pl_init_signal(self.g, seed, None, x0)
+        x1 = torch.empty_like(x0)
+        pl().pl_gift(self.g, self.prm, x0, x1)
+        torch.cuda.synchronize()
+        return x0, x1
+
+
+def to_np(t):
+    return t.view(-1, 2).double().cpu().numpy()
+
+
+def check_weights(wg, wo, wdtype, where):
+    wg = np.asarray(wg, np.float64)
+    wo = np.asarray(wo, np.float64)
+    if wdtype == pl().PL_W_BF16:
+        tol = np.where(wo != 0, 2.0 ** (np.floor(np.log2(np.abs(np.where(wo != 0, wo, 1.0)))) - 7), 1e-45)
+    else:
+        tol = F32_ULP_TOL * np.where(wo != 0, np.spacing(np.abs(wo).astype(np.float32)).astype(np.float64), 1e-45)
+    bad = np.abs(wg - wo) > tol
+    assert not bad.any(), f"{where}: {bad.sum()} weights beyond tolerance, e.g. {wg[bad][:5]} vs {wo[bad][:5]}"
+    return float(np.mean(wg == wo)) if wg.size else 1.0
+
+
+# -------------------------------------------------------------- A1 static
+@pytest.mark.parametrize("cfg,seed,wd,perm", [
+    ("micro", 1, 1, False), ("small", 1, 1, False), ("small", 2, 2, True),
+    ("tiny", 1, 1, False), ("tiny", 3, 2, False), ("medium", 1, 1, False)])
+def test_static_graph_bitexact(cfg, seed, wd, perm):
+    nl = netgen.make_netlist(cfg, seed)
+    if perm:
+        nl = netgen.permuted(nl, 9)
+    s = Side(nl, **cfg_params(cfg, wdtype=wd))
+    ge = s.g.export_static()
+    oe = s.o.static_csr()
+    assert (s.info["macro_pins"], s.info["stars"], s.info["macros"]) == (s.o.Pm, s.o.S, s.o.Mm)
+    assert np.array_equal(ge["rp"], oe["rp"])
+    assert np.array_equal(ge["col"], oe["col"])
+    assert np.array_equal(ge["w"], oe["w_store"])
+    assert np.array_equal(ge["base_w"], oe["base_w"])
+
+
+# -------------------------------------------------------- A2/A3 hints
+def _compare_hints(s, ge, oe):
+    assert np.array_equal(ge["cell_bin"], oe["cell_bin"])
+    assert np.array_equal(ge["Db"], oe["Db"])
+    assert np.array_equal(ge["Cb"], oe["Cb"])
+    assert np.array_equal(ge["phi"], oe["phi"])
+    assert np.array_equal(ge["rp"], oe["rp"])
+    assert np.array_equal(ge["col"], oe["col"])
+    frac = check_weights(ge["w"], oe["w"], s.kw.get("wdtype", 1), "augmented graph")
+    rp = oe["rp"]
+    absw = np.add.reduceat(np.abs(oe["w"]), rp[:-1]) if oe["w"].size else np.zeros(s.N)
+    absw[np.diff(rp) == 0] = 0.0
+    tol = (2e-6 if s.kw.get("wdtype", 1) == 1 else 1e-2) * absw + 1e-12
+    assert (np.abs(ge["deg"] - oe["deg"]) <= tol).all()
+    rel = 2e-6 if s.kw.get("wdtype", 1) == 1 else 1e-2
+    assert ge["lam_up"] == pytest.approx(oe["lam_up"], rel=rel)
+    return frac
+
+
+@pytest.mark.parametrize("cfg,seed,kw", [
+    ("micro", 1, {}), ("small", 1, {}), ("small", 3, dict(wdtype=2)), ("tiny", 1, {}),
+    ("tiny", 2, dict(nbx=32, nby=32)), ("tiny", 4, dict(nbx=20, nby=12, det_ratio=0.3, wdtype=2)),
+    ("medium", 2, {})])
+def test_hints_crossfed(cfg, seed, kw):
+    nl = netgen.make_netlist(cfg, seed)
+    s = Side(nl, **cfg_params(cfg, **kw))
+    _, xy = s.gpu_signal(seed)
+    pl().pl_build_hints(s.g, s.prm, xy)
+    ge = s.g.export()
+    a = to_np(xy)
+    s.o.build_hints(a[:, 0], a[:, 1])
+    oe = s.o.merged()
+    frac = _compare_hints(s, ge, oe)
+    assert frac > 0.5  # most weights bit-identical
+
+
+# ------------------------------------------------------------ A0 / A4
+@pytest.mark.parametrize("cfg,seed,kw", [
+    ("micro", 2, {}), ("small", 1, {}), ("tiny", 1, {}), ("tiny", 2, dict(wdtype=2)),
+    ("tiny", 3, dict(gift_center=1, gift_k=(3, 1, 0), gift_sigma=(1.5, 3.0, 3.0))),
+    ("medium", 1, {})])
+def test_init_and_gift_crossfed(cfg, seed, kw):
+    nl = netgen.make_netlist(cfg, seed)
+    s = Side(nl, **cfg_params(cfg, **kw))
+    x0, x1 = s.gpu_signal(seed)
+    a0 = to_np(x0)
+    ox, oy = s.o.init_signal(seed)
+    mov = nl.cell_kind == 0
+    C = nl.num_cells
+    assert np.array_equal(a0[:C, 0][mov], ox[:C][mov].astype(np.float32))
+    assert np.abs(a0[:, 0] - ox).max() <= 1e-6 * s.die
+    gx, gy = s.o.gift(a0[:, 0], a0[:, 1])
+    a1 = to_np(x1)
+    err = max(np.abs(a1[:, 0] - gx).max(), np.abs(a1[:, 1] - gy).max())
+    assert err <= 1e-4 * s.die, err
+
+
+@pytest.mark.parametrize("cfg,seed,kw", [
+    ("micro", 1, {}), ("small", 2, {}), ("tiny", 1, {}), ("tiny", 2, dict(wdtype=2)),
+    ("tiny", 3, dict(ntaps=3, tap_k=(2, 4, 8, 0), tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))),
+    ("tiny", 4, dict(pin_every_step=1, gamma=0.7)), ("tiny", 5, dict(nbx=32, nby=32)),
+    ("medium", 3, {}), ("medium", 1, dict(wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+                                         tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0)))])
+def test_filter_step_crossfed(cfg, seed, kw):
+    nl = netgen.make_netlist(cfg, seed)
+    s = Side(nl, **cfg_params(cfg, **kw))
+    _, xy = s.gpu_signal(seed)
+    pl().pl_build_hints(s.g, s.prm, xy)
+    out = torch.empty_like(xy)
+    pl().pl_filter_apply(s.g, s.prm, xy, out)
+    torch.cuda.synchronize()
+    a = to_np(xy)
+    s.o.build_hints(a[:, 0], a[:, 1])
+    ox, oy = s.o.filter(a[:, 0], a[:, 1])
+    b = to_np(out)
+    err = max(np.abs(b[:, 0] - ox).max(), np.abs(b[:, 1] - oy).max())
+    assert err <= 1e-4 * s.die, err
+
+
+@pytest.mark.parametrize("cfg,seed,kw", [
+    ("micro", 3, {}), ("small", 1, {}), ("tiny", 1, {}), ("tiny", 2, {}), ("tiny", 3, dict(wdtype=2)),
+    ("tiny", 6, dict(gift_enable=0)), ("tiny", 7, dict(t_hint=0)), ("tiny", 8, dict(gamma=0.0))])
+def test_full_initializer(cfg, seed, kw):
+    nl = netgen.make_netlist(cfg, seed)
+    s = Side(nl, **cfg_params(cfg, **kw))
+    out = torch.empty(nl.num_cells * 2, dtype=torch.float32, device="cuda")
+    pl().pl_filter_init(s.g, s.prm, seed, None, out)
+    torch.cuda.synchronize()
+    gx, gy = s.o.run(seed)
+    b = to_np(out)
+    C = nl.num_cells
+    err = max(np.abs(b[:, 0] - gx[:C]).max(), np.abs(b[:, 1] - gy[:C]).max())
+    assert err <= 1e-4 * s.die, err
+
+
+def test_full_initializer_from_given_placement():
+    nl = netgen.make_netlist("tiny", 9)
+    s = Side(nl, **cfg_params("tiny"))
+    rng = np.random.default_rng(0)
+    xl, yl, xh, yh = nl.region
+    xy0 = np.stack([rng.uniform(xl, xh, nl.num_cells), rng.uniform(yl, yh, nl.num_cells)], 1).astype(np.float32)
+    t0 = torch.tensor(xy0.reshape(-1), device="cuda")
+    out = torch.empty_like(t0)
+    pl().pl_filter_init(s.g, s.prm, 0, t0, out)
+    gx, gy = s.o.run(0, xy0=xy0.reshape(-1))
+    b = to_np(out)
+    err = max(np.abs(b[:, 0] - gx[:nl.num_cells]).max(), np.abs(b[:, 1] - gy[:nl.num_cells]).max())
+    assert err <= 1e-4 * s.die
+
+
+# --------------------------------------------------------------- A5 HPWL
+@pytest.mark.parametrize("cfg,seed", [("micro", 1), ("tiny", 2), ("medium", 1)])
+def test_hpwl(cfg, seed):
+    nl = netgen.make_netlist(cfg, seed)
+    dnl = pl().DeviceNetlist(nl)
+    rng = np.random.default_rng(seed)
+    xl, yl, xh, yh = nl.region
+    xy = np.stack([rng.uniform(xl, xh, nl.num_cells), rng.uniform(yl, yh, nl.num_cells)], 1).astype(np.float32)
+    t = torch.tensor(xy.reshape(-1), device="cuda")
+    ws = pl().hpwl_workspace(nl.num_nets)
+    h = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):  # the second call reuses the workspace
+        pl().pl_hpwl(dnl, t, h, ws)
+        ref = oracle.hpwl(nl, xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64))
+        assert h.item() == pytest.approx(ref, rel=1e-5)
+
+
+def test_hpwl_big_nets_and_empty():
+    cells = 100
+    nl = netgen.Netlist(np.array([0, 0, 1, 41, 100], np.int64),
+                        np.r_[np.arange(1), np.arange(40), np.arange(59) + 40].astype(np.int32) % cells,
+                        np.zeros(100, np.float32), np.zeros(100, np.float32),
+                        np.ones(cells, np.float32), np.ones(cells, np.float32),
+                        np.zeros(cells, np.uint8), np.zeros(cells, np.float32),
+                        np.zeros(cells, np.float32), (0.0, 0.0, 10.0, 10.0))
+    xy = np.random.default_rng(1).uniform(0, 10, (cells, 2)).astype(np.float32)
+    h = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pl().pl_hpwl(pl().DeviceNetlist(nl), torch.tensor(xy.reshape(-1), device="cuda"), h,
+                 pl().hpwl_workspace(4))
+    assert h.item() == pytest.approx(oracle.hpwl(nl, xy[:, 0], xy[:, 1]), rel=1e-6)
+
+
+# ------------------------------------------------------------ failures
+def test_errors_are_reported():
+    m = pl()
+    nl = netgen.make_netlist("micro", 1)
+    bad = netgen.Netlist(nl.net_ptr, nl.pin_cell.copy(), nl.pin_dx, nl.pin_dy, nl.cell_w,
+                         nl.cell_h, nl.cell_kind, nl.fixed_x, nl.fixed_y, nl.region)
+    bad.pin_cell[3] = nl.num_cells + 5
+    with pytest.raises(m.PlError) as e:
+        m.pl_build_graph(m.DeviceNetlist(bad), m.params(nbx=4, nby=4))
+    assert e.value.code == m.PL_ERR_INVALID_ARG
+    with pytest.raises(m.PlError) as e:
+        m.pl_build_graph(m.DeviceNetlist(nl), m.params(nbx=4, nby=4, clique_max=40))
+    assert e.value.code == m.PL_ERR_INVALID_ARG
+    s = Side(nl, nbx=4, nby=4)
+    xy = torch.full((s.N * 2,), float("nan"), device="cuda")
+    with pytest.raises(m.PlError) as e:
+        m.pl_build_hints(s.g, s.prm, xy)
+    assert e.value.code == m.PL_ERR_NONFINITE
+    with pytest.raises(m.PlError) as e:
+        m.pl_build_hints(s.g, m.params(nbx=8, nby=4), xy)
+    assert e.value.code == m.PL_ERR_INVALID_ARG
+    ws = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(m.PlError) as e:
+        m.pl_hpwl(s.dnl, torch.zeros(nl.num_cells * 2, device="cuda"),
+                  torch.zeros(1, dtype=torch.float64, device="cuda"), ws)
+    assert e.value.code == m.PL_ERR_WORKSPACE
+
+
+def test_empty_graph_spectrum_error():
+    m = pl()
+    cells = [(1.0, 1.0, 0, 0.0, 0.0)] * 3
+    nl = netgen.Netlist(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32),
+                        np.zeros(2, np.float32), np.zeros(2, np.float32),
+                        np.ones(3, np.float32), np.ones(3, np.float32), np.zeros(3, np.uint8),
+                        np.zeros(3, np.float32), np.zeros(3, np.float32), (0.0, 0.0, 10.0, 10.0))
+    s = Side(nl, nbx=2, nby=2)
+    x0, x1 = s.gpu_signal(1)
+    with pytest.raises(m.PlError) as e:
+        m.pl_build_hints(s.g, s.prm, x1)
+    assert e.value.code == m.PL_ERR_SPECTRUM
+    assert s.o.build_hints(*to_np(x1).T, check=False) == oracle.ERR_SPECTRUM
+
+
+def test_rebuild_in_place_other_netlist():
+    m = pl()
+    a = netgen.make_netlist("tiny", 1)
+    b = netgen.make_netlist("small", 2)
+    prm = m.params(nbx=8, nby=8)
+    g = m.pl_build_graph(m.DeviceNetlist(a), prm)
+    g = m.pl_build_graph(m.DeviceNetlist(b), prm, graph=g)
+    ge = g.export_static()
+    oe = oracle.Oracle(b, nbx=8, nby=8).static_csr()
+    assert np.array_equal(ge["col"], oe["col"]) and np.array_equal(ge["w"], oe["w_store"])
