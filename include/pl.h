@@ -155,7 +155,9 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
  * cell centre (xy_cells, device) + offset, as one double to *hpwl (device).
  * ws: device scratch of at least pl_hpwl_workspace_size(num_nets) bytes, 256-
  * byte aligned; its contents need no initialisation and are left zeroed for
- * the next call.  Does not synchronize.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+ * the next call.  Does not synchronize.  net_ptr must be valid (as checked
+ * by pl_build_graph); a pin_cell outside [0, num_cells) is not read and makes
+ * *hpwl NaN.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
 size_t pl_hpwl_workspace_size(int32_t num_nets);
 pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, void *ws,
                   size_t ws_bytes, pl_stream stream);

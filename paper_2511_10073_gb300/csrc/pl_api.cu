@@ -313,11 +313,11 @@ pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, voi
                   size_t ws_bytes, pl_stream stream) {
   pl::g_err[0] = 0;
   if (!nl || !xy_cells || !hpwl || !ws) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
-  if (nl->num_nets < 0 || !nl->net_ptr || (nl->num_pins && !nl->pin_cell)) { set_error("bad netlist"); return PL_ERR_INVALID_ARG; }
+  if (nl->num_nets < 0 || nl->num_cells < 0 || !nl->net_ptr || (nl->num_pins && !nl->pin_cell)) { set_error("bad netlist"); return PL_ERR_INVALID_ARG; }
   if (reinterpret_cast<uintptr_t>(ws) % 256) { set_error("workspace must be 256-byte aligned"); return PL_ERR_INVALID_ARG; }
   if (ws_bytes < hpwl_ws_bytes(nl->num_nets)) { set_error("workspace too small: need %zu bytes", hpwl_ws_bytes(nl->num_nets)); return PL_ERR_WORKSPACE; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(ws, 0, 4, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, 8, s);
   if (e == cudaSuccess) e = launch_hpwl(nl, xy_cells, hpwl, ws, s);
   if (e != cudaSuccess) return cuda_fail(e, "pl_hpwl");
   return PL_OK;

@@ -437,7 +437,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->cell_macro, (size_t)(C + 1) * 4));
   TRY(scan_tmp(g, C > NP ? C : NP, &stmp));
   TRY((exclusive_scan<uint8_t, int32_t>(is_macro, P<int32_t>(g->cell_macro), C, stmp, s)));
-  TRY(ensure(g->tmp[1], (size_t)NP + 256));
+  TRY(ensure(g->tmp[1], (size_t)(NP > M ? NP : M) + 256));  // pin flags, later net flags
   uint8_t *pflag = P<uint8_t>(g->tmp[1]);
   TRY(ensure(g->tmp[2], (size_t)(NP + 1) * 4 + 256));
   int32_t *pscan = P<int32_t>(g->tmp[2]);

@@ -4,7 +4,8 @@
 // whole warp.  Pin positions and extrema are FP32 (min/max are exact), each
 // net's span is formed and summed in FP64.  Per-block FP64 sums go to the
 // caller's workspace; the last block to finish (ticket) adds them in block
-// order, so the result does not depend on scheduling.
+// order, so the result does not depend on scheduling.  A pin whose cell index
+// is out of range makes the result NaN (it is not dereferenced).
 #include "pl_internal.h"
 
 namespace pl {
@@ -12,9 +13,17 @@ namespace pl {
 constexpr int kHpwlThreads = 256;
 constexpr int kHpwlBlocks = 152 * 8;
 
+// Pin position; a pin_cell outside [0, C) is counted in *bad and reads cell 0
+// instead (the call then reports NaN).
 __device__ __forceinline__ float2 pin_pos(const float2 *xy, const int32_t *pin_cell,
-                                          const float *dx, const float *dy, long long k) {
-  float2 c = xy[pin_cell[k]];
+                                          const float *dx, const float *dy, long long k,
+                                          int32_t C, int *bad) {
+  int32_t i = pin_cell[k];
+  if ((uint32_t)i >= (uint32_t)C) {
+    atomicAdd(bad, 1);
+    i = 0;
+  }
+  float2 c = xy[i];
   if (dx) c.x += dx[k];
   if (dy) c.y += dy[k];
   return c;
@@ -23,8 +32,8 @@ __device__ __forceinline__ float2 pin_pos(const float2 *xy, const int32_t *pin_c
 __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
                                                        const int32_t *pin_cell, const float *dx,
                                                        const float *dy, const float2 *xy,
-                                                       int32_t M, double *part, int *ticket,
-                                                       double *out) {
+                                                       int32_t M, int32_t C, double *part,
+                                                       int *ticket, double *out) {
   __shared__ double red[kHpwlThreads / 32];
   __shared__ int last;
   const int lane = threadIdx.x & 31;
@@ -40,10 +49,10 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       if (n > 32) {
         big = true;
       } else if (n > 0) {
-        float2 p = pin_pos(xy, pin_cell, dx, dy, b);
+        float2 p = pin_pos(xy, pin_cell, dx, dy, b, C, ticket + 1);
         float x0 = p.x, x1 = p.x, y0 = p.y, y1 = p.y;
         for (long long k = b + 1; k < b + n; ++k) {
-          p = pin_pos(xy, pin_cell, dx, dy, k);
+          p = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
           x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
           y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
         }
@@ -58,7 +67,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       long long b = net_ptr[ee], n = net_ptr[ee + 1] - b;
       float x0 = 3.4e38f, x1 = -3.4e38f, y0 = 3.4e38f, y1 = -3.4e38f;
       for (long long k = b + lane; k < b + n; k += 32) {
-        float2 p = pin_pos(xy, pin_cell, dx, dy, k);
+        float2 p = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
         x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
         y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
       }
@@ -87,8 +96,9 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
     __threadfence();
     double s = 0.0;
     for (int k = 0; k < (int)gridDim.x; ++k) s += __ldcg(&part[k]);
-    *out = s;
-    *ticket = 0;
+    *out = __ldcg(ticket + 1) ? __longlong_as_double(0x7ff8000000000000LL) : s;
+    ticket[0] = 0;
+    ticket[1] = 0;
   }
 }
 
@@ -102,8 +112,8 @@ cudaError_t launch_hpwl(const pl_netlist *nl, const float *xy, double *out, void
   int *ticket = reinterpret_cast<int *>(ws);
   double *part = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
   k_hpwl<<<nb, kHpwlThreads, 0, s>>>(nl->net_ptr, nl->pin_cell, nl->pin_dx, nl->pin_dy,
-                                     reinterpret_cast<const float2 *>(xy), nl->num_nets, part,
-                                     ticket, out);
+                                     reinterpret_cast<const float2 *>(xy), nl->num_nets,
+                                     nl->num_cells, part, ticket, out);
   note_launch();
   return cudaGetLastError();
 }
