@@ -166,6 +166,9 @@ def main():
     ap.add_argument("--config", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-one", action="store_true",
+                    help="warm up, then run one step inside a CUDA profiler range and exit "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -205,9 +208,17 @@ def main():
         pl.pl_filter_init(g, prm, args.seed, None, out)
         pl.pl_hpwl(dnl, out, hp, ws)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, args.warmup) if not args.profile_one else args.warmup):
         step()
     torch.cuda.synchronize()
+    if args.profile_one:
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profile_one": args.config, "movable_cells": nl.num_movable}))
+        return
 
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)

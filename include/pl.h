@@ -181,8 +181,8 @@ void pl_graph_destroy(pl_graph *g);
  * pl_prof_enable(1) clears the records and starts counting: every kernel the
  * library launches is counted, and each sparse-product launch (A0, A4) is
  * bracketed by a CUDA event pair on its own stream.  pl_prof_enable(0) stops
- * recording.  pl_prof_read writes host out[8]:
- *   0 kernel launches since enable
+ * recording and keeps the records.  pl_prof_read writes host out[8]:
+ *   0 kernel launches between enable and disable (or now)
  *   1 refinement-filter (A4) launches  2 their summed time, ms
  *   3 their algorithmic bytes (indices + weights once, row pointers, x read,
  *     y written, one coefficient per row)

@@ -23,7 +23,7 @@ struct ProfRec {
 };
 static std::vector<ProfRec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
-static long long g_launch0 = 0;
+static long long g_launch0 = 0, g_launch1 = -1;
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 bool prof_on() { return g_prof.load(std::memory_order_relaxed); }
@@ -406,12 +406,17 @@ pl_status pl_graph_export(const pl_graph *g, int64_t *rp, int32_t *col, double *
 
 void pl_prof_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  for (ProfRec &r : g_recs) {
-    g_pool.push_back(r.a);
-    g_pool.push_back(r.b);
+  if (on) {
+    for (ProfRec &r : g_recs) {
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    g_launch0 = g_launches.load();
+    g_launch1 = -1;
+  } else if (g_prof.load()) {
+    g_launch1 = g_launches.load();
   }
-  g_recs.clear();
-  g_launch0 = g_launches.load();
   g_prof.store(on != 0);
 }
 
@@ -420,7 +425,7 @@ pl_status pl_prof_read(double *out) {
   if (!out) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (int k = 0; k < 8; ++k) out[k] = 0.0;
-  out[0] = (double)(g_launches.load() - g_launch0);
+  out[0] = (double)((g_launch1 >= 0 ? g_launch1 : g_launches.load()) - g_launch0);
   for (ProfRec &r : g_recs) {
     cudaError_t e = cudaEventSynchronize(r.b);
     float ms = 0.f;

@@ -54,6 +54,34 @@ __device__ __forceinline__ float exp_neg(double r) {
   return expf(-rh) * (1.0f - rl);
 }
 
+// BF16 storage rounds the FP64 weight of the definition once.  The fast FP32
+// value is within a few FP32 ulps of it (FP32 exp: 2 ulps, three roundings),
+// so it rounds to the same bf16 unless it lies within kNearTie FP32 ulps of a
+// bf16 rounding midpoint (low 16 bits near 0x8000); only then the weight is
+// recomputed in FP64 with the exact operation sequence of the definition.
+constexpr int kNearTie = 8;
+__device__ __forceinline__ bool near_bf16_tie(float v) {
+  int d = (int)(__float_as_uint(v) & 0xffffu) - 0x8000;
+  return d >= -kNearTie && d <= kNearTie;
+}
+// -((e^{-maxRatio} * phi) * bw) for cell centre (x, y) and bin (xx, yy), FP64.
+__device__ double bin_w_exact(float x, float y, int xx, int yy, const HintGeo &G, double phi,
+                              double bw) {
+  double xb = __dadd_rn(G.xl, __dmul_rn((double)xx + 0.5, G.wb));
+  double yb = __dadd_rn(G.yl, __dmul_rn((double)yy + 0.5, G.hb));
+  double dx = fabs(__dadd_rn((double)x, -xb)), dy = fabs(__dadd_rn((double)y, -yb));
+  double r = fmax(__ddiv_rn(dx, __dmul_rn(G.wb, 0.5)), __ddiv_rn(dy, __dmul_rn(G.hb, 0.5)));
+  double t = __dmul_rn(__dmul_rn(exp_cw(-r), phi), bw);
+  return -t;
+}
+// -(e^{-maxRatio} * bw) for a cell centre and a macro (centre xm, ym; size wm, hm).
+__device__ double macro_w_exact(float x, float y, float xm, float ym, float wm, float hm,
+                                double bw) {
+  double dx = fabs(__dadd_rn((double)x, -(double)xm)), dy = fabs(__dadd_rn((double)y, -(double)ym));
+  double r = fmax(__ddiv_rn(dx, __dmul_rn((double)wm, 0.5)), __ddiv_rn(dy, __dmul_rn((double)hm, 0.5)));
+  return -__dmul_rn(exp_cw(-r), bw);
+}
+
 // Writes the stored form of v and returns the value it stores.
 __device__ __forceinline__ float store_w(void *wbuf, int wdtype, uint64_t k, float v) {
   if (wdtype == PL_W_BF16) {
@@ -63,6 +91,11 @@ __device__ __forceinline__ float store_w(void *wbuf, int wdtype, uint64_t k, flo
   }
   reinterpret_cast<float *>(wbuf)[k] = v;
   return v;
+}
+// BF16 store of an exactly rounded FP64 weight.
+__device__ __forceinline__ float store_bits(void *wbuf, uint64_t k, uint16_t h) {
+  reinterpret_cast<uint16_t *>(wbuf)[k] = h;
+  return bf16_to_f(h);
 }
 __device__ __forceinline__ float load_w(const void *wbuf, int wdtype, uint64_t k) {
   if (wdtype == PL_W_BF16) return bf16_to_f(reinterpret_cast<const uint16_t *>(wbuf)[k]);
@@ -276,7 +309,8 @@ __global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int
                                 const float *cw, const float *ch, const float *fx, const float *fy,
                                 const int32_t *macro_cell, const int64_t *gptr,
                                 const uint32_t *glist, const double *base_w, const float *phif,
-                                int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
+                                const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum,
+                                uint64_t *mac_base,
                                 uint64_t *bin_base) {
   const int lane = threadIdx.x & 31;
   const int64_t nrows = with_hints ? G.Nst : G.N;
@@ -317,7 +351,11 @@ __global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int
           double ry = fabs((double)p.y - (double)fy[c]) / ((double)ch[c] * 0.5);
           float wv = -(exp_neg(fmax(rx, ry)) * bwf);
           col[k] = (int32_t)(G.mv0 + m);
-          acc_deg(D, Pp, store_w(w, wdtype, k, wv));
+          if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
+            acc_deg(D, Pp, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, fx[c], fy[c], cw[c],
+                                                                   ch[c], base_w[v]))));
+          else
+            acc_deg(D, Pp, store_w(w, wdtype, k, wv));
         }
         written += __popc(hm);
       }
@@ -334,7 +372,11 @@ __global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int
         float wv = -((exp_neg(fmax(rx, ry)) * phif[bb]) * bwf);
         uint64_t k = bb0 + j;
         col[k] = (int32_t)(G.bn0 + bb);
-        acc_deg(D, Pp, store_w(w, wdtype, k, wv));
+        if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
+          acc_deg(D, Pp, store_bits(w, k, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb],
+                                                             base_w[v]))));
+        else
+          acc_deg(D, Pp, store_w(w, wdtype, k, wv));
       }
       if (lane == 0) {
         mac_base[v] = mb;
@@ -614,8 +656,8 @@ pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s) {
   k_assemble_rows<<<grid_for(N * 32, 256), 256, 0, s>>>(
       G, 0, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
       P<int32_t>(m.longidx), P<uint64_t>(m.lptr), nullptr, nullptr, nullptr, nullptr, nullptr,
-      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P<int32_t>(m.col),
-      m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum), nullptr, nullptr);
+      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+      P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum), nullptr, nullptr);
   note_launch();
   TRY(cudaGetLastError());
   return PL_OK;
@@ -716,7 +758,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       P<int32_t>(m.longidx), P<uint64_t>(m.lptr), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
       P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
       P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr), P<uint32_t>(g->glist),
-      P<double>(g->base_w), phif, P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum),
+      P<double>(g->base_w), phif, P<double>(g->phi), P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
+      P<dfl>(m.psum),
       P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
   note_launch();
   // H10: virtual rows
