@@ -450,6 +450,28 @@ void orc_nodes_export(const orc_graph *g, uint8_t *nkind, double *fx, double *fy
 
 /* ------------------------------------- A2 + A3: area hints, signed Laplacian */
 
+/* Sum of a[0..n) in a fixed blocked order: n <= 64 values are added left to
+ * right; longer sequences are cut into consecutive blocks of 64, each block
+ * is added left to right, and the sequence of block sums is summed the same
+ * way (recursively).  Used for bin densities. */
+static double blocked_sum(const double *a, int64_t n) {
+  if (n <= 64) {
+    double s = 0.0;
+    for (int64_t k = 0; k < n; ++k) s += a[k];
+    return s;
+  }
+  int64_t nb = (n + 63) / 64;
+  double *t = (double *)xcalloc(nb, sizeof(double));
+  for (int64_t j = 0; j < nb; ++j) {
+    double s = 0.0;
+    for (int64_t k = 64 * j; k < n && k < 64 * j + 64; ++k) s += a[k];
+    t[j] = s;
+  }
+  double r = blocked_sum(t, nb);
+  free(t);
+  return r;
+}
+
 typedef struct { int32_t cell, m; } mpair_t;
 static int cmp_pair(const void *a, const void *b) {
   const mpair_t *x = (const mpair_t *)a, *y = (const mpair_t *)b;
@@ -533,8 +555,10 @@ static mpair_t *macro_pairs(const orc_graph *g, const double *gx, const double *
  *  - only movable cells with baseWeight > 0 get hint edges;
  *  - "overlaps macro m": the cell rectangle (centre, w, h) and the macro
  *    rectangle intersect with positive area (decided in FP32, overlaps());
- *  - D_b = (sum of w*h of movable cells whose centre lies in b, ascending cell
- *    id) / bin area; the bin of a centre is decided in FP32 (bin_of());
+ *  - D_b = (FP64 sum of w*h of the movable cells whose centre lies in b) / bin
+ *    area; the cells are taken with baseWeight > 0 first, then the others,
+ *    each group in ascending id, and added in the blocked order of
+ *    blocked_sum(); the bin of a centre is decided in FP32 (bin_of());
  *  - capacity of b = C * (A_bin - macro area in b) / A_bin;
  *  - phi_b = 2 / (1 + exp(-mu (D_b - C_b))) - 1  (= 2 sigmoid(.) - 1);
  *  - cell i is in N(b) when its centre bin lies in the n_x x n_y window of b,
@@ -551,8 +575,9 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
   for (int32_t i = 0; i < C; ++i)
     if (g->ckind[i] == 0 && !(isfinite(gx[i]) && isfinite(gy[i]))) return ORC_ERR_NONFINITE;
 
-  /* bin of each movable cell, bin densities, capacities, phi */
-  for (int32_t b = 0; b < g->NB; ++b) g->Db[b] = 0.0;
+  /* bin of each movable cell; each bin's cell sequence: its cells with
+   * baseWeight > 0 in ascending id, then its other movable cells ascending */
+  int64_t *bcnt = (int64_t *)xcalloc(2 * (int64_t)g->NB + 1, sizeof(int64_t));
   for (int32_t i = 0; i < C; ++i) {
     g->cell_bin[i] = -1;
     if (g->ckind[i] != 0) continue;
@@ -560,14 +585,24 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
     int32_t by = bin_of(gy[i], g->yl, g->yh, g->nby);
     int32_t b = by * g->nbx + bx;
     g->cell_bin[i] = b;
-    g->Db[b] += (double)g->cw[i] * (double)g->ch[i];
+    bcnt[2 * (int64_t)b + (g->base_w[i] > 0.0 ? 0 : 1) + 1]++;
+  }
+  for (int64_t k = 0; k < 2 * (int64_t)g->NB; ++k) bcnt[k + 1] += bcnt[k];
+  double *area = (double *)xcalloc(bcnt[2 * (int64_t)g->NB], sizeof(double));
+  int64_t *fillp = (int64_t *)xcalloc(2 * (int64_t)g->NB, sizeof(int64_t));
+  for (int32_t i = 0; i < C; ++i) {
+    if (g->ckind[i] != 0) continue;
+    int64_t k = 2 * (int64_t)g->cell_bin[i] + (g->base_w[i] > 0.0 ? 0 : 1);
+    area[bcnt[k] + fillp[k]++] = (double)g->cw[i] * (double)g->ch[i];
   }
   for (int32_t b = 0; b < g->NB; ++b) {
-    g->Db[b] = g->Db[b] / g->abin;
+    int64_t a0 = bcnt[2 * (int64_t)b], a1 = bcnt[2 * (int64_t)b + 2];
+    g->Db[b] = blocked_sum(area + a0, a1 - a0) / g->abin;
     g->Cb[b] = (pr->capacity * (g->abin - g->amac[b])) / g->abin;
     double t = pr->mu * (g->Db[b] - g->Cb[b]);
     g->phi[b] = 2.0 / (1.0 + orc_exp(-t)) - 1.0;
   }
+  free(bcnt); free(area); free(fillp);
 
   /* (cell, macro) overlap pairs in ascending (cell, macro) order */
   int64_t npairs = 0;

@@ -337,6 +337,7 @@ def test_hint_structure_matches_numpy_statement():
     for i in np.where(mov)[0]:
         Db[bys[i] * nb + bxs[i]] += area[i]
     assert np.allclose(m["Db"], Db / (wb * hb), rtol=1e-14, atol=0)
+    assert np.array_equal(m["cell_bin"][mov], (bys * nb + bxs)[mov])
     macros = np.where(nl.cell_kind == 1)[0]
     st = o.static_csr()
     for i in np.where(mov)[0]:
@@ -365,6 +366,35 @@ def test_hint_structure_matches_numpy_statement():
                         want_w.append(-(np.exp(-r) * m["phi"][b] * bw[i]))
         assert hc == want_c
         assert np.allclose(hw, want_w, rtol=4e-16 * 4, atol=0)
+
+
+def test_bin_density_blocked_sum_order():
+    """D_b adds cell areas in blocks of 64 (hint cells first, then the others,
+    each ascending); with areas that are not exactly summable the blocked
+    order is visible, and it must match an independent statement of it."""
+    n = 200
+    cells = [(float(1.0 + (k % 7) * 0.1), float(1.0 + (k % 5) * 0.013), 0, 0.0, 0.0)
+             for k in range(n)] + [(1.0, 1.0, 0, 0.0, 0.0)]
+    # cells 100, 101 and n have no net (baseWeight 0): they come last
+    nets = [[k, k + 1] for k in range(0, n, 2) if k != 100]
+    nl = make(cells, nets, (0.0, 0.0, 10.0, 10.0))
+    o = oracle.Oracle(nl, nbx=1, nby=1, wdtype=oracle.W_FP64)
+    gx, gy = o.init_signal(1)
+    o.build_hints(gx, gy)
+    areas = [float(np.float32(c[0])) * float(np.float32(c[1])) for c in cells]
+    nonhint = [100, 101, n]
+    seq = [areas[k] for k in range(n + 1) if k not in nonhint] + [areas[k] for k in nonhint]
+
+    def bsum(a):
+        if len(a) <= 64:
+            s = 0.0
+            for v in a:
+                s += v
+            return s
+        return bsum([bsum(a[j:j + 64]) for j in range(0, len(a), 64)])
+
+    assert o.merged()["Db"][0] == bsum(seq) / 100.0
+    assert abs(bsum(seq) - math.fsum(seq)) < 1e-12 * math.fsum(seq)
 
 
 def test_nonfinite_coordinates_rejected():
