@@ -168,7 +168,9 @@ pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, voi
  * Synchronizes the graph's last stream. */
 pl_status pl_graph_export_static(const pl_graph *g, int64_t *rp, int32_t *col, double *w,
                                  double *base_w);
-/* augmented CSR in canonical row order: rp[N+1], col[nnz], w[nnz], deg[N]
+/* augmented CSR in canonical order (rows ascending, columns ascending within
+ * a row; the device stores a bin row as the concatenation of its window bins'
+ * cell lists and this copy sorts it): rp[N+1], col[nnz], w[nnz], deg[N]
  * (signed degree D_ii), *lam_up, Db/Cb/phi[bins], cell_bin[num_cells] (-1 for
  * non-movable cells).  Any pointer may be NULL to skip that array. */
 pl_status pl_graph_export(const pl_graph *g, int64_t *rp, int32_t *col, double *w, double *deg,

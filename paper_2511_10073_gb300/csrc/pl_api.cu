@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -348,13 +349,21 @@ static pl_status export_matrix(const pl_graph *g, const SpMat &m, int64_t rows, 
   if (e == cudaSuccess && deg) e = cudaMemcpyAsync(ds.data(), m.dsum.p, N * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "export");
+  // rows in canonical order; a row stored in another order (bin rows are kept
+  // as the concatenation of their window bins' lists) is sorted by column
+  std::vector<uint64_t> perm;
   int64_t o = 0;
   for (int64_t v = 0; v < rows; ++v) {
     uint64_t a, b;
     if (lidx[v] >= 0) { a = lp[lidx[v]]; b = lp[lidx[v] + 1]; }
     else { a = rps[v]; b = rps[v + 1]; }
     if (rp) rp[v] = o;
-    for (uint64_t k = a; k < b; ++k, ++o) {
+    perm.resize(b - a);
+    for (uint64_t k = a; k < b; ++k) perm[k - a] = k;
+    if (!std::is_sorted(perm.begin(), perm.end(),
+                        [&](uint64_t x, uint64_t y) { return cl[x] < cl[y]; }))
+      std::sort(perm.begin(), perm.end(), [&](uint64_t x, uint64_t y) { return cl[x] < cl[y]; });
+    for (uint64_t k : perm) {
       if (col) col[o] = cl[k];
       if (w) {
         if (g->wdtype == PL_W_BF16) {
@@ -366,6 +375,7 @@ static pl_status export_matrix(const pl_graph *g, const SpMat &m, int64_t rows, 
           w[o] = wf[k];
         }
       }
+      ++o;
     }
     if (deg) deg[v] = (double)ds[v].hi + (double)ds[v].lo;
   }

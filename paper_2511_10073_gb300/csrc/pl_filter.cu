@@ -225,24 +225,42 @@ __device__ void long_chunk(const StepArgs &A, int c) {
     last = ticket == nch - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
+    // the row's partials in chunk order: thread k adds chunks k, k + blockDim,
+    // ... then a fixed tree over threads (deterministic)
     __threadfence();
     double tx = 0.0, ty = 0.0;
-    for (int k = 0; k < nch; ++k) {
+    for (int k = threadIdx.x; k < nch; k += blockDim.x) {
       tx += __ldcg(&A.part[2 * (int64_t)(c0 + k)]);
       ty += __ldcg(&A.part[2 * (int64_t)(c0 + k) + 1]);
     }
-    double av, bv;
-    if (MODE == MODE_HR) {
-      av = A.c64l[l];
-      bv = A.lam[1];
-    } else {
-      av = (double)A.a[v];
-      bv = (double)A.b[v];
+    tx = warp_sum(tx);
+    ty = warp_sum(ty);
+    __shared__ double fin[2][32];
+    if (lane == 0) {
+      fin[0][wid] = tx;
+      fin[1][wid] = ty;
     }
-    float2 xv = A.x[v];
-    epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
-    A.tick[l] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tx = 0.0;
+      ty = 0.0;
+      for (int k = 0; k < nw; ++k) {
+        tx += fin[0][k];
+        ty += fin[1][k];
+      }
+      double av, bv;
+      if (MODE == MODE_HR) {
+        av = A.c64l[l];
+        bv = A.lam[1];
+      } else {
+        av = (double)A.a[v];
+        bv = (double)A.b[v];
+      }
+      float2 xv = A.x[v];
+      epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
+      A.tick[l] = 0;
+    }
   }
   __syncthreads();
 }

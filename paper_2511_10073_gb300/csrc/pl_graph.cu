@@ -155,8 +155,15 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
   }
 }
 
+// 1/d correctly rounded for d = 1..15 (the weight of a pair seen by one
+// clique net of d+1 nodes), filled from the host's IEEE division.
+__constant__ double c_recip[16];
+
 __device__ __forceinline__ double lattice_weight(long long val) {
-  if (val > 0) return __ddiv_rn((double)val, (double)kLattice);
+  if (val > 0) {
+    if (kLattice % val == 0 && kLattice / val <= 15) return c_recip[kLattice / val];
+    return __ddiv_rn((double)val, (double)kLattice);
+  }
   long long p = -val;
   return __ddiv_rn((double)p, (double)(p - 1));
 }
@@ -170,10 +177,11 @@ __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
   return __double2float_rn(w);
 }
 
-// Final static CSR: warp per row copies merged (col, value) and converts the
-// exact lattice values into stored weights; lane 0 forms baseWeight (FP64 mean
-// of the exact weights in column order) and the static degree.
-__global__ void k_static_compact(const int64_t *row_off, const int32_t *mcol, const int64_t *mval,
+// Final static CSR: warp per row converts the merged lattice values into FP64
+// weights once (kept in place of the values), writes columns and stored
+// weights, sums the static degree across lanes and, for cells, forms
+// baseWeight (FP64 mean of the exact weights, added in column order).
+__global__ void k_static_compact(const int64_t *row_off, const int32_t *mcol, int64_t *mval,
                                  const int64_t *srp, int64_t Nst, int32_t C, int wdtype,
                                  const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
                                  uint8_t *hflag, double *sdeg) {
@@ -182,25 +190,25 @@ __global__ void k_static_compact(const int64_t *row_off, const int32_t *mcol, co
        v += ((long long)gridDim.x * blockDim.x) >> 5) {
     long long src = row_off[v], dst = srp[v];
     int m = (int)(srp[v + 1] - dst);
+    double *w64 = reinterpret_cast<double *>(mval) + src;
+    double dsum = 0.0;
     for (int k = lane; k < m; k += 32) {
       double w = lattice_weight(mval[src + k]);
+      w64[k] = w;
       scol[dst + k] = mcol[src + k];
       uint16_t hb = 0;
       float f = stored(w, wdtype, &hb);
       if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dst + k] = hb;
       else reinterpret_cast<float *>(sw)[dst + k] = f;
+      dsum += (double)f;
     }
+    dsum = warp_sum(dsum);
     __syncwarp();
     if (lane == 0) {
-      double s = 0.0, d = 0.0;
-      for (int k = 0; k < m; ++k) {
-        double w = lattice_weight(mval[src + k]);
-        s = __dadd_rn(s, w);
-        uint16_t hb;
-        d = __dadd_rn(d, (double)stored(w, wdtype, &hb));
-      }
-      sdeg[v] = d;
+      sdeg[v] = dsum;
       if (v < C) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s = __dadd_rn(s, w64[k]);
         double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
         base_w[v] = bw;
         hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
@@ -265,32 +273,46 @@ __global__ void k_pin_fixed(const int32_t *pin_node, const int32_t *pin_cell, co
   }
 }
 
-// Macro area inside each bin, summed over macros in macro order (FP64).
+// Macro area inside each bin, summed over macros in macro order (FP64).  Warp
+// per bin: lanes test 32 macros at a time (FP32 box reject, then the FP64
+// overlap), lane 0 adds the overlapping ones in macro order.
 __global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const int32_t *macro_cell,
                                  const float *cw, const float *ch, const float *fx,
                                  const float *fy, double xl, double yl, double wb, double hb,
                                  double *amac) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
-    int bx = b % nbx, by = b / nbx;
+  const int lane = threadIdx.x & 31;
+  for (long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; b < NB;
+       b += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int bx = (int)(b % nbx), by = (int)(b / nbx);
     double bxl = xl + (double)bx * wb, bxh = xl + (double)(bx + 1) * wb;
     double byl = yl + (double)by * hb, byh = yl + (double)(by + 1) * hb;
     float fxl = (float)bxl, fxh = (float)bxh, fyl = (float)byl, fyh = (float)byh;
     double a = 0.0;
-    for (int m = 0; m < Mm; ++m) {
-      int c = macro_cell[m];
-      float hwf = cw[c] * 0.5f, hhf = ch[c] * 0.5f;
-      // cheap reject: FP32 boxes separated by more than rounding
-      if (fx[c] - hwf > fxh + 1.f || fx[c] + hwf < fxl - 1.f || fy[c] - hhf > fyh + 1.f ||
-          fy[c] + hhf < fyl - 1.f)
-        continue;
-      double hwm = __dmul_rn((double)cw[c], 0.5), hhm = __dmul_rn((double)ch[c], 0.5);
-      double ox = __dadd_rn(fmin(bxh, __dadd_rn((double)fx[c], hwm)),
-                            -fmax(bxl, __dadd_rn((double)fx[c], -hwm)));
-      double oy = __dadd_rn(fmin(byh, __dadd_rn((double)fy[c], hhm)),
-                            -fmax(byl, __dadd_rn((double)fy[c], -hhm)));
-      if (ox > 0.0 && oy > 0.0) a = __dadd_rn(a, __dmul_rn(ox, oy));
+    for (int m0 = 0; m0 < Mm; m0 += 32) {
+      int m = m0 + lane;
+      double ov = 0.0;
+      if (m < Mm) {
+        int c = macro_cell[m];
+        float hwf = cw[c] * 0.5f, hhf = ch[c] * 0.5f;
+        if (!(fx[c] - hwf > fxh + 1.f || fx[c] + hwf < fxl - 1.f || fy[c] - hhf > fyh + 1.f ||
+              fy[c] + hhf < fyl - 1.f)) {
+          double hwm = __dmul_rn((double)cw[c], 0.5), hhm = __dmul_rn((double)ch[c], 0.5);
+          double ox = __dadd_rn(fmin(bxh, __dadd_rn((double)fx[c], hwm)),
+                                -fmax(bxl, __dadd_rn((double)fx[c], -hwm)));
+          double oy = __dadd_rn(fmin(byh, __dadd_rn((double)fy[c], hhm)),
+                                -fmax(byl, __dadd_rn((double)fy[c], -hhm)));
+          if (ox > 0.0 && oy > 0.0) ov = __dmul_rn(ox, oy);
+        }
+      }
+      unsigned hit = __ballot_sync(0xffffffffu, ov != 0.0);
+      while (hit) {
+        int src = __ffs(hit) - 1;
+        hit &= hit - 1;
+        double t = __shfl_sync(0xffffffffu, ov, src);
+        a = __dadd_rn(a, t);
+      }
     }
-    amac[b] = a;
+    if (lane == 0) amac[b] = a;
   }
 }
 
@@ -530,6 +552,12 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->base_w, (size_t)C * 8 + 16));
   TRY(ensure(g->hflag, (size_t)C + 16));
   TRY(ensure(g->sdeg, (size_t)Nst * 8 + 16));
+  {
+    double rc[16];
+    rc[0] = 0.0;
+    for (int d = 1; d < 16; ++d) rc[d] = 1.0 / (double)d;
+    TRY(cudaMemcpyToSymbolAsync(c_recip, rc, sizeof(rc), 0, cudaMemcpyHostToDevice, s));
+  }
   k_static_compact<<<grid_for(Nst * 32, 256), 256, 0, s>>>(
       row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
       P<int32_t>(g->scol), g->sw.p, P<double>(g->base_w), P<uint8_t>(g->hflag), P<double>(g->sdeg));
@@ -563,7 +591,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY(ensure(g->amac, (size_t)g->NB * 8 + 16));
   TRY(ensure(g->Cb, (size_t)g->NB * 8 + 16));
-  k_bin_macro_area<<<grid_for(g->NB, 128), 128, 0, s>>>(
+  k_bin_macro_area<<<grid_for((long long)g->NB * 32, 256), 256, 0, s>>>(
       g->NB, g->nbx, g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch),
       P<float>(g->cfx), P<float>(g->cfy), g->xl, g->yl, g->wb, g->hb, P<double>(g->amac));
   note_launch();

@@ -148,18 +148,15 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
   }
 }
 
-__global__ void k_hint_scatter(HintGeo G, const float2 *xy, const uint8_t *ckind,
-                               const uint8_t *hflag, const float *cw, const float *ch,
-                               const float *fx, const float *fy, const int32_t *macro_cell,
-                               const int64_t *gptr, const uint32_t *glist,
-                               const int32_t *cell_bin, int32_t *bcur, uint32_t *blist,
-                               int32_t *mcur, uint32_t *mlist) {
+// Cells overlapping each macro (the macro virtual rows), unordered here and
+// sorted by cell id afterwards.
+__global__ void k_macro_scatter(HintGeo G, const float2 *xy, const uint8_t *ckind,
+                                const uint8_t *hflag, const float *cw, const float *ch,
+                                const float *fx, const float *fy, const int32_t *macro_cell,
+                                const int64_t *gptr, const uint32_t *glist, int32_t *mcur,
+                                uint32_t *mlist) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
-    if (ckind[i] != 0) continue;
-    int b = cell_bin[i];
-    bool hint = hflag[i] != 0;
-    blist[atomicAdd(&bcur[2 * b + (hint ? 0 : 1)], 1)] = (uint32_t)i;
-    if (!hint) continue;
+    if (ckind[i] != 0 || !hflag[i]) continue;
     float2 p = xy[i];
     if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
     int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
@@ -173,40 +170,143 @@ __global__ void k_hint_scatter(HintGeo G, const float2 *xy, const uint8_t *ckind
   }
 }
 
-// ------------------------------------------------ H5: bin density and phi
-// D_b: FP64 sum of w*h over the movable cells of b in ascending cell id (the
-// two sorted buckets of b, hint and non-hint cells, merged on the fly).
-__global__ void k_bin_phi(HintGeo G, const int64_t *boff, const uint32_t *blist, const float *cw,
-                          const float *ch, const double *amac, double abin, double cap, double mu,
-                          double *Db, double *Cb, double *phi, float *phif, int64_t *hub_len) {
-  const int NB = G.nbx * G.nby;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
-    long long a0 = boff[2 * b], a1 = boff[2 * b + 1], c1 = boff[2 * b + 2];
-    long long ia = a0, ic = a1;
-    double s = 0.0;
-    while (ia < a1 || ic < c1) {
-      uint32_t i;
-      if (ic >= c1 || (ia < a1 && blist[ia] < blist[ic])) i = blist[ia++];
-      else i = blist[ic++];
-      s = __dadd_rn(s, __dmul_rn((double)cw[i], (double)ch[i]));
-    }
-    double d = __ddiv_rn(s, abin);
-    double c = __ddiv_rn(__dmul_rn(cap, __dadd_rn(abin, -amac[b])), abin);
-    double t = __dmul_rn(mu, __dadd_rn(d, -c));
-    double ph = __dadd_rn(__ddiv_rn(2.0, __dadd_rn(1.0, exp_cw(-t))), -1.0);
-    Db[b] = d;
-    Cb[b] = c;
-    phi[b] = ph;
-    phif[b] = __double2float_rn(ph);
-    // hub row length: hint cells of the window bins
-    int bx = b % G.nbx, by = b / G.nbx;
-    long long hl = 0;
-    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
-      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
-        int bb = yy * G.nbx + xx;
-        hl += boff[2 * bb + 1] - boff[2 * bb];
+// Bin buckets: key 2*bin + (baseWeight == 0).  A stable counting sort over
+// tiles of kBinTile consecutive cells writes every bucket in ascending cell id
+// directly (no sort).  Counts per (bucket, tile), bucket-major.
+constexpr int kBinTile = 4096;
+constexpr int kMaxSmemBuckets = 12288;
+
+__device__ __forceinline__ int bucket_of(const uint8_t *hflag, const int32_t *cell_bin, int i) {
+  return 2 * cell_bin[i] + (hflag[i] ? 0 : 1);
+}
+
+__global__ void __launch_bounds__(256) k_bin_tile_count(int32_t C, int nbk, int ntile,
+                                                        const uint8_t *ckind,
+                                                        const uint8_t *hflag,
+                                                        const int32_t *cell_bin, int32_t *cnt) {
+  extern __shared__ int32_t sc[];
+  for (int k = threadIdx.x; k < nbk; k += blockDim.x) sc[k] = 0;
+  __syncthreads();
+  const int t = blockIdx.x, i0 = t * kBinTile, i1 = min(C, i0 + kBinTile);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    if (ckind[i] == 0) atomicAdd(&sc[bucket_of(hflag, cell_bin, i)], 1);
+  __syncthreads();
+  for (int k = threadIdx.x; k < nbk; k += blockDim.x) cnt[(long long)k * ntile + t] = sc[k];
+}
+
+// Rounds of blockDim cells; inside a round the warps take turns (so equal
+// buckets keep cell order), lanes of a warp rank themselves with match_any.
+__global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, int ntile,
+                                                          const uint8_t *ckind,
+                                                          const uint8_t *hflag,
+                                                          const int32_t *cell_bin,
+                                                          const int64_t *off, uint32_t *blist) {
+  extern __shared__ int32_t run[];
+  for (int k = threadIdx.x; k < nbk; k += blockDim.x) run[k] = 0;
+  __syncthreads();
+  const int t = blockIdx.x, i0 = t * kBinTile, i1 = min(C, i0 + kBinTile);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = i0; base < i1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool mv = i < i1 && ckind[i] == 0;
+    const int key = mv ? bucket_of(hflag, cell_bin, i) : -1 - lane;
+    for (int w = 0; w < nw; ++w) {
+      if (wid == w) {
+        unsigned grp = __match_any_sync(0xffffffffu, key);
+        int leader = __ffs(grp) - 1;
+        int before = 0;
+        if (mv && lane == leader) {
+          before = run[key];
+          run[key] = before + __popc(grp);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        if (mv) blist[off[(long long)key * ntile + t] + before + __popc(grp & lt)] = (uint32_t)i;
       }
-    hub_len[b] = hl;
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_bucket_starts(int nbk, int ntile, const int64_t *off, int64_t *boff) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nbk; k += gridDim.x * blockDim.x)
+    boff[k] = off[(long long)k * ntile];
+}
+
+// Fallback for bin grids too large for the shared-memory counters: atomic
+// scatter, then the buckets are sorted.
+__global__ void k_bin_scatter_atomic(int32_t C, const uint8_t *ckind, const uint8_t *hflag,
+                                     const int32_t *cell_bin, int32_t *bcur, uint32_t *blist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x)
+    if (ckind[i] == 0) blist[atomicAdd(&bcur[bucket_of(hflag, cell_bin, i)], 1)] = (uint32_t)i;
+}
+
+// ------------------------------------------------ H5: bin density and phi
+// D_b: FP64 sum of the cell areas w*h of bin b's sequence (its hint bucket
+// then its other bucket, each ascending), in the blocked order: blocks of 64
+// added left to right, block sums summed the same way, recursively.  A CTA per
+// bin forms every level in parallel; level l of bin b lives at offset
+// floor(start_{l-1}/64) + b of that level's region, so bins never overlap.
+constexpr int kMaxLevels = 8;
+struct LevelBufs {
+  double *base[kMaxLevels];
+};
+
+__device__ __forceinline__ double cell_area(const float *cw, const float *ch, uint32_t i) {
+  return __dmul_rn((double)cw[i], (double)ch[i]);
+}
+
+__global__ void __launch_bounds__(256) k_bin_density(HintGeo G, const int64_t *boff,
+                                                     const uint32_t *blist, const float *cw,
+                                                     const float *ch, const double *amac,
+                                                     double abin, double cap, double mu,
+                                                     LevelBufs lv, double *Db, double *Cb,
+                                                     double *phi, float *phif, int64_t *hub_len) {
+  const int NB = G.nbx * G.nby;
+  for (int b = blockIdx.x; b < NB; b += gridDim.x) {
+    const int64_t s0 = boff[2 * b];
+    int64_t st = s0, len = boff[2 * b + 2] - s0;
+    const double *prev = nullptr;
+    int level = 0;
+    while (len > 64) {
+      const int64_t nblk = (len + 63) / 64, ost = st / 64 + b;
+      double *out = lv.base[level];
+      for (int64_t j = threadIdx.x; j < nblk; j += blockDim.x) {
+        double acc = 0.0;
+        const int64_t k1 = min(len, 64 * j + 64);
+        for (int64_t k = 64 * j; k < k1; ++k)
+          acc = __dadd_rn(acc, level == 0 ? cell_area(cw, ch, blist[s0 + k]) : prev[st + k]);
+        out[ost + j] = acc;
+      }
+      __syncthreads();
+      prev = out;
+      st = ost;
+      len = nblk;
+      ++level;
+    }
+    if (threadIdx.x == 0) {
+      double acc = 0.0;
+      for (int64_t k = 0; k < len; ++k)
+        acc = __dadd_rn(acc, level == 0 ? cell_area(cw, ch, blist[s0 + k]) : prev[st + k]);
+      double d = __ddiv_rn(acc, abin);
+      double c = __ddiv_rn(__dmul_rn(cap, __dadd_rn(abin, -amac[b])), abin);
+      double t = __dmul_rn(mu, __dadd_rn(d, -c));
+      double ph = __dadd_rn(__ddiv_rn(2.0, __dadd_rn(1.0, exp_cw(-t))), -1.0);
+      Db[b] = d;
+      Cb[b] = c;
+      phi[b] = ph;
+      phif[b] = __double2float_rn(ph);
+      // hub row length: hint cells of the window bins
+      int bx = b % G.nbx, by = b / G.nbx;
+      long long hl = 0;
+      for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
+        for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
+          int bb = yy * G.nbx + xx;
+          hl += boff[2 * bb + 1] - boff[2 * bb];
+        }
+      hub_len[b] = hl;
+    }
+    __syncthreads();
   }
 }
 
@@ -277,17 +377,18 @@ __global__ void k_u64_to_u32(const uint64_t *a, uint32_t *b, long long n) {
     b[i] = (uint32_t)a[i];
 }
 
-// First row owned by each tile: rows whose first short entry lies in
-// [t * kTile, (t+1) * kTile); the last tile owns every row to the end.
+// First row owned by each tile.  Row r has key rp_s[r] + r (entries and rows
+// before it); tile t owns the rows with keys in [t*kTile, (t+1)*kTile), so a
+// tile holds at most kTile rows and fewer than kTile + kLong entries.
 __global__ void k_tiles(const uint32_t *rp_s, int64_t N, int32_t ntiles, int32_t *tile_row) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
     if (t == 0) { tile_row[0] = 0; continue; }
     if (t == ntiles) { tile_row[t] = (int32_t)N; continue; }
     uint64_t target = (uint64_t)t * kTile;
-    long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] >= target
+    long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] + r >= target
     while (lo < hi) {
       long long mid = (lo + hi) >> 1;
-      if ((uint64_t)rp_s[mid] < target) lo = mid + 1; else hi = mid;
+      if ((uint64_t)rp_s[mid] + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
     }
     tile_row[t] = (int32_t)lo;
   }
@@ -392,63 +493,73 @@ __global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int
   }
 }
 
-// Virtual rows: CTA per row.  Macro rows copy their sorted cell list; bin rows
-// gather the window bins' hint lists and merge the sorted runs.  Weights are
-// read back from the cells' own entries, so the matrix is exactly symmetric.
-__global__ void __launch_bounds__(256) k_assemble_hubs(
-    HintGeo G, int wdtype, const int32_t *longidx, const uint64_t *lptr, uint64_t nnz_s,
-    const int64_t *moff, const uint32_t *mlist, const int64_t *boff, const uint32_t *blist,
-    const int32_t *cell_bin, const int32_t *n_ovl, const uint64_t *mac_base,
-    const uint64_t *bin_base, int32_t *col, void *w, int32_t *hubtmp, dfl *dsum, dfl *psum) {
-  __shared__ long long run_off[1032];
+// Virtual rows, in the hub chunks of the sparse-product layout (one CTA per
+// chunk of kChunk entries).  A macro row lists the cells overlapping it (sorted
+// by id); a bin row is the concatenation of its window bins' hint buckets in
+// row-major window order, each ascending (the canonical column order is
+// restored when the graph is exported).  Weights are copied from the cells'
+// own entries, so the matrix is exactly symmetric.  Degree partials per chunk.
+__global__ void __launch_bounds__(256) k_hub_chunks(
+    HintGeo G, int wdtype, int32_t nchunks, const int32_t *chunk_lr, const int32_t *lrow,
+    const uint64_t *lptr, const int32_t *lchunk, const int64_t *moff, const uint32_t *mlist,
+    const int64_t *boff, const uint32_t *blist, const int32_t *cell_bin, const int32_t *n_ovl,
+    const uint64_t *mac_base, const uint64_t *bin_base, int32_t *col, void *w, dfl *cpart) {
+  __shared__ long long roff[1025];
+  __shared__ int rbin[1024];
+  __shared__ int nrun;
   __shared__ dfl red[2][8];
-  const int64_t nvirt = (int64_t)G.Mm + (int64_t)G.nbx * G.nby;
-  for (long long r = blockIdx.x; r < nvirt; r += gridDim.x) {
-    const int64_t v = G.mv0 + r;
-    const int li = longidx[v];
-    const uint64_t base = lptr[li];
-    const long long len = (long long)(lptr[li + 1] - base);
-    if (r < G.Mm) {
-      const int m = (int)r;
-      for (long long k = threadIdx.x; k < len; k += blockDim.x) col[base + k] = (int32_t)mlist[moff[m] + k];
-    } else {
-      const int b = (int)(r - G.Mm), bx = b % G.nbx, by = b / G.nbx;
-      const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
-      const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
-      int nr = 0;
-      long long o = 0;
-      for (int yy = y0; yy <= y1; ++yy)
-        for (int xx = x0; xx <= x1; ++xx) {
-          int bb = yy * G.nbx + xx;
-          long long a = boff[2 * bb], n = boff[2 * bb + 1] - a;
-          if (threadIdx.x == 0) run_off[nr] = o;
-          for (long long k = threadIdx.x; k < n; k += blockDim.x) col[base + o + k] = (int32_t)blist[a + k];
-          o += n;
-          ++nr;
-        }
-      if (threadIdx.x == 0) run_off[nr] = o;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int l = chunk_lr[c];
+    const int64_t v = lrow[l];
+    if (v < G.mv0) continue;  // long rows of real nodes are assembled elsewhere
+    const uint64_t base = lptr[l];
+    const long long len = (long long)(lptr[l + 1] - base);
+    const long long q0 = (long long)(c - lchunk[l]) * kChunk;
+    const long long q1 = min(len, q0 + (long long)kChunk);
+    const bool is_bin = v >= G.bn0;
+    const int b = is_bin ? (int)(v - G.bn0) : 0, m = is_bin ? 0 : (int)(v - G.mv0);
+    const int bxb = b % G.nbx, byb = b / G.nbx;
+    if (is_bin) {
+      if (threadIdx.x == 0) {
+        int nr = 0;
+        long long o = 0;
+        for (int yy = max(0, byb - G.hy); yy <= min(G.nby - 1, byb + G.hy); ++yy)
+          for (int xx = max(0, bxb - G.hx); xx <= min(G.nbx - 1, bxb + G.hx); ++xx) {
+            int bb = yy * G.nbx + xx;
+            roff[nr] = o;
+            rbin[nr] = bb;
+            o += boff[2 * bb + 1] - boff[2 * bb];
+            ++nr;
+          }
+        roff[nr] = o;
+        nrun = nr;
+      }
       __syncthreads();
-      cta_merge_runs<int32_t>(col + base, hubtmp + (base - nnz_s), run_off, nr);
     }
-    __syncthreads();
     dfl D{0.f, 0.f}, Pp{0.f, 0.f};
-    for (long long k = threadIdx.x; k < len; k += blockDim.x) {
-      int i = col[base + k];
+    for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      int i;
       uint64_t src;
-      if (r < G.Mm) {
-        uint64_t mb = mac_base[i];
-        int n = n_ovl[i];
+      if (!is_bin) {
+        i = (int)mlist[moff[m] + q];
+        const uint64_t mb = mac_base[i];
+        const int n = n_ovl[i];
         int j = 0;
         while (j < n - 1 && col[mb + j] != (int32_t)v) ++j;
         src = mb + j;
       } else {
-        const int b = (int)(r - G.Mm), bxb = b % G.nbx, byb = b / G.nbx;
-        int ci = cell_bin[i], bxi = ci % G.nbx, byi = ci / G.nbx;
-        int x0 = max(0, bxi - G.hx), x1 = min(G.nbx - 1, bxi + G.hx);
-        int y0 = max(0, byi - G.hy);
+        int lo = 0, hi = nrun - 1;  // run r with roff[r] <= q < roff[r+1]
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (roff[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        i = (int)blist[boff[2 * rbin[lo]] + (q - roff[lo])];
+        const int ci = cell_bin[i], bxi = ci % G.nbx, byi = ci / G.nbx;
+        const int x0 = max(0, bxi - G.hx), x1 = min(G.nbx - 1, bxi + G.hx), y0 = max(0, byi - G.hy);
         src = bin_base[i] + (uint64_t)((byb - y0) * (x1 - x0 + 1) + (bxb - x0));
       }
-      copy_w(w, w, wdtype, base + k, src);
+      col[base + q] = i;
+      copy_w(w, w, wdtype, base + q, src);
       acc_deg(D, Pp, load_w(w, wdtype, src));
     }
     D = warp_sum_df(D);
@@ -460,15 +571,37 @@ __global__ void __launch_bounds__(256) k_assemble_hubs(
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      dfl a = red[0][0], c = red[1][0];
+      dfl a = red[0][0], e = red[1][0];
       for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
         df_add_df(a, red[0][k]);
-        df_add_df(c, red[1][k]);
+        df_add_df(e, red[1][k]);
       }
-      dsum[v] = df_norm(a);
-      psum[v] = df_norm(c);
+      cpart[2 * (long long)c] = df_norm(a);
+      cpart[2 * (long long)c + 1] = df_norm(e);
     }
     __syncthreads();
+  }
+}
+
+// Degrees of virtual rows from their chunk partials (warp per row).
+__global__ void k_hub_finalize(HintGeo G, int32_t nlong, const int32_t *lrow,
+                               const int32_t *lchunk, const dfl *cpart, dfl *dsum, dfl *psum) {
+  const int lane = threadIdx.x & 31;
+  for (long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; l < nlong;
+       l += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = lrow[l];
+    if (v < G.mv0) continue;
+    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
+    for (int c = lchunk[l] + lane; c < lchunk[l + 1]; c += 32) {
+      df_add_df(D, cpart[2 * (long long)c]);
+      df_add_df(Pp, cpart[2 * (long long)c + 1]);
+    }
+    D = warp_sum_df(D);
+    Pp = warp_sum_df(Pp);
+    if (lane == 0) {
+      dsum[v] = D;
+      psum[v] = Pp;
+    }
   }
 }
 
@@ -620,7 +753,7 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
     k_chunk_owner<<<grid_for(nl, 256), 256, 0, s>>>(nl, P<int32_t>(m.lchunk), P<int32_t>(m.chunk_lr));
     note_launch();
   }
-  m.ntiles = (int32_t)((m.nnz_s + kTile - 1) / kTile);
+  m.ntiles = (int32_t)((m.nnz_s + (uint64_t)N + kTile - 1) / kTile);
   if (m.ntiles < 1) m.ntiles = 1;
   TRY(ensure(m.tile_row, (size_t)(m.ntiles + 1) * 4));
   k_tiles<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(P<uint32_t>(m.rp_s), N, m.ntiles,
@@ -702,30 +835,54 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   int64_t nbl, nml;
   TRY(d2h(&nbl, P<int64_t>(g->boff) + 2 * NB, 1, s));
   TRY(d2h(&nml, P<int64_t>(g->moff) + Mm, 1, s));
-  // H3: scatter into buckets
-  TRY(ensure(g->bcur, (size_t)(2 * NB + 1) * 4));
-  TRY(ensure(g->mcur, (size_t)(Mm + 1) * 4));
+  // H3-H4: bin buckets (ascending cell id) and macro lists (sorted)
+  const int nbk = 2 * NB;
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
-  k_u64_to_u32<<<grid_for(2 * NB, 256), 256, 0, s>>>(P<uint64_t>(g->boff), P<uint32_t>(g->bcur), 2 * NB);
-  note_launch();
+  if (nbk <= kMaxSmemBuckets) {
+    const int ntile = (int)((C + kBinTile - 1) / kBinTile) > 0 ? (int)((C + kBinTile - 1) / kBinTile) : 1;
+    const long long ncm = (long long)nbk * ntile;
+    TRY(ensure(g->tmp[5], (size_t)ncm * 4 + 256));
+    TRY(ensure(g->tmp[6], (size_t)(ncm + 1) * 8 + 256));
+    TRY(ensure(g->tmp[7], scan_tmp_bytes(ncm + 1) + 4096));
+    stmp = g->tmp[7].p;
+    int32_t *cm = P<int32_t>(g->tmp[5]);
+    int64_t *cmo = P<int64_t>(g->tmp[6]);
+    k_bin_tile_count<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
+                                                        P<uint8_t>(g->hflag),
+                                                        P<int32_t>(g->cell_bin), cm);
+    note_launch();
+    TRY((exclusive_scan<int32_t, int64_t>(cm, cmo, ncm, stmp, s)));
+    k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
+                                                          P<uint8_t>(g->hflag),
+                                                          P<int32_t>(g->cell_bin), cmo,
+                                                          P<uint32_t>(g->blist));
+    note_launch();
+  } else {
+    TRY(ensure(g->bcur, (size_t)(nbk + 1) * 4));
+    k_u64_to_u32<<<grid_for(nbk, 256), 256, 0, s>>>(P<uint64_t>(g->boff), P<uint32_t>(g->bcur), nbk);
+    note_launch();
+    k_bin_scatter_atomic<<<grid_for(C, 256), 256, 0, s>>>(C, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag),
+                                                          P<int32_t>(g->cell_bin),
+                                                          P<int32_t>(g->bcur), P<uint32_t>(g->blist));
+    note_launch();
+    TRY(ensure(g->tmp[3], segsort_tmp_bytes(nbk, nbl, 4)));
+    TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->blist), P<int64_t>(g->boff), nbk,
+                                             nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
+  }
   if (Mm) {
+    TRY(ensure(g->mcur, (size_t)(Mm + 1) * 4));
     k_u64_to_u32<<<grid_for(Mm, 256), 256, 0, s>>>(P<uint64_t>(g->moff), P<uint32_t>(g->mcur), Mm);
     note_launch();
-  }
-  k_hint_scatter<<<grid_for(C, 256), 256, 0, s>>>(
-      G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
-      P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
-      P<uint32_t>(g->glist), P<int32_t>(g->cell_bin), P<int32_t>(g->bcur), P<uint32_t>(g->blist),
-      P<int32_t>(g->mcur), P<uint32_t>(g->mlist));
-  note_launch();
-  // H4: sort every bucket by cell id
-  TRY(ensure(g->tmp[3], segsort_tmp_bytes(2 * NB + Mm, nbl + nml, 4)));
-  TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->blist), P<int64_t>(g->boff), 2 * NB,
-                                           nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
-  if (Mm)
+    k_macro_scatter<<<grid_for(C, 256), 256, 0, s>>>(
+        G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
+        P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
+        P<uint32_t>(g->glist), P<int32_t>(g->mcur), P<uint32_t>(g->mlist));
+    note_launch();
+    TRY(ensure(g->tmp[3], segsort_tmp_bytes(Mm, nml, 4)));
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->mlist), P<int64_t>(g->moff), Mm, nml,
                                              nullptr, nullptr, nullptr, g->tmp[3].p, s)));
+  }
   // H5: densities, phi, hub lengths
   TRY(ensure(g->Db, (size_t)NB * 8 + 16));
   TRY(ensure(g->phi, (size_t)NB * 8 + 16));
@@ -733,10 +890,26 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->tmp[4], phib + (size_t)NB * 8 + 256));
   float *phif = P<float>(g->tmp[4]);
   int64_t *hub_len = reinterpret_cast<int64_t *>(P<char>(g->tmp[4]) + phib);
-  k_bin_phi<<<grid_for(NB, 64), 64, 0, s>>>(G, P<int64_t>(g->boff), P<uint32_t>(g->blist),
-                                            P<float>(g->cw), P<float>(g->ch), P<double>(g->amac),
-                                            g->abin, p->capacity, p->mu, P<double>(g->Db),
-                                            P<double>(g->Cb), P<double>(g->phi), phif, hub_len);
+  LevelBufs lv;
+  {
+    size_t sizes[kMaxLevels], tot = 0;
+    size_t prev = (size_t)nbl;
+    for (int k = 0; k < kMaxLevels; ++k) {
+      sizes[k] = prev / 64 + (size_t)NB + 2;
+      tot += sizes[k];
+      prev = sizes[k];
+    }
+    TRY(ensure(g->hubtmp, tot * 8 + 256));
+    double *q = P<double>(g->hubtmp);
+    for (int k = 0; k < kMaxLevels; ++k) {
+      lv.base[k] = q;
+      q += sizes[k];
+    }
+  }
+  k_bin_density<<<NB < 152 * 16 ? NB : 152 * 16, 256, 0, s>>>(
+      G, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch),
+      P<double>(g->amac), g->abin, p->capacity, p->mu, lv, P<double>(g->Db), P<double>(g->Cb),
+      P<double>(g->phi), phif, hub_len);
   note_launch();
   // H6-H7: row lengths and layout
   TRY(ensure(g->slen, (size_t)N * 4 + 16));
@@ -763,17 +936,23 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
   note_launch();
   // H10: virtual rows
-  TRY(ensure(g->hubtmp, (size_t)m.nnz_l * 4 + 64));
-  if (g->hx * 2 + 1 > 32 || g->hy * 2 + 1 > 32) {
+  if (g->hx * 2 + 1 > 31 || g->hy * 2 + 1 > 31 || (2 * g->hx + 1) * (2 * g->hy + 1) > 1024) {
     set_error("detection window larger than 31 x 31 bins");
     return PL_ERR_UNSUPPORTED;
   }
-  k_assemble_hubs<<<152 * 4, 256, 0, s>>>(
-      G, g->wdtype, P<int32_t>(m.longidx), P<uint64_t>(m.lptr), m.nnz_s, P<int64_t>(g->moff),
-      P<uint32_t>(g->mlist), P<int64_t>(g->boff), P<uint32_t>(g->blist), P<int32_t>(g->cell_bin),
-      P<int32_t>(g->n_ovl), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), P<int32_t>(m.col),
-      m.w.p, P<int32_t>(g->hubtmp), P<dfl>(m.dsum), P<dfl>(m.psum));
-  note_launch();
+  TRY(ensure(g->tmp[5], (size_t)(m.nchunks + 1) * 2 * sizeof(dfl) + 256));
+  dfl *cpart = P<dfl>(g->tmp[5]);
+  if (m.nchunks) {
+    k_hub_chunks<<<m.nchunks < 152 * 32 ? m.nchunks : 152 * 32, 256, 0, s>>>(
+        G, g->wdtype, m.nchunks, P<int32_t>(m.chunk_lr), P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
+        P<int32_t>(m.lchunk), P<int64_t>(g->moff), P<uint32_t>(g->mlist), P<int64_t>(g->boff),
+        P<uint32_t>(g->blist), P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
+        P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), P<int32_t>(m.col), m.w.p, cpart);
+    note_launch();
+    k_hub_finalize<<<grid_for((long long)m.nlong * 32, 256), 256, 0, s>>>(
+        G, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<dfl>(m.dsum), P<dfl>(m.psum));
+    note_launch();
+  }
   // H11: lambda_up and coefficients
   unsigned long long *key = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 2);
   TRY(cudaMemsetAsync(key, 0, 8, s));

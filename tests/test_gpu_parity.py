@@ -292,3 +292,40 @@ def test_rebuild_in_place_other_netlist():
     ge = g.export_static()
     oe = oracle.Oracle(b, nbx=8, nby=8).static_csr()
     assert np.array_equal(ge["col"], oe["col"]) and np.array_equal(ge["w"], oe["w_store"])
+
+
+# ------------------------------------------- full size, as the benchmark runs it
+LARGE = dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+             tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))
+
+
+def test_large_workload_steps_crossfed():
+    """The 2.2M-cell workload in the benchmark's configuration: static graph
+    and area-hint graph bit-exact (BF16 weights), one refinement round and
+    HPWL against the oracle on the same FP32 input."""
+    nl = netgen.make_netlist("large", 1)
+    s = Side(nl, **LARGE)
+    ge = s.g.export_static()
+    oe = s.o.static_csr()
+    assert np.array_equal(ge["rp"], oe["rp"]) and np.array_equal(ge["col"], oe["col"])
+    assert np.array_equal(ge["w"], oe["w_store"]) and np.array_equal(ge["base_w"], oe["base_w"])
+    del ge, oe
+    x0, xy = s.gpu_signal(1)
+    a0 = to_np(x0)
+    gx, gy = s.o.gift(a0[:, 0], a0[:, 1])
+    a = to_np(xy)
+    assert max(np.abs(a[:, 0] - gx).max(), np.abs(a[:, 1] - gy).max()) <= 1e-4 * s.die
+    pl().pl_build_hints(s.g, s.prm, xy)
+    s.o.build_hints(a[:, 0], a[:, 1])
+    _compare_hints(s, s.g.export(), s.o.merged())
+    out = torch.empty_like(xy)
+    pl().pl_filter_apply(s.g, s.prm, xy, out)
+    ox, oy = s.o.filter(a[:, 0], a[:, 1])
+    b = to_np(out)
+    err = max(np.abs(b[:, 0] - ox).max(), np.abs(b[:, 1] - oy).max())
+    assert err <= 1e-4 * s.die, err
+    cells = torch.tensor(b[:nl.num_cells].astype(np.float32).reshape(-1), device="cuda")
+    h = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pl().pl_hpwl(s.dnl, cells, h, pl().hpwl_workspace(nl.num_nets))
+    ref = oracle.hpwl(nl, b[:nl.num_cells, 0], b[:nl.num_cells, 1])
+    assert h.item() == pytest.approx(ref, rel=1e-5)
