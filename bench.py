@@ -31,12 +31,16 @@ WORKLOADS = {
     # name: (netgen config, params)
     "large": ("large", dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
                             tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))),
+    "half": ("half", dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+                          tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))),
     "medium": ("medium", dict(nbx=32, nby=32, wdtype=1)),
     "tiny": ("tiny", dict(nbx=16, nby=16, wdtype=1)),
 }
 DESCR = {
     "large": "2.2M std cells, 8k macros, 2.25M nets (degree cap 10k), 8k I/O; BF16 weights, "
              "FP32 coordinates; taps {2,4,8}; 32x32 bins; T_hint 3",
+    "half": "1.1M std cells, 4k macros, 1.125M nets (cap 5k), 4k I/O; large's parameters "
+            "(profiling case: matrix larger than L2, a few GB on the device)",
     "medium": "210k std cells, 550 macros, 220k nets (cap 2k), 1k I/O; FP32 weights; order 8",
     "tiny": "2k std cells, 20 macros, 2.2k nets; FP32; order 8",
 }

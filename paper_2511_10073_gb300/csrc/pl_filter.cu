@@ -131,10 +131,20 @@ __device__ __forceinline__ void load4w(const void *w, uint64_t g, float *o) {
   }
 }
 
+// Rows of up to kThreadRow entries are summed by one thread each (all rows of
+// the tile in parallel, so their epilogue loads overlap); longer rows of the
+// tile are summed by a warp each.
+constexpr int kThreadRow = 32;
+
 template <int WT, int MODE>
 __device__ void short_tile(const StepArgs &A, int t, float2 *sp) {
-  const int r0 = A.tile_row[t], r1 = A.tile_row[t + 1];
+  __shared__ uint32_t srow[kTile + 1];
+  __shared__ int wide[(kTile + kLong) / (kThreadRow + 1) + 1];
+  __shared__ int nwide;
+  const int r0 = A.tile_row[t], r1 = A.tile_row[t + 1], nrows = r1 - r0;
   const uint64_t e0 = A.rp_s[r0], e1 = A.rp_s[r1];
+  if (threadIdx.x == 0) nwide = 0;
+  for (int k = threadIdx.x; k <= nrows; k += blockDim.x) srow[k] = A.rp_s[r0 + k] - (uint32_t)e0;
   // phase 1: products of the tile's entries into shared memory
   const uint64_t g0 = e0 >> 2, g1 = (e1 + 3) >> 2;
   for (uint64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
@@ -152,20 +162,42 @@ __device__ void short_tile(const StepArgs &A, int t, float2 *sp) {
     }
   }
   __syncthreads();
-  // phase 2: a warp per row
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float bconst = MODE == MODE_HR ? (float)A.lam[1] : 0.f;
-  for (int r = r0 + wid; r < r1; r += nw) {
-    const uint32_t a = A.rp_s[r] - (uint32_t)e0, b = A.rp_s[r + 1] - (uint32_t)e0;
+  // phase 2a: thread per short row
+  for (int j = threadIdx.x; j < nrows; j += blockDim.x) {
+    const uint32_t a = srow[j], b = srow[j + 1];
+    if (b - a > (uint32_t)kThreadRow) {
+      wide[atomicAdd(&nwide, 1)] = j;
+      continue;
+    }
+    const int r = r0 + j;
+    if (A.longidx[r] >= 0) continue;
     float sx = 0.f, sy = 0.f;
-    for (uint32_t k = a + lane; k < b; k += 32) {
+    for (uint32_t k = a; k < b; ++k) {
       float2 q = sp[k];
       sx += q.x;
       sy += q.y;
     }
+    float av = A.a[r];
+    float bv = MODE == MODE_HR ? bconst : A.b[r];
+    float2 xv = A.x[r];
+    epilogue<float>(A, r, av * xv.x + bv * sx, av * xv.y + bv * sy);
+  }
+  __syncthreads();
+  // phase 2b: warp per wider row
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = wid; q < nwide; q += nw) {
+    const int j = wide[q], r = r0 + j;
+    const uint32_t a = srow[j], b = srow[j + 1];
+    float sx = 0.f, sy = 0.f;
+    for (uint32_t k = a + lane; k < b; k += 32) {
+      float2 v = sp[k];
+      sx += v.x;
+      sy += v.y;
+    }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
-    if (lane == 0 && A.longidx[r] < 0) {
+    if (lane == 0) {
       float av = A.a[r];
       float bv = MODE == MODE_HR ? bconst : A.b[r];
       float2 xv = A.x[r];

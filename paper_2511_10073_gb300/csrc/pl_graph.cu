@@ -177,42 +177,58 @@ __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
   return __double2float_rn(w);
 }
 
-// Final static CSR: warp per row converts the merged lattice values into FP64
-// weights once (kept in place of the values), writes columns and stored
-// weights, sums the static degree across lanes and, for cells, forms
-// baseWeight (FP64 mean of the exact weights, added in column order).
-__global__ void k_static_compact(const int64_t *row_off, const int32_t *mcol, int64_t *mval,
-                                 const int64_t *srp, int64_t Nst, int32_t C, int wdtype,
-                                 const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
-                                 uint8_t *hflag, double *sdeg) {
+// Final static CSR.  A warp takes 32 consecutive rows: for each row the warp
+// converts the merged lattice values into FP64 weights once (kept in place of
+// the values) and writes columns and stored weights; then each lane forms its
+// own row's static degree and, for cells, baseWeight (FP64 mean of the exact
+// weights, added in column order).
+__global__ void __launch_bounds__(256) k_static_compact(
+    const int64_t *row_off, const int32_t *mcol, int64_t *mval, const int64_t *srp, int64_t Nst,
+    int32_t C, int wdtype, const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
+    uint8_t *hflag, double *sdeg) {
   const int lane = threadIdx.x & 31;
-  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < Nst;
-       v += ((long long)gridDim.x * blockDim.x) >> 5) {
-    long long src = row_off[v], dst = srp[v];
-    int m = (int)(srp[v + 1] - dst);
-    double *w64 = reinterpret_cast<double *>(mval) + src;
-    double dsum = 0.0;
-    for (int k = lane; k < m; k += 32) {
-      double w = lattice_weight(mval[src + k]);
-      w64[k] = w;
-      scol[dst + k] = mcol[src + k];
-      uint16_t hb = 0;
-      float f = stored(w, wdtype, &hb);
-      if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dst + k] = hb;
-      else reinterpret_cast<float *>(sw)[dst + k] = f;
-      dsum += (double)f;
+  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v0 = wg * 32; v0 < Nst; v0 += nwarp * 32) {
+    const long long v = v0 + lane;
+    const bool ok = v < Nst;
+    long long src = 0, dst = 0;
+    int m = 0;
+    if (ok) {
+      src = row_off[v];
+      dst = srp[v];
+      m = (int)(srp[v + 1] - dst);
     }
-    dsum = warp_sum(dsum);
-    __syncwarp();
-    if (lane == 0) {
-      sdeg[v] = dsum;
-      if (v < C) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k) s = __dadd_rn(s, w64[k]);
-        double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
-        base_w[v] = bw;
-        hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
+    const int nv = (int)min((long long)32, Nst - v0);
+    for (int j = 0; j < nv; ++j) {
+      const long long sj = __shfl_sync(0xffffffffu, src, j), dj = __shfl_sync(0xffffffffu, dst, j);
+      const int mj = __shfl_sync(0xffffffffu, m, j);
+      double *w64 = reinterpret_cast<double *>(mval) + sj;
+      for (int k = lane; k < mj; k += 32) {
+        double w = lattice_weight(mval[sj + k]);
+        w64[k] = w;
+        scol[dj + k] = mcol[sj + k];
+        uint16_t hb = 0;
+        float f = stored(w, wdtype, &hb);
+        if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dj + k] = hb;
+        else reinterpret_cast<float *>(sw)[dj + k] = f;
       }
+    }
+    __syncwarp();
+    if (!ok) continue;
+    const double *w64 = reinterpret_cast<const double *>(mval) + src;
+    dfl d{0.f, 0.f};
+    for (int k = 0; k < m; ++k) {
+      uint16_t hb;
+      df_add(d, stored(w64[k], wdtype, &hb));
+    }
+    sdeg[v] = df_to_d(d);
+    if (v < C) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = __dadd_rn(s, w64[k]);
+      double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
+      base_w[v] = bw;
+      hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
     }
   }
 }

@@ -402,93 +402,108 @@ __device__ __forceinline__ void acc_deg(dfl &D, dfl &Pp, float w) {
 
 // Rows of the static node range (cells, macro pins, stars): static part, then
 // for hint cells their macro entries (ascending macro) and window bin entries
-// (row-major).  Warp per row.
-__global__ void k_assemble_rows(HintGeo G, int with_hints, int wdtype, const int64_t *srp,
-                                const int32_t *scol, const void *sw, const uint32_t *rp_s,
-                                const int32_t *longidx, const uint64_t *lptr, const uint8_t *hflag,
-                                const int32_t *cell_bin, const int32_t *n_ovl, const float2 *xy,
-                                const float *cw, const float *ch, const float *fx, const float *fy,
-                                const int32_t *macro_cell, const int64_t *gptr,
-                                const uint32_t *glist, const double *base_w, const float *phif,
-                                const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum,
-                                uint64_t *mac_base,
-                                uint64_t *bin_base) {
+// (row-major).  A warp takes 32 consecutive rows: lanes load the rows'
+// offsets in parallel, the warp copies each row's static part cooperatively,
+// then every lane builds the hint part of its own row.
+__device__ __forceinline__ float hint_bin_w(float px, float py, int xx, int yy, const HintGeo &G,
+                                            const float *phif, const double *phid, float bwf,
+                                            double bw, int wdtype) {
+  double xb = G.xl + ((double)xx + 0.5) * G.wb, yb = G.yl + ((double)yy + 0.5) * G.hb;
+  double rx = fabs((double)px - xb) * G.iwb2, ry = fabs((double)py - yb) * G.ihb2;
+  int bb = yy * G.nbx + xx;
+  return -((exp_neg(fmax(rx, ry)) * phif[bb]) * bwf);
+}
+
+__global__ void __launch_bounds__(256) k_assemble_rows(
+    HintGeo G, int with_hints, int wdtype, const int64_t *srp, const int32_t *scol, const void *sw,
+    const uint32_t *rp_s, const int32_t *longidx, const uint64_t *lptr, const uint8_t *hflag,
+    const int32_t *cell_bin, const int32_t *n_ovl, const float2 *xy, const float *cw,
+    const float *ch, const float *fx, const float *fy, const int32_t *macro_cell,
+    const int64_t *gptr, const uint32_t *glist, const double *base_w, const float *phif,
+    const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
+    uint64_t *bin_base) {
   const int lane = threadIdx.x & 31;
   const int64_t nrows = with_hints ? G.Nst : G.N;
-  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < nrows;
-       v += ((long long)gridDim.x * blockDim.x) >> 5) {
-    int li = longidx[v];
-    uint64_t dst = li >= 0 ? lptr[li] : (uint64_t)rp_s[v];
-    long long s0 = v < G.Nst ? srp[v] : 0, sl = v < G.Nst ? srp[v + 1] - s0 : 0;
-    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
-    for (long long k = lane; k < sl; k += 32) {
-      col[dst + k] = scol[s0 + k];
-      copy_w(w, sw, wdtype, dst + k, s0 + k);
-      acc_deg(D, Pp, load_w(sw, wdtype, s0 + k));
+  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v0 = wg * 32; v0 < nrows; v0 += nwarp * 32) {
+    const long long v = v0 + lane;
+    const bool ok = v < nrows;
+    uint64_t dst = 0;
+    long long s0 = 0, sl = 0;
+    if (ok) {
+      int li = longidx[v];
+      dst = li >= 0 ? lptr[li] : (uint64_t)rp_s[v];
+      if (v < G.Nst) {
+        s0 = srp[v];
+        sl = srp[v + 1] - s0;
+      }
     }
-    if (with_hints && v < G.C && hflag[v]) {
+    dfl Dl{0.f, 0.f}, Pl{0.f, 0.f};
+    const int nv = (int)min((long long)32, nrows - v0);
+    for (int j = 0; j < nv; ++j) {
+      const uint64_t dj = __shfl_sync(0xffffffffu, dst, j);
+      const long long sj = __shfl_sync(0xffffffffu, s0, j), lj = __shfl_sync(0xffffffffu, sl, j);
+      dfl D{0.f, 0.f}, Pp{0.f, 0.f};
+      for (long long k = lane; k < lj; k += 32) {
+        col[dj + k] = scol[sj + k];
+        copy_w(w, sw, wdtype, dj + k, sj + k);
+        acc_deg(D, Pp, load_w(sw, wdtype, sj + k));
+      }
+      D = warp_sum_df(D);
+      Pp = warp_sum_df(Pp);
+      if (lane == j) {
+        Dl = D;
+        Pl = Pp;
+      }
+    }
+    if (ok && with_hints && v < G.C && hflag[v]) {
       float2 p = xy[v];
       if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
-      const float bwf = __double2float_rn(base_w[v]);
-      uint64_t mb = dst + sl;
+      const double bw = base_w[v];
+      const float bwf = __double2float_rn(bw);
+      const uint64_t mb = dst + sl;
       // macro entries, ascending macro id (grid bucket lists are sorted)
       int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
       long long gk = (long long)ky * G.gnx + kx;
-      long long q0 = gptr[gk], q1 = gptr[gk + 1];
-      int written = 0;
-      for (long long qb = q0; qb < q1; qb += 32) {
-        long long q = qb + lane;
-        bool hit = false;
-        int m = 0, c = 0;
-        if (q < q1) {
-          m = (int)glist[q];
-          c = macro_cell[m];
-          hit = overlaps(p.x, p.y, cw[v], ch[v], fx[c], fy[c], cw[c], ch[c]);
-        }
-        unsigned hm = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          uint64_t k = mb + written + __popc(hm & ((1u << lane) - 1u));
-          double rx = fabs((double)p.x - (double)fx[c]) / ((double)cw[c] * 0.5);
-          double ry = fabs((double)p.y - (double)fy[c]) / ((double)ch[c] * 0.5);
-          float wv = -(exp_neg(fmax(rx, ry)) * bwf);
-          col[k] = (int32_t)(G.mv0 + m);
-          if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
-            acc_deg(D, Pp, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, fx[c], fy[c], cw[c],
-                                                                   ch[c], base_w[v]))));
-          else
-            acc_deg(D, Pp, store_w(w, wdtype, k, wv));
-        }
-        written += __popc(hm);
-      }
-      uint64_t bb0 = mb + n_ovl[v];
-      int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
-      int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
-      int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
-      int wx = x1 - x0 + 1, nwin = wx * (y1 - y0 + 1);
-      for (int j = lane; j < nwin; j += 32) {
-        int xx = x0 + j % wx, yy = y0 + j / wx;
-        double xb = G.xl + ((double)xx + 0.5) * G.wb, yb = G.yl + ((double)yy + 0.5) * G.hb;
-        double rx = fabs((double)p.x - xb) * G.iwb2, ry = fabs((double)p.y - yb) * G.ihb2;
-        int bb = yy * G.nbx + xx;
-        float wv = -((exp_neg(fmax(rx, ry)) * phif[bb]) * bwf);
-        uint64_t k = bb0 + j;
-        col[k] = (int32_t)(G.bn0 + bb);
+      uint64_t k = mb;
+      const float cwv = cw[v], chv = ch[v];
+      for (long long q = gptr[gk]; q < gptr[gk + 1]; ++q) {
+        int m = (int)glist[q];
+        int c = macro_cell[m];
+        if (!overlaps(p.x, p.y, cwv, chv, fx[c], fy[c], cw[c], ch[c])) continue;
+        double rx = fabs((double)p.x - (double)fx[c]) / ((double)cw[c] * 0.5);
+        double ry = fabs((double)p.y - (double)fy[c]) / ((double)ch[c] * 0.5);
+        float wv = -(exp_neg(fmax(rx, ry)) * bwf);
+        col[k] = (int32_t)(G.mv0 + m);
         if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
-          acc_deg(D, Pp, store_bits(w, k, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb],
-                                                             base_w[v]))));
+          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, fx[c], fy[c], cw[c],
+                                                                 ch[c], bw))));
         else
-          acc_deg(D, Pp, store_w(w, wdtype, k, wv));
+          acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+        ++k;
       }
-      if (lane == 0) {
-        mac_base[v] = mb;
-        bin_base[v] = bb0;
-      }
+      const uint64_t bb0 = mb + n_ovl[v];
+      const int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
+      const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
+      const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
+      k = bb0;
+      for (int yy = y0; yy <= y1; ++yy)
+        for (int xx = x0; xx <= x1; ++xx, ++k) {
+          float wv = hint_bin_w(p.x, p.y, xx, yy, G, phif, phid, bwf, bw, wdtype);
+          const int bb = yy * G.nbx + xx;
+          col[k] = (int32_t)(G.bn0 + bb);
+          if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
+            acc_deg(Dl, Pl, store_bits(w, k, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))));
+          else
+            acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+        }
+      mac_base[v] = mb;
+      bin_base[v] = bb0;
     }
-    D = warp_sum_df(D);
-    Pp = warp_sum_df(Pp);
-    if (lane == 0) {
-      dsum[v] = D;
-      psum[v] = Pp;
+    if (ok) {
+      dsum[v] = df_norm(Dl);
+      psum[v] = df_norm(Pl);
     }
   }
 }

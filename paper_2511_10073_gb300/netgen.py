@@ -44,6 +44,7 @@ CONFIGS = {
     "tiny": dict(n_std=2000, n_macro=20, n_io=64, n_nets=2200, cap=64, macro_mode="area",
                  macro_area=(100.0, 1600.0)),
     "medium": dict(n_std=210_000, n_macro=550, n_io=1000, n_nets=220_000, cap=2000, macro_mode="frac"),
+    "half": dict(n_std=1_100_000, n_macro=4000, n_io=4000, n_nets=1_125_000, cap=5000, macro_mode="frac"),
     "large": dict(n_std=2_200_000, n_macro=8000, n_io=8000, n_nets=2_250_000, cap=10_000, macro_mode="frac"),
 }
 
