@@ -130,12 +130,14 @@ pl_status pl_build_hints(pl_graph *g, const pl_params *p, const float *xy_nodes,
 /* A4, one round of Algorithm 1 on the current augmented graph:
  * g~ = sum_t alpha_t H_r^{k_t} g, fixed nodes re-pinned, then
  * g' = (1 - gamma) g + gamma g~, re-pinned, movable centres clamped.
- * xy_in, xy_out: device, N pairs each, distinct buffers. */
+ * xy_in, xy_out: device, N pairs each, distinct buffers.  Synchronizes
+ * `stream` to read the device status (TIMEOUT if a bounded wait gave up). */
 pl_status pl_filter_apply(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
                           pl_stream stream);
 
 /* A0 steps 2-3: g' = sum_b alpha_b A~_{sigma_b}^{k_b} g on the static graph,
- * fixed nodes re-pinned, movable centres clamped.  Device, N pairs each. */
+ * fixed nodes re-pinned, movable centres clamped.  Device, N pairs each.
+ * Synchronizes `stream` to read the device status. */
 pl_status pl_gift(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
                   pl_stream stream);
 

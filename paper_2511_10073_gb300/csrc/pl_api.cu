@@ -142,6 +142,7 @@ pl_status read_status(pl_graph *g, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "status read");
   if (st[0] & ST_SPECTRUM) { set_error("lambda_up <= 0 or not finite"); return PL_ERR_SPECTRUM; }
   if (st[0] & ST_NONFINITE) { set_error("non-finite coordinate"); return PL_ERR_NONFINITE; }
+  if (st[0] & ST_TIMEOUT) { set_error("a bounded device-side wait gave up"); return PL_ERR_TIMEOUT; }
   return PL_OK;
 }
 
@@ -241,7 +242,10 @@ pl_status pl_filter_apply(pl_graph *g, const pl_params *p, const float *xy_in, f
   if (!g->have_hints) { set_error("no augmented graph: call pl_build_hints first"); return PL_ERR_INVALID_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
-  return run_filter(g, p, xy_in, xy_out, s);
+  cudaError_t e = cudaMemsetAsync(g->status.p, 0, 32, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
+  st = run_filter(g, p, xy_in, xy_out, s);
+  return st != PL_OK ? st : read_status(g, s);
 }
 
 pl_status pl_gift(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
@@ -253,7 +257,10 @@ pl_status pl_gift(pl_graph *g, const pl_params *p, const float *xy_in, float *xy
   if (st != PL_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
-  return run_gift(g, p, xy_in, xy_out, s);
+  cudaError_t e = cudaMemsetAsync(g->status.p, 0, 32, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
+  st = run_gift(g, p, xy_in, xy_out, s);
+  return st != PL_OK ? st : read_status(g, s);
 }
 
 pl_status pl_init_signal(pl_graph *g, uint64_t seed, const float *xy0_cells, float *xy_nodes,
@@ -284,6 +291,8 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
   if (e == cudaSuccess) e = ensure(g->g0, (size_t)N * 8 + 64);
   if (e != cudaSuccess) return cuda_fail(e, "filter buffers");
   float *cur = P<float>(g->xc), *nxt = P<float>(g->g0);
+  e = cudaMemsetAsync(g->status.p, 0, 32, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
   st = run_init_signal(g, seed, xy0_cells, cur, s);
   if (st != PL_OK) return st;
   if (p->gift_enable) {
@@ -291,9 +300,14 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
   } else {
     st = clamp_nodes(g, p, cur, nxt, s);
   }
+  if (st == PL_OK) st = read_status(g, s);
   if (st != PL_OK) return st;
   std::swap(cur, nxt);
   for (int t = 0; t < p->t_hint; ++t) {
+    if (t) {
+      st = read_status(g, s);
+      if (st != PL_OK) return st;
+    }
     st = build_hints(g, p, cur, s);
     if (st != PL_OK) return st;
     st = run_filter(g, p, cur, nxt, s);
@@ -356,7 +370,7 @@ static pl_status export_matrix(const pl_graph *g, const SpMat &m, int64_t rows, 
   for (int64_t v = 0; v < rows; ++v) {
     uint64_t a, b;
     if (lidx[v] >= 0) { a = lp[lidx[v]]; b = lp[lidx[v] + 1]; }
-    else { a = rps[v]; b = rps[v + 1]; }
+    else { a = rps[v] & kOffMask; b = rps[v + 1] & kOffMask; }
     if (rp) rp[v] = o;
     perm.resize(b - a);
     for (uint64_t k = a; k < b; ++k) perm[k - a] = k;

@@ -23,6 +23,8 @@ namespace pl {
     if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
   } while (0)
 
+constexpr int kMaxWin = 31;  // detection window at most 31 x 31 bins
+
 struct HintGeo {
   float xlf, ylf, sxf, syf;      // bin decision: floor((x - xl) * sx)
   float gxf, gyf, gsxf, gsyf;    // macro grid bucket of a centre
@@ -371,6 +373,16 @@ __global__ void k_chunk_owner(int32_t nlong, const int32_t *lchunk, int32_t *chu
     for (int c = lchunk[l]; c < lchunk[l + 1]; ++c) chunk_lr[c] = l;
 }
 
+// Short-row pointers with the hub flag of each row in bit 31; padded with the
+// end offset so that aligned bulk copies may read a few entries past N.
+__global__ void k_rp_pack(const uint64_t *s64, const uint8_t *lflag, int64_t N, uint32_t *rp) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= N + kRpPad;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (v < N) rp[v] = (uint32_t)s64[v] | (lflag[v] ? kHubFlag : 0u);
+    else rp[v] = (uint32_t)s64[N];
+  }
+}
+
 __global__ void k_u64_to_u32(const uint64_t *a, uint32_t *b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -388,7 +400,7 @@ __global__ void k_tiles(const uint32_t *rp_s, int64_t N, int32_t ntiles, int32_t
     long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] + r >= target
     while (lo < hi) {
       long long mid = (lo + hi) >> 1;
-      if ((uint64_t)rp_s[mid] + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
+      if ((uint64_t)(rp_s[mid] & kOffMask) + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
     }
     tile_row[t] = (int32_t)lo;
   }
@@ -405,15 +417,6 @@ __device__ __forceinline__ void acc_deg(dfl &D, dfl &Pp, float w) {
 // (row-major).  A warp takes 32 consecutive rows: lanes load the rows'
 // offsets in parallel, the warp copies each row's static part cooperatively,
 // then every lane builds the hint part of its own row.
-__device__ __forceinline__ float hint_bin_w(float px, float py, int xx, int yy, const HintGeo &G,
-                                            const float *phif, const double *phid, float bwf,
-                                            double bw, int wdtype) {
-  double xb = G.xl + ((double)xx + 0.5) * G.wb, yb = G.yl + ((double)yy + 0.5) * G.hb;
-  double rx = fabs((double)px - xb) * G.iwb2, ry = fabs((double)py - yb) * G.ihb2;
-  int bb = yy * G.nbx + xx;
-  return -((exp_neg(fmax(rx, ry)) * phif[bb]) * bwf);
-}
-
 __global__ void __launch_bounds__(256) k_assemble_rows(
     HintGeo G, int with_hints, int wdtype, const int64_t *srp, const int32_t *scol, const void *sw,
     const uint32_t *rp_s, const int32_t *longidx, const uint64_t *lptr, const uint8_t *hflag,
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(256) k_assemble_rows(
     long long s0 = 0, sl = 0;
     if (ok) {
       int li = longidx[v];
-      dst = li >= 0 ? lptr[li] : (uint64_t)rp_s[v];
+      dst = li >= 0 ? lptr[li] : (uint64_t)(rp_s[v] & kOffMask);
       if (v < G.Nst) {
         s0 = srp[v];
         sl = srp[v + 1] - s0;
@@ -487,11 +490,26 @@ __global__ void __launch_bounds__(256) k_assemble_rows(
       const int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
       const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
       const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
+      // e^{-max(rx, ry)} = e^{-rx} or e^{-ry}: one exponent per window column
+      // and per window row (kMaxWin each), then a selection per bin
+      float ex[kMaxWin], ey[kMaxWin];
+      double rxv[kMaxWin], ryv[kMaxWin];
+      for (int xx = x0; xx <= x1; ++xx) {
+        double xb = G.xl + ((double)xx + 0.5) * G.wb;
+        rxv[xx - x0] = fabs((double)p.x - xb) * G.iwb2;
+        ex[xx - x0] = exp_neg(rxv[xx - x0]);
+      }
+      for (int yy = y0; yy <= y1; ++yy) {
+        double yb = G.yl + ((double)yy + 0.5) * G.hb;
+        ryv[yy - y0] = fabs((double)p.y - yb) * G.ihb2;
+        ey[yy - y0] = exp_neg(ryv[yy - y0]);
+      }
       k = bb0;
       for (int yy = y0; yy <= y1; ++yy)
         for (int xx = x0; xx <= x1; ++xx, ++k) {
-          float wv = hint_bin_w(p.x, p.y, xx, yy, G, phif, phid, bwf, bw, wdtype);
           const int bb = yy * G.nbx + xx;
+          const float e = rxv[xx - x0] >= ryv[yy - y0] ? ex[xx - x0] : ey[yy - y0];
+          const float wv = -((e * phif[bb]) * bwf);
           col[k] = (int32_t)(G.bn0 + bb);
           if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
             acc_deg(Dl, Pl, store_bits(w, k, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))));
@@ -729,8 +747,8 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
   TRY(d2h(&tot[0], s64 + N, 1, s));
   TRY(d2h(&tot[1], lpos + N, 1, s));
   TRY(d2h(&nl, lscan + N, 1, s));
-  if (tot[0] >= (1ull << 32) - kTile || tot[0] + tot[1] >= (1ull << 40)) {
-    set_error("graph too large for the 32-bit short-row layout (%llu entries)",
+  if (tot[0] >= (uint64_t)kOffMask - 2 * kTile || tot[0] + tot[1] >= (1ull << 40)) {
+    set_error("graph too large for the 31-bit short-row layout (%llu entries)",
               (unsigned long long)tot[0]);
     return PL_ERR_UNSUPPORTED;
   }
@@ -738,8 +756,9 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
   m.nnz_l = tot[1];
   m.nlong = nl;
   m.wbytes = g->wdtype == PL_W_BF16 ? 2 : 4;
-  TRY(ensure(m.rp_s, (size_t)(N + 1) * 4));
-  k_u64_to_u32<<<grid_for(N + 1, 256), 256, 0, s>>>(s64, P<uint32_t>(m.rp_s), N + 1);
+  TRY(ensure(m.rp_s, (size_t)(N + 1 + kRpPad) * 4));
+  k_rp_pack<<<grid_for(N + 1 + kRpPad, 256), 256, 0, s>>>(s64, P<uint8_t>(g->tmp[2]), N,
+                                                         P<uint32_t>(m.rp_s));
   note_launch();
   const uint64_t cap = m.nnz_s + m.nnz_l + kPad;
   TRY(ensure(m.col, cap * 4));

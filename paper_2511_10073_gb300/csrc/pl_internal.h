@@ -17,7 +17,10 @@ namespace pl {
 constexpr int kTile = 2048;
 constexpr int kLong = 1024;
 constexpr int kChunk = 2048;
-constexpr int kPad = 16;  // spare entries after the last one (vector over-reads)
+constexpr int kPad = 16;  // spare entries after the last one (aligned over-reads)
+constexpr int kRpPad = 8;  // spare row pointers after the last one
+constexpr uint32_t kHubFlag = 0x80000000u;  // rp_s bit 31: the row is a hub row
+constexpr uint32_t kOffMask = 0x7fffffffu;
 
 // A split CSR matrix as the SpMM kernels read it.  Entries of short rows come
 // first (row pointers rp_s; long rows have zero length there), entries of hub
@@ -26,7 +29,7 @@ struct SpMat {
   int64_t N = 0;
   uint64_t nnz_s = 0, nnz_l = 0;
   int32_t nlong = 0, ntiles = 0, nchunks = 0;
-  Buf rp_s;     // uint32 [N+1]
+  Buf rp_s;     // uint32 [N+1+kRpPad], bit 31 = hub row
   Buf col;      // int32 [nnz_s + nnz_l + kPad]
   Buf w;        // float or uint16 (bf16) [same]
   Buf lrow;     // int32 [nlong] node of each hub row
