@@ -213,8 +213,10 @@ __device__ void issue_item(const StepArgs &A, long long it, StageT<WT> &st, Item
   mbar_expect_arrive(bar, bytes);
   if (ne) {
     bulk_g2s(smem_u32(st.col), A.col + ea, ne * 4u, bar, policy);
-    bulk_g2s(smem_u32(st.w), reinterpret_cast<const decltype(st.w[0] + 0) *>(A.w) + ea,
-             ne * (uint32_t)sizeof(st.w[0]), bar, policy);
+    using WTy = typename std::conditional<WT == 0, float, uint16_t>::type;
+    static_assert(sizeof(st.w[0]) == sizeof(WTy), "weight element size");
+    bulk_g2s(smem_u32(st.w), reinterpret_cast<const WTy *>(A.w) + ea,
+             ne * (uint32_t)sizeof(WTy), bar, policy);
   }
   if (nr) bulk_g2s(smem_u32(st.rp), A.rp_s + d.ra, nr * 4u, bar, policy);
 }
