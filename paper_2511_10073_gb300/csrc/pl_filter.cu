@@ -119,296 +119,145 @@ __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T y
   }
 }
 
-// ------------------------------------------------ TMA pipeline (bulk copies)
-// Work items: hub chunks [0, nchunks), then short tiles.  A persistent CTA
-// takes items blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps the
-// index/weight range of the next items (and a tile's row pointers) in flight
-// in shared-memory stages with cp.async.bulk on an mbarrier per stage, so the
-// DRAM stream does not wait for the gathers and reductions of the current item.
-// Every wait on an mbarrier is bounded; on expiry the CTA raises ST_TIMEOUT,
-// waits (bounded) for its own copies in flight and returns.
-constexpr int kThreadRow = 32;
-constexpr int kEntCap = kTile + kLong + 16;  // aligned entries of one item
-constexpr int kRowCap = kTile + 8;           // aligned row pointers of one tile
-constexpr long long kWaitLimit = 1LL << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_arrive(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it)
-    if (mbar_try(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1], %2, [%3], %4;" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
-      : "memory");
-}
+// ------------------------------------------------------- warp work units
+// Units: hub chunks [0, nchunks) of kChunk entries, then short tiles of at
+// most kTile keys (rows + entries; rows <= kLong entries).  Each warp takes
+// units gw, gw + nwarps, ...; a unit needs no block-wide barrier.
+//  * tile: the lanes load the unit's indices and weights (all loads issued
+//    before the gathers), write w * x[col] to the warp's shared-memory slice,
+//    then each lane sums whole rows (lane per row) and runs their epilogue;
+//  * hub chunk: exact products accumulated in double-float, reduced over the
+//    warp, written as an FP64 partial; the last warp to finish a row (ticket,
+//    no waiting) adds the row's partials in chunk order (lane-strided, then a
+//    fixed tree) and combines in FP64.
+constexpr int kEntWarp = kTile + kLong;  // entries of one tile < kTile + kLong
+constexpr int kBatch = 4;                // loads in flight per lane and batch
 
 template <int WT>
-struct StageT {
-  int32_t col[kEntCap];
-  typename std::conditional<WT == 0, float, uint16_t>::type w[kEntCap];
-  uint32_t rp[kRowCap];
-};
-
-struct ItemDesc {
-  uint64_t e0, e1, ea;  // entries [e0, e1) of the item; stage holds [ea, ea + count)
-  int32_t r0, r1, ra;   // tile rows [r0, r1); stage row pointers start at ra
-  int32_t chunk;        // >= 0 for a hub chunk
-};
-
-// Decode item `it` and issue its copies into stage `st` (thread 0 only).
-template <int WT>
-__device__ void issue_item(const StepArgs &A, long long it, StageT<WT> &st, ItemDesc &d,
-                           uint32_t bar, uint64_t policy) {
-  uint64_t e0, e1;
-  if (it < A.nchunks) {
-    const int c = (int)it, l = A.chunk_lr[c];
-    const uint64_t beg = A.lptr[l], end = A.lptr[l + 1];
-    e0 = beg + (uint64_t)(c - A.lchunk[l]) * kChunk;
-    e1 = e0 + kChunk < end ? e0 + kChunk : end;
-    d.chunk = c;
-    d.r0 = d.r1 = d.ra = 0;
-  } else {
-    const int t = (int)(it - A.nchunks);
-    d.r0 = A.tile_row[t];
-    d.r1 = A.tile_row[t + 1];
-    e0 = A.rp_s[d.r0] & kOffMask;
-    e1 = A.rp_s[d.r1] & kOffMask;
-    d.chunk = -1;
-  }
-  d.e0 = e0;
-  d.e1 = e1;
-  const uint64_t ea = e0 & ~uint64_t(7), eb = (e1 + 7) & ~uint64_t(7);
-  d.ea = ea;
-  const uint32_t ne = (uint32_t)(eb - ea);
-  uint32_t nr = 0;
-  if (d.chunk < 0) {
-    d.ra = d.r0 & ~3;
-    nr = (uint32_t)((((d.r1 + 1) + 3) & ~3) - d.ra);
-  }
-  const uint32_t bytes = ne * 4u + ne * (uint32_t)sizeof(st.w[0]) + nr * 4u;
-  mbar_expect_arrive(bar, bytes);
-  if (ne) {
-    bulk_g2s(smem_u32(st.col), A.col + ea, ne * 4u, bar, policy);
-    using WTy = typename std::conditional<WT == 0, float, uint16_t>::type;
-    static_assert(sizeof(st.w[0]) == sizeof(WTy), "weight element size");
-    bulk_g2s(smem_u32(st.w), reinterpret_cast<const WTy *>(A.w) + ea,
-             ne * (uint32_t)sizeof(WTy), bar, policy);
-  }
-  if (nr) bulk_g2s(smem_u32(st.rp), A.rp_s + d.ra, nr * 4u, bar, policy);
-}
-
-template <int WT>
-__device__ __forceinline__ float wval(const StageT<WT> &st, uint32_t k) {
-  if (WT == 0) return (float)st.w[k];
-  return __uint_as_float((uint32_t)st.w[k] << 16);
+__device__ __forceinline__ float wload(const void *w, uint64_t k) {
+  if (WT == 0) return __ldcs(reinterpret_cast<const float *>(w) + k);
+  return __uint_as_float((uint32_t)__ldcs(reinterpret_cast<const unsigned short *>(w) + k) << 16);
 }
 
 template <int WT, int MODE>
-__device__ void tile_item(const StepArgs &A, const StageT<WT> &st, const ItemDesc &d, float2 *sp,
-                          int *wide, int *nwide) {
-  const int nrows = d.r1 - d.r0;
-  const uint32_t n = (uint32_t)(d.e1 - d.e0), off = (uint32_t)(d.e0 - d.ea);
-  for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-    const int c = st.col[off + k];
-    const float wv = wval<WT>(st, off + k);
-    const float2 xv = __ldg(A.x + c);
-    sp[k] = make_float2(wv * xv.x, wv * xv.y);
-  }
-  __syncthreads();
-  const float bconst = MODE == MODE_HR ? (float)A.lam[1] : 0.f;
-  const uint32_t base = (uint32_t)d.e0;
-  const int rb = d.r0 - d.ra;
-  for (int j = threadIdx.x; j < nrows; j += blockDim.x) {
-    const uint32_t raw = st.rp[rb + j];
-    if (raw & kHubFlag) continue;
-    const uint32_t a = (raw & kOffMask) - base, b = (st.rp[rb + j + 1] & kOffMask) - base;
-    if (b - a > (uint32_t)kThreadRow) {
-      wide[atomicAdd(nwide, 1)] = j;
-      continue;
+__device__ void warp_tile(const StepArgs &A, int t, float2 *sp) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = A.tile_row[t], r1 = A.tile_row[t + 1];
+  const uint32_t e0 = A.rp_s[r0] & kOffMask, e1 = A.rp_s[r1] & kOffMask;
+  const uint32_t n = e1 - e0;
+  for (uint32_t k0 = 0; k0 < n; k0 += 32 * kBatch) {
+    int c[kBatch];
+    float wv[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t k = k0 + q * 32 + lane;
+      c[q] = k < n ? __ldcs(A.col + e0 + k) : 0;
+      wv[q] = k < n ? wload<WT>(A.w, e0 + k) : 0.f;
     }
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint32_t k = k0 + q * 32 + lane;
+      if (k < n) {
+        const float2 xv = __ldg(A.x + c[q]);
+        sp[k] = make_float2(wv[q] * xv.x, wv[q] * xv.y);
+      }
+    }
+  }
+  __syncwarp();
+  const float bconst = MODE == MODE_HR ? (float)A.lam[1] : 0.f;
+  for (int r = r0 + lane; r < r1; r += 32) {
+    const uint32_t raw = A.rp_s[r];
+    if (raw & kHubFlag) continue;
+    const uint32_t a = (raw & kOffMask) - e0, b = (A.rp_s[r + 1] & kOffMask) - e0;
     float sx = 0.f, sy = 0.f;
     for (uint32_t k = a; k < b; ++k) {
       const float2 q = sp[k];
       sx += q.x;
       sy += q.y;
     }
-    const int r = d.r0 + j;
     const float av = A.a[r];
     const float bv = MODE == MODE_HR ? bconst : A.b[r];
     const float2 xv = A.x[r];
     epilogue<float>(A, r, av * xv.x + bv * sx, av * xv.y + bv * sy);
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = wid; q < *nwide; q += nw) {
-    const int j = wide[q], r = d.r0 + j;
-    const uint32_t a = (st.rp[rb + j] & kOffMask) - base, b = (st.rp[rb + j + 1] & kOffMask) - base;
-    float sx = 0.f, sy = 0.f;
-    for (uint32_t k = a + lane; k < b; k += 32) {
-      const float2 v = sp[k];
-      sx += v.x;
-      sy += v.y;
-    }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) {
-      const float av = A.a[r];
-      const float bv = MODE == MODE_HR ? bconst : A.b[r];
-      const float2 xv = A.x[r];
-      epilogue<float>(A, r, av * xv.x + bv * sx, av * xv.y + bv * sy);
-    }
-  }
+  __syncwarp();
 }
 
 template <int WT, int MODE>
-__device__ void chunk_item(const StepArgs &A, const StageT<WT> &st, const ItemDesc &d,
-                           dfl (*red)[32], double (*fin)[32], int *last) {
-  const int c = d.chunk, l = A.chunk_lr[c];
+__device__ void warp_chunk(const StepArgs &A, int c) {
+  const int lane = threadIdx.x & 31;
+  const int l = A.chunk_lr[c];
   const int64_t v = A.lrow[l];
+  const uint64_t beg = A.lptr[l], end = A.lptr[l + 1];
   const int c0 = A.lchunk[l], nch = A.lchunk[l + 1] - c0;
-  const uint32_t n = (uint32_t)(d.e1 - d.e0), off = (uint32_t)(d.e0 - d.ea);
+  const uint64_t cb = beg + (uint64_t)(c - c0) * kChunk;
+  const uint64_t ce = cb + kChunk < end ? cb + kChunk : end;
   dfl sx{0.f, 0.f}, sy{0.f, 0.f};
-  for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-    const int cc = st.col[off + k];
-    const float wv = wval<WT>(st, off + k);
-    const float2 xv = __ldg(A.x + cc);
-    df_add_prod(sx, wv, xv.x);
-    df_add_prod(sy, wv, xv.y);
+  for (uint64_t k0 = cb; k0 < ce; k0 += 32 * kBatch) {
+    int cc[kBatch];
+    float wv[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint64_t k = k0 + q * 32 + lane;
+      cc[q] = k < ce ? __ldcs(A.col + k) : 0;
+      wv[q] = k < ce ? wload<WT>(A.w, k) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const uint64_t k = k0 + q * 32 + lane;
+      if (k < ce) {
+        const float2 xv = __ldg(A.x + cc[q]);
+        df_add_prod(sx, wv[q], xv.x);
+        df_add_prod(sy, wv[q], xv.y);
+      }
+    }
   }
   sx = warp_sum_df(sx);
   sy = warp_sum_df(sy);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int last = 0;
   if (lane == 0) {
-    red[0][wid] = sx;
-    red[1][wid] = sy;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double px = 0.0, py = 0.0;
-    for (int k = 0; k < nw; ++k) {
-      px += df_to_d(red[0][k]);
-      py += df_to_d(red[1][k]);
-    }
-    A.part[2 * (int64_t)c] = px;
-    A.part[2 * (int64_t)c + 1] = py;
+    A.part[2 * (int64_t)c] = df_to_d(sx);
+    A.part[2 * (int64_t)c + 1] = df_to_d(sy);
     __threadfence();
-    *last = atomicAdd(&A.tick[l], 1) == nch - 1;
+    last = atomicAdd(&A.tick[l], 1) == nch - 1;
   }
-  __syncthreads();
-  if (*last) {
-    // the row's partials in chunk order: thread k adds chunks k, k + blockDim,
-    // ..., then a fixed tree over threads (deterministic)
-    __threadfence();
-    double tx = 0.0, ty = 0.0;
-    for (int k = threadIdx.x; k < nch; k += blockDim.x) {
-      tx += __ldcg(&A.part[2 * (int64_t)(c0 + k)]);
-      ty += __ldcg(&A.part[2 * (int64_t)(c0 + k) + 1]);
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  double tx = 0.0, ty = 0.0;
+  for (int k = lane; k < nch; k += 32) {
+    tx += __ldcg(&A.part[2 * (int64_t)(c0 + k)]);
+    ty += __ldcg(&A.part[2 * (int64_t)(c0 + k) + 1]);
+  }
+  tx = warp_sum(tx);
+  ty = warp_sum(ty);
+  if (lane == 0) {
+    double av, bv;
+    if (MODE == MODE_HR) {
+      av = A.c64l[l];
+      bv = A.lam[1];
+    } else {
+      av = (double)A.a[v];
+      bv = (double)A.b[v];
     }
-    tx = warp_sum(tx);
-    ty = warp_sum(ty);
-    if (lane == 0) {
-      fin[0][wid] = tx;
-      fin[1][wid] = ty;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tx = 0.0;
-      ty = 0.0;
-      for (int k = 0; k < nw; ++k) {
-        tx += fin[0][k];
-        ty += fin[1][k];
-      }
-      double av, bv;
-      if (MODE == MODE_HR) {
-        av = A.c64l[l];
-        bv = A.lam[1];
-      } else {
-        av = (double)A.a[v];
-        bv = (double)A.b[v];
-      }
-      const float2 xv = A.x[v];
-      epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
-      A.tick[l] = 0;
-    }
+    const float2 xv = A.x[v];
+    epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
+    A.tick[l] = 0;
   }
 }
 
-template <int WT>
-constexpr int stages_for() { return WT == 0 ? 2 : 3; }
+constexpr int kSpmmThreads = 256;
 
 template <int WT, int MODE>
-__global__ void __launch_bounds__(256) k_spmm(StepArgs A) {
-  constexpr int S = stages_for<WT>();
-  extern __shared__ __align__(128) unsigned char smem[];
-  StageT<WT> *stage = reinterpret_cast<StageT<WT> *>(smem);
-  float2 *sp = reinterpret_cast<float2 *>(smem + S * sizeof(StageT<WT>));
-  __shared__ __align__(8) uint64_t bars[S];
-  __shared__ ItemDesc desc[S];
-  __shared__ int wide[(kTile + kLong) / (kThreadRow + 1) + 1];
-  __shared__ int nwide, last, abort_;
-  __shared__ dfl red[2][32];
-  __shared__ double fin[2][32];
-  const long long nitems = (long long)A.nchunks + A.ntiles;
-  uint64_t policy = 0;
-  if (threadIdx.x == 0) {
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
-    for (int k = 0; k < S; ++k) mbar_init(smem_u32(&bars[k]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    abort_ = 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < S; ++k) {
-      const long long it = blockIdx.x + (long long)k * gridDim.x;
-      if (it < nitems) issue_item<WT>(A, it, stage[k], desc[k], smem_u32(&bars[k]), policy);
-    }
-  uint32_t phase = 0;  // bit k: parity to wait for on stage k
-  int k = 0;
-  for (long long it = blockIdx.x; it < nitems; it += gridDim.x, k = (k + 1 == S) ? 0 : k + 1) {
-    if (!mbar_wait(smem_u32(&bars[k]), (phase >> k) & 1u)) abort_ = 1;
-    phase ^= 1u << k;
-    if (threadIdx.x == 0) nwide = 0;
-    __syncthreads();
-    if (abort_) break;
-    if (desc[k].chunk >= 0) chunk_item<WT, MODE>(A, stage[k], desc[k], red, fin, &last);
-    else tile_item<WT, MODE>(A, stage[k], desc[k], sp, wide, &nwide);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const long long nx = it + (long long)S * gridDim.x;
-      if (nx < nitems) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_item<WT>(A, nx, stage[k], desc[k], smem_u32(&bars[k]), policy);
-      }
-    }
-  }
-  if (abort_ && threadIdx.x == 0) {
-    flag(A.status, ST_TIMEOUT);
-    // copies possibly still in flight into this CTA's stages: wait (bounded)
-    for (int q = 0; q < S; ++q) mbar_wait(smem_u32(&bars[q]), (phase >> q) & 1u);
+__global__ void __launch_bounds__(kSpmmThreads) k_spmm(StepArgs A) {
+  __shared__ float2 sp_all[kSpmmThreads / 32][kEntWarp];
+  float2 *sp = sp_all[threadIdx.x >> 5];
+  const long long nunits = (long long)A.nchunks + A.ntiles;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = gw; u < nunits; u += nw) {
+    if (u < A.nchunks) warp_chunk<WT, MODE>(A, (int)u);
+    else warp_tile<WT, MODE>(A, (int)(u - A.nchunks), sp);
   }
 }
 
@@ -544,14 +393,9 @@ static double spmm_bytes(const SpMat &m, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
-template <int WT, int MODE>
-static size_t step_smem() {
-  return (size_t)stages_for<WT>() * sizeof(StageT<WT>) + (size_t)(kTile + kLong) * sizeof(float2);
-}
-
 template <int MODE>
 static cudaError_t launch_step(const StepArgs &A, const SpMat &m, int wdtype, cudaStream_t s) {
-  const long long nitems = (long long)A.nchunks + A.ntiles;
+  const long long nunits = (long long)A.nchunks + A.ntiles;
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -559,26 +403,12 @@ static cudaError_t launch_step(const StepArgs &A, const SpMat &m, int wdtype, cu
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  const int grid = (int)(nitems < 2LL * nsm ? nitems : 2LL * nsm);
+  const long long want = (nunits + kSpmmThreads / 32 - 1) / (kSpmmThreads / 32);
+  const int grid = (int)(want < 8LL * nsm ? (want > 0 ? want : 1) : 8LL * nsm);
   const bool prof = prof_on();
   if (prof) prof_begin(s, MODE == MODE_HR ? PROF_HR : PROF_GIFT, spmm_bytes(m, wdtype));
-  if (wdtype == PL_W_BF16) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_spmm<1, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem<1, MODE>());
-      attr = true;
-    }
-    k_spmm<1, MODE><<<grid, 256, step_smem<1, MODE>(), s>>>(A);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_spmm<0, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem<0, MODE>());
-      attr = true;
-    }
-    k_spmm<0, MODE><<<grid, 256, step_smem<0, MODE>(), s>>>(A);
-  }
+  if (wdtype == PL_W_BF16) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
+  else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
   note_launch();
   if (prof) prof_end(s);
   return cudaGetLastError();

@@ -11,12 +11,12 @@
 
 namespace pl {
 
-// SpMM tiling: short rows (<= kLong entries) are cut into tiles owning the rows
-// whose first entry falls in an nnz window of kTile; long rows and every
-// virtual-node row go to the hub path in chunks of kChunk entries.
-constexpr int kTile = 2048;
-constexpr int kLong = 1024;
-constexpr int kChunk = 2048;
+// SpMM work units: short rows (<= kLong entries) are cut into warp tiles of at
+// most kTile keys (rows + entries, the key of row r being rp_s[r] + r); long
+// rows and every virtual-node row go to the hub path in chunks of kChunk.
+constexpr int kTile = 256;
+constexpr int kLong = 128;
+constexpr int kChunk = 512;
 constexpr int kPad = 16;  // spare entries after the last one (aligned over-reads)
 constexpr int kRpPad = 8;  // spare row pointers after the last one
 constexpr uint32_t kHubFlag = 0x80000000u;  // rp_s bit 31: the row is a hub row
