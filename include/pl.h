@@ -164,6 +164,24 @@ size_t pl_hpwl_workspace_size(int32_t num_nets);
 pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, void *ws,
                   size_t ws_bytes, pl_stream stream);
 
+/* pl_hpwl without a workspace, for callers that cannot allocate device memory
+ * or hand scratch to a library: a host that owns all device memory through
+ * its own pool and gives plug-ins no allocator, or a code path where an
+ * allocation (which may synchronize the device) is not allowed.  No counterpart
+ * in the paper.  Same result as pl_hpwl (same kernel and grid).  The scratch is
+ * a fixed device array of about 10 KB inside the library (ticket words plus
+ * one partial sum for each of at most 1216 blocks, the largest grid the HPWL
+ * kernel uses); every GPU that loads the library keeps it until the process
+ * exits.  Any num_nets >= 0 fits; a call that would need more than that array
+ * is rejected with PL_ERR_UNSUPPORTED.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and should be made before any
+ * stream capture.  All calls share the array and each call clears its ticket
+ * words first, so calls that overlap on the GPU (on different streams) race.
+ * Allocates nothing; does not synchronize.  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA. */
+pl_status pl_hpwl_noalloc(const pl_netlist *nl, const float *xy_cells, double *hpwl,
+                          pl_stream stream);
+
 /* Copies of the graph for exact comparison (all HOST buffers):
  * static CSR: rp[static nodes + 1], col[static nnz], w[static nnz] (stored
  * weight as double), base_w[num_cells] (baseWeight_i, FP64).

@@ -79,6 +79,7 @@ def lib():
             "pl_filter_init": (C.c_int, [vp, vp, u64, vp, vp, vp]),
             "pl_hpwl_workspace_size": (sz, [i32]),
             "pl_hpwl": (C.c_int, [vp, vp, vp, vp, sz, vp]),
+            "pl_hpwl_noalloc": (C.c_int, [vp, vp, vp, vp]),
             "pl_graph_export_static": (C.c_int, [vp, vp, vp, vp, vp]),
             "pl_graph_export": (C.c_int, [vp] * 10),
             "pl_graph_destroy": (None, [vp]),
@@ -251,6 +252,12 @@ def pl_hpwl_workspace_size(num_nets: int) -> int:
 def pl_hpwl(dnl: DeviceNetlist, xy_cells, out, ws, stream=None):
     _check(lib().pl_hpwl(C.byref(dnl.struct), _ptr(xy_cells), _ptr(out), _ptr(ws),
                          C.c_size_t(ws.numel() * ws.element_size()), _stream(stream)))
+
+
+def pl_hpwl_noalloc(dnl: DeviceNetlist, xy_cells, out, stream=None):
+    """HPWL into `out` (device double) with the library's fixed scratch: no
+    workspace, no allocation (see include/pl.h)."""
+    _check(lib().pl_hpwl_noalloc(C.byref(dnl.struct), _ptr(xy_cells), _ptr(out), _stream(stream)))
 
 
 def hpwl_workspace(num_nets: int, device="cuda"):

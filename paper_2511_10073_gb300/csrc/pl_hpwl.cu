@@ -6,6 +6,8 @@
 // caller's workspace; the last block to finish (ticket) adds them in block
 // order, so the result does not depend on scheduling.  A pin whose cell index
 // is out of range makes the result NaN (it is not dereferenced).
+#include <mutex>
+
 #include "pl_internal.h"
 
 namespace pl {
@@ -118,4 +120,63 @@ cudaError_t launch_hpwl(const pl_netlist *nl, const float *xy, double *out, void
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- allocation-free variant
+// Scratch of pl_hpwl_noalloc: the ticket words and one FP64 partial per block
+// of the largest grid k_hpwl is ever launched with (kHpwlBlocks), in a
+// file-scope device array of about 10 KB.  Every GPU that loads the library
+// holds it until the process exits, and every call shares it.
+constexpr int kNoAllocBlocks = kHpwlBlocks;
+constexpr size_t kNoAllocBytes = 256 + (size_t)kNoAllocBlocks * sizeof(double);
+static __device__ __align__(256) unsigned char g_hpwl_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device.  Host code cannot use
+// the symbol itself (it names a host-side stand-in), so the address is looked
+// up once per device, with that device current, and cached.
+static cudaError_t noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_hpwl_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace pl
+
+extern "C" pl_status pl_hpwl_noalloc(const pl_netlist *nl, const float *xy_cells, double *hpwl,
+                                     pl_stream stream) {
+  using namespace pl;
+  if (!nl || !xy_cells || !hpwl) {
+    set_error("NULL argument");
+    return PL_ERR_INVALID_ARG;
+  }
+  if (nl->num_nets < 0 || nl->num_cells < 0 || !nl->net_ptr || (nl->num_pins && !nl->pin_cell)) {
+    set_error("bad netlist");
+    return PL_ERR_INVALID_ARG;
+  }
+  const int nb = hpwl_blocks(nl->num_nets);
+  if (nb > kNoAllocBlocks || hpwl_ws_bytes(nl->num_nets) > kNoAllocBytes) {
+    set_error("pl_hpwl_noalloc: %d blocks exceed its fixed scratch of %d blocks", nb,
+              kNoAllocBlocks);
+    return PL_ERR_UNSUPPORTED;
+  }
+  void *scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "pl_hpwl_noalloc scratch lookup");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  e = cudaMemsetAsync(scratch, 0, 8, s);  // ticket and error count start at zero
+  if (e == cudaSuccess) e = launch_hpwl(nl, xy_cells, hpwl, scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pl_hpwl_noalloc");
+  return PL_OK;
+}
