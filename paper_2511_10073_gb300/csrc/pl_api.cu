@@ -118,18 +118,19 @@ static void destroy(pl_graph *g) {
   Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
                  &g->net_p, &g->star_of, &g->star_net, &g->macro_cell, &g->cell_macro, &g->srp,
                  &g->scol, &g->sw, &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
-                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->cell_bin, &g->n_ovl,
+                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->cell_bin, &g->n_ovl,
                  &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur,
-                 &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->lflag, &g->mac_base,
+                 &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->klen, &g->clen, &g->lflag,
+                 &g->mac_base,
                  &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,
                  &g->acc, &g->gsc, &g->status, &g->scr.buf};
   for (Buf *b : bufs) release(*b);
   for (Buf &b : g->tmp) release(b);
   SpMat *ms[] = {&g->st, &g->hm};
   for (SpMat *m : ms) {
-    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->lrow, &m->lptr, &m->lchunk, &m->chunk_lr,
-                 &m->tile_row, &m->longidx, &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam,
-                 &m->part, &m->tick};
+    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->keys, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
+                 &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->tile_row, &m->tdesc, &m->longidx,
+                 &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part, &m->tick};
     for (Buf *b : mb) release(*b);
   }
   delete g;
@@ -214,7 +215,7 @@ pl_status pl_graph_info(const pl_graph *g, int64_t *out) {
   for (int k = 0; k < 16; ++k) out[k] = 0;
   out[0] = g->C; out[1] = g->Pm; out[2] = g->S; out[3] = g->Mm; out[4] = g->NB;
   out[5] = g->Nst; out[6] = g->N; out[7] = (int64_t)g->nnz_static;
-  out[8] = g->have_hints ? (int64_t)(g->hm.nnz_s + g->hm.nnz_l) : 0;
+  out[8] = g->have_hints ? (int64_t)(g->st.nnz_s + g->st.nnz_l + g->hm.nnz_s + g->hm.nnz_l) : 0;
   out[9] = g->hx; out[10] = g->hy; out[11] = g->have_hints ? g->hm.nlong : 0;
   out[12] = g->nmov;
   return PL_OK;
@@ -338,57 +339,85 @@ pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, voi
   return PL_OK;
 }
 
-static pl_status export_matrix(const pl_graph *g, const SpMat &m, int64_t rows, int64_t *rp,
-                               int32_t *col, double *w, double *deg) {
-  cudaStream_t s = g->stream;
+// Host copy of one split matrix.
+struct HostSplit {
+  std::vector<uint32_t> rp;
+  std::vector<int32_t> lidx, col;
+  std::vector<uint64_t> lptr;
+  std::vector<float> w;
+  bool ok = false;
+};
+
+static cudaError_t fetch_split(const pl_graph *g, const SpMat &m, HostSplit &h, cudaStream_t s) {
   const int64_t N = m.N;
   const uint64_t tot = m.nnz_s + m.nnz_l;
-  std::vector<uint32_t> rps(N + 1);
-  std::vector<int32_t> lidx(N), cl(tot + 1);
-  std::vector<uint64_t> lp(m.nlong + 1);
-  std::vector<uint16_t> wb;
-  std::vector<float> wf;
-  std::vector<dfl> ds(N);
-  cudaError_t e = cudaMemcpyAsync(rps.data(), m.rp_s.p, (N + 1) * 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lidx.data(), m.longidx.p, N * 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lp.data(), m.lptr.p, (m.nlong + 1) * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && tot) e = cudaMemcpyAsync(cl.data(), m.col.p, tot * 4, cudaMemcpyDeviceToHost, s);
+  h.rp.resize(N + 1);
+  h.lidx.resize(N);
+  h.lptr.resize(m.nlong + 1);
+  h.col.resize(tot + 1);
+  h.w.resize(tot + 1);
+  cudaError_t e = cudaMemcpyAsync(h.rp.data(), m.rp_s.p, (N + 1) * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.lidx.data(), m.longidx.p, N * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.lptr.data(), m.lptr.p, (m.nlong + 1) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && tot) e = cudaMemcpyAsync(h.col.data(), m.col.p, tot * 4, cudaMemcpyDeviceToHost, s);
   if (g->wdtype == PL_W_BF16) {
-    wb.resize(tot + 1);
+    std::vector<uint16_t> wb(tot + 1);
     if (e == cudaSuccess && tot) e = cudaMemcpyAsync(wb.data(), m.w.p, tot * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (uint64_t k = 0; k < tot; ++k) {
+      uint32_t u = (uint32_t)wb[k] << 16;
+      memcpy(&h.w[k], &u, 4);
+    }
   } else {
-    wf.resize(tot + 1);
-    if (e == cudaSuccess && tot) e = cudaMemcpyAsync(wf.data(), m.w.p, tot * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && tot) e = cudaMemcpyAsync(h.w.data(), m.w.p, tot * 4, cudaMemcpyDeviceToHost, s);
   }
-  if (e == cudaSuccess && deg) e = cudaMemcpyAsync(ds.data(), m.dsum.p, N * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  h.ok = e == cudaSuccess;
+  return e;
+}
+
+static void row_range(const HostSplit &h, int64_t v, uint64_t *a, uint64_t *b) {
+  if (h.lidx[v] >= 0) {
+    *a = h.lptr[h.lidx[v]];
+    *b = h.lptr[h.lidx[v] + 1];
+  } else {
+    *a = h.rp[v] & kOffMask;
+    *b = h.rp[v + 1] & kOffMask;
+  }
+}
+
+// Rows in canonical order: the st piece, then (augmented graph) the hm piece;
+// a row kept in another order on the device (bin rows are the concatenation
+// of their window bins' lists) is sorted by column.
+static pl_status export_matrix(const pl_graph *g, const SpMat &st, const SpMat *hm, int64_t rows,
+                               int64_t *rp, int32_t *col, double *w, double *deg) {
+  cudaStream_t s = g->stream;
+  HostSplit hs, hh;
+  cudaError_t e = fetch_split(g, st, hs, s);
+  if (e == cudaSuccess && hm) e = fetch_split(g, *hm, hh, s);
+  std::vector<dfl> ds(st.N);
+  if (e == cudaSuccess && deg)
+    e = cudaMemcpy(ds.data(), (hm ? hm->dsum : st.dsum).p, st.N * 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "export");
-  // rows in canonical order; a row stored in another order (bin rows are kept
-  // as the concatenation of their window bins' lists) is sorted by column
-  std::vector<uint64_t> perm;
+  std::vector<std::pair<int32_t, float>> ent;
   int64_t o = 0;
   for (int64_t v = 0; v < rows; ++v) {
+    ent.clear();
     uint64_t a, b;
-    if (lidx[v] >= 0) { a = lp[lidx[v]]; b = lp[lidx[v] + 1]; }
-    else { a = rps[v] & kOffMask; b = rps[v + 1] & kOffMask; }
+    row_range(hs, v, &a, &b);
+    for (uint64_t k = a; k < b; ++k) ent.emplace_back(hs.col[k], hs.w[k]);
+    if (hm) {
+      row_range(hh, v, &a, &b);
+      for (uint64_t k = a; k < b; ++k) ent.emplace_back(hh.col[k], hh.w[k]);
+    }
+    auto by_col = [](const std::pair<int32_t, float> &x, const std::pair<int32_t, float> &y) {
+      return x.first < y.first;
+    };
+    if (!std::is_sorted(ent.begin(), ent.end(), by_col)) std::sort(ent.begin(), ent.end(), by_col);
     if (rp) rp[v] = o;
-    perm.resize(b - a);
-    for (uint64_t k = a; k < b; ++k) perm[k - a] = k;
-    if (!std::is_sorted(perm.begin(), perm.end(),
-                        [&](uint64_t x, uint64_t y) { return cl[x] < cl[y]; }))
-      std::sort(perm.begin(), perm.end(), [&](uint64_t x, uint64_t y) { return cl[x] < cl[y]; });
-    for (uint64_t k : perm) {
-      if (col) col[o] = cl[k];
-      if (w) {
-        if (g->wdtype == PL_W_BF16) {
-          uint32_t u = (uint32_t)wb[k] << 16;
-          float f;
-          memcpy(&f, &u, 4);
-          w[o] = f;
-        } else {
-          w[o] = wf[k];
-        }
-      }
+    for (auto &pr : ent) {
+      if (col) col[o] = pr.first;
+      if (w) w[o] = pr.second;
       ++o;
     }
     if (deg) deg[v] = (double)ds[v].hi + (double)ds[v].lo;
@@ -401,7 +430,7 @@ pl_status pl_graph_export_static(const pl_graph *g, int64_t *rp, int32_t *col, d
                                  double *base_w) {
   pl::g_err[0] = 0;
   if (!g) { set_error("NULL graph"); return PL_ERR_INVALID_ARG; }
-  pl_status st = export_matrix(g, g->st, g->Nst, rp, col, w, nullptr);
+  pl_status st = export_matrix(g, g->st, nullptr, g->Nst, rp, col, w, nullptr);
   if (st != PL_OK) return st;
   if (base_w && g->C) {
     cudaError_t e = cudaMemcpy(base_w, g->base_w.p, (size_t)g->C * 8, cudaMemcpyDeviceToHost);
@@ -416,7 +445,7 @@ pl_status pl_graph_export(const pl_graph *g, int64_t *rp, int32_t *col, double *
   pl::g_err[0] = 0;
   if (!g) { set_error("NULL graph"); return PL_ERR_INVALID_ARG; }
   if (!g->have_hints) { set_error("no augmented graph built yet"); return PL_ERR_INVALID_ARG; }
-  pl_status st = export_matrix(g, g->hm, g->N, rp, col, w, deg);
+  pl_status st = export_matrix(g, g->st, &g->hm, g->N, rp, col, w, deg);
   if (st != PL_OK) return st;
   cudaError_t e = cudaSuccess;
   if (lam_up) e = cudaMemcpy(lam_up, g->hm.lam.p, 8, cudaMemcpyDeviceToHost);

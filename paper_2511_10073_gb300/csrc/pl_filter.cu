@@ -32,17 +32,23 @@ namespace pl {
 enum { MODE_HR = 0, MODE_GIFT = 1 };
 
 struct StepArgs {
-  const uint32_t *rp_s;
-  const int32_t *col;
-  const void *w;
-  const int32_t *tile_row;
+  // static part of every row (st) and, for the refinement filter, the hint
+  // part (hm; hrp == nullptr for the GiFt filter, which uses st alone)
+  const uint32_t *srp;
+  const int32_t *scol;
+  const void *sw;
+  const uint32_t *hrp;
+  const int32_t *hcol;
+  const void *hw;
+  // work units of the applied matrix
+  const int4 *tdesc;
   int32_t ntiles;
   const int32_t *lrow;
-  const uint64_t *lptr;
+  const uint64_t *lsb, *lhb;
+  const uint32_t *lsl, *lhl;
   const int32_t *lchunk;
   const int32_t *chunk_lr;
   int32_t nchunks;
-  const int32_t *longidx;
   double *part;
   int32_t *tick;
   const float2 *x;
@@ -66,9 +72,11 @@ struct StepArgs {
   int *status;
 };
 
+// Epilogue of node v with its kind kd and (tap steps) accumulator ac loaded
+// by the caller.
 template <typename T>
-__device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T yy) {
-  const uint8_t kd = A.nkind[v];
+__device__ __forceinline__ void epilogue_k(const StepArgs &A, int64_t v, uint8_t kd, double2 ac,
+                                           T yx, T yy) {
   if (A.pin && kd == 2) {
     float2 f = A.fixedp[v];
     yx = (T)f.x;
@@ -78,7 +86,6 @@ __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T y
   double tx = 0.0, ty = 0.0;
   if (A.tap) {
     double sc = A.tscale ? (double)A.tscale[v] : 1.0;
-    double2 ac = A.acc[v];
     ac.x += A.alpha * ((double)yx * sc);
     ac.y += A.alpha * ((double)yy * sc);
     A.acc[v] = ac;
@@ -119,19 +126,27 @@ __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T y
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T yy) {
+  epilogue_k<T>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0), yx, yy);
+}
+
 // ------------------------------------------------------- warp work units
 // Units: hub chunks [0, nchunks) of kChunk entries, then short tiles of at
 // most kTile keys (rows + entries; rows <= kLong entries).  Each warp takes
-// units gw, gw + nwarps, ...; a unit needs no block-wide barrier.
-//  * tile: the lanes load the unit's indices and weights (all loads issued
-//    before the gathers), write w * x[col] to the warp's shared-memory slice,
-//    then each lane sums whole rows (lane per row) and runs their epilogue;
+// units gw, gw + nwarps, ... and loads the next tile's descriptor while it
+// works on the current unit; a unit needs no block-wide barrier.
+//  * tile: every lane issues the loads of all its entries (index, weight) and
+//    of its row's pointers and coefficient at once, then all its gathers of
+//    x, writes w * x[col] to the warp's shared-memory slice, and sums whole
+//    rows (lane per row) before their epilogue;
 //  * hub chunk: exact products accumulated in double-float, reduced over the
 //    warp, written as an FP64 partial; the last warp to finish a row (ticket,
 //    no waiting) adds the row's partials in chunk order (lane-strided, then a
 //    fixed tree) and combines in FP64.
-constexpr int kEntWarp = kTile + kLong;  // entries of one tile < kTile + kLong
-constexpr int kBatch = 4;                // loads in flight per lane and batch
+constexpr int kEntWarp = kTile + kLong;    // entries of one tile < kTile + kLong
+constexpr int kPer = (kEntWarp + 31) / 32;  // entries per lane of one tile
+constexpr int kChunkBatch = 8;              // loads in flight per lane (hub chunks)
 
 template <int WT>
 __device__ __forceinline__ float wload(const void *w, uint64_t k) {
@@ -139,78 +154,213 @@ __device__ __forceinline__ float wload(const void *w, uint64_t k) {
   return __uint_as_float((uint32_t)__ldcs(reinterpret_cast<const unsigned short *>(w) + k) << 16);
 }
 
-template <int WT, int MODE>
-__device__ void warp_tile(const StepArgs &A, int t, float2 *sp) {
+// Sum of the products of row r (st part at [ra, rb) of the slice, hm part at
+// [ha, hb)), then the epilogue.
+template <int MODE>
+__device__ __forceinline__ void tile_row_out(const StepArgs &A, int r, const float2 *sp,
+                                             uint32_t ra, uint32_t rb, uint32_t ha, uint32_t hb,
+                                             float av, float bv, float2 xr, uint8_t kd,
+                                             double2 ac) {
+  float sx = 0.f, sy = 0.f;
+  for (uint32_t k = ra; k < rb; ++k) {
+    const float2 q = sp[k];
+    sx += q.x;
+    sy += q.y;
+  }
+  for (uint32_t k = ha; k < hb; ++k) {
+    const float2 q = sp[k];
+    sx += q.x;
+    sy += q.y;
+  }
+  epilogue_k<float>(A, r, kd, ac, av * xr.x + bv * sx, av * xr.y + bv * sy);
+}
+
+// Per-warp staging of one tile's indices and weights in shared memory: the
+// st and hm short ranges are copied in aligned 16-byte pieces (cp.async, L2
+// only), so a range [a, b) occupies [a & ~(per - 1), (b + per - 1) & ~(per - 1))
+// of its array; a tile reads fewer than kEntWarp entries, so each buffer needs
+// at most kEntWarp + 4 * 16 / 2 slots of the narrowest type.
+constexpr int kStageCol = kEntWarp + 16;  // int32 slots
+template <int WT>
+struct TileStage {
+  int32_t col[kStageCol];
+  // bf16: at most kEntWarp + 32 halves; float: kEntWarp + 16 words
+  uint32_t w[WT == 1 ? (kEntWarp + 32) / 2 : kEntWarp + 16];
+};
+
+__device__ __forceinline__ void cp16(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Offsets of a tile's pieces inside its stage (entries of each type).
+struct StageMap {
+  uint32_t cs, ch, ws, wh;  // first staged slot of the st / hm range (col, w)
+  uint32_t hcol0, hw0;      // where the hm range starts in the stage
+};
+template <int WT>
+__device__ __forceinline__ StageMap stage_map(uint32_t s0, uint32_t s1, uint32_t h0) {
+  constexpr uint32_t wper = WT == 1 ? 8u : 4u;  // weights per 16 bytes
+  StageMap m;
+  const uint32_t ca = s0 & ~3u, cb = (s1 + 3u) & ~3u;
+  const uint32_t wa = s0 & ~(wper - 1u), wb = (s1 + wper - 1u) & ~(wper - 1u);
+  m.cs = s0 - ca;
+  m.ws = s0 - wa;
+  m.hcol0 = cb - ca;
+  m.hw0 = wb - wa;
+  m.ch = m.hcol0 + (h0 - (h0 & ~3u));
+  m.wh = m.hw0 + (h0 - (h0 & ~(wper - 1u)));
+  return m;
+}
+
+template <int WT>
+__device__ __forceinline__ void stage_tile(const StepArgs &A, const int4 d0, const int4 d1,
+                                           TileStage<WT> *st) {
+  constexpr uint32_t wper = WT == 1 ? 8u : 4u;
+  constexpr uint32_t wsz = WT == 1 ? 2u : 4u;
   const int lane = threadIdx.x & 31;
-  const int r0 = A.tile_row[t], r1 = A.tile_row[t + 1];
-  const uint32_t e0 = A.rp_s[r0] & kOffMask, e1 = A.rp_s[r1] & kOffMask;
-  const uint32_t n = e1 - e0;
-  for (uint32_t k0 = 0; k0 < n; k0 += 32 * kBatch) {
-    int c[kBatch];
-    float wv[kBatch];
-#pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint32_t k = k0 + q * 32 + lane;
-      c[q] = k < n ? __ldcs(A.col + e0 + k) : 0;
-      wv[q] = k < n ? wload<WT>(A.w, e0 + k) : 0.f;
+  const uint32_t s0 = (uint32_t)d0.y, s1 = (uint32_t)d1.y, h0 = (uint32_t)d0.z, h1 = (uint32_t)d1.z;
+  const uint32_t ca = s0 & ~3u, cb = (s1 + 3u) & ~3u;
+  const uint32_t ha = h0 & ~3u, hb = (h1 + 3u) & ~3u;
+  const uint32_t ncs = (cb - ca) >> 2, nch = h1 > h0 ? (hb - ha) >> 2 : 0u;
+  for (uint32_t i = lane; i < ncs + nch; i += 32) {
+    const int32_t *src = i < ncs ? A.scol + ca + 4u * i : A.hcol + ha + 4u * (i - ncs);
+    cp16(st->col + 4u * i, src);
+  }
+  const uint32_t wa = s0 & ~(wper - 1u), wb = (s1 + wper - 1u) & ~(wper - 1u);
+  const uint32_t hwa = h0 & ~(wper - 1u), hwb = (h1 + wper - 1u) & ~(wper - 1u);
+  const uint32_t nws = (wb - wa) / wper, nwh = h1 > h0 ? (hwb - hwa) / wper : 0u;
+  const char *sw = reinterpret_cast<const char *>(A.sw), *hw = reinterpret_cast<const char *>(A.hw);
+  char *dst = reinterpret_cast<char *>(st->w);
+  for (uint32_t i = lane; i < nws + nwh; i += 32) {
+    const char *src = i < nws ? sw + (size_t)(wa + wper * i) * wsz
+                              : hw + (size_t)(hwa + wper * (i - nws)) * wsz;
+    cp16(dst + 16u * i, src);
+  }
+}
+
+template <int WT>
+__device__ __forceinline__ float stage_w(const TileStage<WT> *st, uint32_t k) {
+  if (WT == 0) return __uint_as_float(st->w[k]);
+  const uint16_t h = reinterpret_cast<const uint16_t *>(st->w)[k];
+  return __uint_as_float((uint32_t)h << 16);
+}
+
+// One tile from its stage: gathers of x for every entry (all issued before
+// any use), products to the warp's slice, then row sums and epilogues.
+template <int WT, int MODE>
+__device__ __forceinline__ void warp_tile(const StepArgs &A, const int4 d0, const int4 d1,
+                                          const TileStage<WT> *st, float2 *sp) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = d0.x, r1 = d1.x;
+  const uint32_t s0 = (uint32_t)d0.y, h0 = (uint32_t)d0.z;
+  const uint32_t ns = (uint32_t)d1.y - s0, n = ns + ((uint32_t)d1.z - h0);
+  const bool two = A.hrp != nullptr;
+  const StageMap mp = stage_map<WT>(s0, (uint32_t)d1.y, h0);
+  // this lane's first row: pointers, coefficient, own value
+  const int r = r0 + lane;
+  uint32_t ra = 0, rb = 0, ha = 0, hb = 0;
+  float av = 0.f, bv = 0.f;
+  float2 xr = make_float2(0.f, 0.f);
+  uint8_t kd = 0;
+  double2 ac = make_double2(0.0, 0.0);
+  if (r < r1) {
+    ra = A.srp[r];
+    rb = A.srp[r + 1];
+    if (two) {
+      ha = A.hrp[r];
+      hb = A.hrp[r + 1];
     }
+    av = A.a[r];
+    if (MODE == MODE_GIFT) bv = A.b[r];
+    xr = A.x[r];
+    kd = A.nkind[r];
+    if (A.tap) ac = A.acc[r];
+  }
+  float2 xv[kPer];
+  const int nq = (int)((n + 31u) >> 5);  // warp-uniform
 #pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint32_t k = k0 + q * 32 + lane;
-      if (k < n) {
-        const float2 xv = __ldg(A.x + c[q]);
-        sp[k] = make_float2(wv[q] * xv.x, wv[q] * xv.y);
-      }
+  for (int q = 0; q < kPer; ++q) {
+    if (q >= nq) break;
+    const uint32_t k = q * 32 + lane;
+    int c = 0;
+    if (k < n) c = st->col[k < ns ? mp.cs + k : mp.ch + (k - ns)];
+    xv[q] = k < n ? __ldg(A.x + c) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    if (q >= nq) break;
+    const uint32_t k = q * 32 + lane;
+    if (k < n) {
+      const float wv = stage_w<WT>(st, k < ns ? mp.ws + k : mp.wh + (k - ns));
+      sp[k] = make_float2(wv * xv[q].x, wv * xv[q].y);
     }
   }
   __syncwarp();
-  const float bconst = MODE == MODE_HR ? (float)A.lam[1] : 0.f;
-  for (int r = r0 + lane; r < r1; r += 32) {
-    const uint32_t raw = A.rp_s[r];
-    if (raw & kHubFlag) continue;
-    const uint32_t a = (raw & kOffMask) - e0, b = (A.rp_s[r + 1] & kOffMask) - e0;
-    float sx = 0.f, sy = 0.f;
-    for (uint32_t k = a; k < b; ++k) {
-      const float2 q = sp[k];
-      sx += q.x;
-      sy += q.y;
-    }
-    const float av = A.a[r];
-    const float bv = MODE == MODE_HR ? bconst : A.b[r];
-    const float2 xv = A.x[r];
-    epilogue<float>(A, r, av * xv.x + bv * sx, av * xv.y + bv * sy);
+  if (MODE == MODE_HR) bv = (float)A.lam[1];
+  const uint32_t *skip = two ? A.hrp : A.srp;
+  if (r < r1 && !((two ? ha : ra) & kHubFlag))
+    tile_row_out<MODE>(A, r, sp, (ra & kOffMask) - s0, (rb & kOffMask) - s0,
+                       two ? (ha & kOffMask) - h0 + ns : 0u, two ? (hb & kOffMask) - h0 + ns : 0u,
+                       av, bv, xr, kd, ac);
+  for (int rr = r + 32; rr < r1; rr += 32) {
+    if (skip[rr] & kHubFlag) continue;
+    const uint32_t a2 = A.srp[rr] & kOffMask, b2 = A.srp[rr + 1] & kOffMask;
+    const uint32_t ha2 = two ? (A.hrp[rr] & kOffMask) - h0 + ns : 0u;
+    const uint32_t hb2 = two ? (A.hrp[rr + 1] & kOffMask) - h0 + ns : 0u;
+    tile_row_out<MODE>(A, rr, sp, a2 - s0, b2 - s0, ha2, hb2, A.a[rr],
+                       MODE == MODE_GIFT ? A.b[rr] : bv, A.x[rr], A.nkind[rr],
+                       A.tap ? A.acc[rr] : make_double2(0.0, 0.0));
   }
   __syncwarp();
 }
 
+template <int WT>
+__device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp, uint64_t b,
+                                            uint64_t e, const float2 *x, dfl &sx, dfl &sy) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t k0 = b; k0 < e; k0 += 32 * kChunkBatch) {
+    int cc[kChunkBatch];
+    float wv[kChunkBatch];
+#pragma unroll
+    for (int q = 0; q < kChunkBatch; ++q) {
+      const uint64_t k = k0 + q * 32 + lane;
+      cc[q] = k < e ? __ldcs(colp + k) : 0;
+      wv[q] = k < e ? wload<WT>(wp, k) : 0.f;
+    }
+    float2 xv[kChunkBatch];
+#pragma unroll
+    for (int q = 0; q < kChunkBatch; ++q) {
+      const uint64_t k = k0 + q * 32 + lane;
+      xv[q] = k < e ? __ldg(x + cc[q]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kChunkBatch; ++q) {
+      df_add_prod(sx, wv[q], xv[q].x);
+      df_add_prod(sy, wv[q], xv[q].y);
+    }
+  }
+}
+
+// A hub chunk covers positions [q0, q1) of the row's st piece followed by its
+// hm piece.
 template <int WT, int MODE>
 __device__ void warp_chunk(const StepArgs &A, int c) {
   const int lane = threadIdx.x & 31;
   const int l = A.chunk_lr[c];
   const int64_t v = A.lrow[l];
-  const uint64_t beg = A.lptr[l], end = A.lptr[l + 1];
   const int c0 = A.lchunk[l], nch = A.lchunk[l + 1] - c0;
-  const uint64_t cb = beg + (uint64_t)(c - c0) * kChunk;
-  const uint64_t ce = cb + kChunk < end ? cb + kChunk : end;
+  const uint64_t sl = A.lsl[l], hl = A.lhl[l];
+  const uint64_t q0 = (uint64_t)(c - c0) * kChunk;
+  const uint64_t q1 = q0 + kChunk < sl + hl ? q0 + kChunk : sl + hl;
   dfl sx{0.f, 0.f}, sy{0.f, 0.f};
-  for (uint64_t k0 = cb; k0 < ce; k0 += 32 * kBatch) {
-    int cc[kBatch];
-    float wv[kBatch];
-#pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint64_t k = k0 + q * 32 + lane;
-      cc[q] = k < ce ? __ldcs(A.col + k) : 0;
-      wv[q] = k < ce ? wload<WT>(A.w, k) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < kBatch; ++q) {
-      const uint64_t k = k0 + q * 32 + lane;
-      if (k < ce) {
-        const float2 xv = __ldg(A.x + cc[q]);
-        df_add_prod(sx, wv[q], xv.x);
-        df_add_prod(sy, wv[q], xv.y);
-      }
-    }
+  if (q0 < sl) chunk_piece<WT>(A.scol, A.sw, A.lsb[l] + q0, A.lsb[l] + (q1 < sl ? q1 : sl), A.x, sx, sy);
+  if (q1 > sl) {
+    const uint64_t hb = A.lhb[l];
+    chunk_piece<WT>(A.hcol, A.hw, hb + (q0 > sl ? q0 - sl : 0), hb + (q1 - sl), A.x, sx, sy);
   }
   sx = warp_sum_df(sx);
   sy = warp_sum_df(sy);
@@ -246,19 +396,58 @@ __device__ void warp_chunk(const StepArgs &A, int c) {
   }
 }
 
-constexpr int kSpmmThreads = 256;
+constexpr int kSpmmThreads = 128;
+constexpr int kSpmmWarps = kSpmmThreads / 32;
+constexpr int kSpmmBlocksPerSm = 6;
 
+// Warp w of the grid takes units w, w + nwarps, ...: its hub chunks first,
+// then its tiles as a two-stage pipeline (stage the next tile while the
+// current one is gathered and summed; descriptors one tile further ahead).
 template <int WT, int MODE>
-__global__ void __launch_bounds__(kSpmmThreads) k_spmm(StepArgs A) {
-  __shared__ float2 sp_all[kSpmmThreads / 32][kEntWarp];
-  float2 *sp = sp_all[threadIdx.x >> 5];
+__global__ void __launch_bounds__(kSpmmThreads, kSpmmBlocksPerSm) k_spmm(StepArgs A) {
+  __shared__ __align__(16) TileStage<WT> stage_all[kSpmmWarps][2];
+  __shared__ float2 sp_all[kSpmmWarps][kEntWarp];
+  const int wid = threadIdx.x >> 5;
+  float2 *sp = sp_all[wid];
+  TileStage<WT> *stg = stage_all[wid];
   const long long nunits = (long long)A.nchunks + A.ntiles;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long u = gw; u < nunits; u += nw) {
-    if (u < A.nchunks) warp_chunk<WT, MODE>(A, (int)u);
-    else warp_tile<WT, MODE>(A, (int)(u - A.nchunks), sp);
+  long long u = gw;
+  for (; u < A.nchunks; u += nw) warp_chunk<WT, MODE>(A, (int)u);
+  if (u >= nunits) return;
+  long long t = u - A.nchunks;
+  int4 c0 = __ldg(A.tdesc + t), c1 = __ldg(A.tdesc + t + 1);
+  stage_tile<WT>(A, c0, c1, &stg[0]);
+  cp_commit();
+  long long tn = t + nw;
+  int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+  if (tn < A.ntiles) {
+    n0 = __ldg(A.tdesc + tn);
+    n1 = __ldg(A.tdesc + tn + 1);
   }
+  int cur = 0;
+  while (true) {
+    if (tn < A.ntiles) stage_tile<WT>(A, n0, n1, &stg[cur ^ 1]);
+    cp_commit();
+    const long long tnn = tn + nw;
+    int4 f0 = make_int4(0, 0, 0, 0), f1 = f0;
+    if (tnn < A.ntiles) {
+      f0 = __ldg(A.tdesc + tnn);
+      f1 = __ldg(A.tdesc + tnn + 1);
+    }
+    cp_wait_prev();
+    __syncwarp();
+    warp_tile<WT, MODE>(A, c0, c1, &stg[cur], sp);
+    if (tn >= A.ntiles) break;
+    c0 = n0;
+    c1 = n1;
+    n0 = f0;
+    n1 = f1;
+    tn = tnn;
+    cur ^= 1;
+  }
+  cp_wait_all();
 }
 
 // ------------------------------------------------------------- helpers
@@ -322,19 +511,21 @@ __global__ void k_clamp(int64_t N, const uint8_t *nkind, const float2 *fixedp,
 }
 
 // GiFt per-node coefficients of one sigma: a = sigma/d, b = 1/d, band scale
-// sqrt(d), and u0 = (g - centre)/sqrt(d), d = D_vv + sigma.
+// sqrt(d), and u0 = (g - centre)/sqrt(d), d = D_vv + sigma.  d is formed in
+// FP64 and the rest in FP32, the precision the sparse products run in.
 __global__ void k_gift_prep(int64_t N, int64_t Nst, const double *sdeg, double sigma,
                             const float2 *g, double cx, double cy, float *a, float *b,
                             float *sq, float2 *u0) {
+  const float sf = (float)sigma;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
-    double d = (v < Nst ? sdeg[v] : 0.0) + sigma;
-    double r = sqrt(d);
-    a[v] = (float)(sigma / d);
-    b[v] = (float)(1.0 / d);
-    sq[v] = (float)r;
-    float2 q = g[v];
-    u0[v] = make_float2((float)(((double)q.x - cx) / r), (float)(((double)q.y - cy) / r));
+    const float d = (float)((v < Nst ? sdeg[v] : 0.0) + sigma);
+    const float r = sqrtf(d);
+    a[v] = sf / d;
+    b[v] = 1.0f / d;
+    sq[v] = r;
+    const float2 q = g[v];
+    u0[v] = make_float2((float)((double)q.x - cx) / r, (float)((double)q.y - cy) / r);
   }
 }
 
@@ -370,31 +561,38 @@ __global__ void k_acc_final(int64_t N, const double2 *acc, double cx, double cy,
 }
 
 // --------------------------------------------------------------- drivers
-static void fill_matrix(StepArgs &A, const SpMat &m) {
-  A.rp_s = P<uint32_t>(m.rp_s);
-  A.col = P<int32_t>(m.col);
-  A.w = m.w.p;
-  A.tile_row = P<int32_t>(m.tile_row);
+// st gives every row's static part; units and hub rows come from the applied
+// matrix (hm with hint parts for the refinement filter, st for GiFt).
+static void fill_matrix(StepArgs &A, const SpMat &st, const SpMat *hm) {
+  const SpMat &m = hm ? *hm : st;
+  A.srp = P<uint32_t>(st.rp_s);
+  A.scol = P<int32_t>(st.col);
+  A.sw = st.w.p;
+  A.hrp = hm ? P<uint32_t>(hm->rp_s) : nullptr;
+  A.hcol = hm ? P<int32_t>(hm->col) : nullptr;
+  A.hw = hm ? hm->w.p : nullptr;
+  A.tdesc = P<int4>(m.tdesc);
   A.ntiles = m.ntiles;
   A.lrow = P<int32_t>(m.lrow);
-  A.lptr = P<uint64_t>(m.lptr);
+  A.lsb = P<uint64_t>(m.lsb);
+  A.lhb = P<uint64_t>(m.lhb);
+  A.lsl = P<uint32_t>(m.lsl);
+  A.lhl = P<uint32_t>(m.lhl);
   A.lchunk = P<int32_t>(m.lchunk);
   A.chunk_lr = P<int32_t>(m.chunk_lr);
   A.nchunks = m.nchunks;
-  A.longidx = P<int32_t>(m.longidx);
   A.part = const_cast<double *>(P<double>(m.part));
   A.tick = const_cast<int32_t *>(P<int32_t>(m.tick));
 }
 
 // Algorithmic bytes of one sparse product over (x, y) pairs: indices and
 // weights once, row pointers, x read, y written, one coefficient per row.
-static double spmm_bytes(const SpMat &m, int wdtype) {
-  const double nnz = (double)(m.nnz_s + m.nnz_l), N = (double)m.N;
+static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
 template <int MODE>
-static cudaError_t launch_step(const StepArgs &A, const SpMat &m, int wdtype, cudaStream_t s) {
+static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s) {
   const long long nunits = (long long)A.nchunks + A.ntiles;
   static int nsm = 0;
   if (!nsm) {
@@ -403,11 +601,21 @@ static cudaError_t launch_step(const StepArgs &A, const SpMat &m, int wdtype, cu
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  const long long want = (nunits + kSpmmThreads / 32 - 1) / (kSpmmThreads / 32);
-  const int grid = (int)(want < 8LL * nsm ? (want > 0 ? want : 1) : 8LL * nsm);
+  // one wave of resident blocks (units are dealt to warps statically)
+  static int occ[2] = {0, 0};
+  const int wi = wdtype == PL_W_BF16 ? 1 : 0;
+  if (!occ[wi]) {
+    int b = 0;
+    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm<1, MODE>, kSpmmThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm<0, MODE>, kSpmmThreads, 0);
+    occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
+  }
+  const long long want = (nunits + kSpmmWarps - 1) / kSpmmWarps;
+  const long long cap = (long long)occ[wi] * nsm;
+  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   const bool prof = prof_on();
-  if (prof) prof_begin(s, MODE == MODE_HR ? PROF_HR : PROF_GIFT, spmm_bytes(m, wdtype));
-  if (wdtype == PL_W_BF16) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
+  if (prof) prof_begin(s, MODE == MODE_HR ? PROF_HR : PROF_GIFT, bytes);
+  if (wi) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
   else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
   note_launch();
   if (prof) prof_end(s);
@@ -467,7 +675,8 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
   TRY(ensure(g->xa, (size_t)N * 8 + 64));
   float *ga = P<float>(g->gsc), *gb = ga + N, *gq = gb + N;
   StepArgs A{};
-  fill_matrix(A, g->st);
+  fill_matrix(A, g->st, nullptr);
+  const double bytes = spmm_bytes((double)(g->st.nnz_s + g->st.nnz_l), (double)N, g->wdtype);
   fill_nodes(A, g);
   A.acc = P<double2>(g->acc);
   A.tscale = gq;
@@ -508,7 +717,7 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
       A.cx = A.fin ? cx : 0.0;
       A.cy = A.fin ? cy : 0.0;
       A.pin = 0;
-      TRY(launch_step<MODE_GIFT>(A, g->st, g->wdtype, s));
+      TRY(launch_step<MODE_GIFT>(A, bytes, g->wdtype, s));
       any = true;
       float2 *tt = x;
       x = y;
@@ -548,7 +757,9 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   }
   const SpMat &m = g->hm;
   StepArgs A{};
-  fill_matrix(A, m);
+  fill_matrix(A, g->st, &m);
+  const double bytes = spmm_bytes((double)(g->st.nnz_s + g->st.nnz_l + m.nnz_s + m.nnz_l),
+                                  (double)N, g->wdtype);
   fill_nodes(A, g);
   A.a = P<float>(m.c32);
   A.b = nullptr;
@@ -578,7 +789,7 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
           A.alpha = p->tap_alpha[j];
         }
     A.fin = t == kmax;
-    TRY(launch_step<MODE_HR>(A, m, g->wdtype, s));
+    TRY(launch_step<MODE_HR>(A, bytes, g->wdtype, s));
     x = bufs[t & 1];
   }
   return PL_OK;

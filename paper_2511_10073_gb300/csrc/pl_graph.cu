@@ -159,13 +159,76 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
 // clique net of d+1 nodes), filled from the host's IEEE division.
 __constant__ double c_recip[16];
 
-__device__ __forceinline__ double lattice_weight(long long val) {
-  if (val > 0) {
-    if (kLattice % val == 0 && kLattice / val <= 15) return c_recip[kLattice / val];
-    return __ddiv_rn((double)val, (double)kLattice);
+// Weight of a merged entry from its lattice value: val > 0 is a sum of clique
+// lattice units (weight val / kLattice), val < 0 is -p for a star edge of a
+// p-node net (weight p / (p - 1)).  A single clique edge (val = kLattice / d,
+// d <= 15) takes the table; every other value needs an IEEE division.
+__device__ __forceinline__ bool lattice_easy(long long val, double *w) {
+  if (val >= kLattice / 15 && val <= kLattice) {
+    const int d = (int)((float)kLattice / (float)val + 0.5f);
+    if (d >= 1 && d <= 15 && (long long)d * val == kLattice) {
+      *w = c_recip[d];
+      return true;
+    }
   }
-  long long p = -val;
+  return false;
+}
+__device__ __forceinline__ double lattice_div(long long val) {
+  if (val > 0) return __ddiv_rn((double)val, (double)kLattice);
+  const long long p = -val;
   return __ddiv_rn((double)p, (double)(p - 1));
+}
+
+// Table weights in place of the merged values (warp per 32 rows, lanes over a
+// row's entries); entries that need a division are listed, so that the
+// divisions run together in k_static_div instead of stalling whole warps.
+__global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, int64_t *mval,
+                                                        const int64_t *srp, int64_t Nst,
+                                                        uint32_t *list,
+                                                        unsigned long long *nlist) {
+  const int lane = threadIdx.x & 31;
+  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v0 = wg * 32; v0 < Nst; v0 += nwarp * 32) {
+    const long long v = v0 + lane;
+    long long src = 0;
+    int m = 0;
+    if (v < Nst) {
+      src = row_off[v];
+      m = (int)(srp[v + 1] - srp[v]);
+    }
+    const int nv = (int)min((long long)32, Nst - v0);
+    for (int j = 0; j < nv; ++j) {
+      const long long sj = __shfl_sync(0xffffffffu, src, j);
+      const int mj = __shfl_sync(0xffffffffu, m, j);
+      for (int k0 = 0; k0 < mj; k0 += 32) {
+        const int k = k0 + lane;
+        bool hard = false;
+        if (k < mj) {
+          double w;
+          if (lattice_easy(mval[sj + k], &w)) reinterpret_cast<double *>(mval)[sj + k] = w;
+          else hard = true;
+        }
+        const unsigned hm = __ballot_sync(0xffffffffu, hard);
+        if (hm) {
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(nlist, (unsigned long long)__popc(hm));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (hard) list[base + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)(sj + k);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_static_div(const uint32_t *list, const unsigned long long *nlist,
+                             int64_t *mval) {
+  const unsigned long long n = *nlist;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t k = list[i];
+    reinterpret_cast<double *>(mval)[k] = lattice_div(mval[k]);
+  }
 }
 
 __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
@@ -177,14 +240,14 @@ __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
   return __double2float_rn(w);
 }
 
-// Final static CSR.  A warp takes 32 consecutive rows: for each row the warp
-// converts the merged lattice values into FP64 weights once (kept in place of
-// the values) and writes columns and stored weights; then each lane forms its
-// own row's static degree and, for cells, baseWeight (FP64 mean of the exact
-// weights, added in column order).
+// Final static CSR from the FP64 weights (in place of the merged values).  A
+// warp takes 32 consecutive rows: for each row the warp writes columns and
+// stored weights and reduces the row's static degree (double-float, over the
+// stored weights); then each lane forms, for a cell, baseWeight (FP64 mean of
+// the exact weights, added in column order).
 __global__ void __launch_bounds__(256) k_static_compact(
-    const int64_t *row_off, const int32_t *mcol, int64_t *mval, const int64_t *srp, int64_t Nst,
-    int32_t C, int wdtype, const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
+    const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
+    int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
     uint8_t *hflag, double *sdeg) {
   const int lane = threadIdx.x & 31;
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -199,31 +262,30 @@ __global__ void __launch_bounds__(256) k_static_compact(
       dst = srp[v];
       m = (int)(srp[v + 1] - dst);
     }
+    dfl dl{0.f, 0.f};
     const int nv = (int)min((long long)32, Nst - v0);
     for (int j = 0; j < nv; ++j) {
       const long long sj = __shfl_sync(0xffffffffu, src, j), dj = __shfl_sync(0xffffffffu, dst, j);
       const int mj = __shfl_sync(0xffffffffu, m, j);
-      double *w64 = reinterpret_cast<double *>(mval) + sj;
+      const double *w64 = reinterpret_cast<const double *>(mval) + sj;
+      dfl d{0.f, 0.f};
       for (int k = lane; k < mj; k += 32) {
-        double w = lattice_weight(mval[sj + k]);
-        w64[k] = w;
+        const double w = w64[k];
         scol[dj + k] = mcol[sj + k];
         uint16_t hb = 0;
         float f = stored(w, wdtype, &hb);
         if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dj + k] = hb;
         else reinterpret_cast<float *>(sw)[dj + k] = f;
+        df_add(d, f);
       }
+      d = warp_sum_df(d);
+      if (lane == j) dl = d;
     }
     __syncwarp();
     if (!ok) continue;
-    const double *w64 = reinterpret_cast<const double *>(mval) + src;
-    dfl d{0.f, 0.f};
-    for (int k = 0; k < m; ++k) {
-      uint16_t hb;
-      df_add(d, stored(w64[k], wdtype, &hb));
-    }
-    sdeg[v] = df_to_d(d);
+    sdeg[v] = df_to_d(dl);
     if (v < C) {
+      const double *w64 = reinterpret_cast<const double *>(mval) + src;
       double s = 0.0;
       for (int k = 0; k < m; ++k) s = __dadd_rn(s, w64[k]);
       double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
@@ -333,17 +395,20 @@ __global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const int3
 }
 
 // Macro lookup grid: every macro is listed in the grid buckets its rectangle,
-// grown by half the largest movable cell and one bucket of margin, touches.
+// grown by half the largest movable cell, touches, widened by mgx / mgy bucket
+// units: more than the FP32 error of a cell centre's bucket coordinate, so the
+// bucket of every overlapping cell lists the macro.
 __device__ __forceinline__ void macro_bucket_range(int m, const int32_t *macro_cell,
                                                    const float *cw, const float *ch,
                                                    const float *fx, const float *fy, float wmax,
                                                    float hmax, double xl, double yl, double sx,
-                                                   double sy, int gnx, int gny, int *k) {
+                                                   double sy, double mgx, double mgy, int gnx,
+                                                   int gny, int *k) {
   int c = macro_cell[m];
   double ex = 0.5 * ((double)cw[c] + (double)wmax) * (1.0 + 1e-6) + 1e-6;
   double ey = 0.5 * ((double)ch[c] + (double)hmax) * (1.0 + 1e-6) + 1e-6;
-  double a0 = floor(((double)fx[c] - ex - xl) * sx) - 1.0, a1 = floor(((double)fx[c] + ex - xl) * sx) + 1.0;
-  double b0 = floor(((double)fy[c] - ey - yl) * sy) - 1.0, b1 = floor(((double)fy[c] + ey - yl) * sy) + 1.0;
+  double a0 = floor(((double)fx[c] - ex - xl) * sx - mgx), a1 = floor(((double)fx[c] + ex - xl) * sx + mgx);
+  double b0 = floor(((double)fy[c] - ey - yl) * sy - mgy), b1 = floor(((double)fy[c] + ey - yl) * sy + mgy);
   k[0] = (int)fmin(fmax(a0, 0.0), (double)(gnx - 1));
   k[1] = (int)fmin(fmax(a1, 0.0), (double)(gnx - 1));
   k[2] = (int)fmin(fmax(b0, 0.0), (double)(gny - 1));
@@ -352,11 +417,12 @@ __device__ __forceinline__ void macro_bucket_range(int m, const int32_t *macro_c
 
 __global__ void k_grid_count(int32_t Mm, const int32_t *macro_cell, const float *cw,
                              const float *ch, const float *fx, const float *fy, float wmax,
-                             float hmax, double xl, double yl, double sx, double sy, int gnx,
-                             int gny, int32_t *cnt) {
+                             float hmax, double xl, double yl, double sx, double sy, double mgx,
+                             double mgy, int gnx, int gny, int32_t *cnt) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mm; m += gridDim.x * blockDim.x) {
     int k[4];
-    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, gnx, gny, k);
+    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, mgx, mgy, gnx,
+                       gny, k);
     for (int y = k[2]; y <= k[3]; ++y)
       for (int x = k[0]; x <= k[1]; ++x) atomicAdd(&cnt[(long long)y * gnx + x], 1);
   }
@@ -364,13 +430,26 @@ __global__ void k_grid_count(int32_t Mm, const int32_t *macro_cell, const float 
 
 __global__ void k_grid_fill(int32_t Mm, const int32_t *macro_cell, const float *cw,
                             const float *ch, const float *fx, const float *fy, float wmax,
-                            float hmax, double xl, double yl, double sx, double sy, int gnx,
-                            int gny, int32_t *cur, uint32_t *list) {
+                            float hmax, double xl, double yl, double sx, double sy, double mgx,
+                            double mgy, int gnx, int gny, int32_t *cur, uint32_t *list) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mm; m += gridDim.x * blockDim.x) {
     int k[4];
-    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, gnx, gny, k);
+    macro_bucket_range(m, macro_cell, cw, ch, fx, fy, wmax, hmax, xl, yl, sx, sy, mgx, mgy, gnx,
+                       gny, k);
     for (int y = k[2]; y <= k[3]; ++y)
       for (int x = k[0]; x <= k[1]; ++x) list[atomicAdd(&cur[(long long)y * gnx + x], 1)] = m;
+  }
+}
+
+// Centre and size of each macro listed in the lookup grid, beside its id, so
+// that a lookup reads the list and the geometry in one step.
+__global__ void k_grid_geo(long long n, const uint32_t *list, const int32_t *macro_cell,
+                           const float *fx, const float *fy, const float *cw, const float *ch,
+                           float4 *geo) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = macro_cell[list[i]];
+    geo[i] = make_float4(fx[c], fy[c], cw[c], ch[c]);
   }
 }
 
@@ -574,6 +653,21 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     for (int d = 1; d < 16; ++d) rc[d] = 1.0 / (double)d;
     TRY(cudaMemcpyToSymbolAsync(c_recip, rc, sizeof(rc), 0, cudaMemcpyHostToDevice, s));
   }
+  {
+    // keys are consumed by the merge: their buffer holds the division list
+    if ((unsigned long long)npre >= (1ull << 32)) {
+      set_error("static graph too large (%lld entries before merging)", (long long)npre);
+      return PL_ERR_UNSUPPORTED;
+    }
+    unsigned long long *nlist = reinterpret_cast<unsigned long long *>(keys);
+    uint32_t *list = reinterpret_cast<uint32_t *>(keys + 2);
+    TRY(cudaMemsetAsync(nlist, 0, 8, s));
+    k_static_weights<<<grid_for(Nst * 32, 256), 256, 0, s>>>(row_off, mval, P<int64_t>(g->srp),
+                                                            Nst, list, nlist);
+    note_launch();
+    k_static_div<<<152 * 8, 256, 0, s>>>(list, nlist, mval);
+    note_launch();
+  }
   k_static_compact<<<grid_for(Nst * 32, 256), 256, 0, s>>>(
       row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
       P<int32_t>(g->scol), g->sw.p, P<double>(g->base_w), P<uint8_t>(g->hflag), P<double>(g->sdeg));
@@ -618,13 +712,18 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   g->gny = (int)fmin(2048.0, fmax(1.0, ceil((g->yh - g->yl) / gs)));
   const long long ng = (long long)g->gnx * g->gny;
   const double sx = (double)g->gnx / (g->xh - g->xl), sy = (double)g->gny / (g->yh - g->yl);
+  // FP32 bucket coordinate of a centre: a few half-ulps of the coordinate and
+  // of the bucket index, far below these margins
+  const double u24 = 1.0 / 16777216.0;
+  const double mgx = 0.01 + 8.0 * u24 * (fmax(fabs(g->xl), fabs(g->xh)) * sx + g->gnx);
+  const double mgy = 0.01 + 8.0 * u24 * (fmax(fabs(g->yl), fabs(g->yh)) * sy + g->gny);
   TRY(ensure(g->gptr, (size_t)(ng + 1) * 8 + 16));
   TRY(ensure(g->tmp[4], (size_t)(ng + 1) * 4 + 256));
   int32_t *gcnt = P<int32_t>(g->tmp[4]);
   TRY(cudaMemsetAsync(gcnt, 0, (size_t)(ng + 1) * 4, s));
   k_grid_count<<<grid_for(g->Mm, 128), 128, 0, s>>>(
       g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
-      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, g->gnx, g->gny, gcnt);
+      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, mgx, mgy, g->gnx, g->gny, gcnt);
   note_launch();
   int64_t *gptr = P<int64_t>(g->gptr);
   TRY(scan_tmp(g, ng, &stmp));
@@ -642,12 +741,20 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   note_launch();
   k_grid_fill<<<grid_for(g->Mm, 128), 128, 0, s>>>(
       g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
-      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, g->gnx, g->gny, gcur,
+      P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, mgx, mgy, g->gnx, g->gny, gcur,
       P<uint32_t>(g->glist));
   note_launch();
   TRY(ensure(g->tmp[3], segsort_tmp_bytes(ng, nreg, 4)));
   TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->glist), gptr, ng, nreg, nullptr,
                                            nullptr, nullptr, g->tmp[3].p, s)));
+  TRY(ensure(g->ggeo, (size_t)nreg * 16 + 16));
+  if (nreg) {
+    k_grid_geo<<<grid_for(nreg, 256), 256, 0, s>>>(nreg, P<uint32_t>(g->glist),
+                                                   P<int32_t>(g->macro_cell), P<float>(g->cfx),
+                                                   P<float>(g->cfy), P<float>(g->cw),
+                                                   P<float>(g->ch), P<float4>(g->ggeo));
+    note_launch();
+  }
   g->gsz = gs;
   g->gsx = sx;
   g->gsy = sy;

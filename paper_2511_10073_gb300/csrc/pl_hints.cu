@@ -23,12 +23,14 @@ namespace pl {
     if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
   } while (0)
 
-constexpr int kMaxWin = 31;  // detection window at most 31 x 31 bins
+constexpr int kMaxWin = 31;  // detection window at most 31 x 31 bins (a window row fits a warp)
 
 struct HintGeo {
   float xlf, ylf, sxf, syf;      // bin decision: floor((x - xl) * sx)
   float gxf, gyf, gsxf, gsyf;    // macro grid bucket of a centre
   double xl, yl, wb, hb, iwb2, ihb2;  // bin centres; 2 / w_b, 2 / h_b
+  float xlh, xll, ylh, yll;          // x_l, y_l as double-floats
+  float iwh, iwl, ihh, ihl;          // 2 / w_b, 2 / h_b as double-floats
   int nbx, nby, hx, hy, gnx, gny;
   int32_t C, Pm, S, Mm;
   int64_t Nst, mv0, bn0, N;
@@ -114,9 +116,9 @@ __device__ __forceinline__ void copy_w(void *dst, const void *src, int wdtype, u
 // --------------------------------------------------------- H1: cells
 __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
                              const uint8_t *hflag, const float *cw, const float *ch,
-                             const float *fx, const float *fy, const int32_t *macro_cell,
-                             const int64_t *gptr, const uint32_t *glist, int32_t *cell_bin,
-                             int32_t *n_ovl, int32_t *bcnt, int32_t *mcnt, int *status) {
+                             const int64_t *gptr, const uint32_t *glist, const float4 *ggeo,
+                             int32_t *cell_bin, int32_t *n_ovl, int32_t *bcnt, int32_t *mcnt,
+                             int *status) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
     if (ckind[i] != 0) {
       cell_bin[i] = -1;
@@ -137,12 +139,12 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
     if (hint) {
       int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
       long long k = (long long)ky * G.gnx + kx;
+      const float cwi = cw[i], chi = ch[i];
       for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
-        int m = (int)glist[q];
-        int c = macro_cell[m];
-        if (overlaps(p.x, p.y, cw[i], ch[i], fx[c], fy[c], cw[c], ch[c])) {
+        const float4 mg = ggeo[q];
+        if (overlaps(p.x, p.y, cwi, chi, mg.x, mg.y, mg.z, mg.w)) {
           ++n;
-          atomicAdd(&mcnt[m], 1);
+          atomicAdd(&mcnt[glist[q]], 1);
         }
       }
     }
@@ -154,20 +156,19 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
 // sorted by cell id afterwards.
 __global__ void k_macro_scatter(HintGeo G, const float2 *xy, const uint8_t *ckind,
                                 const uint8_t *hflag, const float *cw, const float *ch,
-                                const float *fx, const float *fy, const int32_t *macro_cell,
-                                const int64_t *gptr, const uint32_t *glist, int32_t *mcur,
-                                uint32_t *mlist) {
+                                const int64_t *gptr, const uint32_t *glist, const float4 *ggeo,
+                                int32_t *mcur, uint32_t *mlist) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
     if (ckind[i] != 0 || !hflag[i]) continue;
     float2 p = xy[i];
     if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
     int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
     long long k = (long long)ky * G.gnx + kx;
+    const float cwi = cw[i], chi = ch[i];
     for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
-      int m = (int)glist[q];
-      int c = macro_cell[m];
-      if (overlaps(p.x, p.y, cw[i], ch[i], fx[c], fy[c], cw[c], ch[c]))
-        mlist[atomicAdd(&mcur[m], 1)] = (uint32_t)i;
+      const float4 mg = ggeo[q];
+      if (overlaps(p.x, p.y, cwi, chi, mg.x, mg.y, mg.z, mg.w))
+        mlist[atomicAdd(&mcur[glist[q]], 1)] = (uint32_t)i;
     }
   }
 }
@@ -258,6 +259,8 @@ __device__ __forceinline__ double cell_area(const float *cw, const float *ch, ui
   return __dmul_rn((double)cw[i], (double)ch[i]);
 }
 
+constexpr int kDensStage = 4096;  // cell areas staged per pass (a multiple of 64)
+
 __global__ void __launch_bounds__(256) k_bin_density(HintGeo G, const int64_t *boff,
                                                      const uint32_t *blist, const float *cw,
                                                      const float *ch, const double *amac,
@@ -265,11 +268,36 @@ __global__ void __launch_bounds__(256) k_bin_density(HintGeo G, const int64_t *b
                                                      LevelBufs lv, double *Db, double *Cb,
                                                      double *phi, float *phif, int64_t *hub_len) {
   const int NB = G.nbx * G.nby;
+  __shared__ double sa[kDensStage];
   for (int b = blockIdx.x; b < NB; b += gridDim.x) {
     const int64_t s0 = boff[2 * b];
     int64_t st = s0, len = boff[2 * b + 2] - s0;
     const double *prev = nullptr;
     int level = 0;
+    if (len > 64) {
+      // level 0: cell areas staged in shared memory by all threads (coalesced
+      // list reads, independent gathers), then one thread per 64-block
+      const int64_t nblk = (len + 63) / 64, ost = st / 64 + b;
+      double *out = lv.base[0];
+      for (int64_t c0 = 0; c0 < len; c0 += kDensStage) {
+        const int cl = (int)min((int64_t)kDensStage, len - c0);
+        for (int t = threadIdx.x; t < cl; t += blockDim.x)
+          sa[t] = cell_area(cw, ch, blist[s0 + c0 + t]);
+        __syncthreads();
+        const int nb = (cl + 63) / 64;
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+          double acc = 0.0;
+          const int k1 = min(cl, 64 * j + 64);
+          for (int k = 64 * j; k < k1; ++k) acc = __dadd_rn(acc, sa[k]);
+          out[ost + c0 / 64 + j] = acc;
+        }
+        __syncthreads();
+      }
+      prev = out;
+      st = ost;
+      len = nblk;
+      level = 1;
+    }
     while (len > 64) {
       const int64_t nblk = (len + 63) / 64, ost = st / 64 + b;
       double *out = lv.base[level];
@@ -319,36 +347,52 @@ __device__ __forceinline__ int win_count(int bx, int by, const HintGeo &G) {
   return nx * ny;
 }
 
+// Per-row lengths of a split matrix.  Static mode: the st rows (hub when
+// longer than kLong).  Hint mode: the hm rows; a row is a hub row when it is a
+// virtual node or its static plus hint entries exceed kLong.  klen is what a
+// tile reads of the row (st short part + hm short part), clen the length the
+// hub chunks cover (st part + hm part).
 __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const uint8_t *hflag,
                           const int32_t *cell_bin, const int32_t *n_ovl, const int64_t *moff,
-                          const int64_t *hub_len, uint32_t *slen, uint64_t *llen,
-                          uint8_t *lflag) {
+                          const int64_t *hub_len, uint32_t *slen, uint64_t *llen, uint8_t *lflag,
+                          uint32_t *klen, uint64_t *clen) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.N;
        v += (long long)gridDim.x * blockDim.x) {
-    long long len = v < G.Nst ? srp[v + 1] - srp[v] : 0;
-    bool hub = false;
-    if (with_hints) {
-      if (v < G.C && hflag[v]) {
-        int b = cell_bin[v];
-        len += n_ovl[v] + win_count(b % G.nbx, b / G.nbx, G);
-      } else if (v >= G.mv0 && v < G.bn0) {
-        len += moff[v - G.mv0 + 1] - moff[v - G.mv0];
-        hub = true;
-      } else if (v >= G.bn0) {
-        len += hub_len[v - G.bn0];
-        hub = true;
-      }
+    const long long sl = v < G.Nst ? srp[v + 1] - srp[v] : 0;
+    if (!with_hints) {
+      const bool hub = sl > kLong;
+      slen[v] = hub ? 0u : (uint32_t)sl;
+      llen[v] = hub ? (uint64_t)sl : 0ull;
+      lflag[v] = hub ? 1 : 0;
+      klen[v] = hub ? 0u : (uint32_t)sl;
+      clen[v] = hub ? (uint64_t)sl : 0ull;
+      continue;
     }
-    if (len > kLong) hub = true;
-    slen[v] = hub ? 0u : (uint32_t)len;
-    llen[v] = hub ? (uint64_t)len : 0ull;
+    long long hl = 0;
+    bool virt = false;
+    if (v < G.C && hflag[v]) {
+      int b = cell_bin[v];
+      hl = n_ovl[v] + win_count(b % G.nbx, b / G.nbx, G);
+    } else if (v >= G.mv0 && v < G.bn0) {
+      hl = moff[v - G.mv0 + 1] - moff[v - G.mv0];
+      virt = true;
+    } else if (v >= G.bn0) {
+      hl = hub_len[v - G.bn0];
+      virt = true;
+    }
+    const bool hub = virt || sl + hl > kLong;
+    slen[v] = hub ? 0u : (uint32_t)hl;
+    llen[v] = hub ? (uint64_t)hl : 0ull;
     lflag[v] = hub ? 1 : 0;
+    klen[v] = (uint32_t)((sl <= kLong ? sl : 0) + (hub ? 0 : hl));
+    clen[v] = hub ? (uint64_t)(sl + hl) : 0ull;
   }
 }
 
 __global__ void k_layout_long(int64_t N, const uint8_t *lflag, const int32_t *lscan,
-                              const uint64_t *lpos, uint64_t nnz_s, int32_t *lrow, uint64_t *lptr,
-                              int32_t *longidx, int32_t *nchunk_of) {
+                              const uint64_t *lpos, const uint64_t *clen, uint64_t nnz_s,
+                              int32_t *lrow, uint64_t *lptr, int32_t *longidx,
+                              int32_t *nchunk_of) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
     if (lflag[v]) {
@@ -356,7 +400,7 @@ __global__ void k_layout_long(int64_t N, const uint8_t *lflag, const int32_t *ls
       lrow[li] = (int32_t)v;
       lptr[li] = nnz_s + lpos[v];
       longidx[v] = li;
-      uint64_t len = lpos[v + 1] - lpos[v];
+      const uint64_t len = clen[v];
       nchunk_of[li] = len == 0 ? 1 : (int32_t)((len + kChunk - 1) / kChunk);
     } else {
       longidx[v] = -1;
@@ -389,10 +433,37 @@ __global__ void k_u64_to_u32(const uint64_t *a, uint32_t *b, long long n) {
     b[i] = (uint32_t)a[i];
 }
 
-// First row owned by each tile.  Row r has key rp_s[r] + r (entries and rows
-// before it); tile t owns the rows with keys in [t*kTile, (t+1)*kTile), so a
-// tile holds at most kTile rows and fewer than kTile + kLong entries.
-__global__ void k_tiles(const uint32_t *rp_s, int64_t N, int32_t ntiles, int32_t *tile_row) {
+// st and hm pieces of every hub row (see SpMat).  Static matrix: its own hub
+// region only.  Hint matrix: the row's st part (short or hub region of st) and
+// its hm hub part.
+__global__ void k_hub_desc(int32_t nlong, int with_hints, const int32_t *lrow,
+                           const uint64_t *lptr, const int64_t *srp, int64_t Nst,
+                           const uint32_t *st_rp, const int32_t *st_longidx,
+                           const uint64_t *st_lptr, uint64_t *lsb, uint32_t *lsl, uint64_t *lhb,
+                           uint32_t *lhl) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlong; l += gridDim.x * blockDim.x) {
+    if (!with_hints) {
+      lsb[l] = lptr[l];
+      lsl[l] = (uint32_t)(lptr[l + 1] - lptr[l]);
+      lhb[l] = 0;
+      lhl[l] = 0;
+      continue;
+    }
+    const int64_t v = lrow[l];
+    const long long sl = v < Nst ? srp[v + 1] - srp[v] : 0;
+    const int sli = v < Nst ? st_longidx[v] : -1;
+    lsb[l] = sli >= 0 ? st_lptr[sli] : (uint64_t)(st_rp[v] & kOffMask);
+    lsl[l] = (uint32_t)sl;
+    lhb[l] = lptr[l];
+    lhl[l] = (uint32_t)(lptr[l + 1] - lptr[l]);
+  }
+}
+
+// First row owned by each tile.  Row r has key keys[r] + r (entries a tile
+// reads and rows before it); tile t owns the rows with keys in [t*kTile,
+// (t+1)*kTile), so a tile holds at most kTile rows and reads fewer than
+// kTile + kLong entries.
+__global__ void k_tiles(const uint32_t *keys, int64_t N, int32_t ntiles, int32_t *tile_row) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
     if (t == 0) { tile_row[0] = 0; continue; }
     if (t == ntiles) { tile_row[t] = (int32_t)N; continue; }
@@ -400,9 +471,19 @@ __global__ void k_tiles(const uint32_t *rp_s, int64_t N, int32_t ntiles, int32_t
     long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] + r >= target
     while (lo < hi) {
       long long mid = (lo + hi) >> 1;
-      if ((uint64_t)(rp_s[mid] & kOffMask) + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
+      if ((uint64_t)keys[mid] + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
     }
     tile_row[t] = (int32_t)lo;
+  }
+}
+
+// Tile descriptors: first row and the offsets of its entries in the st and
+// hm short regions (hm_rp == nullptr: the tile reads st alone).
+__global__ void k_tile_desc(int32_t ntiles, const int32_t *tile_row, const uint32_t *st_rp,
+                            const uint32_t *hm_rp, int4 *tdesc) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
+    const int r = tile_row[t];
+    tdesc[t] = make_int4(r, (int)(st_rp[r] & kOffMask), hm_rp ? (int)(hm_rp[r] & kOffMask) : 0, 0);
   }
 }
 
@@ -412,38 +493,30 @@ __device__ __forceinline__ void acc_deg(dfl &D, dfl &Pp, float w) {
   if (w > 0.f) df_add(Pp, w);
 }
 
-// Rows of the static node range (cells, macro pins, stars): static part, then
-// for hint cells their macro entries (ascending macro) and window bin entries
-// (row-major).  A warp takes 32 consecutive rows: lanes load the rows'
-// offsets in parallel, the warp copies each row's static part cooperatively,
-// then every lane builds the hint part of its own row.
-__global__ void __launch_bounds__(256) k_assemble_rows(
-    HintGeo G, int with_hints, int wdtype, const int64_t *srp, const int32_t *scol, const void *sw,
-    const uint32_t *rp_s, const int32_t *longidx, const uint64_t *lptr, const uint8_t *hflag,
-    const int32_t *cell_bin, const int32_t *n_ovl, const float2 *xy, const float *cw,
-    const float *ch, const float *fx, const float *fy, const int32_t *macro_cell,
-    const int64_t *gptr, const uint32_t *glist, const double *base_w, const float *phif,
-    const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
-    uint64_t *bin_base) {
+// The static matrix st in its split form: a warp takes 32 consecutive rows,
+// lanes load the rows' offsets in parallel, the warp copies each row
+// cooperatively and reduces its degree sums (double-float).
+__global__ void __launch_bounds__(256) k_assemble_static(
+    int64_t N, int64_t Nst, int wdtype, const int64_t *srp, const int32_t *scol, const void *sw,
+    const uint32_t *rp_s, const int32_t *longidx, const uint64_t *lptr, int32_t *col, void *w,
+    dfl *dsum, dfl *psum) {
   const int lane = threadIdx.x & 31;
-  const int64_t nrows = with_hints ? G.Nst : G.N;
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long v0 = wg * 32; v0 < nrows; v0 += nwarp * 32) {
+  for (long long v0 = wg * 32; v0 < N; v0 += nwarp * 32) {
     const long long v = v0 + lane;
-    const bool ok = v < nrows;
     uint64_t dst = 0;
     long long s0 = 0, sl = 0;
-    if (ok) {
-      int li = longidx[v];
+    if (v < N) {
+      const int li = longidx[v];
       dst = li >= 0 ? lptr[li] : (uint64_t)(rp_s[v] & kOffMask);
-      if (v < G.Nst) {
+      if (v < Nst) {
         s0 = srp[v];
         sl = srp[v + 1] - s0;
       }
     }
     dfl Dl{0.f, 0.f}, Pl{0.f, 0.f};
-    const int nv = (int)min((long long)32, nrows - v0);
+    const int nv = (int)min((long long)32, N - v0);
     for (int j = 0; j < nv; ++j) {
       const uint64_t dj = __shfl_sync(0xffffffffu, dst, j);
       const long long sj = __shfl_sync(0xffffffffu, s0, j), lj = __shfl_sync(0xffffffffu, sl, j);
@@ -460,28 +533,97 @@ __global__ void __launch_bounds__(256) k_assemble_rows(
         Pl = Pp;
       }
     }
-    if (ok && with_hints && v < G.C && hflag[v]) {
+    if (v < N) {
+      dsum[v] = df_norm(Dl);
+      psum[v] = df_norm(Pl);
+    }
+  }
+}
+
+// |u - c| as a normalized double-float, for u = uh + ul (ul the rounding
+// residue of uh) and an exactly representable c: TwoSum of uh and -c, then
+// the low parts.
+__device__ __forceinline__ dfl df_absdiff(float uh, float ul, float c) {
+  dfl s{uh, 0.f};
+  df_add(s, -c);
+  s.lo = __fadd_rn(s.lo, ul);
+  s = df_norm(s);
+  if (s.hi < 0.f) s = dfl{-s.hi, -s.lo};
+  return s;
+}
+__device__ __forceinline__ bool df_ge(dfl a, dfl b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
+}
+// e^{-r} for r = hi + lo >= 0, the form of exp_neg.
+__device__ __forceinline__ float exp_neg_df(dfl r) { return expf(-r.hi) * (1.0f - r.lo); }
+
+// (x - o) * s for a float x, o = oh + ol and s = sh + sl (double-floats), to
+// about 44 bits with FP32 operations only.
+__device__ __forceinline__ dfl df_offset_scale(float x, float oh, float ol, float sh, float sl) {
+  dfl d{x, 0.f};
+  df_add(d, -oh);
+  d.lo = __fadd_rn(d.lo, -ol);
+  d = df_norm(d);
+  const float ph = __fmul_rn(d.hi, sh);
+  float pl = __fmaf_rn(d.hi, sh, -ph);
+  pl = __fmaf_rn(d.hi, sl, pl);
+  pl = __fmaf_rn(d.lo, sh, pl);
+  return df_norm(dfl{ph, pl});
+}
+// |x - c| / h for floats x, c and h > 0 as a double-float: the difference
+// is exact (TwoSum), the quotient carries its FMA remainder.
+__device__ __forceinline__ dfl df_ratio(float x, float c, float h) {
+  if (!(h > 0.f)) return dfl{__int_as_float(0x7f800000), 0.f};
+  dfl d{x, 0.f};
+  df_add(d, -c);
+  d = df_norm(d);
+  if (d.hi < 0.f) d = dfl{-d.hi, -d.lo};
+  const float q = __fdiv_rn(d.hi, h);
+  const float r = __fmaf_rn(-q, h, d.hi);
+  return df_norm(dfl{q, __fdiv_rn(__fadd_rn(r, d.lo), h)});
+}
+
+// Hint part of the rows of cells, macro pins and stars (thread per row): for a
+// hint cell its macro entries (ascending macro) and window bin entries
+// (row-major), written to the row's hm place; the degree sums of the whole
+// augmented row are the static ones plus the hint entries.  The window ratios
+// |x - x_b| / (w_b / 2) = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u
+// (double-float, once per cell) as exact double-float differences; macro
+// ratios are double-float quotients.  No FP64 arithmetic on this path except
+// the recomputation of weights near a bf16 rounding midpoint.
+__global__ void __launch_bounds__(256) k_assemble_hints(
+    HintGeo G, int wdtype, const uint32_t *hrp, const int32_t *longidx, const uint64_t *lptr,
+    const dfl *sdsum, const dfl *spsum, const uint8_t *hflag, const int32_t *cell_bin,
+    const int32_t *n_ovl, const float2 *xy, const float *cw, const float *ch,
+    const int64_t *gptr, const uint32_t *glist, const float4 *ggeo, const double *base_w,
+    const float *phif, const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum,
+    uint64_t *mac_base, uint64_t *bin_base) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.Nst;
+       v += (long long)gridDim.x * blockDim.x) {
+    dfl Dl = sdsum[v], Pl = spsum[v];
+    if (v < G.C && hflag[v]) {
+      const int li = longidx[v];
+      const uint64_t mb = li >= 0 ? lptr[li] : (uint64_t)(hrp[v] & kOffMask);
       float2 p = xy[v];
       if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
       const double bw = base_w[v];
       const float bwf = __double2float_rn(bw);
-      const uint64_t mb = dst + sl;
       // macro entries, ascending macro id (grid bucket lists are sorted)
-      int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
-      long long gk = (long long)ky * G.gnx + kx;
+      const int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
+      const long long gk = (long long)ky * G.gnx + kx;
       uint64_t k = mb;
       const float cwv = cw[v], chv = ch[v];
       for (long long q = gptr[gk]; q < gptr[gk + 1]; ++q) {
-        int m = (int)glist[q];
-        int c = macro_cell[m];
-        if (!overlaps(p.x, p.y, cwv, chv, fx[c], fy[c], cw[c], ch[c])) continue;
-        double rx = fabs((double)p.x - (double)fx[c]) / ((double)cw[c] * 0.5);
-        double ry = fabs((double)p.y - (double)fy[c]) / ((double)ch[c] * 0.5);
-        float wv = -(exp_neg(fmax(rx, ry)) * bwf);
+        const float4 mg = ggeo[q];
+        if (!overlaps(p.x, p.y, cwv, chv, mg.x, mg.y, mg.z, mg.w)) continue;
+        const int m = (int)glist[q];
+        const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
+        const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
+        const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
         col[k] = (int32_t)(G.mv0 + m);
         if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
-          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, fx[c], fy[c], cw[c],
-                                                                 ch[c], bw))));
+          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
+                                                                 mg.w, bw))));
         else
           acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
         ++k;
@@ -490,25 +632,18 @@ __global__ void __launch_bounds__(256) k_assemble_rows(
       const int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
       const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
       const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
-      // e^{-max(rx, ry)} = e^{-rx} or e^{-ry}: one exponent per window column
-      // and per window row (kMaxWin each), then a selection per bin
-      float ex[kMaxWin], ey[kMaxWin];
-      double rxv[kMaxWin], ryv[kMaxWin];
-      for (int xx = x0; xx <= x1; ++xx) {
-        double xb = G.xl + ((double)xx + 0.5) * G.wb;
-        rxv[xx - x0] = fabs((double)p.x - xb) * G.iwb2;
-        ex[xx - x0] = exp_neg(rxv[xx - x0]);
-      }
-      for (int yy = y0; yy <= y1; ++yy) {
-        double yb = G.yl + ((double)yy + 0.5) * G.hb;
-        ryv[yy - y0] = fabs((double)p.y - yb) * G.ihb2;
-        ey[yy - y0] = exp_neg(ryv[yy - y0]);
-      }
+      const dfl ux = df_offset_scale(p.x, G.xlh, G.xll, G.iwh, G.iwl);
+      const dfl uy = df_offset_scale(p.y, G.ylh, G.yll, G.ihh, G.ihl);
+      const float uxh = ux.hi, uxl = ux.lo, uyh = uy.hi, uyl = uy.lo;
       k = bb0;
-      for (int yy = y0; yy <= y1; ++yy)
+      for (int yy = y0; yy <= y1; ++yy) {
+        // e^{-max(rx, ry)} is e^{-rx} or e^{-ry}
+        const dfl ry = df_absdiff(uyh, uyl, (float)(2 * yy + 1));
+        const float ey = exp_neg_df(ry);
         for (int xx = x0; xx <= x1; ++xx, ++k) {
+          const dfl rx = df_absdiff(uxh, uxl, (float)(2 * xx + 1));
+          const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
           const int bb = yy * G.nbx + xx;
-          const float e = rxv[xx - x0] >= ryv[yy - y0] ? ex[xx - x0] : ey[yy - y0];
           const float wv = -((e * phif[bb]) * bwf);
           col[k] = (int32_t)(G.bn0 + bb);
           if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
@@ -516,13 +651,12 @@ __global__ void __launch_bounds__(256) k_assemble_rows(
           else
             acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
         }
+      }
       mac_base[v] = mb;
       bin_base[v] = bb0;
     }
-    if (ok) {
-      dsum[v] = df_norm(Dl);
-      psum[v] = df_norm(Pl);
-    }
+    dsum[v] = df_norm(Dl);
+    psum[v] = df_norm(Pl);
   }
 }
 
@@ -709,6 +843,14 @@ static HintGeo make_geo(const pl_graph *g) {
   G.hb = g->hb;
   G.iwb2 = 2.0 / g->wb;
   G.ihb2 = 2.0 / g->hb;
+  auto split = [](double d, float *h, float *l) {
+    *h = (float)d;
+    *l = (float)(d - (double)*h);
+  };
+  split(G.xl, &G.xlh, &G.xll);
+  split(G.yl, &G.ylh, &G.yll);
+  split(G.iwb2, &G.iwh, &G.iwl);
+  split(G.ihb2, &G.ihh, &G.ihl);
   G.nbx = g->nbx;
   G.nby = g->nby;
   G.hx = g->hx;
@@ -727,7 +869,9 @@ static HintGeo make_geo(const pl_graph *g) {
 }
 
 // Layout of a split matrix from per-row lengths already in g->slen/llen/lflag.
-static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
+// Layout of a split matrix from per-row lengths in g->slen/llen/klen/clen and
+// hub flags in g->tmp[2].
+static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   const int64_t N = g->N;
   m.N = N;
   void *stmp;
@@ -742,12 +886,17 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
   TRY(ensure(g->lflag, (size_t)(N + 1) * 4 + 256));
   int32_t *lscan = P<int32_t>(g->lflag);
   TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->tmp[2]), lscan, N, stmp, s)));
-  uint64_t tot[2];
+  TRY(ensure(g->tmp[6], (size_t)(N + 1) * 8 + 256));
+  uint64_t *k64 = P<uint64_t>(g->tmp[6]);
+  TRY((exclusive_scan<uint32_t, uint64_t>(P<uint32_t>(g->klen), k64, N, stmp, s)));
+  uint64_t tot[3];
   int32_t nl;
   TRY(d2h(&tot[0], s64 + N, 1, s));
   TRY(d2h(&tot[1], lpos + N, 1, s));
+  TRY(d2h(&tot[2], k64 + N, 1, s));
   TRY(d2h(&nl, lscan + N, 1, s));
-  if (tot[0] >= (uint64_t)kOffMask - 2 * kTile || tot[0] + tot[1] >= (1ull << 40)) {
+  if (tot[0] >= (uint64_t)kOffMask - 2 * kTile || tot[2] + (uint64_t)N >= (uint64_t)kOffMask ||
+      tot[0] + tot[1] >= (1ull << 40)) {
     set_error("graph too large for the 31-bit short-row layout (%llu entries)",
               (unsigned long long)tot[0]);
     return PL_ERR_UNSUPPORTED;
@@ -760,16 +909,24 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
   k_rp_pack<<<grid_for(N + 1 + kRpPad, 256), 256, 0, s>>>(s64, P<uint8_t>(g->tmp[2]), N,
                                                          P<uint32_t>(m.rp_s));
   note_launch();
+  TRY(ensure(m.keys, (size_t)(N + 1) * 4 + 16));
+  k_u64_to_u32<<<grid_for(N + 1, 256), 256, 0, s>>>(k64, P<uint32_t>(m.keys), N + 1);
+  note_launch();
   const uint64_t cap = m.nnz_s + m.nnz_l + kPad;
   TRY(ensure(m.col, cap * 4));
   TRY(ensure(m.w, cap * m.wbytes));
   TRY(ensure(m.lrow, (size_t)nl * 4 + 16));
   TRY(ensure(m.lptr, (size_t)(nl + 1) * 8));
+  TRY(ensure(m.lsb, (size_t)nl * 8 + 16));
+  TRY(ensure(m.lhb, (size_t)nl * 8 + 16));
+  TRY(ensure(m.lsl, (size_t)nl * 4 + 16));
+  TRY(ensure(m.lhl, (size_t)nl * 4 + 16));
   TRY(ensure(m.longidx, (size_t)N * 4 + 16));
   TRY(ensure(m.lchunk, (size_t)(nl + 1) * 4));
   TRY(ensure(g->tmp[3], (size_t)(nl + 1) * 4 + 256));
   int32_t *nch = P<int32_t>(g->tmp[3]);
-  k_layout_long<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->tmp[2]), lscan, lpos, m.nnz_s,
+  k_layout_long<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->tmp[2]), lscan, lpos,
+                                                 P<uint64_t>(g->clen), m.nnz_s,
                                                  P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
                                                  P<int32_t>(m.longidx), nch);
   note_launch();
@@ -781,17 +938,27 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
     int32_t nc;
     TRY(d2h(&nc, P<int32_t>(m.lchunk) + nl, 1, s));
     m.nchunks = nc;
+    k_hub_desc<<<grid_for(nl, 256), 256, 0, s>>>(
+        nl, with_hints, P<int32_t>(m.lrow), P<uint64_t>(m.lptr), P<int64_t>(g->srp), g->Nst,
+        P<uint32_t>(g->st.rp_s), P<int32_t>(g->st.longidx), P<uint64_t>(g->st.lptr),
+        P<uint64_t>(m.lsb), P<uint32_t>(m.lsl), P<uint64_t>(m.lhb), P<uint32_t>(m.lhl));
+    note_launch();
   }
   TRY(ensure(m.chunk_lr, (size_t)m.nchunks * 4 + 16));
   if (nl) {
     k_chunk_owner<<<grid_for(nl, 256), 256, 0, s>>>(nl, P<int32_t>(m.lchunk), P<int32_t>(m.chunk_lr));
     note_launch();
   }
-  m.ntiles = (int32_t)((m.nnz_s + (uint64_t)N + kTile - 1) / kTile);
+  m.ntiles = (int32_t)((tot[2] + (uint64_t)N + kTile - 1) / kTile);
   if (m.ntiles < 1) m.ntiles = 1;
   TRY(ensure(m.tile_row, (size_t)(m.ntiles + 1) * 4));
-  k_tiles<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(P<uint32_t>(m.rp_s), N, m.ntiles,
+  k_tiles<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(P<uint32_t>(m.keys), N, m.ntiles,
                                                      P<int32_t>(m.tile_row));
+  note_launch();
+  TRY(ensure(m.tdesc, (size_t)(m.ntiles + 1) * 16));
+  k_tile_desc<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(
+      m.ntiles, P<int32_t>(m.tile_row), with_hints ? P<uint32_t>(g->st.rp_s) : P<uint32_t>(m.rp_s),
+      with_hints ? P<uint32_t>(m.rp_s) : nullptr, P<int4>(m.tdesc));
   note_launch();
   TRY(ensure(m.dsum, (size_t)N * 8 + 16));
   TRY(ensure(m.psum, (size_t)N * 8 + 16));
@@ -807,24 +974,33 @@ static pl_status layout(pl_graph *g, SpMat &m, cudaStream_t s) {
   return PL_OK;
 }
 
+static pl_status ensure_row_arrays(pl_graph *g) {
+  const int64_t N = g->N;
+  TRY(ensure(g->slen, (size_t)N * 4 + 16));
+  TRY(ensure(g->llen, (size_t)N * 8 + 16));
+  TRY(ensure(g->klen, (size_t)N * 4 + 16));
+  TRY(ensure(g->clen, (size_t)N * 8 + 16));
+  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  return PL_OK;
+}
+
 pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s) {
   const int64_t N = g->N;
   HintGeo G = make_geo(g);
-  TRY(ensure(g->slen, (size_t)N * 4 + 16));
-  TRY(ensure(g->llen, (size_t)N * 8 + 16));
-  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  pl_status st = ensure_row_arrays(g);
+  if (st != PL_OK) return st;
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 0, P<int64_t>(g->srp), nullptr, nullptr, nullptr,
                                              nullptr, nullptr, P<uint32_t>(g->slen),
-                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]));
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]),
+                                             P<uint32_t>(g->klen), P<uint64_t>(g->clen));
   note_launch();
-  pl_status st = layout(g, g->st, s);
+  st = layout(g, g->st, 0, s);
   if (st != PL_OK) return st;
   SpMat &m = g->st;
-  k_assemble_rows<<<grid_for(N * 32, 256), 256, 0, s>>>(
-      G, 0, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
-      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), nullptr, nullptr, nullptr, nullptr, nullptr,
-      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-      P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum), P<dfl>(m.psum), nullptr, nullptr);
+  k_assemble_static<<<grid_for(N * 32, 256), 256, 0, s>>>(
+      N, g->Nst, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
+      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
+      P<dfl>(m.psum));
   note_launch();
   TRY(cudaGetLastError());
   return PL_OK;
@@ -836,6 +1012,10 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   const float2 *xy = reinterpret_cast<const float2 *>(xy_in);
   HintGeo G = make_geo(g);
   g->have_hints = false;
+  if (g->hx * 2 + 1 > kMaxWin || g->hy * 2 + 1 > kMaxWin) {
+    set_error("detection window larger than 31 x 31 bins");
+    return PL_ERR_UNSUPPORTED;
+  }
   TRY(cudaMemsetAsync(g->status.p, 0, 32, s));
   int *status = P<int>(g->status);
   void *stmp;
@@ -851,9 +1031,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(cudaMemsetAsync(g->mcnt.p, 0, (size_t)(Mm + 1) * 4, s));
   k_hint_cells<<<grid_for(C, 256), 256, 0, s>>>(
       G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
-      P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
-      P<uint32_t>(g->glist), P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl), P<int32_t>(g->bcnt),
-      P<int32_t>(g->mcnt), status);
+      P<int64_t>(g->gptr), P<uint32_t>(g->glist), P<float4>(g->ggeo), P<int32_t>(g->cell_bin),
+      P<int32_t>(g->n_ovl), P<int32_t>(g->bcnt), P<int32_t>(g->mcnt), status);
   note_launch();
   // H2: bucket offsets
   TRY(ensure(g->boff, (size_t)(2 * NB + 1) * 8));
@@ -910,8 +1089,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     note_launch();
     k_macro_scatter<<<grid_for(C, 256), 256, 0, s>>>(
         G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
-        P<float>(g->cfx), P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr),
-        P<uint32_t>(g->glist), P<int32_t>(g->mcur), P<uint32_t>(g->mlist));
+        P<int64_t>(g->gptr), P<uint32_t>(g->glist), P<float4>(g->ggeo), P<int32_t>(g->mcur),
+        P<uint32_t>(g->mlist));
     note_launch();
     TRY(ensure(g->tmp[3], segsort_tmp_bytes(Mm, nml, 4)));
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->mlist), P<int64_t>(g->moff), Mm, nml,
@@ -946,34 +1125,29 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       P<double>(g->phi), phif, hub_len);
   note_launch();
   // H6-H7: row lengths and layout
-  TRY(ensure(g->slen, (size_t)N * 4 + 16));
-  TRY(ensure(g->llen, (size_t)N * 8 + 16));
-  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  pl_status st = ensure_row_arrays(g);
+  if (st != PL_OK) return st;
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 1, P<int64_t>(g->srp), P<uint8_t>(g->hflag),
                                              P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
                                              P<int64_t>(g->moff), hub_len, P<uint32_t>(g->slen),
-                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]));
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]),
+                                             P<uint32_t>(g->klen), P<uint64_t>(g->clen));
   note_launch();
-  pl_status st = layout(g, g->hm, s);
+  st = layout(g, g->hm, 1, s);
   if (st != PL_OK) return st;
   SpMat &m = g->hm;
-  // H9: rows of cells, macro pins and stars
+  // H9: hint parts of cells (and degrees of every real node)
   TRY(ensure(g->mac_base, (size_t)C * 8 + 16));
   TRY(ensure(g->bin_base, (size_t)C * 8 + 16));
-  k_assemble_rows<<<grid_for(g->Nst * 32, 256), 256, 0, s>>>(
-      G, 1, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
-      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
-      P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
-      P<float>(g->cfy), P<int32_t>(g->macro_cell), P<int64_t>(g->gptr), P<uint32_t>(g->glist),
-      P<double>(g->base_w), phif, P<double>(g->phi), P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
-      P<dfl>(m.psum),
-      P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
+  k_assemble_hints<<<grid_for(g->Nst, 256), 256, 0, s>>>(
+      G, g->wdtype, P<uint32_t>(m.rp_s), P<int32_t>(m.longidx), P<uint64_t>(m.lptr),
+      P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
+      P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<int64_t>(g->gptr),
+      P<uint32_t>(g->glist), P<float4>(g->ggeo), P<double>(g->base_w), phif, P<double>(g->phi),
+      P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
+      P<dfl>(m.psum), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
   note_launch();
   // H10: virtual rows
-  if (g->hx * 2 + 1 > 31 || g->hy * 2 + 1 > 31 || (2 * g->hx + 1) * (2 * g->hy + 1) > 1024) {
-    set_error("detection window larger than 31 x 31 bins");
-    return PL_ERR_UNSUPPORTED;
-  }
   TRY(ensure(g->tmp[5], (size_t)(m.nchunks + 1) * 2 * sizeof(dfl) + 256));
   dfl *cpart = P<dfl>(g->tmp[5]);
   if (m.nchunks) {

@@ -23,8 +23,17 @@ constexpr uint32_t kHubFlag = 0x80000000u;  // rp_s bit 31: the row is a hub row
 constexpr uint32_t kOffMask = 0x7fffffffu;
 
 // A split CSR matrix as the SpMM kernels read it.  Entries of short rows come
-// first (row pointers rp_s; long rows have zero length there), entries of hub
-// rows follow at absolute offsets lptr.
+// first (row pointers rp_s; hub rows have zero length there and bit 31 set),
+// entries of hub rows follow at absolute offsets lptr.  Two matrices exist:
+//  * st, the static instance graph, built once per netlist;
+//  * hm, the hint part of the augmented graph, rebuilt every round.  A row of
+//    the augmented graph is its st part followed by its hm part; it is a hub
+//    row (bit 31 of hm.rp_s) when it is a virtual node or has more than kLong
+//    entries in total, and its st part then may sit in st's short region.
+// Tiles own the rows whose key (keys[r] + r) falls in a window of kTile; keys
+// count the entries a tile reads (st short entries + hm short entries).  Per
+// hub row, lsb/lsl give its st piece and lhb/lhl its hm piece (absolute
+// offsets, lengths); chunks of kChunk cover the concatenation.
 struct SpMat {
   int64_t N = 0;
   uint64_t nnz_s = 0, nnz_l = 0;
@@ -32,13 +41,17 @@ struct SpMat {
   Buf rp_s;     // uint32 [N+1+kRpPad], bit 31 = hub row
   Buf col;      // int32 [nnz_s + nnz_l + kPad]
   Buf w;        // float or uint16 (bf16) [same]
+  Buf keys;     // uint32 [N+1] tile keys without the row count
   Buf lrow;     // int32 [nlong] node of each hub row
-  Buf lptr;     // uint64 [nlong+1] absolute entry offsets
+  Buf lptr;     // uint64 [nlong+1] this matrix's part of each hub row (absolute)
+  Buf lsb, lhb; // uint64 [nlong] st piece / hm piece of each hub row
+  Buf lsl, lhl; // uint32 [nlong] their lengths
   Buf lchunk;   // int32 [nlong+1] first chunk of each hub row
   Buf chunk_lr; // int32 [nchunks] hub row of each chunk
   Buf tile_row; // int32 [ntiles+1] first row owned by each tile
+  Buf tdesc;    // int4 [ntiles+1] per tile: first row, st short offset, hm short offset
   Buf longidx;  // int32 [N] hub index or -1
-  Buf dsum;     // dfl [N] signed degree D_ii
+  Buf dsum;     // dfl [N] signed degree D_ii (hm: of the whole augmented row)
   Buf psum;     // dfl [N] sum of positive weights
   Buf c32;      // float [N] 1 - D_ii / lambda_up
   Buf c64l;     // double [nlong] same, FP64, hub rows
@@ -85,7 +98,8 @@ struct pl_graph {
   // macro lookup grid
   int32_t gnx = 1, gny = 1;
   double gsz = 1.0, gsx = 1.0, gsy = 1.0;
-  pl::Buf gptr, glist; // int32 [gnx*gny+1], [..]
+  pl::Buf gptr, glist; // int64 [gnx*gny+1], uint32 macro ids
+  pl::Buf ggeo;        // float4 [..] centre and size of each listed macro
   // per refinement round
   pl::Buf cell_bin;    // int32 [C]
   pl::Buf n_ovl;       // int32 [C]
@@ -93,8 +107,10 @@ struct pl_graph {
   pl::Buf mcnt, moff, mlist, mcur;  // cells overlapping each macro
   pl::Buf Db, phi;     // double [NB]
   pl::Buf hlen;        // int64 [N] augmented row length
-  pl::Buf slen;        // uint32 [N] short-row length (0 for hub rows)
-  pl::Buf llen;        // uint64 [N] hub length per node (0 for short rows)
+  pl::Buf slen;        // uint32 [N] short-region length (0 for hub rows)
+  pl::Buf llen;        // uint64 [N] hub-region length (0 for short rows)
+  pl::Buf klen;        // uint32 [N] tile key length
+  pl::Buf clen;        // uint64 [N] chunked length of hub rows
   pl::Buf lflag;       // int32 [N+1] hub flag scan
   pl::Buf mac_base;    // uint64 [C] entry offset of a cell's first macro entry
   pl::Buf bin_base;    // uint64 [C] entry offset of a cell's first bin entry
