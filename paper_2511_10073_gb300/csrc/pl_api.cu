@@ -117,8 +117,8 @@ static void destroy(pl_graph *g) {
   if (!g) return;
   Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
                  &g->net_p, &g->star_of, &g->star_net, &g->macro_cell, &g->cell_macro, &g->srp,
-                 &g->scol, &g->sw, &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
-                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->cell_bin, &g->n_ovl,
+                 &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
+                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
                  &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur,
                  &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->klen, &g->clen, &g->lflag,
                  &g->mac_base,
@@ -197,7 +197,6 @@ pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *
     created = true;
   }
   st = build_static(*gp, nl, p, s);
-  if (st == PL_OK) st = prepare_static_matrix(*gp, s);
   if (st == PL_OK && xy_nodes) st = build_hints(*gp, p, xy_nodes, s);
   if (st == PL_OK) {
     cudaError_t e = cudaStreamSynchronize(s);

@@ -182,11 +182,24 @@ __device__ __forceinline__ double lattice_div(long long val) {
 // Table weights in place of the merged values (warp per 32 rows, lanes over a
 // row's entries); entries that need a division are listed, so that the
 // divisions run together in k_static_div instead of stalling whole warps.
+constexpr int kDivBuf = 256;  // listed entries a warp buffers before one global append
+
 __global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, int64_t *mval,
                                                         const int64_t *srp, int64_t Nst,
                                                         uint32_t *list,
                                                         unsigned long long *nlist) {
+  __shared__ uint32_t wbuf[8][kDivBuf];
   const int lane = threadIdx.x & 31;
+  uint32_t *buf = wbuf[threadIdx.x >> 5];
+  int nb = 0;  // warp-uniform
+  auto flush = [&]() {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(nlist, (unsigned long long)nb);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < nb; i += 32) list[base + i] = buf[i];
+    __syncwarp();
+    nb = 0;
+  };
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long v0 = wg * 32; v0 < Nst; v0 += nwarp * 32) {
@@ -210,15 +223,14 @@ __global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, 
           else hard = true;
         }
         const unsigned hm = __ballot_sync(0xffffffffu, hard);
-        if (hm) {
-          unsigned long long base = 0;
-          if (lane == 0) base = atomicAdd(nlist, (unsigned long long)__popc(hm));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (hard) list[base + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)(sj + k);
-        }
+        if (nb + 32 > kDivBuf) flush();
+        if (hard) buf[nb + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)(sj + k);
+        nb += __popc(hm);
+        __syncwarp();
       }
     }
   }
+  if (nb) flush();
 }
 
 __global__ void k_static_div(const uint32_t *list, const unsigned long long *nlist,
@@ -240,15 +252,18 @@ __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
   return __double2float_rn(w);
 }
 
-// Final static CSR from the FP64 weights (in place of the merged values).  A
-// warp takes 32 consecutive rows: for each row the warp writes columns and
-// stored weights and reduces the row's static degree (double-float, over the
-// stored weights); then each lane forms, for a cell, baseWeight (FP64 mean of
-// the exact weights, added in column order).
+// Final static matrix, written straight into its split layout, from the FP64
+// weights (in place of the merged values).  A warp takes 32 consecutive rows:
+// for each row the warp writes columns and stored weights at the row's place
+// (short region or hub region) and reduces the row's static degree
+// (double-float, over the stored weights; every static weight is positive, so
+// it is also the positive sum); then each lane forms, for a cell, baseWeight
+// (FP64 mean of the exact weights, added in column order).
 __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
-    int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, int32_t *scol, void *sw, double *base_w,
-    uint8_t *hflag, double *sdeg) {
+    int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, const uint32_t *rp_s,
+    const int32_t *longidx, const uint64_t *lptr, int32_t *scol, void *sw, dfl *dsum, dfl *psum,
+    double *base_w, uint8_t *hflag, double *sdeg) {
   const int lane = threadIdx.x & 31;
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -259,8 +274,9 @@ __global__ void __launch_bounds__(256) k_static_compact(
     int m = 0;
     if (ok) {
       src = row_off[v];
-      dst = srp[v];
-      m = (int)(srp[v + 1] - dst);
+      m = (int)(srp[v + 1] - srp[v]);
+      const int li = longidx[v];
+      dst = li >= 0 ? (long long)lptr[li] : (long long)(rp_s[v] & kOffMask);
     }
     dfl dl{0.f, 0.f};
     const int nv = (int)min((long long)32, Nst - v0);
@@ -284,6 +300,8 @@ __global__ void __launch_bounds__(256) k_static_compact(
     __syncwarp();
     if (!ok) continue;
     sdeg[v] = df_to_d(dl);
+    dsum[v] = dl;
+    psum[v] = dl;
     if (v < C) {
       const double *w64 = reinterpret_cast<const double *>(mval) + src;
       double s = 0.0;
@@ -642,8 +660,10 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   int64_t nnz;
   TRY(d2h(&nnz, P<int64_t>(g->srp) + Nst, 1, s));
   g->nnz_static = (uint64_t)nnz;
-  TRY(ensure(g->scol, (size_t)nnz * 4 + 64));
-  TRY(ensure(g->sw, (size_t)nnz * 4 + 64));
+  {
+    pl_status ls = prepare_static_layout(g, s);
+    if (ls != PL_OK) return ls;
+  }
   TRY(ensure(g->base_w, (size_t)C * 8 + 16));
   TRY(ensure(g->hflag, (size_t)C + 16));
   TRY(ensure(g->sdeg, (size_t)Nst * 8 + 16));
@@ -668,10 +688,17 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     k_static_div<<<152 * 8, 256, 0, s>>>(list, nlist, mval);
     note_launch();
   }
+  SpMat &sm = g->st;
   k_static_compact<<<grid_for(Nst * 32, 256), 256, 0, s>>>(
       row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
-      P<int32_t>(g->scol), g->sw.p, P<double>(g->base_w), P<uint8_t>(g->hflag), P<double>(g->sdeg));
+      P<uint32_t>(sm.rp_s), P<int32_t>(sm.longidx), P<uint64_t>(sm.lptr), P<int32_t>(sm.col),
+      sm.w.p, P<dfl>(sm.dsum), P<dfl>(sm.psum), P<double>(g->base_w), P<uint8_t>(g->hflag),
+      P<double>(g->sdeg));
   note_launch();
+  if (g->N > Nst) {
+    TRY(cudaMemsetAsync(P<dfl>(sm.dsum) + Nst, 0, (size_t)(g->N - Nst) * sizeof(dfl), s));
+    TRY(cudaMemsetAsync(P<dfl>(sm.psum) + Nst, 0, (size_t)(g->N - Nst) * sizeof(dfl), s));
+  }
   TRY(cudaGetLastError());
 
   // node tables

@@ -134,7 +134,7 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
     int b = by * G.nbx + bx;
     cell_bin[i] = b;
     bool hint = hflag[i] != 0;
-    atomicAdd(&bcnt[2 * b + (hint ? 0 : 1)], 1);
+    if (bcnt) atomicAdd(&bcnt[2 * b + (hint ? 0 : 1)], 1);
     int n = 0;
     if (hint) {
       int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
@@ -259,84 +259,103 @@ __device__ __forceinline__ double cell_area(const float *cw, const float *ch, ui
   return __dmul_rn((double)cw[i], (double)ch[i]);
 }
 
-constexpr int kDensStage = 4096;  // cell areas staged per pass (a multiple of 64)
+// A_mov(b) as a blocked FP64 sum: the bin's cells (hint cells ascending,
+// then the others ascending) in blocks of 64 added left to right, the block
+// sums blocked again, until at most 64 values remain, which are added left to
+// right.  Level L of bin b reads len_L(b) values starting at st_L(b) (level
+// 0: cell areas through the bucket list) and writes its block sums to
+// out_L(b) = st_L(b) / 64 + b onwards; these ranges are disjoint and
+// increasing in b, so every block of every bin is one thread of one launch.
+struct DensLevel {
+  int64_t st, len, out;
+};
+__device__ __forceinline__ DensLevel dens_level(const int64_t *boff, int b, int L) {
+  DensLevel d;
+  d.st = boff[2 * b];
+  d.len = boff[2 * b + 2] - d.st;
+  d.out = d.st / 64 + b;
+  for (int l = 0; l < L; ++l) {
+    d.st = d.out;
+    d.len = (d.len + 63) / 64;
+    d.out = d.st / 64 + b;
+  }
+  return d;
+}
 
-__global__ void __launch_bounds__(256) k_bin_density(HintGeo G, const int64_t *boff,
-                                                     const uint32_t *blist, const float *cw,
-                                                     const float *ch, const double *amac,
-                                                     double abin, double cap, double mu,
-                                                     LevelBufs lv, double *Db, double *Cb,
-                                                     double *phi, float *phif, int64_t *hub_len) {
+__global__ void __launch_bounds__(256) k_dens_level(int NB, int L, const int64_t *boff,
+                                                    const uint32_t *blist, const float *cw,
+                                                    const float *ch, const double *prev,
+                                                    double *out, long long nidx) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nidx;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = NB - 1;  // last bin with out_L(b) <= idx
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (dens_level(boff, mid, L).out <= idx) lo = mid; else hi = mid - 1;
+    }
+    const DensLevel d = dens_level(boff, lo, L);
+    const int64_t j = idx - d.out;
+    if (d.len <= 64 || j < 0 || j >= (d.len + 63) / 64) continue;
+    const int64_t k0 = d.st + 64 * j, k1 = min(d.st + d.len, k0 + 64);
+    double acc = 0.0;
+    if (L == 0) {
+      for (int64_t k = k0; k < k1; k += 16) {
+        double a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = k + q < k1 ? cell_area(cw, ch, blist[k + q]) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (k + q < k1) acc = __dadd_rn(acc, a[q]);
+      }
+    } else {
+      for (int64_t k = k0; k < k1; ++k) acc = __dadd_rn(acc, prev[k]);
+    }
+    out[idx] = acc;
+  }
+}
+
+// Per bin: the last (at most 64-value) sum, D_b, C_b, phi_b and the hub row
+// length (hint cells of the window bins).
+__global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uint32_t *blist,
+                             const float *cw, const float *ch, LevelBufs lv, const double *amac,
+                             double abin, double cap, double mu, double *Db, double *Cb,
+                             double *phi, float *phif, int64_t *hub_len) {
   const int NB = G.nbx * G.nby;
-  __shared__ double sa[kDensStage];
-  for (int b = blockIdx.x; b < NB; b += gridDim.x) {
-    const int64_t s0 = boff[2 * b];
-    int64_t st = s0, len = boff[2 * b + 2] - s0;
-    const double *prev = nullptr;
-    int level = 0;
-    if (len > 64) {
-      // level 0: cell areas staged in shared memory by all threads (coalesced
-      // list reads, independent gathers), then one thread per 64-block
-      const int64_t nblk = (len + 63) / 64, ost = st / 64 + b;
-      double *out = lv.base[0];
-      for (int64_t c0 = 0; c0 < len; c0 += kDensStage) {
-        const int cl = (int)min((int64_t)kDensStage, len - c0);
-        for (int t = threadIdx.x; t < cl; t += blockDim.x)
-          sa[t] = cell_area(cw, ch, blist[s0 + c0 + t]);
-        __syncthreads();
-        const int nb = (cl + 63) / 64;
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-          double acc = 0.0;
-          const int k1 = min(cl, 64 * j + 64);
-          for (int k = 64 * j; k < k1; ++k) acc = __dadd_rn(acc, sa[k]);
-          out[ost + c0 / 64 + j] = acc;
-        }
-        __syncthreads();
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
+    int L = 0;
+    DensLevel d = dens_level(boff, b, 0);
+    while (d.len > 64 && L < nlev) {
+      ++L;
+      d = dens_level(boff, b, L);
+    }
+    const double *src = L ? lv.base[L - 1] : nullptr;
+    double acc = 0.0;
+    for (int64_t k = 0; k < d.len; k += 16) {
+      double a[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        a[q] = k + q < d.len ? (L == 0 ? cell_area(cw, ch, blist[d.st + k + q]) : src[d.st + k + q])
+                             : 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (k + q < d.len) acc = __dadd_rn(acc, a[q]);
+    }
+    const double dd = __ddiv_rn(acc, abin);
+    const double c = __ddiv_rn(__dmul_rn(cap, __dadd_rn(abin, -amac[b])), abin);
+    const double t = __dmul_rn(mu, __dadd_rn(dd, -c));
+    const double ph = __dadd_rn(__ddiv_rn(2.0, __dadd_rn(1.0, exp_cw(-t))), -1.0);
+    Db[b] = dd;
+    Cb[b] = c;
+    phi[b] = ph;
+    phif[b] = __double2float_rn(ph);
+    const int bx = b % G.nbx, by = b / G.nbx;
+    long long hl = 0;
+    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
+      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
+        const int bb = yy * G.nbx + xx;
+        hl += boff[2 * bb + 1] - boff[2 * bb];
       }
-      prev = out;
-      st = ost;
-      len = nblk;
-      level = 1;
-    }
-    while (len > 64) {
-      const int64_t nblk = (len + 63) / 64, ost = st / 64 + b;
-      double *out = lv.base[level];
-      for (int64_t j = threadIdx.x; j < nblk; j += blockDim.x) {
-        double acc = 0.0;
-        const int64_t k1 = min(len, 64 * j + 64);
-        for (int64_t k = 64 * j; k < k1; ++k)
-          acc = __dadd_rn(acc, level == 0 ? cell_area(cw, ch, blist[s0 + k]) : prev[st + k]);
-        out[ost + j] = acc;
-      }
-      __syncthreads();
-      prev = out;
-      st = ost;
-      len = nblk;
-      ++level;
-    }
-    if (threadIdx.x == 0) {
-      double acc = 0.0;
-      for (int64_t k = 0; k < len; ++k)
-        acc = __dadd_rn(acc, level == 0 ? cell_area(cw, ch, blist[s0 + k]) : prev[st + k]);
-      double d = __ddiv_rn(acc, abin);
-      double c = __ddiv_rn(__dmul_rn(cap, __dadd_rn(abin, -amac[b])), abin);
-      double t = __dmul_rn(mu, __dadd_rn(d, -c));
-      double ph = __dadd_rn(__ddiv_rn(2.0, __dadd_rn(1.0, exp_cw(-t))), -1.0);
-      Db[b] = d;
-      Cb[b] = c;
-      phi[b] = ph;
-      phif[b] = __double2float_rn(ph);
-      // hub row length: hint cells of the window bins
-      int bx = b % G.nbx, by = b / G.nbx;
-      long long hl = 0;
-      for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
-        for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
-          int bb = yy * G.nbx + xx;
-          hl += boff[2 * bb + 1] - boff[2 * bb];
-        }
-      hub_len[b] = hl;
-    }
-    __syncthreads();
+    hub_len[b] = hl;
   }
 }
 
@@ -491,53 +510,6 @@ __global__ void k_tile_desc(int32_t ntiles, const int32_t *tile_row, const uint3
 __device__ __forceinline__ void acc_deg(dfl &D, dfl &Pp, float w) {
   df_add(D, w);
   if (w > 0.f) df_add(Pp, w);
-}
-
-// The static matrix st in its split form: a warp takes 32 consecutive rows,
-// lanes load the rows' offsets in parallel, the warp copies each row
-// cooperatively and reduces its degree sums (double-float).
-__global__ void __launch_bounds__(256) k_assemble_static(
-    int64_t N, int64_t Nst, int wdtype, const int64_t *srp, const int32_t *scol, const void *sw,
-    const uint32_t *rp_s, const int32_t *longidx, const uint64_t *lptr, int32_t *col, void *w,
-    dfl *dsum, dfl *psum) {
-  const int lane = threadIdx.x & 31;
-  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long v0 = wg * 32; v0 < N; v0 += nwarp * 32) {
-    const long long v = v0 + lane;
-    uint64_t dst = 0;
-    long long s0 = 0, sl = 0;
-    if (v < N) {
-      const int li = longidx[v];
-      dst = li >= 0 ? lptr[li] : (uint64_t)(rp_s[v] & kOffMask);
-      if (v < Nst) {
-        s0 = srp[v];
-        sl = srp[v + 1] - s0;
-      }
-    }
-    dfl Dl{0.f, 0.f}, Pl{0.f, 0.f};
-    const int nv = (int)min((long long)32, N - v0);
-    for (int j = 0; j < nv; ++j) {
-      const uint64_t dj = __shfl_sync(0xffffffffu, dst, j);
-      const long long sj = __shfl_sync(0xffffffffu, s0, j), lj = __shfl_sync(0xffffffffu, sl, j);
-      dfl D{0.f, 0.f}, Pp{0.f, 0.f};
-      for (long long k = lane; k < lj; k += 32) {
-        col[dj + k] = scol[sj + k];
-        copy_w(w, sw, wdtype, dj + k, sj + k);
-        acc_deg(D, Pp, load_w(sw, wdtype, sj + k));
-      }
-      D = warp_sum_df(D);
-      Pp = warp_sum_df(Pp);
-      if (lane == j) {
-        Dl = D;
-        Pl = Pp;
-      }
-    }
-    if (v < N) {
-      dsum[v] = df_norm(Dl);
-      psum[v] = df_norm(Pl);
-    }
-  }
 }
 
 // |u - c| as a normalized double-float, for u = uh + ul (ul the rounding
@@ -870,24 +842,24 @@ static HintGeo make_geo(const pl_graph *g) {
 
 // Layout of a split matrix from per-row lengths already in g->slen/llen/lflag.
 // Layout of a split matrix from per-row lengths in g->slen/llen/klen/clen and
-// hub flags in g->tmp[2].
+// hub flags in g->hubf.
 static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   const int64_t N = g->N;
   m.N = N;
   void *stmp;
   TRY(ensure(g->tmp[7], scan_tmp_bytes(N + 1) + 4096));
   stmp = g->tmp[7].p;
-  TRY(ensure(g->tmp[0], (size_t)(N + 1) * 8 + 256));
-  uint64_t *s64 = P<uint64_t>(g->tmp[0]);
+  TRY(ensure(g->lay[0], (size_t)(N + 1) * 8 + 256));
+  uint64_t *s64 = P<uint64_t>(g->lay[0]);
   TRY((exclusive_scan<uint32_t, uint64_t>(P<uint32_t>(g->slen), s64, N, stmp, s)));
-  TRY(ensure(g->tmp[1], (size_t)(N + 1) * 8 + 256));
-  uint64_t *lpos = P<uint64_t>(g->tmp[1]);
+  TRY(ensure(g->lay[1], (size_t)(N + 1) * 8 + 256));
+  uint64_t *lpos = P<uint64_t>(g->lay[1]);
   TRY((exclusive_scan<uint64_t, uint64_t>(P<uint64_t>(g->llen), lpos, N, stmp, s)));
   TRY(ensure(g->lflag, (size_t)(N + 1) * 4 + 256));
   int32_t *lscan = P<int32_t>(g->lflag);
-  TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->tmp[2]), lscan, N, stmp, s)));
-  TRY(ensure(g->tmp[6], (size_t)(N + 1) * 8 + 256));
-  uint64_t *k64 = P<uint64_t>(g->tmp[6]);
+  TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->hubf), lscan, N, stmp, s)));
+  TRY(ensure(g->lay[2], (size_t)(N + 1) * 8 + 256));
+  uint64_t *k64 = P<uint64_t>(g->lay[2]);
   TRY((exclusive_scan<uint32_t, uint64_t>(P<uint32_t>(g->klen), k64, N, stmp, s)));
   uint64_t tot[3];
   int32_t nl;
@@ -906,7 +878,7 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   m.nlong = nl;
   m.wbytes = g->wdtype == PL_W_BF16 ? 2 : 4;
   TRY(ensure(m.rp_s, (size_t)(N + 1 + kRpPad) * 4));
-  k_rp_pack<<<grid_for(N + 1 + kRpPad, 256), 256, 0, s>>>(s64, P<uint8_t>(g->tmp[2]), N,
+  k_rp_pack<<<grid_for(N + 1 + kRpPad, 256), 256, 0, s>>>(s64, P<uint8_t>(g->hubf), N,
                                                          P<uint32_t>(m.rp_s));
   note_launch();
   TRY(ensure(m.keys, (size_t)(N + 1) * 4 + 16));
@@ -923,9 +895,9 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   TRY(ensure(m.lhl, (size_t)nl * 4 + 16));
   TRY(ensure(m.longidx, (size_t)N * 4 + 16));
   TRY(ensure(m.lchunk, (size_t)(nl + 1) * 4));
-  TRY(ensure(g->tmp[3], (size_t)(nl + 1) * 4 + 256));
-  int32_t *nch = P<int32_t>(g->tmp[3]);
-  k_layout_long<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->tmp[2]), lscan, lpos,
+  TRY(ensure(g->lay[3], (size_t)(nl + 1) * 4 + 256));
+  int32_t *nch = P<int32_t>(g->lay[3]);
+  k_layout_long<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->hubf), lscan, lpos,
                                                  P<uint64_t>(g->clen), m.nnz_s,
                                                  P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
                                                  P<int32_t>(m.longidx), nch);
@@ -980,30 +952,25 @@ static pl_status ensure_row_arrays(pl_graph *g) {
   TRY(ensure(g->llen, (size_t)N * 8 + 16));
   TRY(ensure(g->klen, (size_t)N * 4 + 16));
   TRY(ensure(g->clen, (size_t)N * 8 + 16));
-  TRY(ensure(g->tmp[2], (size_t)N + 256));
+  TRY(ensure(g->hubf, (size_t)N + 256));
   return PL_OK;
 }
 
-pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s) {
+// Layout of the static split matrix from the static row pointers; the
+// entries and degree sums are written by the static compaction.
+pl_status prepare_static_layout(pl_graph *g, cudaStream_t s) {
   const int64_t N = g->N;
-  HintGeo G = make_geo(g);
+  HintGeo G{};
+  G.N = N;
+  G.Nst = g->Nst;
   pl_status st = ensure_row_arrays(g);
   if (st != PL_OK) return st;
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 0, P<int64_t>(g->srp), nullptr, nullptr, nullptr,
                                              nullptr, nullptr, P<uint32_t>(g->slen),
-                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]),
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
                                              P<uint32_t>(g->klen), P<uint64_t>(g->clen));
   note_launch();
-  st = layout(g, g->st, 0, s);
-  if (st != PL_OK) return st;
-  SpMat &m = g->st;
-  k_assemble_static<<<grid_for(N * 32, 256), 256, 0, s>>>(
-      N, g->Nst, g->wdtype, P<int64_t>(g->srp), P<int32_t>(g->scol), g->sw.p, P<uint32_t>(m.rp_s),
-      P<int32_t>(m.longidx), P<uint64_t>(m.lptr), P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
-      P<dfl>(m.psum));
-  note_launch();
-  TRY(cudaGetLastError());
-  return PL_OK;
+  return layout(g, g->st, 0, s);
 }
 
 pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaStream_t s) {
@@ -1022,23 +989,47 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->tmp[7], scan_tmp_bytes(N + 1) + 4096));
   stmp = g->tmp[7].p;
 
-  // H1: bins and macro overlaps of movable cells
+  // H1: bins and macro overlaps of movable cells (bucket counts by atomics
+  // only when the buckets do not fit the tiled counting sort)
+  const int nbk = 2 * NB;
+  const bool tiled = nbk <= kMaxSmemBuckets;
   TRY(ensure(g->cell_bin, (size_t)C * 4 + 16));
   TRY(ensure(g->n_ovl, (size_t)C * 4 + 16));
-  TRY(ensure(g->bcnt, (size_t)(2 * NB + 1) * 4));
+  TRY(ensure(g->bcnt, (size_t)(nbk + 1) * 4));
   TRY(ensure(g->mcnt, (size_t)(Mm + 1) * 4));
-  TRY(cudaMemsetAsync(g->bcnt.p, 0, (size_t)(2 * NB + 1) * 4, s));
+  if (!tiled) TRY(cudaMemsetAsync(g->bcnt.p, 0, (size_t)(nbk + 1) * 4, s));
   TRY(cudaMemsetAsync(g->mcnt.p, 0, (size_t)(Mm + 1) * 4, s));
   k_hint_cells<<<grid_for(C, 256), 256, 0, s>>>(
       G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
       P<int64_t>(g->gptr), P<uint32_t>(g->glist), P<float4>(g->ggeo), P<int32_t>(g->cell_bin),
-      P<int32_t>(g->n_ovl), P<int32_t>(g->bcnt), P<int32_t>(g->mcnt), status);
+      P<int32_t>(g->n_ovl), tiled ? nullptr : P<int32_t>(g->bcnt), P<int32_t>(g->mcnt), status);
   note_launch();
   // H2: bucket offsets
-  TRY(ensure(g->boff, (size_t)(2 * NB + 1) * 8));
+  TRY(ensure(g->boff, (size_t)(nbk + 1) * 8));
   TRY(ensure(g->moff, (size_t)(Mm + 1) * 8));
-  TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->bcnt), P<int64_t>(g->boff), 2 * NB, stmp, s)));
   TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->mcnt), P<int64_t>(g->moff), Mm, stmp, s)));
+  int32_t *cm = nullptr;
+  int64_t *cmo = nullptr;
+  int ntile = 1;
+  if (tiled) {
+    ntile = (int)((C + kBinTile - 1) / kBinTile) > 0 ? (int)((C + kBinTile - 1) / kBinTile) : 1;
+    const long long ncm = (long long)nbk * ntile;
+    TRY(ensure(g->tmp[5], (size_t)ncm * 4 + 256));
+    TRY(ensure(g->tmp[6], (size_t)(ncm + 1) * 8 + 256));
+    TRY(ensure(g->tmp[7], scan_tmp_bytes(ncm + 1) + 4096));
+    stmp = g->tmp[7].p;
+    cm = P<int32_t>(g->tmp[5]);
+    cmo = P<int64_t>(g->tmp[6]);
+    k_bin_tile_count<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
+                                                        P<uint8_t>(g->hflag),
+                                                        P<int32_t>(g->cell_bin), cm);
+    note_launch();
+    TRY((exclusive_scan<int32_t, int64_t>(cm, cmo, ncm, stmp, s)));
+    k_bucket_starts<<<grid_for(nbk + 1, 256), 256, 0, s>>>(nbk, ntile, cmo, P<int64_t>(g->boff));
+    note_launch();
+  } else {
+    TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->bcnt), P<int64_t>(g->boff), nbk, stmp, s)));
+  }
   int hst[8];
   TRY(d2h(hst, g->status.p, 8, s));
   if (hst[0] & ST_NONFINITE) {
@@ -1046,26 +1037,12 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     return PL_ERR_NONFINITE;
   }
   int64_t nbl, nml;
-  TRY(d2h(&nbl, P<int64_t>(g->boff) + 2 * NB, 1, s));
+  TRY(d2h(&nbl, P<int64_t>(g->boff) + nbk, 1, s));
   TRY(d2h(&nml, P<int64_t>(g->moff) + Mm, 1, s));
   // H3-H4: bin buckets (ascending cell id) and macro lists (sorted)
-  const int nbk = 2 * NB;
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
-  if (nbk <= kMaxSmemBuckets) {
-    const int ntile = (int)((C + kBinTile - 1) / kBinTile) > 0 ? (int)((C + kBinTile - 1) / kBinTile) : 1;
-    const long long ncm = (long long)nbk * ntile;
-    TRY(ensure(g->tmp[5], (size_t)ncm * 4 + 256));
-    TRY(ensure(g->tmp[6], (size_t)(ncm + 1) * 8 + 256));
-    TRY(ensure(g->tmp[7], scan_tmp_bytes(ncm + 1) + 4096));
-    stmp = g->tmp[7].p;
-    int32_t *cm = P<int32_t>(g->tmp[5]);
-    int64_t *cmo = P<int64_t>(g->tmp[6]);
-    k_bin_tile_count<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
-                                                        P<uint8_t>(g->hflag),
-                                                        P<int32_t>(g->cell_bin), cm);
-    note_launch();
-    TRY((exclusive_scan<int32_t, int64_t>(cm, cmo, ncm, stmp, s)));
+  if (tiled) {
     k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
                                                           P<uint8_t>(g->hflag),
                                                           P<int32_t>(g->cell_bin), cmo,
@@ -1104,6 +1081,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   float *phif = P<float>(g->tmp[4]);
   int64_t *hub_len = reinterpret_cast<int64_t *>(P<char>(g->tmp[4]) + phib);
   LevelBufs lv;
+  int nlev = 0;  // launches: level L exists while 64^(L+1) < the longest bin
   {
     size_t sizes[kMaxLevels], tot = 0;
     size_t prev = (size_t)nbl;
@@ -1118,10 +1096,21 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       lv.base[k] = q;
       q += sizes[k];
     }
+    double span = 64.0;
+    while (nlev < kMaxLevels && (double)nbl > span) {
+      ++nlev;
+      span *= 64.0;
+    }
+    for (int L = 0; L < nlev; ++L) {
+      k_dens_level<<<grid_for((long long)sizes[L], 256, 152 * 16), 256, 0, s>>>(
+          NB, L, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch),
+          L ? lv.base[L - 1] : nullptr, lv.base[L], (long long)sizes[L]);
+      note_launch();
+    }
   }
-  k_bin_density<<<NB < 152 * 16 ? NB : 152 * 16, 256, 0, s>>>(
-      G, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch),
-      P<double>(g->amac), g->abin, p->capacity, p->mu, lv, P<double>(g->Db), P<double>(g->Cb),
+  k_dens_final<<<grid_for(NB, 128), 128, 0, s>>>(
+      G, nlev, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch), lv,
+      P<double>(g->amac), g->abin, p->capacity, p->mu, P<double>(g->Db), P<double>(g->Cb),
       P<double>(g->phi), phif, hub_len);
   note_launch();
   // H6-H7: row lengths and layout
@@ -1130,7 +1119,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 1, P<int64_t>(g->srp), P<uint8_t>(g->hflag),
                                              P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
                                              P<int64_t>(g->moff), hub_len, P<uint32_t>(g->slen),
-                                             P<uint64_t>(g->llen), P<uint8_t>(g->tmp[2]),
+                                             P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
                                              P<uint32_t>(g->klen), P<uint64_t>(g->clen));
   note_launch();
   st = layout(g, g->hm, 1, s);

@@ -85,9 +85,7 @@ struct pl_graph {
   pl::Buf star_net;    // int32 [S]
   pl::Buf macro_cell;  // int32 [Mm]
   pl::Buf cell_macro;  // int32 [C+1] scan of macro flags
-  pl::Buf srp;         // int64 [Nst+1]
-  pl::Buf scol;        // int32 [nnz_static]
-  pl::Buf sw;          // float / uint16 [nnz_static]
+  pl::Buf srp;         // int64 [Nst+1] static row pointers (entries live in st)
   pl::Buf base_w;      // double [C]
   pl::Buf hflag;       // uint8 [C] movable with baseWeight > 0
   pl::Buf sdeg;        // double [Nst] static degree (stored weights)
@@ -125,6 +123,8 @@ struct pl_graph {
   pl::Buf status;         // int32 [8]
   pl::Scratch scr;
   pl::Buf tmp[8];
+  pl::Buf lay[4];         // layout scratch (scans of row lengths, chunk counts)
+  pl::Buf hubf;           // uint8 [N] hub flags of a layout
 };
 
 namespace pl {
@@ -134,7 +134,7 @@ pl_status cuda_fail(cudaError_t e, const char *what);
 
 pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cudaStream_t s);
 pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy, cudaStream_t s);
-pl_status prepare_static_matrix(pl_graph *g, cudaStream_t s);
+pl_status prepare_static_layout(pl_graph *g, cudaStream_t s);
 pl_status run_init_signal(pl_graph *g, uint64_t seed, const float *xy0, float *xy, cudaStream_t s);
 pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
 pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
