@@ -400,9 +400,17 @@ constexpr int kSpmmThreads = 128;
 constexpr int kSpmmWarps = kSpmmThreads / 32;
 constexpr int kSpmmBlocksPerSm = 6;
 
-// Warp w of the grid takes units w, w + nwarps, ...: its hub chunks first,
-// then its tiles as a two-stage pipeline (stage the next tile while the
-// current one is gathered and summed; descriptors one tile further ahead).
+// Hub chunks: warp w of the grid takes chunks w, w + nwarps, ...
+template <int WT, int MODE>
+__global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT, MODE>(A, (int)c);
+}
+
+// Short tiles: warp w of the grid takes tiles w, w + nwarps, ... as a
+// two-stage pipeline (stage the next tile while the current one is gathered
+// and summed; descriptors one tile further ahead).
 template <int WT, int MODE>
 __global__ void __launch_bounds__(kSpmmThreads, kSpmmBlocksPerSm) k_spmm(StepArgs A) {
   __shared__ __align__(16) TileStage<WT> stage_all[kSpmmWarps][2];
@@ -410,13 +418,10 @@ __global__ void __launch_bounds__(kSpmmThreads, kSpmmBlocksPerSm) k_spmm(StepArg
   const int wid = threadIdx.x >> 5;
   float2 *sp = sp_all[wid];
   TileStage<WT> *stg = stage_all[wid];
-  const long long nunits = (long long)A.nchunks + A.ntiles;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  long long u = gw;
-  for (; u < A.nchunks; u += nw) warp_chunk<WT, MODE>(A, (int)u);
-  if (u >= nunits) return;
-  long long t = u - A.nchunks;
+  long long t = gw;
+  if (t >= A.ntiles) return;
   int4 c0 = __ldg(A.tdesc + t), c1 = __ldg(A.tdesc + t + 1);
   stage_tile<WT>(A, c0, c1, &stg[0]);
   cp_commit();
@@ -591,9 +596,9 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
+// One sparse product: the hub chunks, then the short tiles (same stream).
 template <int MODE>
 static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s) {
-  const long long nunits = (long long)A.nchunks + A.ntiles;
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -601,7 +606,7 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  // one wave of resident blocks (units are dealt to warps statically)
+  // one wave of resident blocks (tiles are dealt to warps statically)
   static int occ[2] = {0, 0};
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
@@ -610,11 +615,18 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm<0, MODE>, kSpmmThreads, 0);
     occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
   }
-  const long long want = (nunits + kSpmmWarps - 1) / kSpmmWarps;
-  const long long cap = (long long)occ[wi] * nsm;
-  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   const bool prof = prof_on();
   if (prof) prof_begin(s, MODE == MODE_HR ? PROF_HR : PROF_GIFT, bytes);
+  if (A.nchunks > 0) {
+    const long long want = ((long long)A.nchunks + 7) / 8;
+    const int hgrid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
+    if (wi) k_spmm_hub<1, MODE><<<hgrid, 256, 0, s>>>(A);
+    else k_spmm_hub<0, MODE><<<hgrid, 256, 0, s>>>(A);
+    note_launch();
+  }
+  const long long want = ((long long)A.ntiles + kSpmmWarps - 1) / kSpmmWarps;
+  const long long cap = (long long)occ[wi] * nsm;
+  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   if (wi) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
   else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
   note_launch();
