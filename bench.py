@@ -108,16 +108,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(cells_target_s: float = 20.0):
-    """The FP64 oracle (single host thread) on a bounded sample of the
-    workload: one netlist of the same recipe at 210k cells (the medium
-    configuration), full path (static graph, GSP init, 3 refinement rounds,
-    HPWL).  Returns movable cells per second."""
+def oracle_params(config):
+    """The oracle's parameters for a bench workload (same names as the library's)."""
+    return dict(WORKLOADS[config][1])
+
+
+def oracle_sample(nl, config):
+    """The FP64 oracle (single host thread) on one step of the bench workload
+    itself (the same netlist: static graph, GSP init, 3 refinement rounds,
+    HPWL); about 10-30 s on one core.  Returns movable cells per second and
+    the seconds it took."""
     import oracle
-    from paper_2511_10073_gb300 import netgen
-    nl = netgen.make_netlist("medium", 1)
-    kw = dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
-              tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))
+    oracle.build()
+    kw = oracle_params(config)
     t0 = time.perf_counter()
     o = oracle.Oracle(nl, **kw)
     gx, gy = o.run(1)
@@ -133,8 +136,10 @@ def run_reference(args):
     import oracle
     from paper_2511_10073_gb300 import netgen
     oracle.build()
-    nl = netgen.make_netlist("medium", args.seed)
-    kw = dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0), tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))
+    # each step: the half-size netlist of the workload's recipe with its parameters
+    sample = "half" if args.config == "large" else args.config
+    nl = netgen.make_netlist(WORKLOADS[sample][0], args.seed)
+    kw = oracle_params(args.config)
 
     def step():
         o = oracle.Oracle(nl, **kw)
@@ -153,9 +158,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.config, "sample": "210k-cell netlist of the same recipe"},
+        "config": {"workload": args.config, "sample": f"{sample} netlist of the same recipe"},
         "cpu_baseline": {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": "one 210k-cell netlist of the workload's recipe per step "
+                         "sample": f"one {sample} netlist of the workload's recipe per step "
                                    "(full path: static graph, GSP init, 3 refinement rounds, HPWL)"},
         "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -221,7 +226,10 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         if rank == 0:
-            print(json.dumps({"profile_one": args.config, "movable_cells": nl.num_movable}))
+            info = g.info()
+            print(json.dumps({"profile_one": args.config, "movable_cells": nl.num_movable,
+                              "nodes": info["N"], "static_nnz": info["static_nnz"],
+                              "augmented_nnz": info["nnz"], "hub_rows": info["hub_rows"]}))
         return
 
     try:
@@ -324,7 +332,8 @@ def main():
                    "augmented_nnz": info["nnz"], "hub_rows": info["hub_rows"],
                    "l2": "inputs larger than L2 (each sparse product streams >400 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_spmm (refinement filter A4)", "bound": "hbm",
+        "roofline": {"kernel": "k_spmm_hub + k_spmm (one sparse product of the refinement filter, A4)",
+                     "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": "measured" if pk else "fallback",
@@ -337,10 +346,10 @@ def main():
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_sample()
+        v, dt = oracle_sample(nl, args.config)
         line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one 210k-cell netlist of the same recipe, full path "
-                                          f"(static graph, GSP init, 3 refinement rounds, HPWL), "
+                                "sample": f"one step of the bench workload itself ({args.config}: "
+                                          f"static graph, GSP init, 3 refinement rounds, HPWL), "
                                           f"{dt:.1f} s single-threaded"}
     print(json.dumps(line), flush=True)
     if dist:

@@ -118,10 +118,10 @@ static void destroy(pl_graph *g) {
   Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
                  &g->net_p, &g->star_of, &g->star_net, &g->macro_cell, &g->cell_macro, &g->srp,
                  &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
-                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
+                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
                  &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur,
                  &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->klen, &g->clen, &g->lflag,
-                 &g->mac_base,
+                 &g->crank, &g->tpos, &g->mac_base,
                  &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,
                  &g->acc, &g->gsc, &g->status, &g->scr.buf};
   for (Buf *b : bufs) release(*b);

@@ -49,7 +49,7 @@ struct StepArgs {
   const int32_t *lchunk;
   const int32_t *chunk_lr;
   int32_t nchunks;
-  double *part;
+  float4 *part;  // per hub chunk: (sx.hi, sx.lo, sy.hi, sy.lo)
   int32_t *tick;
   const float2 *x;
   float2 *y;
@@ -347,6 +347,15 @@ __device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp,
 
 // A hub chunk covers positions [q0, q1) of the row's st piece followed by its
 // hm piece.
+// Ticket of a hub row: a device-scope atomic add with release semantics, so
+// the partial written before it is visible to whichever warp sees the last
+// ticket (that warp fences before reading the partials).
+__device__ __forceinline__ int ticket_add_release(int *p) {
+  int old;
+  asm volatile("atom.add.release.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
 template <int WT, int MODE>
 __device__ void warp_chunk(const StepArgs &A, int c) {
   const int lane = threadIdx.x & 31;
@@ -366,22 +375,22 @@ __device__ void warp_chunk(const StepArgs &A, int c) {
   sy = warp_sum_df(sy);
   int last = 0;
   if (lane == 0) {
-    A.part[2 * (int64_t)c] = df_to_d(sx);
-    A.part[2 * (int64_t)c + 1] = df_to_d(sy);
-    __threadfence();
-    last = atomicAdd(&A.tick[l], 1) == nch - 1;
+    A.part[c] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+    last = ticket_add_release(&A.tick[l]) == nch - 1;
   }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
-  double tx = 0.0, ty = 0.0;
+  dfl px{0.f, 0.f}, py{0.f, 0.f};
   for (int k = lane; k < nch; k += 32) {
-    tx += __ldcg(&A.part[2 * (int64_t)(c0 + k)]);
-    ty += __ldcg(&A.part[2 * (int64_t)(c0 + k) + 1]);
+    const float4 q = __ldcg(&A.part[c0 + k]);
+    df_add_df(px, dfl{q.x, q.y});
+    df_add_df(py, dfl{q.z, q.w});
   }
-  tx = warp_sum(tx);
-  ty = warp_sum(ty);
+  px = warp_sum_df(px);
+  py = warp_sum_df(py);
   if (lane == 0) {
+    const double tx = df_to_d(px), ty = df_to_d(py);
     double av, bv;
     if (MODE == MODE_HR) {
       av = A.c64l[l];
@@ -586,7 +595,7 @@ static void fill_matrix(StepArgs &A, const SpMat &st, const SpMat *hm) {
   A.lchunk = P<int32_t>(m.lchunk);
   A.chunk_lr = P<int32_t>(m.chunk_lr);
   A.nchunks = m.nchunks;
-  A.part = const_cast<double *>(P<double>(m.part));
+  A.part = const_cast<float4 *>(P<float4>(m.part));
   A.tick = const_cast<int32_t *>(P<int32_t>(m.tick));
 }
 

@@ -372,10 +372,19 @@ __global__ void k_pin_fixed(const int32_t *pin_node, const int32_t *pin_cell, co
 // Macro area inside each bin, summed over macros in macro order (FP64).  Warp
 // per bin: lanes test 32 macros at a time (FP32 box reject, then the FP64
 // overlap), lane 0 adds the overlapping ones in macro order.
-__global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const int32_t *macro_cell,
-                                 const float *cw, const float *ch, const float *fx,
-                                 const float *fy, double xl, double yl, double wb, double hb,
-                                 double *amac) {
+// Centre and size of every macro (float4), read by the area and grid kernels.
+__global__ void k_macro_geo(int32_t Mm, const int32_t *macro_cell, const float *fx,
+                            const float *fy, const float *cw, const float *ch, float4 *geo) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mm; m += gridDim.x * blockDim.x) {
+    const int c = macro_cell[m];
+    geo[m] = make_float4(fx[c], fy[c], cw[c], ch[c]);
+  }
+}
+
+// Macro area inside each bin (warp per bin): lanes test 32 macros at a time,
+// four such groups loaded at once; the overlaps are added in macro order.
+__global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const float4 *mgeo,
+                                 double xl, double yl, double wb, double hb, double *amac) {
   const int lane = threadIdx.x & 31;
   for (long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; b < NB;
        b += ((long long)gridDim.x * blockDim.x) >> 5) {
@@ -384,28 +393,37 @@ __global__ void k_bin_macro_area(int32_t NB, int32_t nbx, int32_t Mm, const int3
     double byl = yl + (double)by * hb, byh = yl + (double)(by + 1) * hb;
     float fxl = (float)bxl, fxh = (float)bxh, fyl = (float)byl, fyh = (float)byh;
     double a = 0.0;
-    for (int m0 = 0; m0 < Mm; m0 += 32) {
-      int m = m0 + lane;
-      double ov = 0.0;
-      if (m < Mm) {
-        int c = macro_cell[m];
-        float hwf = cw[c] * 0.5f, hhf = ch[c] * 0.5f;
-        if (!(fx[c] - hwf > fxh + 1.f || fx[c] + hwf < fxl - 1.f || fy[c] - hhf > fyh + 1.f ||
-              fy[c] + hhf < fyl - 1.f)) {
-          double hwm = __dmul_rn((double)cw[c], 0.5), hhm = __dmul_rn((double)ch[c], 0.5);
-          double ox = __dadd_rn(fmin(bxh, __dadd_rn((double)fx[c], hwm)),
-                                -fmax(bxl, __dadd_rn((double)fx[c], -hwm)));
-          double oy = __dadd_rn(fmin(byh, __dadd_rn((double)fy[c], hhm)),
-                                -fmax(byl, __dadd_rn((double)fy[c], -hhm)));
-          if (ox > 0.0 && oy > 0.0) ov = __dmul_rn(ox, oy);
-        }
+    for (int m0 = 0; m0 < Mm; m0 += 4 * 32) {
+      float4 g4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = m0 + u * 32 + lane;
+        g4[u] = m < Mm ? mgeo[m] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      unsigned hit = __ballot_sync(0xffffffffu, ov != 0.0);
-      while (hit) {
-        int src = __ffs(hit) - 1;
-        hit &= hit - 1;
-        double t = __shfl_sync(0xffffffffu, ov, src);
-        a = __dadd_rn(a, t);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = m0 + u * 32 + lane;
+        const float4 g = g4[u];
+        double ov = 0.0;
+        if (m < Mm) {
+          float hwf = g.z * 0.5f, hhf = g.w * 0.5f;
+          if (!(g.x - hwf > fxh + 1.f || g.x + hwf < fxl - 1.f || g.y - hhf > fyh + 1.f ||
+                g.y + hhf < fyl - 1.f)) {
+            double hwm = __dmul_rn((double)g.z, 0.5), hhm = __dmul_rn((double)g.w, 0.5);
+            double ox = __dadd_rn(fmin(bxh, __dadd_rn((double)g.x, hwm)),
+                                  -fmax(bxl, __dadd_rn((double)g.x, -hwm)));
+            double oy = __dadd_rn(fmin(byh, __dadd_rn((double)g.y, hhm)),
+                                  -fmax(byl, __dadd_rn((double)g.y, -hhm)));
+            if (ox > 0.0 && oy > 0.0) ov = __dmul_rn(ox, oy);
+          }
+        }
+        unsigned hit = __ballot_sync(0xffffffffu, ov != 0.0);
+        while (hit) {
+          int src = __ffs(hit) - 1;
+          hit &= hit - 1;
+          double t = __shfl_sync(0xffffffffu, ov, src);
+          a = __dadd_rn(a, t);
+        }
       }
     }
     if (lane == 0) amac[b] = a;
@@ -728,9 +746,16 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY(ensure(g->amac, (size_t)g->NB * 8 + 16));
   TRY(ensure(g->Cb, (size_t)g->NB * 8 + 16));
+  TRY(ensure(g->mgeo, (size_t)g->Mm * 16 + 16));
+  if (g->Mm) {
+    k_macro_geo<<<grid_for(g->Mm, 256), 256, 0, s>>>(g->Mm, P<int32_t>(g->macro_cell),
+                                                     P<float>(g->cfx), P<float>(g->cfy),
+                                                     P<float>(g->cw), P<float>(g->ch),
+                                                     P<float4>(g->mgeo));
+    note_launch();
+  }
   k_bin_macro_area<<<grid_for((long long)g->NB * 32, 256), 256, 0, s>>>(
-      g->NB, g->nbx, g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch),
-      P<float>(g->cfx), P<float>(g->cfy), g->xl, g->yl, g->wb, g->hb, P<double>(g->amac));
+      g->NB, g->nbx, g->Mm, P<float4>(g->mgeo), g->xl, g->yl, g->wb, g->hb, P<double>(g->amac));
   note_launch();
 
   // macro lookup grid

@@ -69,7 +69,8 @@ __device__ __forceinline__ bool near_bf16_tie(float v) {
   return d >= -kNearTie && d <= kNearTie;
 }
 // -((e^{-maxRatio} * phi) * bw) for cell centre (x, y) and bin (xx, yy), FP64.
-__device__ double bin_w_exact(float x, float y, int xx, int yy, const HintGeo &G, double phi,
+// Kept out of line: the fast path must not carry any of its FP64 work.
+__device__ __noinline__ double bin_w_exact(float x, float y, int xx, int yy, const HintGeo &G, double phi,
                               double bw) {
   double xb = __dadd_rn(G.xl, __dmul_rn((double)xx + 0.5, G.wb));
   double yb = __dadd_rn(G.yl, __dmul_rn((double)yy + 0.5, G.hb));
@@ -79,7 +80,7 @@ __device__ double bin_w_exact(float x, float y, int xx, int yy, const HintGeo &G
   return -t;
 }
 // -(e^{-maxRatio} * bw) for a cell centre and a macro (centre xm, ym; size wm, hm).
-__device__ double macro_w_exact(float x, float y, float xm, float ym, float wm, float hm,
+__device__ __noinline__ double macro_w_exact(float x, float y, float xm, float ym, float wm, float hm,
                                 double bw) {
   double dx = fabs(__dadd_rn((double)x, -(double)xm)), dy = fabs(__dadd_rn((double)y, -(double)ym));
   double r = fmax(__ddiv_rn(dx, __dmul_rn((double)wm, 0.5)), __ddiv_rn(dy, __dmul_rn((double)hm, 0.5)));
@@ -111,6 +112,25 @@ __device__ __forceinline__ void copy_w(void *dst, const void *src, int wdtype, u
     reinterpret_cast<uint16_t *>(dst)[kd] = reinterpret_cast<const uint16_t *>(src)[ks];
   else
     reinterpret_cast<float *>(dst)[kd] = reinterpret_cast<const float *>(src)[ks];
+}
+
+// Stores the stored form of v at k and, when k2 is not ~0, at k2 (the
+// transposed entry of a symmetric pair); returns the value it stores.
+__device__ __forceinline__ float store_w2(void *wbuf, int wdtype, uint64_t k, uint64_t k2, float v) {
+  if (wdtype == PL_W_BF16) {
+    const uint16_t h = f2bf16(v);
+    reinterpret_cast<uint16_t *>(wbuf)[k] = h;
+    if (k2 != ~0ull) reinterpret_cast<uint16_t *>(wbuf)[k2] = h;
+    return bf16_to_f(h);
+  }
+  reinterpret_cast<float *>(wbuf)[k] = v;
+  if (k2 != ~0ull) reinterpret_cast<float *>(wbuf)[k2] = v;
+  return v;
+}
+__device__ __forceinline__ float store_bits2(void *wbuf, uint64_t k, uint64_t k2, uint16_t h) {
+  reinterpret_cast<uint16_t *>(wbuf)[k] = h;
+  if (k2 != ~0ull) reinterpret_cast<uint16_t *>(wbuf)[k2] = h;
+  return bf16_to_f(h);
 }
 
 // --------------------------------------------------------- H1: cells
@@ -199,11 +219,13 @@ __global__ void __launch_bounds__(256) k_bin_tile_count(int32_t C, int nbk, int 
 
 // Rounds of blockDim cells; inside a round the warps take turns (so equal
 // buckets keep cell order), lanes of a warp rank themselves with match_any.
+// A hint cell's place in the list goes to crank.
 __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, int ntile,
                                                           const uint8_t *ckind,
                                                           const uint8_t *hflag,
                                                           const int32_t *cell_bin,
-                                                          const int64_t *off, uint32_t *blist) {
+                                                          const int64_t *off, uint32_t *blist,
+                                                          int32_t *crank) {
   extern __shared__ int32_t run[];
   for (int k = threadIdx.x; k < nbk; k += blockDim.x) run[k] = 0;
   __syncthreads();
@@ -224,7 +246,13 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
           run[key] = before + __popc(grp);
         }
         before = __shfl_sync(0xffffffffu, before, leader);
-        if (mv) blist[off[(long long)key * ntile + t] + before + __popc(grp & lt)] = (uint32_t)i;
+        if (mv) {
+          const long long pos = off[(long long)key * ntile + t] + before + __popc(grp & lt);
+          blist[pos] = (uint32_t)i;
+          // a hint cell's place in the bucket list (its rank once the
+          // bucket's start is taken off)
+          if (!(key & 1)) crank[i] = (int32_t)pos;
+        }
       }
       __syncthreads();
     }
@@ -557,19 +585,21 @@ __device__ __forceinline__ dfl df_ratio(float x, float c, float h) {
 
 // Hint part of the rows of cells, macro pins and stars (thread per row): for a
 // hint cell its macro entries (ascending macro) and window bin entries
-// (row-major), written to the row's hm place; the degree sums of the whole
-// augmented row are the static ones plus the hint entries.  The window ratios
-// |x - x_b| / (w_b / 2) = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u
-// (double-float, once per cell) as exact double-float differences; macro
-// ratios are double-float quotients.  No FP64 arithmetic on this path except
-// the recomputation of weights near a bf16 rounding midpoint.
-__global__ void __launch_bounds__(256) k_assemble_hints(
+// (row-major), written to the row's hm place, and (tpos given) the same bin
+// entries in the bin rows; the degree sums of the whole augmented row are the
+// static ones plus the hint entries.  The window ratios |x - x_b| / (w_b / 2)
+// = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u (double-float, once
+// per cell) as exact double-float differences; macro ratios are double-float
+// quotients.  FP64 only recomputes weights near a bf16 rounding midpoint.
+__global__ void __launch_bounds__(256, 3) k_assemble_hints(
     HintGeo G, int wdtype, const uint32_t *hrp, const int32_t *longidx, const uint64_t *lptr,
     const dfl *sdsum, const dfl *spsum, const uint8_t *hflag, const int32_t *cell_bin,
     const int32_t *n_ovl, const float2 *xy, const float *cw, const float *ch,
     const int64_t *gptr, const uint32_t *glist, const float4 *ggeo, const double *base_w,
-    const float *phif, const double *phid, int32_t *col, void *w, dfl *dsum, dfl *psum,
-    uint64_t *mac_base, uint64_t *bin_base) {
+    const float *phif, const double *phid, const uint64_t *tpos, int W, const int32_t *crank,
+    const int64_t *boff, int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
+    uint64_t *bin_base) {
+  const bool bf = wdtype == PL_W_BF16;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.Nst;
        v += (long long)gridDim.x * blockDim.x) {
     dfl Dl = sdsum[v], Pl = spsum[v];
@@ -585,20 +615,28 @@ __global__ void __launch_bounds__(256) k_assemble_hints(
       const long long gk = (long long)ky * G.gnx + kx;
       uint64_t k = mb;
       const float cwv = cw[v], chv = ch[v];
-      for (long long q = gptr[gk]; q < gptr[gk + 1]; ++q) {
-        const float4 mg = ggeo[q];
-        if (!overlaps(p.x, p.y, cwv, chv, mg.x, mg.y, mg.z, mg.w)) continue;
-        const int m = (int)glist[q];
-        const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
-        const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
-        const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
-        col[k] = (int32_t)(G.mv0 + m);
-        if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
-          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
-                                                                 mg.w, bw))));
-        else
-          acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
-        ++k;
+      const long long qa = gptr[gk], qb = gptr[gk + 1];
+      for (long long q0 = qa; q0 < qb; q0 += 4) {
+        float4 mgs[4];  // four grid entries' geometry loaded at once
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mgs[u] = q0 + u < qb ? ggeo[q0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long q = q0 + u;
+          const float4 mg = mgs[u];
+          if (q >= qb || !overlaps(p.x, p.y, cwv, chv, mg.x, mg.y, mg.z, mg.w)) continue;
+          const int m = (int)glist[q];
+          const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
+          const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
+          const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
+          col[k] = (int32_t)(G.mv0 + m);
+          if (bf && near_bf16_tie(wv))
+            acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
+                                                                   mg.w, bw))));
+          else
+            acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+          ++k;
+        }
       }
       const uint64_t bb0 = mb + n_ovl[v];
       const int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
@@ -606,22 +644,47 @@ __global__ void __launch_bounds__(256) k_assemble_hints(
       const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
       const dfl ux = df_offset_scale(p.x, G.xlh, G.xll, G.iwh, G.iwl);
       const dfl uy = df_offset_scale(p.y, G.ylh, G.yll, G.ihh, G.ihl);
-      const float uxh = ux.hi, uxl = ux.lo, uyh = uy.hi, uyl = uy.lo;
+      const uint64_t rk = tpos ? (uint64_t)(crank[v] - boff[2 * b]) : 0ull;
       k = bb0;
       for (int yy = y0; yy <= y1; ++yy) {
         // e^{-max(rx, ry)} is e^{-rx} or e^{-ry}
-        const dfl ry = df_absdiff(uyh, uyl, (float)(2 * yy + 1));
+        const dfl ry = df_absdiff(uy.hi, uy.lo, (float)(2 * yy + 1));
         const float ey = exp_neg_df(ry);
-        for (int xx = x0; xx <= x1; ++xx, ++k) {
-          const dfl rx = df_absdiff(uxh, uxl, (float)(2 * xx + 1));
-          const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
-          const int bb = yy * G.nbx + xx;
-          const float wv = -((e * phif[bb]) * bwf);
-          col[k] = (int32_t)(G.bn0 + bb);
-          if (wdtype == PL_W_BF16 && near_bf16_tie(wv))
-            acc_deg(Dl, Pl, store_bits(w, k, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))));
-          else
-            acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+        const int y0b = max(0, yy - G.hy);
+        for (int xc = x0; xc <= x1; xc += 4) {
+          // four window bins' phi and bin-row places loaded at once
+          float ph[4];
+          uint64_t tp[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int xx = xc + u, bb = yy * G.nbx + xx;
+            ph[u] = xx <= x1 ? phif[bb] : 0.f;
+            tp[u] = ~0ull;
+            if (tpos && xx <= x1) {
+              const int x0b = max(0, xx - G.hx);
+              const int nxb = min(G.nbx - 1, xx + G.hx) - x0b + 1;
+              tp[u] = tpos[(long long)bb * W + (by - y0b) * nxb + (bx - x0b)] + rk;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int xx = xc + u;
+            if (xx > x1) break;
+            const dfl rx = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
+            const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
+            const int bb = yy * G.nbx + xx;
+            const float wv = -((e * ph[u]) * bwf);
+            col[k] = (int32_t)(G.bn0 + bb);
+            // the same entry in the row of bin bb: this cell's bucket run
+            // inside bb's window, at the cell's rank
+            const uint64_t k2 = tp[u];
+            if (k2 != ~0ull) col[k2] = (int32_t)v;
+            if (bf && near_bf16_tie(wv))
+              acc_deg(Dl, Pl, store_bits2(w, k, k2, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))));
+            else
+              acc_deg(Dl, Pl, store_w2(w, wdtype, k, k2, wv));
+            ++k;
+          }
         }
       }
       mac_base[v] = mb;
@@ -629,6 +692,51 @@ __global__ void __launch_bounds__(256) k_assemble_hints(
     }
     dsum[v] = df_norm(Dl);
     psum[v] = df_norm(Pl);
+  }
+}
+
+// Where the cells of each window bin start in a bin row: the row of bin b is
+// the concatenation of the hint buckets of its window bins in row-major
+// order, so window position j of b starts at the row's first entry plus the
+// sizes of the buckets before it.
+__global__ void k_bin_tpos(HintGeo G, int W, const int64_t *boff, const int32_t *longidx,
+                           const uint64_t *lptr, uint64_t *tpos) {
+  const int NB = G.nbx * G.nby;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
+    const int bx = b % G.nbx, by = b / G.nbx;
+    uint64_t o = lptr[longidx[G.bn0 + b]];
+    int j = 0;
+    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
+      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx, ++j) {
+        const int bb = yy * G.nbx + xx;
+        tpos[(long long)b * W + j] = o;
+        o += (uint64_t)(boff[2 * bb + 1] - boff[2 * bb]);
+      }
+  }
+}
+
+// Degree partials of the chunks of bin rows (entries written by the cells'
+// assembly), one warp per chunk, double-float, in entry order per lane then
+// a fixed tree.
+__global__ void k_bin_sums(HintGeo G, int wdtype, int32_t nchunks, const int32_t *chunk_lr,
+                           const int32_t *lrow, const uint64_t *lptr, const int32_t *lchunk,
+                           const void *w, dfl *cpart) {
+  const int lane = threadIdx.x & 31;
+  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nchunks;
+       c += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int l = chunk_lr[c];
+    if (lrow[l] < G.bn0) continue;
+    const uint64_t base = lptr[l], len = lptr[l + 1] - base;
+    const uint64_t q0 = (uint64_t)(c - lchunk[l]) * kChunk;
+    const uint64_t q1 = q0 + kChunk < len ? q0 + kChunk : len;
+    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
+    for (uint64_t q = q0 + lane; q < q1; q += 32) acc_deg(D, Pp, load_w(w, wdtype, base + q));
+    D = warp_sum_df(D);
+    Pp = warp_sum_df(Pp);
+    if (lane == 0) {
+      cpart[2 * c] = D;
+      cpart[2 * c + 1] = Pp;
+    }
   }
 }
 
@@ -642,7 +750,8 @@ __global__ void __launch_bounds__(256) k_hub_chunks(
     HintGeo G, int wdtype, int32_t nchunks, const int32_t *chunk_lr, const int32_t *lrow,
     const uint64_t *lptr, const int32_t *lchunk, const int64_t *moff, const uint32_t *mlist,
     const int64_t *boff, const uint32_t *blist, const int32_t *cell_bin, const int32_t *n_ovl,
-    const uint64_t *mac_base, const uint64_t *bin_base, int32_t *col, void *w, dfl *cpart) {
+    const uint64_t *mac_base, const uint64_t *bin_base, int skip_bins, int32_t *col, void *w,
+    dfl *cpart) {
   __shared__ long long roff[1025];
   __shared__ int rbin[1024];
   __shared__ int nrun;
@@ -651,6 +760,7 @@ __global__ void __launch_bounds__(256) k_hub_chunks(
     const int l = chunk_lr[c];
     const int64_t v = lrow[l];
     if (v < G.mv0) continue;  // long rows of real nodes are assembled elsewhere
+    if (skip_bins && v >= G.bn0) continue;  // written by the cells' assembly
     const uint64_t base = lptr[l];
     const long long len = (long long)(lptr[l + 1] - base);
     const long long q0 = (long long)(c - lchunk[l]) * kChunk;
@@ -1043,10 +1153,12 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
   if (tiled) {
+    TRY(ensure(g->crank, (size_t)C * 4 + 16));
     k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
                                                           P<uint8_t>(g->hflag),
                                                           P<int32_t>(g->cell_bin), cmo,
-                                                          P<uint32_t>(g->blist));
+                                                          P<uint32_t>(g->blist),
+                                                          P<int32_t>(g->crank));
     note_launch();
   } else {
     TRY(ensure(g->bcur, (size_t)(nbk + 1) * 4));
@@ -1125,15 +1237,26 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   st = layout(g, g->hm, 1, s);
   if (st != PL_OK) return st;
   SpMat &m = g->hm;
-  // H9: hint parts of cells (and degrees of every real node)
+  // H9: hint parts of cells (and degrees of every real node); with the
+  // tiled bucket sort the cells also write their entries of the bin rows
   TRY(ensure(g->mac_base, (size_t)C * 8 + 16));
   TRY(ensure(g->bin_base, (size_t)C * 8 + 16));
+  const int W = (2 * g->hx + 1) * (2 * g->hy + 1);
+  uint64_t *tpos = nullptr;
+  if (tiled) {
+    TRY(ensure(g->tpos, (size_t)NB * W * 8 + 16));
+    tpos = P<uint64_t>(g->tpos);
+    k_bin_tpos<<<grid_for(NB, 128), 128, 0, s>>>(G, W, P<int64_t>(g->boff), P<int32_t>(m.longidx),
+                                                 P<uint64_t>(m.lptr), tpos);
+    note_launch();
+  }
   k_assemble_hints<<<grid_for(g->Nst, 256), 256, 0, s>>>(
       G, g->wdtype, P<uint32_t>(m.rp_s), P<int32_t>(m.longidx), P<uint64_t>(m.lptr),
       P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
       P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<int64_t>(g->gptr),
       P<uint32_t>(g->glist), P<float4>(g->ggeo), P<double>(g->base_w), phif, P<double>(g->phi),
-      P<int32_t>(m.col), m.w.p, P<dfl>(m.dsum),
+      tpos, W, tiled ? P<int32_t>(g->crank) : nullptr, P<int64_t>(g->boff), P<int32_t>(m.col),
+      m.w.p, P<dfl>(m.dsum),
       P<dfl>(m.psum), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
   note_launch();
   // H10: virtual rows
@@ -1144,8 +1267,15 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
         G, g->wdtype, m.nchunks, P<int32_t>(m.chunk_lr), P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
         P<int32_t>(m.lchunk), P<int64_t>(g->moff), P<uint32_t>(g->mlist), P<int64_t>(g->boff),
         P<uint32_t>(g->blist), P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
-        P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), P<int32_t>(m.col), m.w.p, cpart);
+        P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), tiled ? 1 : 0, P<int32_t>(m.col),
+        m.w.p, cpart);
     note_launch();
+    if (tiled) {
+      k_bin_sums<<<grid_for((long long)m.nchunks * 32, 256), 256, 0, s>>>(
+          G, g->wdtype, m.nchunks, P<int32_t>(m.chunk_lr), P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
+          P<int32_t>(m.lchunk), m.w.p, cpart);
+      note_launch();
+    }
     k_hub_finalize<<<grid_for((long long)m.nlong * 32, 256), 256, 0, s>>>(
         G, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<dfl>(m.dsum), P<dfl>(m.psum));
     note_launch();

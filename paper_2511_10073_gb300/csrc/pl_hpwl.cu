@@ -14,6 +14,7 @@ namespace pl {
 
 constexpr int kHpwlThreads = 256;
 constexpr int kHpwlBlocks = 152 * 8;
+constexpr int kHpwlStage = 512;  // pins of one batch of 32 nets staged per warp
 
 // Pin position; a pin_cell outside [0, C) is counted in *bad and reads cell 0
 // instead (the call then reports NaN).
@@ -38,6 +39,8 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
                                                        int *ticket, double *out) {
   __shared__ double red[kHpwlThreads / 32];
   __shared__ int last;
+  __shared__ float2 stage_all[kHpwlThreads / 32][kHpwlStage];
+  float2 *stg = stage_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   double acc = 0.0;
   // each warp takes batches of 32 consecutive nets (warp-uniform loop)
@@ -45,6 +48,40 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = wg * 32; base < M; base += nwarp * 32) {
     const long long e = base + lane;
+    const long long p0 = net_ptr[base], p1 = net_ptr[base + 32 < M ? base + 32 : M];
+    if (p1 - p0 <= kHpwlStage) {
+      // the batch's pins fit the warp's stage: lanes load all of them (all
+      // gathers in flight), then each lane spans its own net from the stage
+      for (long long k0 = p0; k0 < p1; k0 += 4 * 32) {
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long k = k0 + u * 32 + lane;
+          if (k < p1) q[u] = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long k = k0 + u * 32 + lane;
+          if (k < p1) stg[k - p0] = q[u];
+        }
+      }
+      __syncwarp();
+      if (e < M) {
+        const long long b = net_ptr[e] - p0, n = net_ptr[e + 1] - net_ptr[e];
+        if (n > 0) {
+          float2 p = stg[b];
+          float x0 = p.x, x1 = p.x, y0 = p.y, y1 = p.y;
+          for (long long k = b + 1; k < b + n; ++k) {
+            p = stg[k];
+            x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
+            y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
+          }
+          acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     bool big = false;
     if (e < M) {
       long long b = net_ptr[e], n = net_ptr[e + 1] - b;

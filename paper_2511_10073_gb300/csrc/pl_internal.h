@@ -56,7 +56,7 @@ struct SpMat {
   Buf c32;      // float [N] 1 - D_ii / lambda_up
   Buf c64l;     // double [nlong] same, FP64, hub rows
   Buf lam;      // double [4]: lambda_up, 1/lambda_up, and the raw max key
-  Buf part;     // double [nchunks * 6] hub partial sums
+  Buf part;     // float4 [nchunks] hub partial sums (two double-floats)
   Buf tick;     // int32 [nlong] arrival tickets, zero between launches
   int wbytes = 4;
 };
@@ -98,6 +98,7 @@ struct pl_graph {
   double gsz = 1.0, gsx = 1.0, gsy = 1.0;
   pl::Buf gptr, glist; // int64 [gnx*gny+1], uint32 macro ids
   pl::Buf ggeo;        // float4 [..] centre and size of each listed macro
+  pl::Buf mgeo;        // float4 [Mm] centre and size of each macro
   // per refinement round
   pl::Buf cell_bin;    // int32 [C]
   pl::Buf n_ovl;       // int32 [C]
@@ -110,6 +111,8 @@ struct pl_graph {
   pl::Buf klen;        // uint32 [N] tile key length
   pl::Buf clen;        // uint64 [N] chunked length of hub rows
   pl::Buf lflag;       // int32 [N+1] hub flag scan
+  pl::Buf crank;       // int32 [C] place of a hint cell in the bucket list
+  pl::Buf tpos;        // uint64 [NB * window] place of each window bin's cells in a bin row
   pl::Buf mac_base;    // uint64 [C] entry offset of a cell's first macro entry
   pl::Buf bin_base;    // uint64 [C] entry offset of a cell's first bin entry
   pl::Buf hubtmp;      // int32 scratch for merging bin rows

@@ -160,9 +160,25 @@ __device__ __forceinline__ K key_max() { return ~K(0); }
 template <typename K>
 __device__ __forceinline__ int32_t key_col(K k) { return (int32_t)((uint64_t)k >> 32); }
 
+// Segments are sorted by size class: up to 8, 16 and 32 keys by groups of 8,
+// 16 or 32 lanes (several segments per warp); up to 64..512 keys by one warp
+// holding 2..16 keys per lane; up to SEG_CAP by a CTA in shared memory; the
+// rest by a CTA merge sort in global memory.
+constexpr int kSegClasses = 9;  // <=8, <=16, <=32, <=64, <=128, <=256, <=512, <=SEG_CAP, more
 struct SegLists {
-  int32_t n_med, n_big;
+  int32_t n[kSegClasses];
 };
+__device__ __forceinline__ int seg_class(long long n) {
+  if (n <= 8) return 0;
+  if (n <= 16) return 1;
+  if (n <= 32) return 2;
+  if (n <= 64) return 3;
+  if (n <= 128) return 4;
+  if (n <= 256) return 5;
+  if (n <= 512) return 6;
+  if (n <= SEG_CAP) return 7;
+  return 8;
+}
 
 template <typename K, int MODE>
 __device__ __forceinline__ void write_single(K key, long long o, int32_t *cnt, long long s,
@@ -174,71 +190,199 @@ __device__ __forceinline__ void write_single(K key, long long o, int32_t *cnt, l
   if (MODE != MODE_SORT) cnt[s] = 1;
 }
 
+// Segment lists per class (warp-aggregated appends); segments of 0 or 1 key
+// are finished here.
 template <typename K, int MODE>
 __global__ void k_seg_classify(K *keys, const int64_t *off, long long nseg, int32_t *cnt,
-                               int32_t *mcol, int64_t *mval, int32_t *med, int32_t *big,
-                               SegLists *lists) {
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nseg;
-       s += (long long)gridDim.x * blockDim.x) {
-    long long o = off[s], n = off[s + 1] - o;
-    if (n <= 0) {
-      if (MODE != MODE_SORT) cnt[s] = 0;
-    } else if (n == 1) {
-      write_single<K, MODE>(keys[o], o, cnt, s, mcol, mval);
-    } else if (n <= 32) {
-      // warp kernel
-    } else if (n <= SEG_CAP) {
-      med[atomicAdd(&lists->n_med, 1)] = (int32_t)s;
-    } else {
-      big[atomicAdd(&lists->n_big, 1)] = (int32_t)s;
+                               int32_t *mcol, int64_t *mval, int32_t *lists,
+                               SegLists *ln) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (long long s0 = (blockIdx.x * (long long)blockDim.x) + (threadIdx.x & ~31); s0 < nseg;
+       s0 += (long long)gridDim.x * blockDim.x) {
+    const long long s = s0 + lane;
+    int cls = -1;
+    if (s < nseg) {
+      const long long o = off[s], n = off[s + 1] - o;
+      if (n <= 0) {
+        if (MODE != MODE_SORT) cnt[s] = 0;
+      } else if (n == 1) {
+        write_single<K, MODE>(keys[o], o, cnt, s, mcol, mval);
+      } else {
+        cls = seg_class(n);
+      }
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, cls);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (cls >= 0 && lane == leader) base = atomicAdd(&ln->n[cls], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cls >= 0) lists[(long long)cls * nseg + base + __popc(grp & lt)] = (int32_t)s;
+  }
+}
+
+// Bitonic sort of 32*R keys held R per lane (element r*32 + lane), ascending.
+template <typename K, int R>
+__device__ __forceinline__ void warp_bitonic_regs(K (&key)[R], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int jr = j >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r & jr) continue;
+          const bool up = (((r << 5) | lane) & k) == 0;
+          const K a = key[r], b = key[r + jr];
+          const bool sw = up ? (b < a) : (a < b);
+          key[r] = sw ? b : a;
+          key[r + jr] = sw ? a : b;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const K other = __shfl_xor_sync(0xffffffffu, key[r], j);
+          const bool up = (((r << 5) | lane) & k) == 0;
+          const bool lower = (lane & j) == 0;
+          key[r] = (lower == up) ? (other < key[r] ? other : key[r])
+                                 : (other > key[r] ? other : key[r]);
+        }
+      }
     }
   }
 }
 
-template <typename K, int MODE>
-__global__ void k_seg_warp(K *keys, const int64_t *off, long long nseg, int32_t *cnt,
-                           int32_t *mcol, int64_t *mval) {
-  const int lane = threadIdx.x & 31;
+// Groups of W lanes (W = 8, 16, 32) each sort one segment of at most W keys.
+template <typename K, int MODE, int W>
+__global__ void __launch_bounds__(256) k_seg_group(K *keys, const int64_t *off, int32_t *cnt,
+                                                   int32_t *mcol, int64_t *mval,
+                                                   const int32_t *list, const SegLists *ln,
+                                                   int cls) {
+  const int lane = threadIdx.x & 31, sub = lane & (W - 1);
+  const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << (lane & ~(W - 1)));
   const unsigned lt = (1u << lane) - 1u;
-  for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < nseg;
-       s += ((long long)gridDim.x * blockDim.x) >> 5) {
-    long long o = off[s];
-    int n = (int)(off[s + 1] - o);
-    if (n < 2 || n > 32) continue;
-    K key = lane < n ? keys[o + lane] : key_max<K>();
-    key = warp_bitonic<K>(key, lane);
+  const int nl = ln->n[cls];
+  const long long per = 32 / W;
+  for (long long i0 = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * per; i0 < nl;
+       i0 += (((long long)gridDim.x * blockDim.x) >> 5) * per) {
+    const long long it = i0 + lane / W;
+    long long o = 0, s = 0;
+    int n = 0;
+    if (it < nl) {
+      s = list[it];
+      o = off[s];
+      n = (int)(off[s + 1] - o);
+    }
+    K key = sub < n ? keys[o + sub] : key_max<K>();
+#pragma unroll
+    for (int k = 2; k <= W; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const K other = __shfl_xor_sync(0xffffffffu, key, j);
+        const bool up = (sub & k) == 0;
+        const bool lower = (sub & j) == 0;
+        key = (lower == up) ? (other < key ? other : key) : (other > key ? other : key);
+      }
+    }
     if (MODE == MODE_SORT) {
-      if (lane < n) keys[o + lane] = key;
+      if (sub < n) keys[o + sub] = key;
       continue;
     }
     if (MODE == MODE_UNIQUE) {
-      K prev = __shfl_up_sync(0xffffffffu, key, 1);
-      bool head = lane < n && (lane == 0 || prev != key);
-      unsigned hm = __ballot_sync(0xffffffffu, head);
+      const K prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool head = sub < n && (sub == 0 || prev != key);
+      const unsigned hm = __ballot_sync(0xffffffffu, head) & gmask;
       if (head) keys[o + __popc(hm & lt)] = key;
-      if (lane == 0) cnt[s] = __popc(hm);
+      if (sub == 0 && it < nl) cnt[s] = __popc(hm);
       continue;
     }
-    // MODE_MERGE
-    int32_t col = key_col<K>(key);
+    // MODE_MERGE: sum the values of equal columns
+    const int32_t col = key_col<K>(key);
     long long val = (long long)(int32_t)(uint32_t)((uint64_t)key & 0xffffffffu);
-    int32_t pcol = __shfl_up_sync(0xffffffffu, col, 1);
-    bool head = lane < n && (lane == 0 || pcol != col);
-    unsigned hm = __ballot_sync(0xffffffffu, head);
-    int seg = 31 - __clz(hm & (lt | (1u << lane)));
+    const int32_t pcol = __shfl_up_sync(0xffffffffu, col, 1);
+    const bool head = sub < n && (sub == 0 || pcol != col);
+    const unsigned hm = __ballot_sync(0xffffffffu, head) & gmask;
+    const int seg = 31 - __clz(hm & (lt | (1u << lane)));
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      long long ov = __shfl_up_sync(0xffffffffu, val, d);
-      int os = __shfl_up_sync(0xffffffffu, seg, d);
-      if (lane >= d && os == seg) val += ov;
+    for (int d = 1; d < W; d <<= 1) {
+      const long long ov = __shfl_up_sync(0xffffffffu, val, d);
+      const int os = __shfl_up_sync(0xffffffffu, seg, d);
+      if (sub >= d && os == seg) val += ov;
     }
-    bool nexthead = lane + 1 >= n || ((hm >> (lane + 1)) & 1u);
-    if (lane < n && nexthead) {
-      int idx = __popc(hm & (lt | (1u << lane))) - 1;
+    const bool tail = sub < n && (sub + 1 >= n || ((hm >> (lane + 1)) & 1u));
+    if (tail) {
+      const int idx = __popc(hm & (lt | (1u << lane))) - 1;
       mcol[o + idx] = col;
       mval[o + idx] = val;
     }
-    if (lane == 0) cnt[s] = __popc(hm);
+    if (sub == 0 && it < nl) cnt[s] = __popc(hm);
+  }
+}
+
+// One warp per segment of 33..32*R keys, R keys per lane; the sorted keys go
+// through the warp's shared-memory slice for the compaction (each lane a
+// contiguous run of R positions).
+template <typename K, int MODE, int R>
+__global__ void __launch_bounds__(256) k_seg_regs(K *keys, const int64_t *off, int32_t *cnt,
+                                                  int32_t *mcol, int64_t *mval,
+                                                  const int32_t *list, const SegLists *ln,
+                                                  int cls) {
+  __shared__ K sk[8][32 * R];
+  const int lane = threadIdx.x & 31;
+  K *a = sk[threadIdx.x >> 5];
+  const int nl = ln->n[cls];
+  for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < nl;
+       it += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long s = list[it];
+    const long long o = off[s];
+    const int n = (int)(off[s + 1] - o);
+    K key[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = (r << 5) | lane;
+      key[r] = e < n ? keys[o + e] : key_max<K>();
+    }
+    warp_bitonic_regs<K, R>(key, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[(r << 5) | lane] = key[r];
+    __syncwarp();
+    const int e0 = lane * R, e1 = min(n, e0 + R);
+    if (MODE == MODE_SORT) {
+      for (int e = e0; e < e1; ++e) keys[o + e] = a[e];
+      __syncwarp();
+      continue;
+    }
+    int nh = 0;
+    for (int e = e0; e < e1; ++e) {
+      const bool head = MODE == MODE_MERGE ? (e == 0 || key_col<K>(a[e]) != key_col<K>(a[e - 1]))
+                                           : (e == 0 || a[e] != a[e - 1]);
+      nh += head;
+    }
+    int x = nh;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    int w = x - nh;
+    for (int e = e0; e < e1; ++e) {
+      if (MODE == MODE_MERGE) {
+        if (!(e == 0 || key_col<K>(a[e]) != key_col<K>(a[e - 1]))) continue;
+        const int32_t col = key_col<K>(a[e]);
+        long long v = 0;
+        for (int q = e; q < n && key_col<K>(a[q]) == col; ++q)
+          v += (long long)(int32_t)(uint32_t)((uint64_t)a[q] & 0xffffffffu);
+        mcol[o + w] = col;
+        mval[o + w] = v;
+      } else {
+        if (!(e == 0 || a[e] != a[e - 1])) continue;
+        keys[o + w] = a[e];
+      }
+      ++w;
+    }
+    if (lane == 31) cnt[s] = x;
+    __syncwarp();
   }
 }
 
@@ -299,7 +443,7 @@ __global__ void __launch_bounds__(SEG_T) k_seg_cta(K *keys, const int64_t *off, 
                                                    const int32_t *med, const SegLists *lists) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K *a = reinterpret_cast<K *>(smraw);
-  const int nmed = lists->n_med;
+  const int nmed = lists->n[7];
   for (int it = blockIdx.x; it < nmed; it += gridDim.x) {
     long long s = med[it];
     long long o = off[s];
@@ -326,7 +470,7 @@ __global__ void __launch_bounds__(SEG_T) k_seg_big(K *keys, K *scratch, const in
                                                    const int32_t *big, const SegLists *lists) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K *a = reinterpret_cast<K *>(smraw);
-  const int nbig = lists->n_big;
+  const int nbig = lists->n[8];
   for (int it = blockIdx.x; it < nbig; it += gridDim.x) {
     long long s = big[it];
     long long o = off[s];
@@ -372,7 +516,8 @@ __global__ void __launch_bounds__(SEG_T) k_seg_big(K *keys, K *scratch, const in
 }
 
 size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes) {
-  return 1024 + 2 * (size_t)(nseg + 1) * sizeof(int32_t) + (size_t)nkeys * key_bytes + 512;
+  return 1024 + (size_t)kSegClasses * (size_t)(nseg + 1) * sizeof(int32_t) +
+         (size_t)nkeys * key_bytes + 512;
 }
 
 template <typename K, int MODE>
@@ -382,17 +527,23 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   if (nseg <= 0) return cudaSuccess;
   char *t = static_cast<char *>(tmp);
   SegLists *lists = reinterpret_cast<SegLists *>(t);
-  int32_t *med = reinterpret_cast<int32_t *>(t + 256);
-  int32_t *big = med + nseg;
-  size_t kb = ((256 + 2 * (size_t)(nseg + 1) * sizeof(int32_t)) + 255) & ~size_t(255);
+  int32_t *cl = reinterpret_cast<int32_t *>(t + 256);
+  size_t kb = ((256 + (size_t)kSegClasses * (size_t)(nseg + 1) * sizeof(int32_t)) + 255) & ~size_t(255);
   K *scratch = reinterpret_cast<K *>(t + kb);
   cudaError_t e = cudaMemsetAsync(lists, 0, sizeof(SegLists), s);
   if (e != cudaSuccess) return e;
   k_seg_classify<K, MODE><<<grid_for(nseg, 256), 256, 0, s>>>(keys, off, nseg, cnt, mcol, mval,
-                                                              med, big, lists);
+                                                              cl, lists);
   note_launch();
-  k_seg_warp<K, MODE><<<grid_for(nseg * 32, 256), 256, 0, s>>>(keys, off, nseg, cnt, mcol, mval);
-  note_launch();
+  const int gb = 152 * 8;
+  k_seg_group<K, MODE, 8><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl, lists, 0);
+  k_seg_group<K, MODE, 16><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + nseg, lists, 1);
+  k_seg_group<K, MODE, 32><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 2 * nseg, lists, 2);
+  k_seg_regs<K, MODE, 2><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 3 * nseg, lists, 3);
+  k_seg_regs<K, MODE, 4><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 4 * nseg, lists, 4);
+  k_seg_regs<K, MODE, 8><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 5 * nseg, lists, 5);
+  k_seg_regs<K, MODE, 16><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 6 * nseg, lists, 6);
+  for (int q = 0; q < 7; ++q) note_launch();
   size_t sm = SEG_CAP * sizeof(K);
   static bool attr_done = false;
   if (!attr_done) {
@@ -400,9 +551,10 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
     cudaFuncSetAttribute(k_seg_big<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr_done = true;
   }
-  k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, med, lists);
+  k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, cl + 7 * nseg, lists);
   note_launch();
-  k_seg_big<K, MODE><<<152, SEG_T, sm, s>>>(keys, scratch, off, cnt, mcol, mval, big, lists);
+  k_seg_big<K, MODE><<<152, SEG_T, sm, s>>>(keys, scratch, off, cnt, mcol, mval, cl + 8 * nseg,
+                                             lists);
   note_launch();
   (void)nkeys;
   return cudaGetLastError();
