@@ -55,9 +55,10 @@ struct StepArgs {
   float2 *y;
   // coefficients
   const float *a;        // per row a_v (FP32)
-  const float *b;        // per row b_v (GIFT) or nullptr (HR: lam[1])
+  const float *b;        // per row b_v (GIFT) or nullptr (HR: binv)
   const double *c64l;    // HR hub rows: a_v in FP64
-  const double *lam;     // HR: lambda_up, 1/lambda_up
+  double binv;           // HR: 1 / lambda_up
+  float binvf;           // the same, rounded to FP32
   const float *tscale;   // GIFT: band value = u * tscale (sqrt(d_v)); nullptr: 1
   // epilogue
   int pin, tap, fin, relax, clamp;
@@ -300,7 +301,7 @@ __device__ __forceinline__ void warp_tile(const StepArgs &A, const int4 d0, cons
     }
   }
   __syncwarp();
-  if (MODE == MODE_HR) bv = (float)A.lam[1];
+  if (MODE == MODE_HR) bv = A.binvf;
   const uint32_t *skip = two ? A.hrp : A.srp;
   if (r < r1 && !((two ? ha : ra) & kHubFlag))
     tile_row_out<MODE>(A, r, sp, (ra & kOffMask) - s0, (rb & kOffMask) - s0,
@@ -394,7 +395,7 @@ __device__ void warp_chunk(const StepArgs &A, int c) {
     double av, bv;
     if (MODE == MODE_HR) {
       av = A.c64l[l];
-      bv = A.lam[1];
+      bv = A.binv;
     } else {
       av = (double)A.a[v];
       bv = (double)A.b[v];
@@ -785,7 +786,8 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   A.a = P<float>(m.c32);
   A.b = nullptr;
   A.c64l = P<double>(m.c64l);
-  A.lam = P<double>(m.lam);
+  A.binv = g->lam_h[1];
+  A.binvf = (float)g->lam_h[1];
   A.tscale = nullptr;
   A.acc = P<double2>(g->acc);
   A.g0 = gin;

@@ -872,16 +872,20 @@ __global__ void k_lambda_max(int64_t N, const dfl *psum, unsigned long long *key
   if ((threadIdx.x & 31) == 0) atomicMax(key, best);
 }
 
+// lambda_up and 1 / lambda_up, also copied to status words 4..7 so that the
+// host reads them with the status.
 __global__ void k_lambda_final(double *lam, const unsigned long long *key, int *status) {
   double l = df_from_maxkey(*key);
+  double il = 0.0;
   if (!(l > 0.0) || isinf(l)) {
     flag(status, ST_SPECTRUM);
-    lam[0] = l;
-    lam[1] = 0.0;
   } else {
-    lam[0] = l;
-    lam[1] = __ddiv_rn(1.0, l);
+    il = __ddiv_rn(1.0, l);
   }
+  lam[0] = l;
+  lam[1] = il;
+  reinterpret_cast<double *>(status + 4)[0] = l;
+  reinterpret_cast<double *>(status + 4)[1] = il;
 }
 
 __global__ void k_coef(int64_t N, const dfl *dsum, const double *lam, float *c32) {
@@ -1296,6 +1300,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   }
   TRY(cudaGetLastError());
   TRY(d2h(hst, g->status.p, 8, s));
+  memcpy(g->lam_h, hst + 4, sizeof(g->lam_h));
   g->have_hints = true;
   if (hst[0] & ST_SPECTRUM) {
     set_error("lambda_up <= 0 or not finite: the refinement filter is undefined");

@@ -75,6 +75,7 @@ struct pl_graph {
   double det_ratio = 0.1;
   cudaStream_t stream = nullptr;
   bool have_hints = false;
+  double lam_h[2] = {0.0, 0.0};  // lambda_up, 1 / lambda_up of the current hints
 
   // copies of the netlist
   pl::Buf cw, ch, ckind, cfx, cfy, net_ptr;
