@@ -14,6 +14,7 @@
 #include "orc.h"
 
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -116,6 +117,31 @@ double orc_u01(uint64_t seed, uint64_t ctr) {
 /* Value an FP64 edge weight takes once stored: unchanged, IEEE FP32 round to
  * nearest even, or bfloat16 (8 significant bits, FP32 exponent range) round to
  * nearest even directly from FP64. */
+/* The sum of n positive doubles, each at least 2^-15, rounded once to the
+   nearest double (ties to even).  Every such value is an integer multiple of
+   2^-67, so the sum is taken exactly in 128-bit fixed point and converted
+   once.  baseWeight is the mean of a cell's weights: this sum over n. */
+static double exact_sum(const double *w, int64_t n) {
+  unsigned __int128 acc = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    int e;
+    double m = frexp(w[k], &e); /* w = m 2^e, 0.5 <= m < 1 */
+    if (!(w[k] > 0.0) || e < -14) {
+      fprintf(stderr, "orc: weight %g outside the exact-sum range\n", w[k]);
+      abort();
+    }
+    uint64_t M = (uint64_t)ldexp(m, 53); /* w = M 2^(e - 53) */
+    acc += (unsigned __int128)M << (e + 14); /* w 2^67 */
+  }
+  /* round to 53 bits: the top 64 bits with a sticky bit, then one correctly
+     rounded conversion */
+  int sh = 0;
+  while ((acc >> sh) >> 64) ++sh;
+  uint64_t top = (uint64_t)(acc >> sh);
+  if (sh && (acc & ((((unsigned __int128)1) << sh) - 1))) top |= 1;
+  return ldexp((double)top, sh - 67);
+}
+
 double orc_store(double w, int dtype) {
   if (dtype == ORC_W_FP32) return (double)(float)w;
   if (dtype == ORC_W_BF16) {
@@ -321,9 +347,7 @@ orc_graph *orc_create(const orc_netlist *nl, const orc_params *pr, int *err) {
   for (int32_t i = 0; i < C; ++i) {
     int64_t n = g->srp[i + 1] - g->srp[i];
     if (n == 0) continue;
-    double s = 0.0;
-    for (int64_t k = g->srp[i]; k < g->srp[i + 1]; ++k) s += g->sw_exact[k];
-    g->base_w[i] = s / (double)n;
+    g->base_w[i] = exact_sum(g->sw_exact + g->srp[i], n) / (double)n;
   }
 
   /* macros and virtual nodes */

@@ -26,24 +26,43 @@ constexpr long long kMaxNetPins = 32768;
 __global__ void k_validate_cells(const float *w, const float *h, const uint8_t *kind,
                                  const float *fx, const float *fy, int32_t C, int *status,
                                  uint8_t *is_macro, unsigned *maxdims) {
+  // per-thread counts and maxima, combined over the warp before one atomic
+  // each (one counter hit by every cell would serialize)
+  const int lane = threadIdx.x & 31;
+  int nmov = 0;
+  unsigned mx[4] = {0u, 0u, 0u, 0u};
+  bool bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
     uint8_t k = kind[i];
     float wi = w[i], hi = h[i];
     bool ok = k <= 2 && isfinite(wi) && isfinite(hi) && wi >= 0.f && hi >= 0.f;
     if (k == 1) ok = ok && wi > 0.f && hi > 0.f;
     if (k != 0) ok = ok && isfinite(fx[i]) && isfinite(fy[i]);
-    if (!ok) flag(status, ST_BAD_CELL);
+    bad |= !ok;
     is_macro[i] = k == 1;
-    if (k == 0) atomicAdd(&status[12], 1);
+    if (k == 0) ++nmov;
     if (ok) {
       if (k == 0) {
-        atomicMax(&maxdims[0], __float_as_uint(wi));
-        atomicMax(&maxdims[1], __float_as_uint(hi));
+        mx[0] = max(mx[0], __float_as_uint(wi));
+        mx[1] = max(mx[1], __float_as_uint(hi));
       } else if (k == 1) {
-        atomicMax(&maxdims[2], __float_as_uint(wi));
-        atomicMax(&maxdims[3], __float_as_uint(hi));
+        mx[2] = max(mx[2], __float_as_uint(wi));
+        mx[3] = max(mx[3], __float_as_uint(hi));
       }
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nmov += __shfl_xor_sync(0xffffffffu, nmov, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mx[q] = max(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) flag(status, ST_BAD_CELL);
+  if (lane == 0) {
+    if (nmov) atomicAdd(&status[12], nmov);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (mx[q]) atomicMax(&maxdims[q], mx[q]);
   }
 }
 
@@ -105,50 +124,108 @@ __global__ void k_star_list(const uint8_t *f, const int32_t *scan, int32_t M, in
 
 // ---------------------------------------------------- edge expansion
 // Row counts of the unmerged edge list: warp per net.
+// Unmerged row lengths: a clique net adds p - 1 to each of its nodes' rows, a
+// star net 1 (and p to its star's row).  A thread takes a net of up to 32
+// distinct nodes; larger nets are taken by the whole warp in turn.
 __global__ void k_row_count(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
                             const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
                             int32_t *cnt) {
   const int lane = threadIdx.x & 31;
-  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < M;
-       e += ((long long)gridDim.x * blockDim.x) >> 5) {
-    int p = net_p[e];
-    if (p < 2) continue;
-    long long b = ptr[e];
-    int add = p <= cmax ? p - 1 : 1;
-    for (int k = lane; k < p; k += 32) atomicAdd(&cnt[nd[b + k]], add);
-    if (p > cmax && lane == 0) cnt[star0 + star_of[e]] = p;
+  for (long long e0 = (blockIdx.x * (long long)blockDim.x) + (threadIdx.x & ~31); e0 < M;
+       e0 += (long long)gridDim.x * blockDim.x) {
+    const long long e = e0 + lane;
+    int p = 0;
+    long long b = 0;
+    if (e < M) {
+      p = net_p[e];
+      b = ptr[e];
+    }
+    const bool big = p > 32;
+    if (!big && p >= 2) {
+      const int add = p <= cmax ? p - 1 : 1;
+      for (int k = 0; k < p; ++k) atomicAdd(&cnt[nd[b + k]], add);
+      if (p > cmax) cnt[star0 + star_of[e]] = p;
+    }
+    unsigned bm = __ballot_sync(0xffffffffu, big);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const long long ee = e0 + src;
+      const int pp = __shfl_sync(0xffffffffu, p, src);
+      const long long bb = __shfl_sync(0xffffffffu, b, src);
+      const int add = pp <= cmax ? pp - 1 : 1;
+      for (int k = lane; k < pp; k += 32) atomicAdd(&cnt[nd[bb + k]], add);
+      if (pp > cmax && lane == 0) cnt[star0 + star_of[ee]] = pp;
+    }
   }
 }
 
+constexpr int kScatterRegs = 8;  // clique nets up to this size kept in registers
+
 // Unmerged entries as (col << 32 | value): value = 360360/(p-1) for a clique
 // pair, -p for a star edge.  Star rows are written in node order directly.
+// A thread takes a clique net (each node reserves its p - 1 slots with one
+// atomic, all of a small net's reservations in flight at once); star nets are
+// taken by the whole warp in turn.
 __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
                           const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
                           const int64_t *row_off, unsigned long long *cursor, uint64_t *keys) {
   const int lane = threadIdx.x & 31;
-  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < M;
-       e += ((long long)gridDim.x * blockDim.x) >> 5) {
-    int p = net_p[e];
-    if (p < 2) continue;
-    long long b = ptr[e];
-    if (p <= cmax) {
-      uint32_t lat = (uint32_t)(kLattice / (p - 1));
-      int npair = p * (p - 1);
-      for (int q = lane; q < npair; q += 32) {
-        int a = q / (p - 1), c = q % (p - 1);
-        c += c >= a;
-        uint32_t ra = nd[b + a], rc = nd[b + c];
-        unsigned long long slot = atomicAdd(&cursor[ra], 1ull);
-        keys[slot] = ((uint64_t)rc << 32) | lat;
+  for (long long e0 = (blockIdx.x * (long long)blockDim.x) + (threadIdx.x & ~31); e0 < M;
+       e0 += (long long)gridDim.x * blockDim.x) {
+    const long long e = e0 + lane;
+    int p = 0;
+    long long b = 0;
+    if (e < M) {
+      p = net_p[e];
+      b = ptr[e];
+    }
+    if (p >= 2 && p <= cmax) {
+      const uint32_t lat = (uint32_t)(kLattice / (p - 1));
+      if (p <= kScatterRegs) {
+        uint32_t node[kScatterRegs];
+        unsigned long long slot[kScatterRegs];
+#pragma unroll
+        for (int a = 0; a < kScatterRegs; ++a)
+          if (a < p) node[a] = nd[b + a];
+#pragma unroll
+        for (int a = 0; a < kScatterRegs; ++a)
+          if (a < p) slot[a] = atomicAdd(&cursor[node[a]], (unsigned long long)(p - 1));
+#pragma unroll
+        for (int a = 0; a < kScatterRegs; ++a) {
+          if (a >= p) break;
+          unsigned long long k = slot[a];
+#pragma unroll
+          for (int c = 0; c < kScatterRegs; ++c) {
+            if (c >= p) break;
+            if (c != a) keys[k++] = ((uint64_t)node[c] << 32) | lat;
+          }
+        }
+      } else {
+        for (int a = 0; a < p; ++a) {
+          const uint32_t ra = nd[b + a];
+          unsigned long long k = atomicAdd(&cursor[ra], (unsigned long long)(p - 1));
+          for (int c = 0; c < p; ++c) {
+            if (c == a) continue;
+            keys[k++] = ((uint64_t)nd[b + c] << 32) | lat;
+          }
+        }
       }
-    } else {
-      long long s = star0 + star_of[e];
-      uint32_t code = (uint32_t)(-p);
-      long long so = row_off[s];
-      for (int k = lane; k < p; k += 32) {
-        uint32_t v = nd[b + k];
-        unsigned long long slot = atomicAdd(&cursor[v], 1ull);
-        keys[slot] = ((uint64_t)(uint32_t)s << 32) | code;
+    }
+    unsigned bm = __ballot_sync(0xffffffffu, p > cmax);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const long long ee = e0 + src;
+      const int pp = __shfl_sync(0xffffffffu, p, src);
+      const long long bb = __shfl_sync(0xffffffffu, b, src);
+      const long long st = star0 + star_of[ee];
+      const uint32_t code = (uint32_t)(-pp);
+      const long long so = row_off[st];
+      for (int k = lane; k < pp; k += 32) {
+        const uint32_t v = nd[bb + k];
+        const unsigned long long slot = atomicAdd(&cursor[v], 1ull);
+        keys[slot] = ((uint64_t)(uint32_t)st << 32) | code;
         keys[so + k] = ((uint64_t)v << 32) | code;
       }
     }
@@ -252,13 +329,56 @@ __device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
   return __double2float_rn(w);
 }
 
+// A positive double of at least 2^-15 in 128-bit fixed point with 2^-67
+// resolution (exact: its last mantissa bit is worth at least 2^-67).
+struct Fix128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ void fix_add_double(Fix128 &a, double w) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;  // w = M 2^(e - 52)
+  const unsigned long long M = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int sh = e + 15;                            // w 2^67 = M << (e + 15)
+  unsigned long long lo, hi;
+  if (sh >= 64) {
+    lo = 0;
+    hi = M << (sh - 64);
+  } else if (sh > 0) {
+    lo = M << sh;
+    hi = M >> (64 - sh);
+  } else {
+    lo = M >> (-sh);  // not reached for weights >= 2^-15
+    hi = 0;
+  }
+  const unsigned long long t = a.lo + lo;
+  a.hi += hi + (t < a.lo ? 1ull : 0ull);
+  a.lo = t;
+}
+// The fixed-point value rounded once to the nearest double (ties to even):
+// the top 64 bits with a sticky bit, then one correctly rounded conversion.
+__device__ __forceinline__ double fix_to_double(const Fix128 &a) {
+  if (a.hi == 0) return ldexp(__ull2double_rn(a.lo), -67);
+  const int sh = 64 - __clzll((long long)a.hi);  // bits of hi, 1..64
+  unsigned long long top, rest;
+  if (sh == 64) {
+    top = a.hi;
+    rest = a.lo;
+  } else {
+    top = (a.hi << (64 - sh)) | (a.lo >> sh);
+    rest = a.lo & ((1ull << sh) - 1ull);
+  }
+  if (rest) top |= 1ull;
+  return ldexp(__ull2double_rn(top), sh - 67);
+}
+
 // Final static matrix, written straight into its split layout, from the FP64
 // weights (in place of the merged values).  A warp takes 32 consecutive rows:
 // for each row the warp writes columns and stored weights at the row's place
-// (short region or hub region) and reduces the row's static degree
+// (short region or hub region), reduces the row's static degree
 // (double-float, over the stored weights; every static weight is positive, so
-// it is also the positive sum); then each lane forms, for a cell, baseWeight
-// (FP64 mean of the exact weights, added in column order).
+// it is also the positive sum); then each lane forms, for a cell, the exact
+// sum of its row's FP64 weights (128-bit fixed point, order-free) and
+// baseWeight = RN(sum) / count.
 __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
     int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, const uint32_t *rp_s,
@@ -303,10 +423,11 @@ __global__ void __launch_bounds__(256) k_static_compact(
     dsum[v] = dl;
     psum[v] = dl;
     if (v < C) {
+      // the lane's own row, in integer arithmetic (no FP64 per entry)
       const double *w64 = reinterpret_cast<const double *>(mval) + src;
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s = __dadd_rn(s, w64[k]);
-      double bw = m > 0 ? __ddiv_rn(s, (double)m) : 0.0;
+      Fix128 fl{0ull, 0ull};
+      for (int k = 0; k < m; ++k) fix_add_double(fl, w64[k]);
+      const double bw = m > 0 ? __ddiv_rn(fix_to_double(fl), (double)m) : 0.0;
       base_w[v] = bw;
       hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
     }
@@ -647,7 +768,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->tmp[4], (size_t)(Nst + 1) * 4 + 256));
   int32_t *cnt = P<int32_t>(g->tmp[4]);
   TRY(cudaMemsetAsync(cnt, 0, (size_t)(Nst + 1) * 4, s));
-  k_row_count<<<grid_for((long long)M * 32, 256), 256, 0, s>>>(
+  k_row_count<<<grid_for((long long)M, 256), 256, 0, s>>>(
       P<int64_t>(g->net_ptr), P<uint32_t>(g->nd), P<int32_t>(g->net_p), P<int32_t>(g->star_of),
       M, p->clique_max, star0, cnt);
   note_launch();
@@ -663,7 +784,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   uint64_t *keys = P<uint64_t>(g->tmp[6]);
   unsigned long long *cursor = reinterpret_cast<unsigned long long *>(keys + npre + 1);
   TRY(cudaMemcpyAsync(cursor, row_off, (size_t)Nst * 8, cudaMemcpyDeviceToDevice, s));
-  k_scatter<<<grid_for((long long)M * 32, 256), 256, 0, s>>>(
+  k_scatter<<<grid_for((long long)M, 256), 256, 0, s>>>(
       P<int64_t>(g->net_ptr), P<uint32_t>(g->nd), P<int32_t>(g->net_p), P<int32_t>(g->star_of),
       M, p->clique_max, star0, row_off, cursor, keys);
   note_launch();

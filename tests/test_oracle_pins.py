@@ -189,9 +189,10 @@ def test_static_graph_equals_dense_brute_force(cfg, seed, perm):
             assert we[rp[i] + k] == float(W[i][j])          # correctly rounded exact sum
             assert ws[rp[i] + k] == _bf16_brute(float(W[i][j]))
     for i in range(o.C):
+        # baseWeight: the correctly rounded sum of the row's weights over their count
         row = we[rp[i]:rp[i + 1]]
         want = math.fsum(row) / len(row) if len(row) else 0.0
-        assert st["base_w"][i] == pytest.approx(want, rel=1e-15, abs=0.0)
+        assert st["base_w"][i] == want
     # fixed positions of macro pin nodes: macro centre + pin offset
     for p, v in enumerate(pin_node):
         if v >= o.C:
