@@ -26,8 +26,8 @@ constexpr long long kMaxNetPins = 32768;
 __global__ void k_validate_cells(const float *w, const float *h, const uint8_t *kind,
                                  const float *fx, const float *fy, int32_t C, int *status,
                                  uint8_t *is_macro, unsigned *maxdims) {
-  // per-thread counts and maxima, combined over the warp before one atomic
-  // each (one counter hit by every cell would serialize)
+  // per-thread counts and maxima (a grid of a few blocks per SM, each thread
+  // many cells), combined over the warp
   const int lane = threadIdx.x & 31;
   int nmov = 0;
   unsigned mx[4] = {0u, 0u, 0u, 0u};
@@ -57,12 +57,32 @@ __global__ void k_validate_cells(const float *w, const float *h, const uint8_t *
 #pragma unroll
     for (int q = 0; q < 4; ++q) mx[q] = max(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) flag(status, ST_BAD_CELL);
+  // then over the block (one atomic per block and counter)
+  __shared__ int s_n[32], s_bad[32];
+  __shared__ unsigned s_mx[32][4];
+  const int wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const bool anybad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    if (nmov) atomicAdd(&status[12], nmov);
+    s_n[wid] = nmov;
+    s_bad[wid] = anybad;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s_mx[wid][q] = mx[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0, b = 0;
+    unsigned m[4] = {0u, 0u, 0u, 0u};
+    for (int k = 0; k < nw; ++k) {
+      n += s_n[k];
+      b |= s_bad[k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[q] = max(m[q], s_mx[k][q]);
+    }
+    if (b) flag(status, ST_BAD_CELL);
+    if (n) atomicAdd(&status[12], n);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (mx[q]) atomicMax(&maxdims[q], mx[q]);
+      if (m[q]) atomicMax(&maxdims[q], m[q]);
   }
 }
 
@@ -675,7 +695,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   uint8_t *is_macro;
   TRY(ensure(g->tmp[0], (size_t)C + 256));
   is_macro = P<uint8_t>(g->tmp[0]);
-  k_validate_cells<<<grid_for(C, 256), 256, 0, s>>>(P<float>(g->cw), P<float>(g->ch),
+  k_validate_cells<<<grid_for(C, 256, 152 * 4), 256, 0, s>>>(P<float>(g->cw), P<float>(g->ch),
                                                     P<uint8_t>(g->ckind), P<float>(g->cfx),
                                                     P<float>(g->cfy), C, status, is_macro, maxdims);
   note_launch();
