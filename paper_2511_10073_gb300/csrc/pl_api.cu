@@ -130,7 +130,7 @@ static void destroy(pl_graph *g) {
   for (SpMat *m : ms) {
     Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->keys, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
                  &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->tile_row, &m->tdesc, &m->longidx,
-                 &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part, &m->tick};
+                 &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part};
     for (Buf *b : mb) release(*b);
   }
   delete g;

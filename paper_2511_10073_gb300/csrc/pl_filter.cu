@@ -10,10 +10,10 @@
 // Short rows (<= kLong entries): a CTA stages the products of an nnz tile in
 // shared memory (coalesced 16-byte index/weight loads, gathered x), then sums
 // each row with a warp.  Hub rows (virtual nodes, very long rows): chunks of
-// kChunk entries accumulate exact products in double-float; the last chunk of
-// a row to finish (ticket) adds the partials in chunk order in FP64 and does
-// the combine in FP64, since those rows amplify rounding error by up to
-// a_v^k when D_vv < 0.
+// kChunk entries accumulate exact products in double-float (one launch); the
+// next launch adds each hub row's partials in a fixed order and does the
+// combine in FP64, since those rows amplify rounding error by up to a_v^k when
+// D_vv < 0.
 // The epilogue also applies the taps (FP64 accumulation), the re-pinning of
 // fixed nodes, the relaxation of Algorithm 1 (FP64) and the clamping.
 #include <cmath>
@@ -49,8 +49,8 @@ struct StepArgs {
   const int32_t *lchunk;
   const int32_t *chunk_lr;
   int32_t nchunks;
+  int32_t nlong;
   float4 *part;  // per hub chunk: (sx.hi, sx.lo, sy.hi, sy.lo)
-  int32_t *tick;
   const float2 *x;
   float2 *y;
   // coefficients
@@ -133,18 +133,19 @@ __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T y
 }
 
 // ------------------------------------------------------- warp work units
-// Units: hub chunks [0, nchunks) of kChunk entries, then short tiles of at
-// most kTile keys (rows + entries; rows <= kLong entries).  Each warp takes
-// units gw, gw + nwarps, ... and loads the next tile's descriptor while it
-// works on the current unit; a unit needs no block-wide barrier.
+// Units: hub chunks [0, nchunks) of kChunk entries (first launch), hub rows
+// (second launch), then short tiles of at most kTile keys (rows + entries;
+// rows <= kLong entries; third launch).  Each warp takes units gw, gw + nwarps, ... and
+// loads the next tile's descriptor while it works on the current unit; a
+// unit needs no block-wide barrier.
 //  * tile: every lane issues the loads of all its entries (index, weight) and
 //    of its row's pointers and coefficient at once, then all its gathers of
 //    x, writes w * x[col] to the warp's shared-memory slice, and sums whole
 //    rows (lane per row) before their epilogue;
 //  * hub chunk: exact products accumulated in double-float, reduced over the
-//    warp, written as an FP64 partial; the last warp to finish a row (ticket,
-//    no waiting) adds the row's partials in chunk order (lane-strided, then a
-//    fixed tree) and combines in FP64.
+//    warp, written as a double-float partial;
+//  * hub row: the row's partials added by a warp in a fixed order, then
+//    combined in FP64 by a lane per row.
 constexpr int kEntWarp = kTile + kLong;    // entries of one tile < kTile + kLong
 constexpr int kPer = (kEntWarp + 31) / 32;  // entries per lane of one tile
 constexpr int kChunkBatch = 8;              // loads in flight per lane (hub chunks)
@@ -347,22 +348,12 @@ __device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp,
 }
 
 // A hub chunk covers positions [q0, q1) of the row's st piece followed by its
-// hm piece.
-// Ticket of a hub row: a device-scope atomic add with release semantics, so
-// the partial written before it is visible to whichever warp sees the last
-// ticket (that warp fences before reading the partials).
-__device__ __forceinline__ int ticket_add_release(int *p) {
-  int old;
-  asm volatile("atom.add.release.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
-  return old;
-}
-
-template <int WT, int MODE>
+// hm piece; its double-float sums over the warp are the chunk's partial.
+template <int WT>
 __device__ void warp_chunk(const StepArgs &A, int c) {
   const int lane = threadIdx.x & 31;
   const int l = A.chunk_lr[c];
-  const int64_t v = A.lrow[l];
-  const int c0 = A.lchunk[l], nch = A.lchunk[l + 1] - c0;
+  const int c0 = A.lchunk[l];
   const uint64_t sl = A.lsl[l], hl = A.lhl[l];
   const uint64_t q0 = (uint64_t)(c - c0) * kChunk;
   const uint64_t q1 = q0 + kChunk < sl + hl ? q0 + kChunk : sl + hl;
@@ -374,36 +365,7 @@ __device__ void warp_chunk(const StepArgs &A, int c) {
   }
   sx = warp_sum_df(sx);
   sy = warp_sum_df(sy);
-  int last = 0;
-  if (lane == 0) {
-    A.part[c] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
-    last = ticket_add_release(&A.tick[l]) == nch - 1;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (!last) return;
-  __threadfence();
-  dfl px{0.f, 0.f}, py{0.f, 0.f};
-  for (int k = lane; k < nch; k += 32) {
-    const float4 q = __ldcg(&A.part[c0 + k]);
-    df_add_df(px, dfl{q.x, q.y});
-    df_add_df(py, dfl{q.z, q.w});
-  }
-  px = warp_sum_df(px);
-  py = warp_sum_df(py);
-  if (lane == 0) {
-    const double tx = df_to_d(px), ty = df_to_d(py);
-    double av, bv;
-    if (MODE == MODE_HR) {
-      av = A.c64l[l];
-      bv = A.binv;
-    } else {
-      av = (double)A.a[v];
-      bv = (double)A.b[v];
-    }
-    const float2 xv = A.x[v];
-    epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
-    A.tick[l] = 0;
-  }
+  if (lane == 0) A.part[c] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
 }
 
 constexpr int kSpmmThreads = 128;
@@ -415,7 +377,47 @@ template <int WT, int MODE>
 __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT, MODE>(A, (int)c);
+  for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT>(A, (int)c);
+}
+
+// Hub rows, after the chunk launch: a block takes kHubRows rows, a warp per
+// row adding the row's partials in a fixed order (lane-strided over the
+// chunks, then a fixed tree); one warp then does the combines in FP64, a lane
+// per row, so the FP64 work of kHubRows rows shares its instructions.
+constexpr int kHubRows = 8;
+template <int MODE>
+__global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
+  __shared__ float4 sums[kHubRows];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long l = (long long)blockIdx.x * kHubRows + w;
+  if (l < A.nlong) {
+    const int c0 = A.lchunk[l], nch = A.lchunk[l + 1] - c0;
+    dfl px{0.f, 0.f}, py{0.f, 0.f};
+    for (int k = lane; k < nch; k += 32) {
+      const float4 q = __ldcg(&A.part[c0 + k]);
+      df_add_df(px, dfl{q.x, q.y});
+      df_add_df(py, dfl{q.z, q.w});
+    }
+    px = warp_sum_df(px);
+    py = warp_sum_df(py);
+    if (lane == 0) sums[w] = make_float4(px.hi, px.lo, py.hi, py.lo);
+  }
+  __syncthreads();
+  const long long lr = (long long)blockIdx.x * kHubRows + lane;
+  if (w != 0 || lane >= kHubRows || lr >= A.nlong) return;
+  const float4 q = sums[lane];
+  const int64_t v = A.lrow[lr];
+  const double tx = df_to_d(dfl{q.x, q.y}), ty = df_to_d(dfl{q.z, q.w});
+  double av, bv;
+  if (MODE == MODE_HR) {
+    av = A.c64l[lr];
+    bv = A.binv;
+  } else {
+    av = (double)A.a[v];
+    bv = (double)A.b[v];
+  }
+  const float2 xv = A.x[v];
+  epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
 }
 
 // Short tiles: warp w of the grid takes tiles w, w + nwarps, ... as a
@@ -431,10 +433,17 @@ __global__ void __launch_bounds__(kSpmmThreads, kSpmmBlocksPerSm) k_spmm(StepArg
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   long long t = gw;
-  if (t >= A.ntiles) return;
-  int4 c0 = __ldg(A.tdesc + t), c1 = __ldg(A.tdesc + t + 1);
-  stage_tile<WT>(A, c0, c1, &stg[0]);
+  int4 c0 = make_int4(0, 0, 0, 0), c1 = c0;
+  if (t < A.ntiles) {
+    c0 = __ldg(A.tdesc + t);
+    c1 = __ldg(A.tdesc + t + 1);
+    stage_tile<WT>(A, c0, c1, &stg[0]);
+  }
   cp_commit();
+  if (t >= A.ntiles) {
+    cp_wait_all();
+    return;
+  }
   long long tn = t + nw;
   int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
   if (tn < A.ntiles) {
@@ -596,8 +605,8 @@ static void fill_matrix(StepArgs &A, const SpMat &st, const SpMat *hm) {
   A.lchunk = P<int32_t>(m.lchunk);
   A.chunk_lr = P<int32_t>(m.chunk_lr);
   A.nchunks = m.nchunks;
+  A.nlong = m.nlong;
   A.part = const_cast<float4 *>(P<float4>(m.part));
-  A.tick = const_cast<int32_t *>(P<int32_t>(m.tick));
 }
 
 // Algorithmic bytes of one sparse product over (x, y) pairs: indices and
@@ -606,7 +615,8 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
-// One sparse product: the hub chunks, then the short tiles (same stream).
+// One sparse product: the hub chunks, the hub rows, then the short tiles
+// (same stream).
 template <int MODE>
 static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s) {
   static int nsm = 0;
@@ -632,6 +642,8 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     const int hgrid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
     if (wi) k_spmm_hub<1, MODE><<<hgrid, 256, 0, s>>>(A);
     else k_spmm_hub<0, MODE><<<hgrid, 256, 0, s>>>(A);
+    k_hub_rows<MODE><<<(int)(((long long)A.nlong + kHubRows - 1) / kHubRows), kHubRows * 32, 0, s>>>(A);
+    note_launch();
     note_launch();
   }
   const long long want = ((long long)A.ntiles + kSpmmWarps - 1) / kSpmmWarps;

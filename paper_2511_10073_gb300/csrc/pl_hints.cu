@@ -1053,8 +1053,6 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   TRY(ensure(m.lam, 64));
   size_t pbytes = (size_t)(m.nchunks + 1) * 6 * 8;
   TRY(ensure(m.part, pbytes));
-  TRY(ensure(m.tick, (size_t)nl * 4 + 16));
-  TRY(cudaMemsetAsync(m.tick.p, 0, (size_t)nl * 4 + 16, s));
   TRY(cudaMemsetAsync(P<char>(m.col) + (m.nnz_s + m.nnz_l) * 4, 0, kPad * 4, s));
   TRY(cudaMemsetAsync(P<char>(m.w) + (m.nnz_s + m.nnz_l) * m.wbytes, 0, kPad * m.wbytes, s));
   return PL_OK;

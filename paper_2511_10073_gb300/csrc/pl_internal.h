@@ -57,7 +57,6 @@ struct SpMat {
   Buf c64l;     // double [nlong] same, FP64, hub rows
   Buf lam;      // double [4]: lambda_up, 1/lambda_up, and the raw max key
   Buf part;     // float4 [nchunks] hub partial sums (two double-floats)
-  Buf tick;     // int32 [nlong] arrival tickets, zero between launches
   int wbytes = 4;
 };
 

@@ -167,6 +167,7 @@ __device__ __forceinline__ int32_t key_col(K k) { return (int32_t)((uint64_t)k >
 constexpr int kSegClasses = 9;  // <=8, <=16, <=32, <=64, <=128, <=256, <=512, <=SEG_CAP, more
 struct SegLists {
   int32_t n[kSegClasses];
+  int32_t maxbig;  // keys of the longest segment above SEG_CAP
 };
 __device__ __forceinline__ int seg_class(long long n) {
   if (n <= 8) return 0;
@@ -218,6 +219,7 @@ __global__ void k_seg_classify(K *keys, const int64_t *off, long long nseg, int3
     if (cls >= 0 && lane == leader) base = atomicAdd(&ln->n[cls], __popc(grp));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (cls >= 0) lists[(long long)cls * nseg + base + __popc(grp & lt)] = (int32_t)s;
+    if (cls == kSegClasses - 1) atomicMax(&ln->maxbig, (int32_t)(off[s + 1] - off[s]));
   }
 }
 
@@ -462,55 +464,143 @@ __global__ void __launch_bounds__(SEG_T) k_seg_cta(K *keys, const int64_t *off, 
   }
 }
 
-// Segments longer than SEG_CAP: sort SEG_CAP chunks in shared memory, then
-// merge runs of doubling size between the key array and a scratch copy.
-template <typename K, int MODE>
-__global__ void __launch_bounds__(SEG_T) k_seg_big(K *keys, K *scratch, const int64_t *off,
-                                                   int32_t *cnt, int32_t *mcol, int64_t *mval,
-                                                   const int32_t *big, const SegLists *lists) {
+// Segments longer than SEG_CAP, spread over all CTAs: each is cut into units
+// of SEG_CAP keys; bpre[i] is the first unit of the i-th listed segment.  The
+// units are sorted in shared memory, then runs of doubling length are merged
+// pass by pass (one launch per pass, every CTA merging one unit of output),
+// between the key array and a scratch copy.
+__global__ void __launch_bounds__(SEG_T) k_big_prefix(const int32_t *big, const SegLists *lists,
+                                                      const int64_t *off, long long *bpre) {
+  const int nbig = lists->n[kSegClasses - 1];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int i0 = 0; i0 <= nbig; i0 += SEG_T) {
+    const int i = i0 + threadIdx.x;
+    long long u = 0;
+    if (i < nbig) {
+      const long long sgm = big[i];
+      u = (off[sgm + 1] - off[sgm] + SEG_CAP - 1) / SEG_CAP;
+    }
+    long long tot;
+    const long long ex = block_excl_scan<long long>(u, &tot);
+    if (i <= nbig) bpre[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+// The listed segment holding unit u (binary search over bpre): its key
+// offset and length, and u's index inside it; false past the last unit.
+__device__ __forceinline__ bool big_unit(const int32_t *big, int nbig, const long long *bpre,
+                                         const int64_t *off, long long u, long long *o,
+                                         long long *n, long long *c) {
+  if (u >= bpre[nbig]) return false;
+  int lo = 0, hi = nbig - 1;  // last i with bpre[i] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bpre[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  const long long sgm = big[lo];
+  *o = off[sgm];
+  *n = off[sgm + 1] - *o;
+  *c = u - bpre[lo];
+  return true;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(SEG_T) k_big_units(K *keys, const int32_t *big,
+                                                     const SegLists *lists,
+                                                     const long long *bpre, const int64_t *off) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K *a = reinterpret_cast<K *>(smraw);
-  const int nbig = lists->n[8];
+  const int nbig = lists->n[kSegClasses - 1];
+  long long o, n, c;
+  for (long long u = blockIdx.x; big_unit(big, nbig, bpre, off, u, &o, &n, &c); u += gridDim.x) {
+    const long long c0 = c * SEG_CAP;
+    const int m = (int)(n - c0 < SEG_CAP ? n - c0 : SEG_CAP);
+    for (int q = threadIdx.x; q < SEG_CAP; q += SEG_T) a[q] = q < m ? keys[o + c0 + q] : key_max<K>();
+    __syncthreads();
+    cta_bitonic<K>(a, SEG_CAP);
+    for (int q = threadIdx.x; q < m; q += SEG_T) keys[o + c0 + q] = a[q];
+    __syncthreads();
+  }
+}
+
+// One merge pass over runs of R keys: output unit c of a segment lies inside
+// one pair of runs (2R is a multiple of SEG_CAP); each thread merges 16
+// consecutive outputs from its merge-path split.  A segment of at most R keys
+// (one run) is copied.
+template <typename K>
+__global__ void __launch_bounds__(SEG_T) k_big_merge(const K *src, K *dst, const int32_t *big,
+                                                     const SegLists *lists,
+                                                     const long long *bpre, const int64_t *off,
+                                                     long long R) {
+  const int nbig = lists->n[kSegClasses - 1];
+  if (R >= lists->maxbig) return;
+  long long o, n, c;
+  for (long long u = blockIdx.x; big_unit(big, nbig, bpre, off, u, &o, &n, &c); u += gridDim.x) {
+    const long long t0 = c * SEG_CAP, t1 = t0 + SEG_CAP < n ? t0 + SEG_CAP : n;
+    const long long base = (t0 / (2 * R)) * (2 * R);
+    const long long na = n - base < R ? n - base : R;
+    const long long nb = n - base - na < R ? n - base - na : R;
+    const K *A = src + o + base, *B = A + na;
+    if (nb <= 0) {
+      for (long long q = t0 + threadIdx.x; q < t1; q += SEG_T) dst[o + q] = src[o + q];
+      continue;
+    }
+    const int E = 16;
+    for (long long d0 = t0 - base + (long long)threadIdx.x * E; d0 < t1 - base;
+         d0 += (long long)SEG_T * E) {
+      const long long d1 = d0 + E < t1 - base ? d0 + E : t1 - base;
+      long long i = co_rank(A, na, B, nb, d0);
+      long long j = d0 - i;
+      for (long long d = d0; d < d1; ++d) {
+        const bool takeA = j >= nb || (i < na && A[i] <= B[j]);
+        dst[o + base + d] = takeA ? A[i++] : B[j++];
+      }
+    }
+  }
+}
+
+// After the merge passes: the keys are in the scratch copy when the number of
+// passes that ran (runs of SEG_CAP doubling while below the longest segment)
+// is odd.
+template <typename K>
+__global__ void __launch_bounds__(SEG_T) k_big_copy(const K *src, K *dst, const int32_t *big,
+                                                    const SegLists *lists, const long long *bpre,
+                                                    const int64_t *off) {
+  const int nbig = lists->n[kSegClasses - 1];
+  int passes = 0;
+  for (long long R = SEG_CAP; R < lists->maxbig; R <<= 1) ++passes;
+  if (!(passes & 1)) return;
+  long long o, n, c;
+  for (long long u = blockIdx.x; big_unit(big, nbig, bpre, off, u, &o, &n, &c); u += gridDim.x) {
+    const long long t0 = c * SEG_CAP, t1 = t0 + SEG_CAP < n ? t0 + SEG_CAP : n;
+    for (long long q = t0 + threadIdx.x; q < t1; q += SEG_T) dst[o + q] = src[o + q];
+  }
+}
+
+// Compaction of the sorted big segments (UNIQUE / MERGE), a CTA each.
+template <typename K, int MODE>
+__global__ void __launch_bounds__(SEG_T) k_big_compact(K *keys, K *scratch, const int64_t *off,
+                                                       int32_t *cnt, int32_t *mcol, int64_t *mval,
+                                                       const int32_t *big, const SegLists *lists) {
+  const int nbig = lists->n[kSegClasses - 1];
   for (int it = blockIdx.x; it < nbig; it += gridDim.x) {
-    long long s = big[it];
-    long long o = off[s];
-    long long n = off[s + 1] - o;
-    for (long long c0 = 0; c0 < n; c0 += SEG_CAP) {
-      int m = (int)(n - c0 < SEG_CAP ? n - c0 : SEG_CAP);
-      for (int q = threadIdx.x; q < SEG_CAP; q += SEG_T) a[q] = q < m ? keys[o + c0 + q] : key_max<K>();
+    const long long sgm = big[it];
+    const long long o = off[sgm], n = off[sgm + 1] - o;
+    // UNIQUE output goes to scratch first (the input would be overwritten
+    // while read), then back
+    if (MODE == MODE_UNIQUE) {
+      cta_compact<K, MODE>(keys + o, n, 0, sgm, cnt, mcol, mval, scratch + o);
+      const int m = cnt[sgm];
       __syncthreads();
-      cta_bitonic<K>(a, SEG_CAP);
-      for (int q = threadIdx.x; q < m; q += SEG_T) keys[o + c0 + q] = a[q];
+      for (long long q = threadIdx.x; q < m; q += SEG_T) keys[o + q] = scratch[o + q];
       __syncthreads();
-    }
-    K *src = keys + o, *dst = scratch + o;
-    for (long long R = SEG_CAP; R < n; R <<= 1) {
-      for (long long r0 = 0; r0 < n; r0 += 2 * R) {
-        long long na = n - r0 < R ? n - r0 : R;
-        long long nb = n - r0 - na < R ? n - r0 - na : R;
-        if (nb > 0) cta_merge<K>(src + r0, na, src + r0 + na, nb, dst + r0);
-        else
-          for (long long q = threadIdx.x; q < na; q += SEG_T) dst[r0 + q] = src[r0 + q];
-      }
-      __syncthreads();
-      K *t = src; src = dst; dst = t;
-    }
-    if (src != keys + o) {
-      for (long long q = threadIdx.x; q < n; q += SEG_T) keys[o + q] = src[q];
-      __syncthreads();
-    }
-    if (MODE != MODE_SORT) {
-      // compaction reads from the sorted keys; UNIQUE output goes to scratch
-      // first (the input would be overwritten while read), then back.
-      if (MODE == MODE_UNIQUE) {
-        cta_compact<K, MODE>(keys + o, n, 0, s, cnt, mcol, mval, scratch + o);
-        int m = cnt[s];
-        __syncthreads();
-        for (long long q = threadIdx.x; q < m; q += SEG_T) keys[o + q] = scratch[o + q];
-        __syncthreads();
-      } else {
-        cta_compact<K, MODE>(keys + o, n, o, s, cnt, mcol, mval, keys);
-      }
+    } else {
+      cta_compact<K, MODE>(keys + o, n, o, sgm, cnt, mcol, mval, keys);
     }
   }
 }
@@ -535,6 +625,8 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   k_seg_classify<K, MODE><<<grid_for(nseg, 256), 256, 0, s>>>(keys, off, nseg, cnt, mcol, mval,
                                                               cl, lists);
   note_launch();
+  // every class kernel reads its list length on the device (no host round
+  // trip); an empty class costs one launch that returns at once
   const int gb = 152 * 8;
   k_seg_group<K, MODE, 8><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl, lists, 0);
   k_seg_group<K, MODE, 16><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + nseg, lists, 1);
@@ -548,14 +640,39 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(k_seg_cta<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_seg_big<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_big_units<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr_done = true;
   }
   k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, cl + 7 * nseg, lists);
   note_launch();
-  k_seg_big<K, MODE><<<152, SEG_T, sm, s>>>(keys, scratch, off, cnt, mcol, mval, cl + 8 * nseg,
-                                             lists);
-  note_launch();
+  if (nkeys > SEG_CAP) {
+    // The unit prefix overwrites the lists of the small classes (consumed by
+    // the launches above): (nbig + 1) 8-byte entries fit below the list of
+    // class 8 at byte 32 * nseg, since nbig <= nseg.
+    const int32_t *big = cl + 8 * nseg;
+    long long *bpre = reinterpret_cast<long long *>(t + 256);
+    k_big_prefix<<<1, SEG_T, 0, s>>>(big, lists, off, bpre);
+    k_big_units<K><<<152 * 4, SEG_T, sm, s>>>(keys, big, lists, bpre, off);
+    note_launch();
+    note_launch();
+    // passes while R < the longest segment (a pass past it returns at once);
+    // nkeys bounds that length
+    int npass = 0;
+    for (long long R = SEG_CAP; R < nkeys; R <<= 1) {
+      k_big_merge<K><<<152 * 4, SEG_T, 0, s>>>(npass & 1 ? scratch : keys, npass & 1 ? keys : scratch,
+                                               big, lists, bpre, off, R);
+      note_launch();
+      ++npass;
+    }
+    if (npass) {
+      k_big_copy<K><<<152 * 4, SEG_T, 0, s>>>(scratch, keys, big, lists, bpre, off);
+      note_launch();
+    }
+    if (MODE != MODE_SORT) {
+      k_big_compact<K, MODE><<<152, SEG_T, 0, s>>>(keys, scratch, off, cnt, mcol, mval, big, lists);
+      note_launch();
+    }
+  }
   (void)nkeys;
   return cudaGetLastError();
 }
