@@ -43,6 +43,7 @@ struct StepArgs {
   // work units of the applied matrix
   const int4 *tdesc;
   int32_t ntiles;
+  int64_t nrows;  // rows of the applied matrix
   const int32_t *lrow;
   const uint64_t *lsb, *lhb;
   const uint32_t *lsl, *lhl;
@@ -380,6 +381,84 @@ __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
   for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT>(A, (int)c);
 }
 
+// Short rows, row-split: a group of kRowLanes lanes per row reads the row's
+// st and hm pieces straight from global memory (lane m takes entries m,
+// m + kRowLanes, ...; kRowUnroll index and weight loads in flight, then their
+// gathers of x), a butterfly over the group sums them, and the group's first
+// lane applies the epilogue.  Hub rows are skipped (their own launches).
+constexpr bool kRowKernel = true;
+constexpr int kRowLanes = 2;
+constexpr int kRowUnroll = 8;
+constexpr int kRowThreads = 256;
+
+template <int WT, int L>
+__device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uint32_t k,
+                                          uint32_t e, const float2 *x, float &sx, float &sy) {
+  for (; k < e; k += kRowUnroll * L) {
+    int c[kRowUnroll];
+    float wv[kRowUnroll];
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      const uint32_t kk = k + u * L;
+      c[u] = kk < e ? __ldcs(col + kk) : -1;
+      wv[u] = kk < e ? wload<WT>(w, kk) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      if (c[u] >= 0) {
+        const float2 xv = __ldg(x + c[u]);
+        sx = fmaf(wv[u], xv.x, sx);
+        sy = fmaf(wv[u], xv.y, sy);
+      }
+    }
+  }
+}
+
+template <int WT, int MODE>
+__global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
+  const int64_t N = A.nrows;
+  constexpr int L = kRowLanes, RPW = 32 / L;
+  const int lane = threadIdx.x & 31, m = lane & (L - 1);
+  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
+  const bool two = A.hrp != nullptr;
+  for (long long base = gw * RPW; base < N; base += nw * RPW) {
+    const long long v = base + lane / L;
+    bool live = false;
+    uint32_t sa = 0, sb = 0, ha = 0, hb = 0;
+    if (v < N) {
+      const uint32_t f0 = A.srp[v], f1 = A.srp[v + 1];
+      sa = f0 & kOffMask;
+      sb = f1 & kOffMask;
+      if (two) {
+        const uint32_t h0 = A.hrp[v];
+        ha = h0 & kOffMask;
+        hb = A.hrp[v + 1] & kOffMask;
+        live = !(h0 & kHubFlag);
+      } else {
+        live = !(f0 & kHubFlag);
+      }
+    }
+    float sx = 0.f, sy = 0.f;
+    if (live) {
+      row_piece<WT, L>(A.scol, A.sw, sa + m, sb, A.x, sx, sy);
+      if (two) row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
+    }
+#pragma unroll
+    for (int d = 1; d < L; d <<= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, d);
+      sy += __shfl_xor_sync(0xffffffffu, sy, d);
+    }
+    if (live && m == 0) {
+      const float av = A.a[v];
+      const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
+      const float2 xr = A.x[v];
+      epilogue_k<float>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0),
+                        av * xr.x + bv * sx, av * xr.y + bv * sy);
+    }
+  }
+}
+
 // Hub rows, after the chunk launch: a block takes kHubRows rows, a warp per
 // row adding the row's partials in a fixed order (lane-strided over the
 // chunks, then a fixed tree); one warp then does the combines in FP64, a lane
@@ -597,6 +676,7 @@ static void fill_matrix(StepArgs &A, const SpMat &st, const SpMat *hm) {
   A.hw = hm ? hm->w.p : nullptr;
   A.tdesc = P<int4>(m.tdesc);
   A.ntiles = m.ntiles;
+  A.nrows = m.N;
   A.lrow = P<int32_t>(m.lrow);
   A.lsb = P<uint64_t>(m.lsb);
   A.lhb = P<uint64_t>(m.lhb);
@@ -646,12 +726,29 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     note_launch();
     note_launch();
   }
-  const long long want = ((long long)A.ntiles + kSpmmWarps - 1) / kSpmmWarps;
-  const long long cap = (long long)occ[wi] * nsm;
-  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-  if (wi) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
-  else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
-  note_launch();
+  if (kRowKernel) {
+    static int occr[2] = {0, 0};
+    if (!occr[wi]) {
+      int b = 0;
+      cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<1, MODE>, kRowThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<0, MODE>, kRowThreads, 0);
+      occr[wi] = (e == cudaSuccess && b > 0) ? b : 1;
+    }
+    const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
+    const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
+    const long long cap = (long long)occr[wi] * nsm;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
+    else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
+    note_launch();
+  } else {
+    const long long want = ((long long)A.ntiles + kSpmmWarps - 1) / kSpmmWarps;
+    const long long cap = (long long)occ[wi] * nsm;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    if (wi) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
+    else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
+    note_launch();
+  }
   if (prof) prof_end(s);
   return cudaGetLastError();
 }
