@@ -120,7 +120,7 @@ static void destroy(pl_graph *g) {
                  &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
                  &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
                  &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur,
-                 &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->klen, &g->clen, &g->lflag,
+                 &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->clen, &g->lflag,
                  &g->crank, &g->tpos, &g->mac_base,
                  &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,
                  &g->acc, &g->gsc, &g->status, &g->scr.buf};
@@ -128,8 +128,8 @@ static void destroy(pl_graph *g) {
   for (Buf &b : g->tmp) release(b);
   SpMat *ms[] = {&g->st, &g->hm};
   for (SpMat *m : ms) {
-    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->keys, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
-                 &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->tile_row, &m->tdesc, &m->longidx,
+    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
+                 &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->longidx,
                  &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part};
     for (Buf *b : mb) release(*b);
   }

@@ -7,9 +7,9 @@
 //   GiFt band filter   (Sec. IV): with u = D_sigma^{-1/2} g carried between
 //                                 steps, a_v = sigma / d_v, b_v = 1 / d_v,
 //                                 d_v = D_vv + sigma, i.e. u' = D_sigma^{-1}(A + sigma I) u.
-// Short rows (<= kLong entries): a CTA stages the products of an nnz tile in
-// shared memory (coalesced 16-byte index/weight loads, gathered x), then sums
-// each row with a warp.  Hub rows (virtual nodes, very long rows): chunks of
+// Short rows (<= kLong entries): a group of two lanes per row reads the row's
+// indices and weights from global memory with several loads in flight per
+// lane, gathers x and sums in FP32.  Hub rows (virtual nodes, very long rows): chunks of
 // kChunk entries accumulate exact products in double-float (one launch); the
 // next launch adds each hub row's partials in a fixed order and does the
 // combine in FP64, since those rows amplify rounding error by up to a_v^k when
@@ -41,8 +41,6 @@ struct StepArgs {
   const int32_t *hcol;
   const void *hw;
   // work units of the applied matrix
-  const int4 *tdesc;
-  int32_t ntiles;
   int64_t nrows;  // rows of the applied matrix
   const int32_t *lrow;
   const uint64_t *lsb, *lhb;
@@ -133,192 +131,21 @@ __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T y
   epilogue_k<T>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0), yx, yy);
 }
 
-// ------------------------------------------------------- warp work units
-// Units: hub chunks [0, nchunks) of kChunk entries (first launch), hub rows
-// (second launch), then short tiles of at most kTile keys (rows + entries;
-// rows <= kLong entries; third launch).  Each warp takes units gw, gw + nwarps, ... and
-// loads the next tile's descriptor while it works on the current unit; a
-// unit needs no block-wide barrier.
-//  * tile: every lane issues the loads of all its entries (index, weight) and
-//    of its row's pointers and coefficient at once, then all its gathers of
-//    x, writes w * x[col] to the warp's shared-memory slice, and sums whole
-//    rows (lane per row) before their epilogue;
+// ------------------------------------------------------- work units
+// Hub chunks [0, nchunks) of kChunk entries (first launch), hub rows (second
+// launch), then the short rows (third launch); warps take units gw,
+// gw + nwarps, ... and no unit needs a block-wide barrier.
 //  * hub chunk: exact products accumulated in double-float, reduced over the
 //    warp, written as a double-float partial;
 //  * hub row: the row's partials added by a warp in a fixed order, then
-//    combined in FP64 by a lane per row.
-constexpr int kEntWarp = kTile + kLong;    // entries of one tile < kTile + kLong
-constexpr int kPer = (kEntWarp + 31) / 32;  // entries per lane of one tile
-constexpr int kChunkBatch = 8;              // loads in flight per lane (hub chunks)
+//    combined in FP64 by a lane per row;
+//  * short rows: a group of lanes per row (below).
+constexpr int kChunkBatch = 8;  // loads in flight per lane (hub chunks)
 
 template <int WT>
 __device__ __forceinline__ float wload(const void *w, uint64_t k) {
   if (WT == 0) return __ldcs(reinterpret_cast<const float *>(w) + k);
   return __uint_as_float((uint32_t)__ldcs(reinterpret_cast<const unsigned short *>(w) + k) << 16);
-}
-
-// Sum of the products of row r (st part at [ra, rb) of the slice, hm part at
-// [ha, hb)), then the epilogue.
-template <int MODE>
-__device__ __forceinline__ void tile_row_out(const StepArgs &A, int r, const float2 *sp,
-                                             uint32_t ra, uint32_t rb, uint32_t ha, uint32_t hb,
-                                             float av, float bv, float2 xr, uint8_t kd,
-                                             double2 ac) {
-  float sx = 0.f, sy = 0.f;
-  for (uint32_t k = ra; k < rb; ++k) {
-    const float2 q = sp[k];
-    sx += q.x;
-    sy += q.y;
-  }
-  for (uint32_t k = ha; k < hb; ++k) {
-    const float2 q = sp[k];
-    sx += q.x;
-    sy += q.y;
-  }
-  epilogue_k<float>(A, r, kd, ac, av * xr.x + bv * sx, av * xr.y + bv * sy);
-}
-
-// Per-warp staging of one tile's indices and weights in shared memory: the
-// st and hm short ranges are copied in aligned 16-byte pieces (cp.async, L2
-// only), so a range [a, b) occupies [a & ~(per - 1), (b + per - 1) & ~(per - 1))
-// of its array; a tile reads fewer than kEntWarp entries, so each buffer needs
-// at most kEntWarp + 4 * 16 / 2 slots of the narrowest type.
-constexpr int kStageCol = kEntWarp + 16;  // int32 slots
-template <int WT>
-struct TileStage {
-  int32_t col[kStageCol];
-  // bf16: at most kEntWarp + 32 halves; float: kEntWarp + 16 words
-  uint32_t w[WT == 1 ? (kEntWarp + 32) / 2 : kEntWarp + 16];
-};
-
-__device__ __forceinline__ void cp16(void *sdst, const void *gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Offsets of a tile's pieces inside its stage (entries of each type).
-struct StageMap {
-  uint32_t cs, ch, ws, wh;  // first staged slot of the st / hm range (col, w)
-  uint32_t hcol0, hw0;      // where the hm range starts in the stage
-};
-template <int WT>
-__device__ __forceinline__ StageMap stage_map(uint32_t s0, uint32_t s1, uint32_t h0) {
-  constexpr uint32_t wper = WT == 1 ? 8u : 4u;  // weights per 16 bytes
-  StageMap m;
-  const uint32_t ca = s0 & ~3u, cb = (s1 + 3u) & ~3u;
-  const uint32_t wa = s0 & ~(wper - 1u), wb = (s1 + wper - 1u) & ~(wper - 1u);
-  m.cs = s0 - ca;
-  m.ws = s0 - wa;
-  m.hcol0 = cb - ca;
-  m.hw0 = wb - wa;
-  m.ch = m.hcol0 + (h0 - (h0 & ~3u));
-  m.wh = m.hw0 + (h0 - (h0 & ~(wper - 1u)));
-  return m;
-}
-
-template <int WT>
-__device__ __forceinline__ void stage_tile(const StepArgs &A, const int4 d0, const int4 d1,
-                                           TileStage<WT> *st) {
-  constexpr uint32_t wper = WT == 1 ? 8u : 4u;
-  constexpr uint32_t wsz = WT == 1 ? 2u : 4u;
-  const int lane = threadIdx.x & 31;
-  const uint32_t s0 = (uint32_t)d0.y, s1 = (uint32_t)d1.y, h0 = (uint32_t)d0.z, h1 = (uint32_t)d1.z;
-  const uint32_t ca = s0 & ~3u, cb = (s1 + 3u) & ~3u;
-  const uint32_t ha = h0 & ~3u, hb = (h1 + 3u) & ~3u;
-  const uint32_t ncs = (cb - ca) >> 2, nch = h1 > h0 ? (hb - ha) >> 2 : 0u;
-  for (uint32_t i = lane; i < ncs + nch; i += 32) {
-    const int32_t *src = i < ncs ? A.scol + ca + 4u * i : A.hcol + ha + 4u * (i - ncs);
-    cp16(st->col + 4u * i, src);
-  }
-  const uint32_t wa = s0 & ~(wper - 1u), wb = (s1 + wper - 1u) & ~(wper - 1u);
-  const uint32_t hwa = h0 & ~(wper - 1u), hwb = (h1 + wper - 1u) & ~(wper - 1u);
-  const uint32_t nws = (wb - wa) / wper, nwh = h1 > h0 ? (hwb - hwa) / wper : 0u;
-  const char *sw = reinterpret_cast<const char *>(A.sw), *hw = reinterpret_cast<const char *>(A.hw);
-  char *dst = reinterpret_cast<char *>(st->w);
-  for (uint32_t i = lane; i < nws + nwh; i += 32) {
-    const char *src = i < nws ? sw + (size_t)(wa + wper * i) * wsz
-                              : hw + (size_t)(hwa + wper * (i - nws)) * wsz;
-    cp16(dst + 16u * i, src);
-  }
-}
-
-template <int WT>
-__device__ __forceinline__ float stage_w(const TileStage<WT> *st, uint32_t k) {
-  if (WT == 0) return __uint_as_float(st->w[k]);
-  const uint16_t h = reinterpret_cast<const uint16_t *>(st->w)[k];
-  return __uint_as_float((uint32_t)h << 16);
-}
-
-// One tile from its stage: gathers of x for every entry (all issued before
-// any use), products to the warp's slice, then row sums and epilogues.
-template <int WT, int MODE>
-__device__ __forceinline__ void warp_tile(const StepArgs &A, const int4 d0, const int4 d1,
-                                          const TileStage<WT> *st, float2 *sp) {
-  const int lane = threadIdx.x & 31;
-  const int r0 = d0.x, r1 = d1.x;
-  const uint32_t s0 = (uint32_t)d0.y, h0 = (uint32_t)d0.z;
-  const uint32_t ns = (uint32_t)d1.y - s0, n = ns + ((uint32_t)d1.z - h0);
-  const bool two = A.hrp != nullptr;
-  const StageMap mp = stage_map<WT>(s0, (uint32_t)d1.y, h0);
-  // this lane's first row: pointers, coefficient, own value
-  const int r = r0 + lane;
-  uint32_t ra = 0, rb = 0, ha = 0, hb = 0;
-  float av = 0.f, bv = 0.f;
-  float2 xr = make_float2(0.f, 0.f);
-  uint8_t kd = 0;
-  double2 ac = make_double2(0.0, 0.0);
-  if (r < r1) {
-    ra = A.srp[r];
-    rb = A.srp[r + 1];
-    if (two) {
-      ha = A.hrp[r];
-      hb = A.hrp[r + 1];
-    }
-    av = A.a[r];
-    if (MODE == MODE_GIFT) bv = A.b[r];
-    xr = A.x[r];
-    kd = A.nkind[r];
-    if (A.tap) ac = A.acc[r];
-  }
-  float2 xv[kPer];
-  const int nq = (int)((n + 31u) >> 5);  // warp-uniform
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    if (q >= nq) break;
-    const uint32_t k = q * 32 + lane;
-    int c = 0;
-    if (k < n) c = st->col[k < ns ? mp.cs + k : mp.ch + (k - ns)];
-    xv[q] = k < n ? __ldg(A.x + c) : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    if (q >= nq) break;
-    const uint32_t k = q * 32 + lane;
-    if (k < n) {
-      const float wv = stage_w<WT>(st, k < ns ? mp.ws + k : mp.wh + (k - ns));
-      sp[k] = make_float2(wv * xv[q].x, wv * xv[q].y);
-    }
-  }
-  __syncwarp();
-  if (MODE == MODE_HR) bv = A.binvf;
-  const uint32_t *skip = two ? A.hrp : A.srp;
-  if (r < r1 && !((two ? ha : ra) & kHubFlag))
-    tile_row_out<MODE>(A, r, sp, (ra & kOffMask) - s0, (rb & kOffMask) - s0,
-                       two ? (ha & kOffMask) - h0 + ns : 0u, two ? (hb & kOffMask) - h0 + ns : 0u,
-                       av, bv, xr, kd, ac);
-  for (int rr = r + 32; rr < r1; rr += 32) {
-    if (skip[rr] & kHubFlag) continue;
-    const uint32_t a2 = A.srp[rr] & kOffMask, b2 = A.srp[rr + 1] & kOffMask;
-    const uint32_t ha2 = two ? (A.hrp[rr] & kOffMask) - h0 + ns : 0u;
-    const uint32_t hb2 = two ? (A.hrp[rr + 1] & kOffMask) - h0 + ns : 0u;
-    tile_row_out<MODE>(A, rr, sp, a2 - s0, b2 - s0, ha2, hb2, A.a[rr],
-                       MODE == MODE_GIFT ? A.b[rr] : bv, A.x[rr], A.nkind[rr],
-                       A.tap ? A.acc[rr] : make_double2(0.0, 0.0));
-  }
-  __syncwarp();
 }
 
 template <int WT>
@@ -369,10 +196,6 @@ __device__ void warp_chunk(const StepArgs &A, int c) {
   if (lane == 0) A.part[c] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
 }
 
-constexpr int kSpmmThreads = 128;
-constexpr int kSpmmWarps = kSpmmThreads / 32;
-constexpr int kSpmmBlocksPerSm = 6;
-
 // Hub chunks: warp w of the grid takes chunks w, w + nwarps, ...
 template <int WT, int MODE>
 __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
@@ -386,7 +209,6 @@ __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
 // m + kRowLanes, ...; kRowUnroll index and weight loads in flight, then their
 // gathers of x), a butterfly over the group sums them, and the group's first
 // lane applies the epilogue.  Hub rows are skipped (their own launches).
-constexpr bool kRowKernel = true;
 constexpr int kRowLanes = 2;
 constexpr int kRowUnroll = 8;
 constexpr int kRowThreads = 256;
@@ -497,60 +319,6 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
   }
   const float2 xv = A.x[v];
   epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
-}
-
-// Short tiles: warp w of the grid takes tiles w, w + nwarps, ... as a
-// two-stage pipeline (stage the next tile while the current one is gathered
-// and summed; descriptors one tile further ahead).
-template <int WT, int MODE>
-__global__ void __launch_bounds__(kSpmmThreads, kSpmmBlocksPerSm) k_spmm(StepArgs A) {
-  __shared__ __align__(16) TileStage<WT> stage_all[kSpmmWarps][2];
-  __shared__ float2 sp_all[kSpmmWarps][kEntWarp];
-  const int wid = threadIdx.x >> 5;
-  float2 *sp = sp_all[wid];
-  TileStage<WT> *stg = stage_all[wid];
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  long long t = gw;
-  int4 c0 = make_int4(0, 0, 0, 0), c1 = c0;
-  if (t < A.ntiles) {
-    c0 = __ldg(A.tdesc + t);
-    c1 = __ldg(A.tdesc + t + 1);
-    stage_tile<WT>(A, c0, c1, &stg[0]);
-  }
-  cp_commit();
-  if (t >= A.ntiles) {
-    cp_wait_all();
-    return;
-  }
-  long long tn = t + nw;
-  int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
-  if (tn < A.ntiles) {
-    n0 = __ldg(A.tdesc + tn);
-    n1 = __ldg(A.tdesc + tn + 1);
-  }
-  int cur = 0;
-  while (true) {
-    if (tn < A.ntiles) stage_tile<WT>(A, n0, n1, &stg[cur ^ 1]);
-    cp_commit();
-    const long long tnn = tn + nw;
-    int4 f0 = make_int4(0, 0, 0, 0), f1 = f0;
-    if (tnn < A.ntiles) {
-      f0 = __ldg(A.tdesc + tnn);
-      f1 = __ldg(A.tdesc + tnn + 1);
-    }
-    cp_wait_prev();
-    __syncwarp();
-    warp_tile<WT, MODE>(A, c0, c1, &stg[cur], sp);
-    if (tn >= A.ntiles) break;
-    c0 = n0;
-    c1 = n1;
-    n0 = f0;
-    n1 = f1;
-    tn = tnn;
-    cur ^= 1;
-  }
-  cp_wait_all();
 }
 
 // ------------------------------------------------------------- helpers
@@ -674,8 +442,6 @@ static void fill_matrix(StepArgs &A, const SpMat &st, const SpMat *hm) {
   A.hrp = hm ? P<uint32_t>(hm->rp_s) : nullptr;
   A.hcol = hm ? P<int32_t>(hm->col) : nullptr;
   A.hw = hm ? hm->w.p : nullptr;
-  A.tdesc = P<int4>(m.tdesc);
-  A.ntiles = m.ntiles;
   A.nrows = m.N;
   A.lrow = P<int32_t>(m.lrow);
   A.lsb = P<uint64_t>(m.lsb);
@@ -695,7 +461,7 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
-// One sparse product: the hub chunks, the hub rows, then the short tiles
+// One sparse product: the hub chunks, the hub rows, then the short rows
 // (same stream).
 template <int MODE>
 static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s) {
@@ -706,13 +472,13 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  // one wave of resident blocks (tiles are dealt to warps statically)
+  // short rows: one wave of resident blocks, row groups dealt round robin
   static int occ[2] = {0, 0};
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
     int b = 0;
-    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm<1, MODE>, kSpmmThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm<0, MODE>, kSpmmThreads, 0);
+    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<1, MODE>, kRowThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<0, MODE>, kRowThreads, 0);
     occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
   }
   const bool prof = prof_on();
@@ -726,29 +492,13 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     note_launch();
     note_launch();
   }
-  if (kRowKernel) {
-    static int occr[2] = {0, 0};
-    if (!occr[wi]) {
-      int b = 0;
-      cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<1, MODE>, kRowThreads, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<0, MODE>, kRowThreads, 0);
-      occr[wi] = (e == cudaSuccess && b > 0) ? b : 1;
-    }
-    const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
-    const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
-    const long long cap = (long long)occr[wi] * nsm;
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
-    else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
-    note_launch();
-  } else {
-    const long long want = ((long long)A.ntiles + kSpmmWarps - 1) / kSpmmWarps;
-    const long long cap = (long long)occ[wi] * nsm;
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    if (wi) k_spmm<1, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
-    else k_spmm<0, MODE><<<grid, kSpmmThreads, 0, s>>>(A);
-    note_launch();
-  }
+  const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
+  const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
+  const long long cap = (long long)occ[wi] * nsm;
+  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  note_launch();
   if (prof) prof_end(s);
   return cudaGetLastError();
 }

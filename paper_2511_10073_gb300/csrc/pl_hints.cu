@@ -396,13 +396,12 @@ __device__ __forceinline__ int win_count(int bx, int by, const HintGeo &G) {
 
 // Per-row lengths of a split matrix.  Static mode: the st rows (hub when
 // longer than kLong).  Hint mode: the hm rows; a row is a hub row when it is a
-// virtual node or its static plus hint entries exceed kLong.  klen is what a
-// tile reads of the row (st short part + hm short part), clen the length the
-// hub chunks cover (st part + hm part).
+// virtual node or its static plus hint entries exceed kLong.  clen is the
+// length the hub chunks cover (st part + hm part).
 __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const uint8_t *hflag,
                           const int32_t *cell_bin, const int32_t *n_ovl, const int64_t *moff,
                           const int64_t *hub_len, uint32_t *slen, uint64_t *llen, uint8_t *lflag,
-                          uint32_t *klen, uint64_t *clen) {
+                          uint64_t *clen) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.N;
        v += (long long)gridDim.x * blockDim.x) {
     const long long sl = v < G.Nst ? srp[v + 1] - srp[v] : 0;
@@ -411,7 +410,6 @@ __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const u
       slen[v] = hub ? 0u : (uint32_t)sl;
       llen[v] = hub ? (uint64_t)sl : 0ull;
       lflag[v] = hub ? 1 : 0;
-      klen[v] = hub ? 0u : (uint32_t)sl;
       clen[v] = hub ? (uint64_t)sl : 0ull;
       continue;
     }
@@ -431,7 +429,6 @@ __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const u
     slen[v] = hub ? 0u : (uint32_t)hl;
     llen[v] = hub ? (uint64_t)hl : 0ull;
     lflag[v] = hub ? 1 : 0;
-    klen[v] = (uint32_t)((sl <= kLong ? sl : 0) + (hub ? 0 : hl));
     clen[v] = hub ? (uint64_t)(sl + hl) : 0ull;
   }
 }
@@ -503,34 +500,6 @@ __global__ void k_hub_desc(int32_t nlong, int with_hints, const int32_t *lrow,
     lsl[l] = (uint32_t)sl;
     lhb[l] = lptr[l];
     lhl[l] = (uint32_t)(lptr[l + 1] - lptr[l]);
-  }
-}
-
-// First row owned by each tile.  Row r has key keys[r] + r (entries a tile
-// reads and rows before it); tile t owns the rows with keys in [t*kTile,
-// (t+1)*kTile), so a tile holds at most kTile rows and reads fewer than
-// kTile + kLong entries.
-__global__ void k_tiles(const uint32_t *keys, int64_t N, int32_t ntiles, int32_t *tile_row) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
-    if (t == 0) { tile_row[0] = 0; continue; }
-    if (t == ntiles) { tile_row[t] = (int32_t)N; continue; }
-    uint64_t target = (uint64_t)t * kTile;
-    long long lo = 0, hi = N;  // first r in [0, N] with rp_s[r] + r >= target
-    while (lo < hi) {
-      long long mid = (lo + hi) >> 1;
-      if ((uint64_t)keys[mid] + (uint64_t)mid < target) lo = mid + 1; else hi = mid;
-    }
-    tile_row[t] = (int32_t)lo;
-  }
-}
-
-// Tile descriptors: first row and the offsets of its entries in the st and
-// hm short regions (hm_rp == nullptr: the tile reads st alone).
-__global__ void k_tile_desc(int32_t ntiles, const int32_t *tile_row, const uint32_t *st_rp,
-                            const uint32_t *hm_rp, int4 *tdesc) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) {
-    const int r = tile_row[t];
-    tdesc[t] = make_int4(r, (int)(st_rp[r] & kOffMask), hm_rp ? (int)(hm_rp[r] & kOffMask) : 0, 0);
   }
 }
 
@@ -955,7 +924,7 @@ static HintGeo make_geo(const pl_graph *g) {
 }
 
 // Layout of a split matrix from per-row lengths already in g->slen/llen/lflag.
-// Layout of a split matrix from per-row lengths in g->slen/llen/klen/clen and
+// Layout of a split matrix from per-row lengths in g->slen/llen/clen and
 // hub flags in g->hubf.
 static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   const int64_t N = g->N;
@@ -972,17 +941,12 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   TRY(ensure(g->lflag, (size_t)(N + 1) * 4 + 256));
   int32_t *lscan = P<int32_t>(g->lflag);
   TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->hubf), lscan, N, stmp, s)));
-  TRY(ensure(g->lay[2], (size_t)(N + 1) * 8 + 256));
-  uint64_t *k64 = P<uint64_t>(g->lay[2]);
-  TRY((exclusive_scan<uint32_t, uint64_t>(P<uint32_t>(g->klen), k64, N, stmp, s)));
-  uint64_t tot[3];
+  uint64_t tot[2];
   int32_t nl;
   TRY(d2h(&tot[0], s64 + N, 1, s));
   TRY(d2h(&tot[1], lpos + N, 1, s));
-  TRY(d2h(&tot[2], k64 + N, 1, s));
   TRY(d2h(&nl, lscan + N, 1, s));
-  if (tot[0] >= (uint64_t)kOffMask - 2 * kTile || tot[2] + (uint64_t)N >= (uint64_t)kOffMask ||
-      tot[0] + tot[1] >= (1ull << 40)) {
+  if (tot[0] + kPad >= (uint64_t)kOffMask || tot[0] + tot[1] >= (1ull << 40)) {
     set_error("graph too large for the 31-bit short-row layout (%llu entries)",
               (unsigned long long)tot[0]);
     return PL_ERR_UNSUPPORTED;
@@ -994,9 +958,6 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   TRY(ensure(m.rp_s, (size_t)(N + 1 + kRpPad) * 4));
   k_rp_pack<<<grid_for(N + 1 + kRpPad, 256), 256, 0, s>>>(s64, P<uint8_t>(g->hubf), N,
                                                          P<uint32_t>(m.rp_s));
-  note_launch();
-  TRY(ensure(m.keys, (size_t)(N + 1) * 4 + 16));
-  k_u64_to_u32<<<grid_for(N + 1, 256), 256, 0, s>>>(k64, P<uint32_t>(m.keys), N + 1);
   note_launch();
   const uint64_t cap = m.nnz_s + m.nnz_l + kPad;
   TRY(ensure(m.col, cap * 4));
@@ -1035,17 +996,6 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
     k_chunk_owner<<<grid_for(nl, 256), 256, 0, s>>>(nl, P<int32_t>(m.lchunk), P<int32_t>(m.chunk_lr));
     note_launch();
   }
-  m.ntiles = (int32_t)((tot[2] + (uint64_t)N + kTile - 1) / kTile);
-  if (m.ntiles < 1) m.ntiles = 1;
-  TRY(ensure(m.tile_row, (size_t)(m.ntiles + 1) * 4));
-  k_tiles<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(P<uint32_t>(m.keys), N, m.ntiles,
-                                                     P<int32_t>(m.tile_row));
-  note_launch();
-  TRY(ensure(m.tdesc, (size_t)(m.ntiles + 1) * 16));
-  k_tile_desc<<<grid_for(m.ntiles + 1, 256), 256, 0, s>>>(
-      m.ntiles, P<int32_t>(m.tile_row), with_hints ? P<uint32_t>(g->st.rp_s) : P<uint32_t>(m.rp_s),
-      with_hints ? P<uint32_t>(m.rp_s) : nullptr, P<int4>(m.tdesc));
-  note_launch();
   TRY(ensure(m.dsum, (size_t)N * 8 + 16));
   TRY(ensure(m.psum, (size_t)N * 8 + 16));
   TRY(ensure(m.c32, (size_t)N * 4 + 16));
@@ -1062,7 +1012,6 @@ static pl_status ensure_row_arrays(pl_graph *g) {
   const int64_t N = g->N;
   TRY(ensure(g->slen, (size_t)N * 4 + 16));
   TRY(ensure(g->llen, (size_t)N * 8 + 16));
-  TRY(ensure(g->klen, (size_t)N * 4 + 16));
   TRY(ensure(g->clen, (size_t)N * 8 + 16));
   TRY(ensure(g->hubf, (size_t)N + 256));
   return PL_OK;
@@ -1080,7 +1029,7 @@ pl_status prepare_static_layout(pl_graph *g, cudaStream_t s) {
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 0, P<int64_t>(g->srp), nullptr, nullptr, nullptr,
                                              nullptr, nullptr, P<uint32_t>(g->slen),
                                              P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
-                                             P<uint32_t>(g->klen), P<uint64_t>(g->clen));
+                                             P<uint64_t>(g->clen));
   note_launch();
   return layout(g, g->st, 0, s);
 }
@@ -1234,7 +1183,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
                                              P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
                                              P<int64_t>(g->moff), hub_len, P<uint32_t>(g->slen),
                                              P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
-                                             P<uint32_t>(g->klen), P<uint64_t>(g->clen));
+                                             P<uint64_t>(g->clen));
   note_launch();
   st = layout(g, g->hm, 1, s);
   if (st != PL_OK) return st;

@@ -11,13 +11,12 @@
 
 namespace pl {
 
-// SpMM work units: short rows (<= kLong entries) are cut into warp tiles of at
-// most kTile keys (rows + entries, the key of row r being rp_s[r] + r); long
-// rows and every virtual-node row go to the hub path in chunks of kChunk.
-constexpr int kTile = 256;
+// SpMM work units: short rows (<= kLong entries) are read by a group of lanes
+// each; long rows and every virtual-node row go to the hub path in chunks of
+// kChunk.
 constexpr int kLong = 128;
 constexpr int kChunk = 512;
-constexpr int kPad = 16;  // spare entries after the last one (aligned over-reads)
+constexpr int kPad = 16;  // spare entries after the last one
 constexpr int kRpPad = 8;  // spare row pointers after the last one
 constexpr uint32_t kHubFlag = 0x80000000u;  // rp_s bit 31: the row is a hub row
 constexpr uint32_t kOffMask = 0x7fffffffu;
@@ -30,26 +29,21 @@ constexpr uint32_t kOffMask = 0x7fffffffu;
 //    the augmented graph is its st part followed by its hm part; it is a hub
 //    row (bit 31 of hm.rp_s) when it is a virtual node or has more than kLong
 //    entries in total, and its st part then may sit in st's short region.
-// Tiles own the rows whose key (keys[r] + r) falls in a window of kTile; keys
-// count the entries a tile reads (st short entries + hm short entries).  Per
-// hub row, lsb/lsl give its st piece and lhb/lhl its hm piece (absolute
+// Per hub row, lsb/lsl give its st piece and lhb/lhl its hm piece (absolute
 // offsets, lengths); chunks of kChunk cover the concatenation.
 struct SpMat {
   int64_t N = 0;
   uint64_t nnz_s = 0, nnz_l = 0;
-  int32_t nlong = 0, ntiles = 0, nchunks = 0;
+  int32_t nlong = 0, nchunks = 0;
   Buf rp_s;     // uint32 [N+1+kRpPad], bit 31 = hub row
   Buf col;      // int32 [nnz_s + nnz_l + kPad]
   Buf w;        // float or uint16 (bf16) [same]
-  Buf keys;     // uint32 [N+1] tile keys without the row count
   Buf lrow;     // int32 [nlong] node of each hub row
   Buf lptr;     // uint64 [nlong+1] this matrix's part of each hub row (absolute)
   Buf lsb, lhb; // uint64 [nlong] st piece / hm piece of each hub row
   Buf lsl, lhl; // uint32 [nlong] their lengths
   Buf lchunk;   // int32 [nlong+1] first chunk of each hub row
   Buf chunk_lr; // int32 [nchunks] hub row of each chunk
-  Buf tile_row; // int32 [ntiles+1] first row owned by each tile
-  Buf tdesc;    // int4 [ntiles+1] per tile: first row, st short offset, hm short offset
   Buf longidx;  // int32 [N] hub index or -1
   Buf dsum;     // dfl [N] signed degree D_ii (hm: of the whole augmented row)
   Buf psum;     // dfl [N] sum of positive weights
@@ -108,7 +102,6 @@ struct pl_graph {
   pl::Buf hlen;        // int64 [N] augmented row length
   pl::Buf slen;        // uint32 [N] short-region length (0 for hub rows)
   pl::Buf llen;        // uint64 [N] hub-region length (0 for short rows)
-  pl::Buf klen;        // uint32 [N] tile key length
   pl::Buf clen;        // uint64 [N] chunked length of hub rows
   pl::Buf lflag;       // int32 [N+1] hub flag scan
   pl::Buf crank;       // int32 [C] place of a hint cell in the bucket list
