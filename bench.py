@@ -332,7 +332,7 @@ def main():
                    "augmented_nnz": info["nnz"], "hub_rows": info["hub_rows"],
                    "l2": "inputs larger than L2 (each sparse product streams >400 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_spmm_hub + k_hub_rows + k_spmm (one sparse product of the refinement filter, A4)",
+        "roofline": {"kernel": "k_spmm_hub + k_hub_rows + k_spmm_rows (one sparse product of the refinement filter, A4)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
