@@ -268,6 +268,16 @@ struct Buf {
   size_t bytes = 0;
 };
 cudaError_t ensure(Buf &b, size_t bytes);  // grow-only (contents not kept)
+
+// Several small device values to the host with one synchronisation: each is
+// copied device to device (asynchronously) into the staging buffer, then one
+// copy brings them all back.
+struct D2H {
+  void *h;
+  const void *d;
+  size_t n;  // bytes, at most 64 each
+};
+cudaError_t d2h_many(Buf &stage, const D2H *items, int count, cudaStream_t s);
 void release(Buf &b);
 template <typename T>
 inline T *P(Buf &b) { return reinterpret_cast<T *>(b.p); }

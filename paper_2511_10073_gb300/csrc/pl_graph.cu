@@ -741,8 +741,10 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY((exclusive_scan<uint8_t, int32_t>(pflag, pscan, NP, stmp, s)));
   int32_t sizes2[2];
-  TRY(d2h(&sizes2[0], P<int32_t>(g->cell_macro) + C, 1, s));
-  TRY(d2h(&sizes2[1], pscan + NP, 1, s));
+  {
+    const D2H it[2] = {{&sizes2[0], P<int32_t>(g->cell_macro) + C, 4}, {&sizes2[1], pscan + NP, 4}};
+    TRY(d2h_many(g->stage, it, 2, s));
+  }
   g->Mm = sizes2[0];
   g->Pm = sizes2[1];
   TRY(ensure(g->macro_cell, (size_t)g->Mm * 4 + 16));

@@ -943,9 +943,10 @@ static pl_status layout(pl_graph *g, SpMat &m, int with_hints, cudaStream_t s) {
   TRY((exclusive_scan<uint8_t, int32_t>(P<uint8_t>(g->hubf), lscan, N, stmp, s)));
   uint64_t tot[2];
   int32_t nl;
-  TRY(d2h(&tot[0], s64 + N, 1, s));
-  TRY(d2h(&tot[1], lpos + N, 1, s));
-  TRY(d2h(&nl, lscan + N, 1, s));
+  {
+    const D2H it[3] = {{&tot[0], s64 + N, 8}, {&tot[1], lpos + N, 8}, {&nl, lscan + N, 4}};
+    TRY(d2h_many(g->stage, it, 3, s));
+  }
   if (tot[0] + kPad >= (uint64_t)kOffMask || tot[0] + tot[1] >= (1ull << 40)) {
     set_error("graph too large for the 31-bit short-row layout (%llu entries)",
               (unsigned long long)tot[0]);
@@ -1092,14 +1093,16 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->bcnt), P<int64_t>(g->boff), nbk, stmp, s)));
   }
   int hst[8];
-  TRY(d2h(hst, g->status.p, 8, s));
+  int64_t nbl, nml;
+  {
+    const D2H it[3] = {{hst, g->status.p, 32}, {&nbl, P<int64_t>(g->boff) + nbk, 8},
+                       {&nml, P<int64_t>(g->moff) + Mm, 8}};
+    TRY(d2h_many(g->stage, it, 3, s));
+  }
   if (hst[0] & ST_NONFINITE) {
     set_error("non-finite movable cell coordinate");
     return PL_ERR_NONFINITE;
   }
-  int64_t nbl, nml;
-  TRY(d2h(&nbl, P<int64_t>(g->boff) + nbk, 1, s));
-  TRY(d2h(&nml, P<int64_t>(g->moff) + Mm, 1, s));
   // H3-H4: bin buckets (ascending cell id) and macro lists (sorted)
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));

@@ -117,6 +117,7 @@ struct pl_graph {
   pl::Buf acc;            // double2 [N]
   pl::Buf gsc;            // float [3 * N] GiFt scales (1/sqrt(D+sigma))
   pl::Buf status;         // int32 [8]
+  pl::Buf stage;          // staging words of batched device-to-host reads
   pl::Scratch scr;
   pl::Buf tmp[8];
   pl::Buf lay[4];         // layout scratch (scans of row lengths, chunk counts)

@@ -20,6 +20,25 @@ cudaError_t ensure(Buf &b, size_t bytes) {
   return cudaSuccess;
 }
 
+cudaError_t d2h_many(Buf &stage, const D2H *items, int count, cudaStream_t s) {
+  constexpr int kMax = 8, kSlot = 64;
+  if (count < 1 || count > kMax) return cudaErrorInvalidValue;
+  cudaError_t e = ensure(stage, (size_t)kMax * kSlot);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < count; ++i) {
+    if (items[i].n > (size_t)kSlot) return cudaErrorInvalidValue;
+    e = cudaMemcpyAsync(static_cast<char *>(stage.p) + i * kSlot, items[i].d, items[i].n,
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  unsigned char host[kMax * kSlot];
+  e = cudaMemcpyAsync(host, stage.p, (size_t)count * kSlot, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < count; ++i) memcpy(items[i].h, host + i * kSlot, items[i].n);
+  return cudaSuccess;
+}
+
 void release(Buf &b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
