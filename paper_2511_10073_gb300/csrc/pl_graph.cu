@@ -392,61 +392,42 @@ __device__ __forceinline__ double fix_to_double(const Fix128 &a) {
 }
 
 // Final static matrix, written straight into its split layout, from the FP64
-// weights (in place of the merged values).  A warp takes 32 consecutive rows:
-// for each row the warp writes columns and stored weights at the row's place
-// (short region or hub region), reduces the row's static degree
-// (double-float, over the stored weights; every static weight is positive, so
-// it is also the positive sum); then each lane forms, for a cell, the exact
-// sum of its row's FP64 weights (128-bit fixed point, order-free) and
-// baseWeight = RN(sum) / count.
+// weights (in place of the merged values), a thread per row: it writes the
+// row's columns and stored weights at the row's place (short region or hub
+// region), sums its static degree (double-float, in entry order, over the
+// stored weights; every static weight is positive, so it is also the
+// positive sum) and, for a cell, the exact sum of its FP64 weights (128-bit
+// fixed point, order-free) for baseWeight = RN(sum) / count.
 __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
     int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, const uint32_t *rp_s,
     const int32_t *longidx, const uint64_t *lptr, int32_t *scol, void *sw, dfl *dsum, dfl *psum,
     double *base_w, uint8_t *hflag, double *sdeg) {
-  const int lane = threadIdx.x & 31;
-  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long v0 = wg * 32; v0 < Nst; v0 += nwarp * 32) {
-    const long long v = v0 + lane;
-    const bool ok = v < Nst;
-    long long src = 0, dst = 0;
-    int m = 0;
-    if (ok) {
-      src = row_off[v];
-      m = (int)(srp[v + 1] - srp[v]);
-      const int li = longidx[v];
-      dst = li >= 0 ? (long long)lptr[li] : (long long)(rp_s[v] & kOffMask);
-    }
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nst;
+       v += (long long)gridDim.x * blockDim.x) {
+    const long long src = row_off[v];
+    const int m = (int)(srp[v + 1] - srp[v]);
+    const int li = longidx[v];
+    const long long dst = li >= 0 ? (long long)lptr[li] : (long long)(rp_s[v] & kOffMask);
+    const double *w64 = reinterpret_cast<const double *>(mval) + src;
+    const bool cell = v < C;
     dfl dl{0.f, 0.f};
-    const int nv = (int)min((long long)32, Nst - v0);
-    for (int j = 0; j < nv; ++j) {
-      const long long sj = __shfl_sync(0xffffffffu, src, j), dj = __shfl_sync(0xffffffffu, dst, j);
-      const int mj = __shfl_sync(0xffffffffu, m, j);
-      const double *w64 = reinterpret_cast<const double *>(mval) + sj;
-      dfl d{0.f, 0.f};
-      for (int k = lane; k < mj; k += 32) {
-        const double w = w64[k];
-        scol[dj + k] = mcol[sj + k];
-        uint16_t hb = 0;
-        float f = stored(w, wdtype, &hb);
-        if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dj + k] = hb;
-        else reinterpret_cast<float *>(sw)[dj + k] = f;
-        df_add(d, f);
-      }
-      d = warp_sum_df(d);
-      if (lane == j) dl = d;
+    Fix128 fl{0ull, 0ull};
+    for (int k = 0; k < m; ++k) {
+      const double w = w64[k];
+      scol[dst + k] = mcol[src + k];
+      uint16_t hb = 0;
+      const float f = stored(w, wdtype, &hb);
+      if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dst + k] = hb;
+      else reinterpret_cast<float *>(sw)[dst + k] = f;
+      df_add(dl, f);
+      if (cell) fix_add_double(fl, w);
     }
-    __syncwarp();
-    if (!ok) continue;
+    dl = df_norm(dl);
     sdeg[v] = df_to_d(dl);
     dsum[v] = dl;
     psum[v] = dl;
-    if (v < C) {
-      // the lane's own row, in integer arithmetic (no FP64 per entry)
-      const double *w64 = reinterpret_cast<const double *>(mval) + src;
-      Fix128 fl{0ull, 0ull};
-      for (int k = 0; k < m; ++k) fix_add_double(fl, w64[k]);
+    if (cell) {
       const double bw = m > 0 ? __ddiv_rn(fix_to_double(fl), (double)m) : 0.0;
       base_w[v] = bw;
       hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
@@ -850,7 +831,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     note_launch();
   }
   SpMat &sm = g->st;
-  k_static_compact<<<grid_for(Nst * 32, 256), 256, 0, s>>>(
+  k_static_compact<<<grid_for(Nst, 256), 256, 0, s>>>(
       row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
       P<uint32_t>(sm.rp_s), P<int32_t>(sm.longidx), P<uint64_t>(sm.lptr), P<int32_t>(sm.col),
       sm.w.p, P<dfl>(sm.dsum), P<dfl>(sm.psum), P<double>(g->base_w), P<uint8_t>(g->hflag),

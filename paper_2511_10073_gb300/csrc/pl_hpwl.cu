@@ -3,8 +3,9 @@
 // offset.  A thread takes a net of up to 32 pins; larger nets are taken by the
 // whole warp.  Pin positions and extrema are FP32 (min/max are exact), each
 // net's span is formed and summed in FP64.  Per-block FP64 sums go to the
-// caller's workspace; the last block to finish (ticket) adds them in block
-// order, so the result does not depend on scheduling.  A pin whose cell index
+// caller's workspace; the last block to finish (ticket) adds them in a fixed
+// order (strided over its threads, then a fixed tree), so the result does not
+// depend on scheduling.  A pin whose cell index
 // is out of range makes the result NaN (it is not dereferenced).
 #include <mutex>
 
@@ -131,11 +132,19 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
     last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double s = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) s += __ldcg(&part[k]);
-    *out = __ldcg(ticket + 1) ? __longlong_as_double(0x7ff8000000000000LL) : s;
+  if (!last) return;
+  // the last block: thread t adds partials t, t + 256, ... in order, then a
+  // fixed tree over the threads
+  __threadfence();
+  double s = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += kHpwlThreads) s += __ldcg(&part[k]);
+  s = warp_sum(s);
+  if (lane == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kHpwlThreads / 32; ++k) t += red[k];
+    *out = __ldcg(ticket + 1) ? __longlong_as_double(0x7ff8000000000000LL) : t;
     ticket[0] = 0;
     ticket[1] = 0;
   }
