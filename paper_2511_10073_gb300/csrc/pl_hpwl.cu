@@ -1,12 +1,15 @@
 // A5: half-perimeter wirelength (the quality metric of Sec. VII-VIII):
 // sum over nets of (max - min) pin x + (max - min) pin y, pin = cell centre +
-// offset.  A thread takes a net of up to 32 pins; larger nets are taken by the
-// whole warp.  Pin positions and extrema are FP32 (min/max are exact), each
-// net's span is formed and summed in FP64.  Per-block FP64 sums go to the
-// caller's workspace; the last block to finish (ticket) adds them in a fixed
-// order (strided over its threads, then a fixed tree), so the result does not
-// depend on scheduling.  A pin whose cell index
-// is out of range makes the result NaN (it is not dereferenced).
+// offset.  A thread takes a net of up to 32 pins (a warp stages the pins of 32
+// consecutive nets when they fit), a warp a net of up to 1024; each block then
+// spans the larger nets of its own range of nets, one at a time with all its
+// threads.  Pin positions
+// and extrema are FP32 (min/max are exact), each net's span is formed and
+// summed in FP64.  Per-block FP64 sums go to the caller's workspace; the last
+// block to finish (ticket) adds them in a fixed order (strided over its
+// threads, then a fixed tree), so the result does not depend on scheduling.
+// A pin whose cell index is out of range makes the result NaN (it is not
+// dereferenced).
 #include <mutex>
 
 #include "pl_internal.h"
@@ -16,6 +19,7 @@ namespace pl {
 constexpr int kHpwlThreads = 256;
 constexpr int kHpwlBlocks = 152 * 8;
 constexpr int kHpwlStage = 512;  // pins of one batch of 32 nets staged per warp
+constexpr int kHpwlWarpMax = 1024;  // longer nets are spanned by a whole block
 
 // Pin position; a pin_cell outside [0, C) is counted in *bad and reads cell 0
 // instead (the call then reports NaN).
@@ -41,10 +45,16 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
   __shared__ double red[kHpwlThreads / 32];
   __shared__ int last;
   __shared__ float2 stage_all[kHpwlThreads / 32][kHpwlStage];
+  __shared__ int32_t bigs[kHpwlThreads];
+  __shared__ int wcnt[kHpwlThreads / 32];
+  __shared__ float4 mm[kHpwlThreads / 32];
   float2 *stg = stage_all[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double acc = 0.0;
-  // each warp takes batches of 32 consecutive nets (warp-uniform loop)
+  // each warp takes batches of 32 consecutive nets (warp-uniform loop): a
+  // staged batch spans every net in it from shared memory; otherwise a lane
+  // spans each net of at most 32 pins and the warp each one of at most
+  // kHpwlWarpMax; longer nets are left to the block pass below
   const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = wg * 32; base < M; base += nwarp * 32) {
@@ -69,7 +79,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       __syncwarp();
       if (e < M) {
         const long long b = net_ptr[e] - p0, n = net_ptr[e + 1] - net_ptr[e];
-        if (n > 0) {
+        if (n > 0 && n <= kHpwlWarpMax) {
           float2 p = stg[b];
           float x0 = p.x, x1 = p.x, y0 = p.y, y1 = p.y;
           for (long long k = b + 1; k < b + n; ++k) {
@@ -83,12 +93,10 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       __syncwarp();
       continue;
     }
-    bool big = false;
+    bool mid = false;
     if (e < M) {
-      long long b = net_ptr[e], n = net_ptr[e + 1] - b;
-      if (n > 32) {
-        big = true;
-      } else if (n > 0) {
+      const long long b = net_ptr[e], n = net_ptr[e + 1] - b;
+      if (n > 0 && n <= 32) {
         float2 p = pin_pos(xy, pin_cell, dx, dy, b, C, ticket + 1);
         float x0 = p.x, x1 = p.x, y0 = p.y, y1 = p.y;
         for (long long k = b + 1; k < b + n; ++k) {
@@ -98,16 +106,17 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
         }
         acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
       }
+      mid = n > 32 && n <= kHpwlWarpMax;
     }
-    unsigned bm = __ballot_sync(0xffffffffu, big);
+    // nets of 33..kHpwlWarpMax pins: the whole warp, one net at a time
+    unsigned bm = __ballot_sync(0xffffffffu, mid);
     while (bm) {
-      int src = __ffs(bm) - 1;
+      const int src = __ffs(bm) - 1;
       bm &= bm - 1;
-      long long ee = base + src;
-      long long b = net_ptr[ee], n = net_ptr[ee + 1] - b;
+      const long long b = net_ptr[base + src], n = net_ptr[base + src + 1] - b;
       float x0 = 3.4e38f, x1 = -3.4e38f, y0 = 3.4e38f, y1 = -3.4e38f;
       for (long long k = b + lane; k < b + n; k += 32) {
-        float2 p = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
+        const float2 p = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
         x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
         y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
       }
@@ -121,13 +130,60 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       if (lane == src) acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
     }
   }
+  // nets of more than kHpwlWarpMax pins in this block's range of nets, in
+  // net order, each spanned by the whole block (strided pins, then a fixed
+  // tree)
+  double bigacc = 0.0;  // thread 0
+  const long long R = ((long long)M + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * R, r1 = r0 + R < M ? r0 + R : M;
+  for (long long c0 = r0; c0 < r1; c0 += kHpwlThreads) {
+    const long long e = c0 + threadIdx.x;
+    const bool big = e < r1 && net_ptr[e + 1] - net_ptr[e] > kHpwlWarpMax;
+    const unsigned bal = __ballot_sync(0xffffffffu, big);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, nbig = 0;
+    for (int w = 0; w < kHpwlThreads / 32; ++w) {
+      before += w < wid ? wcnt[w] : 0;
+      nbig += wcnt[w];
+    }
+    if (big) bigs[before + __popc(bal & ((1u << lane) - 1u))] = (int32_t)e;
+    __syncthreads();
+    for (int i = 0; i < nbig; ++i) {
+      const long long ee = bigs[i], b = net_ptr[ee], n = net_ptr[ee + 1] - b;
+      float x0 = 3.4e38f, x1 = -3.4e38f, y0 = 3.4e38f, y1 = -3.4e38f;
+      for (long long k = b + threadIdx.x; k < b + n; k += kHpwlThreads) {
+        const float2 p = pin_pos(xy, pin_cell, dx, dy, k, C, ticket + 1);
+        x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
+        y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
+      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, m));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, m));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, m));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, m));
+      }
+      if (lane == 0) mm[wid] = make_float4(x0, x1, y0, y1);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float4 t = mm[0];
+        for (int w = 1; w < kHpwlThreads / 32; ++w) {
+          t.x = fminf(t.x, mm[w].x); t.y = fmaxf(t.y, mm[w].y);
+          t.z = fminf(t.z, mm[w].z); t.w = fmaxf(t.w, mm[w].w);
+        }
+        bigacc += ((double)t.y - (double)t.x) + ((double)t.w - (double)t.z);
+      }
+      __syncthreads();
+    }
+  }
   acc = warp_sum(acc);
-  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  if (lane == 0) red[wid] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < kHpwlThreads / 32; ++k) s += red[k];
-    part[blockIdx.x] = s;
+    part[blockIdx.x] = s + bigacc;
     __threadfence();
     last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
   }
@@ -139,7 +195,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
   double s = 0.0;
   for (int k = threadIdx.x; k < (int)gridDim.x; k += kHpwlThreads) s += __ldcg(&part[k]);
   s = warp_sum(s);
-  if (lane == 0) red[threadIdx.x >> 5] = s;
+  if (lane == 0) red[wid] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
