@@ -260,7 +260,11 @@ __constant__ double c_recip[16];
 // lattice units (weight val / kLattice), val < 0 is -p for a star edge of a
 // p-node net (weight p / (p - 1)).  A single clique edge (val = kLattice / d,
 // d <= 15) takes the table; every other value needs an IEEE division.
-__device__ __forceinline__ bool lattice_easy(long long val, double *w) {
+__device__ __forceinline__ bool lattice_easy(long long val, const double *star_w, double *w) {
+  if (val < 0 && -val <= kMaxNetPins) {  // star edge of a (-val)-node net
+    *w = star_w[-val];
+    return true;
+  }
   if (val >= kLattice / 15 && val <= kLattice) {
     const int d = (int)((float)kLattice / (float)val + 0.5f);
     if (d >= 1 && d <= 15 && (long long)d * val == kLattice) {
@@ -276,6 +280,14 @@ __device__ __forceinline__ double lattice_div(long long val) {
   return __ddiv_rn((double)p, (double)(p - 1));
 }
 
+// p / (p - 1) for p = 2..kMaxNetPins, the weight of a star edge of a p-node
+// net, each an IEEE division (filled once per graph).
+__global__ void k_star_weights(double *star_w) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p <= kMaxNetPins;
+       p += (long long)gridDim.x * blockDim.x)
+    star_w[p] = p >= 2 ? __ddiv_rn((double)p, (double)(p - 1)) : 0.0;
+}
+
 // Table weights in place of the merged values (warp per 32 rows, lanes over a
 // row's entries); entries that need a division are listed, so that the
 // divisions run together in k_static_div instead of stalling whole warps.
@@ -283,7 +295,7 @@ constexpr int kDivBuf = 256;  // listed entries a warp buffers before one global
 
 __global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, int64_t *mval,
                                                         const int64_t *srp, int64_t Nst,
-                                                        uint32_t *list,
+                                                        const double *star_w, uint32_t *list,
                                                         unsigned long long *nlist) {
   __shared__ uint32_t wbuf[8][kDivBuf];
   const int lane = threadIdx.x & 31;
@@ -316,7 +328,7 @@ __global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, 
         bool hard = false;
         if (k < mj) {
           double w;
-          if (lattice_easy(mval[sj + k], &w)) reinterpret_cast<double *>(mval)[sj + k] = w;
+          if (lattice_easy(mval[sj + k], star_w, &w)) reinterpret_cast<double *>(mval)[sj + k] = w;
           else hard = true;
         }
         const unsigned hm = __ballot_sync(0xffffffffu, hard);
@@ -809,11 +821,17 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->base_w, (size_t)C * 8 + 16));
   TRY(ensure(g->hflag, (size_t)C + 16));
   TRY(ensure(g->sdeg, (size_t)Nst * 8 + 16));
-  {
+  if (!g->star_w_ok) {
+    // weight tables, once per graph: 1/d (host IEEE division) and p / (p - 1)
     double rc[16];
     rc[0] = 0.0;
     for (int d = 1; d < 16; ++d) rc[d] = 1.0 / (double)d;
     TRY(cudaMemcpyToSymbolAsync(c_recip, rc, sizeof(rc), 0, cudaMemcpyHostToDevice, s));
+    TRY(ensure(g->star_w, (size_t)(kMaxNetPins + 1) * 8));
+    k_star_weights<<<grid_for(kMaxNetPins + 1, 256), 256, 0, s>>>(P<double>(g->star_w));
+    note_launch();
+    TRY(cudaStreamSynchronize(s));  // rc lives on this stack frame
+    g->star_w_ok = true;
   }
   {
     // keys are consumed by the merge: their buffer holds the division list
@@ -825,7 +843,8 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     uint32_t *list = reinterpret_cast<uint32_t *>(keys + 2);
     TRY(cudaMemsetAsync(nlist, 0, 8, s));
     k_static_weights<<<grid_for(Nst * 32, 256), 256, 0, s>>>(row_off, mval, P<int64_t>(g->srp),
-                                                            Nst, list, nlist);
+                                                            Nst, P<double>(g->star_w), list,
+                                                            nlist);
     note_launch();
     k_static_div<<<152 * 8, 256, 0, s>>>(list, nlist, mval);
     note_launch();

@@ -118,6 +118,8 @@ struct pl_graph {
   pl::Buf gsc;            // float [3 * N] GiFt scales (1/sqrt(D+sigma))
   pl::Buf status;         // int32 [8]
   pl::Buf stage;          // staging words of batched device-to-host reads
+  pl::Buf star_w;         // double [kMaxNetPins + 1] star edge weights p / (p - 1)
+  bool star_w_ok = false;
   pl::Scratch scr;
   pl::Buf tmp[8];
   pl::Buf lay[4];         // layout scratch (scans of row lengths, chunk counts)
