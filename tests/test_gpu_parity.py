@@ -243,6 +243,31 @@ def test_hpwl_big_nets_and_empty():
     assert h.item() == pytest.approx(oracle.hpwl(nl, xy[:, 0], xy[:, 1]), rel=1e-6)
 
 
+def test_hpwl_net_size_classes():
+    # nets at every boundary of the kernel's classes (a lane up to 32 pins, a
+    # warp up to 1024, a block beyond), the largest allowed net, spread over
+    # the blocks' net ranges among many small nets
+    rng = np.random.default_rng(7)
+    cells = 40000
+    sizes = rng.integers(0, 6, 3000)
+    for pos, n in [(5, 32), (6, 33), (700, 1024), (701, 1025), (1500, 4097), (2200, 32768),
+                   (2999, 2000), (0, 1500)]:
+        sizes[pos] = n
+    ptr = np.r_[0, np.cumsum(sizes)].astype(np.int64)
+    pins = np.concatenate([rng.choice(cells, n, replace=False) for n in sizes]).astype(np.int32)
+    dx = rng.uniform(-0.4, 0.4, len(pins)).astype(np.float32)
+    dy = rng.uniform(-0.4, 0.4, len(pins)).astype(np.float32)
+    nl = netgen.Netlist(ptr, pins, dx, dy, np.ones(cells, np.float32), np.ones(cells, np.float32),
+                        np.zeros(cells, np.uint8), np.zeros(cells, np.float32),
+                        np.zeros(cells, np.float32), (0.0, 0.0, 1000.0, 1000.0))
+    xy = rng.uniform(0, 1000, (cells, 2)).astype(np.float32)
+    h = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.tensor(xy.reshape(-1), device="cuda")
+    pl().pl_hpwl(pl().DeviceNetlist(nl), t, h, pl().hpwl_workspace(len(sizes)))
+    ref = oracle.hpwl(nl, xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64))
+    assert h.item() == pytest.approx(ref, rel=1e-6)
+
+
 # ------------------------------------------------------------ failures
 def test_errors_are_reported():
     m = pl()
