@@ -119,7 +119,7 @@ static void destroy(pl_graph *g) {
                  &g->net_p, &g->star_of, &g->star_net, &g->macro_cell, &g->cell_macro, &g->srp,
                  &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
                  &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
-                 &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur,
+                 &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem,
                  &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->clen, &g->lflag,
                  &g->crank, &g->tpos, &g->mac_base,
                  &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,

@@ -133,12 +133,19 @@ __device__ __forceinline__ float store_bits2(void *wbuf, uint64_t k, uint64_t k2
   return bf16_to_f(h);
 }
 
+// Cells are taken in tiles of kBinTile consecutive ids by the stable counting
+// sorts (bin buckets, macro lists).
+constexpr int kBinTile = 4096;
+constexpr int kMaxSmemBuckets = 12288;
+constexpr int kMacroSlots = 8;        // macros one cell may overlap in the tiled macro lists
+constexpr int kMaxSmemMacros = 12288;  // macros of the tiled macro lists (runs and masks in smem)
+
 // --------------------------------------------------------- H1: cells
 __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
                              const uint8_t *hflag, const float *cw, const float *ch,
                              const int64_t *gptr, const uint32_t *glist, const float4 *ggeo,
                              int32_t *cell_bin, int32_t *n_ovl, int32_t *bcnt, int32_t *mcnt,
-                             int *status) {
+                             int32_t *mtc, int ntile, int32_t *cmem, int *status) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
     if (ckind[i] != 0) {
       cell_bin[i] = -1;
@@ -163,10 +170,17 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
       for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
         const float4 mg = ggeo[q];
         if (overlaps(p.x, p.y, cwi, chi, mg.x, mg.y, mg.z, mg.w)) {
+          const uint32_t m = glist[q];
+          if (mtc) {
+            atomicAdd(&mtc[(long long)m * ntile + i / kBinTile], 1);
+            if (n < kMacroSlots) cmem[(long long)i * kMacroSlots + n] = (int32_t)m;
+          } else {
+            atomicAdd(&mcnt[m], 1);
+          }
           ++n;
-          atomicAdd(&mcnt[glist[q]], 1);
         }
       }
+      if (mtc && n > kMacroSlots) flag(status, ST_MANY_OVL);
     }
     n_ovl[i] = n;
   }
@@ -193,11 +207,67 @@ __global__ void k_macro_scatter(HintGeo G, const float2 *xy, const uint8_t *ckin
   }
 }
 
+// Macro lists in ascending cell id without a sort: a CTA per tile of kBinTile
+// cells, counts per (macro, tile) macro-major and each cell's macros (at most
+// kMacroSlots) from k_hint_cells.  In rounds of blockDim cells the warps take
+// turns; inside a turn the lanes mark their macros in a per-macro lane mask,
+// and a membership's place is its macro's tile start (loaded before the
+// turns), the macro's run so far and the number of lower lanes marked.
+__global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int32_t *n_ovl,
+                                                            const int32_t *cmem, int Mm,
+                                                            int ntile, const int64_t *off,
+                                                            uint32_t *mlist) {
+  extern __shared__ int32_t run[];  // [Mm] runs, then [Mm] lane masks
+  uint32_t *lmask = reinterpret_cast<uint32_t *>(run + Mm);
+  for (int k = threadIdx.x; k < Mm; k += blockDim.x) {
+    run[k] = 0;
+    lmask[k] = 0u;
+  }
+  __syncthreads();
+  const int t = blockIdx.x, i0 = t * kBinTile, i1 = min(C, i0 + kBinTile);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = i0; base < i1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    // n_ovl is 0 for cells other than movable hint cells
+    const int n = i < i1 ? min(n_ovl[i], kMacroSlots) : 0;
+    int32_t mk[kMacroSlots];
+    long long tst[kMacroSlots];
+#pragma unroll
+    for (int j = 0; j < kMacroSlots; ++j) {
+      mk[j] = j < n ? cmem[(long long)i * kMacroSlots + j] : 0;
+      tst[j] = j < n ? off[(long long)mk[j] * ntile + t] : 0;
+    }
+    for (int w = 0; w < nw; ++w) {
+      if (wid == w) {
+#pragma unroll
+        for (int j = 0; j < kMacroSlots; ++j)
+          if (j < n) atomicOr(&lmask[mk[j]], 1u << lane);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kMacroSlots; ++j)
+          if (j < n) mlist[tst[j] + run[mk[j]] + __popc(lmask[mk[j]] & lt)] = (uint32_t)i;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kMacroSlots; ++j) {
+          if (j < n) {
+            const uint32_t msk = lmask[mk[j]];
+            if (msk && lane == __ffs(msk) - 1) {
+              run[mk[j]] += __popc(msk);
+              lmask[mk[j]] = 0u;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Bin buckets: key 2*bin + (baseWeight == 0).  A stable counting sort over
 // tiles of kBinTile consecutive cells writes every bucket in ascending cell id
 // directly (no sort).  Counts per (bucket, tile), bucket-major.
-constexpr int kBinTile = 4096;
-constexpr int kMaxSmemBuckets = 12288;
 
 __device__ __forceinline__ int bucket_of(const uint8_t *hflag, const int32_t *cell_bin, int i) {
   return 2 * cell_bin[i] + (hflag[i] ? 0 : 1);
@@ -236,6 +306,7 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
     const int i = base + threadIdx.x;
     const bool mv = i < i1 && ckind[i] == 0;
     const int key = mv ? bucket_of(hflag, cell_bin, i) : -1 - lane;
+    const long long tst = mv ? off[(long long)key * ntile + t] : 0;  // loaded before the turns
     for (int w = 0; w < nw; ++w) {
       if (wid == w) {
         unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -247,7 +318,7 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
         }
         before = __shfl_sync(0xffffffffu, before, leader);
         if (mv) {
-          const long long pos = off[(long long)key * ntile + t] + before + __popc(grp & lt);
+          const long long pos = tst + before + __popc(grp & lt);
           blist[pos] = (uint32_t)i;
           // a hint cell's place in the bucket list (its rank once the
           // bucket's start is taken off)
@@ -1060,21 +1131,42 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->bcnt, (size_t)(nbk + 1) * 4));
   TRY(ensure(g->mcnt, (size_t)(Mm + 1) * 4));
   if (!tiled) TRY(cudaMemsetAsync(g->bcnt.p, 0, (size_t)(nbk + 1) * 4, s));
-  TRY(cudaMemsetAsync(g->mcnt.p, 0, (size_t)(Mm + 1) * 4, s));
+  const int ntile = (int)((C + kBinTile - 1) / kBinTile) > 0 ? (int)((C + kBinTile - 1) / kBinTile) : 1;
+  // macro lists by a tiled counting sort when the macros' run counters fit
+  // shared memory (else: scatter by atomics, then a segmented sort)
+  const bool tiledm = Mm > 0 && Mm <= kMaxSmemMacros;
+  const long long nmt = (long long)Mm * ntile;
+  if (tiledm) {
+    TRY(ensure(g->mtc, (size_t)nmt * 4 + 16));
+    TRY(ensure(g->cmem, (size_t)C * kMacroSlots * 4 + 16));
+    TRY(cudaMemsetAsync(g->mtc.p, 0, (size_t)nmt * 4, s));
+  } else {
+    TRY(cudaMemsetAsync(g->mcnt.p, 0, (size_t)(Mm + 1) * 4, s));
+  }
   k_hint_cells<<<grid_for(C, 256), 256, 0, s>>>(
       G, xy, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<float>(g->cw), P<float>(g->ch),
       P<int64_t>(g->gptr), P<uint32_t>(g->glist), P<float4>(g->ggeo), P<int32_t>(g->cell_bin),
-      P<int32_t>(g->n_ovl), tiled ? nullptr : P<int32_t>(g->bcnt), P<int32_t>(g->mcnt), status);
+      P<int32_t>(g->n_ovl), tiled ? nullptr : P<int32_t>(g->bcnt), P<int32_t>(g->mcnt),
+      tiledm ? P<int32_t>(g->mtc) : nullptr, ntile, tiledm ? P<int32_t>(g->cmem) : nullptr,
+      status);
   note_launch();
   // H2: bucket offsets
   TRY(ensure(g->boff, (size_t)(nbk + 1) * 8));
   TRY(ensure(g->moff, (size_t)(Mm + 1) * 8));
-  TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->mcnt), P<int64_t>(g->moff), Mm, stmp, s)));
+  if (tiledm) {
+    TRY(ensure(g->mtoff, (size_t)(nmt + 1) * 8 + 256));
+    TRY(ensure(g->tmp[7], scan_tmp_bytes(nmt + 1) + 4096));
+    stmp = g->tmp[7].p;
+    TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->mtc), P<int64_t>(g->mtoff), nmt, stmp, s)));
+    k_bucket_starts<<<grid_for(Mm + 1, 256), 256, 0, s>>>(Mm, ntile, P<int64_t>(g->mtoff),
+                                                         P<int64_t>(g->moff));
+    note_launch();
+  } else {
+    TRY((exclusive_scan<int32_t, int64_t>(P<int32_t>(g->mcnt), P<int64_t>(g->moff), Mm, stmp, s)));
+  }
   int32_t *cm = nullptr;
   int64_t *cmo = nullptr;
-  int ntile = 1;
   if (tiled) {
-    ntile = (int)((C + kBinTile - 1) / kBinTile) > 0 ? (int)((C + kBinTile - 1) / kBinTile) : 1;
     const long long ncm = (long long)nbk * ntile;
     TRY(ensure(g->tmp[5], (size_t)ncm * 4 + 256));
     TRY(ensure(g->tmp[6], (size_t)(ncm + 1) * 8 + 256));
@@ -1126,7 +1218,19 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->blist), P<int64_t>(g->boff), nbk,
                                              nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
   }
-  if (Mm) {
+  if (tiledm && !(hst[0] & ST_MANY_OVL)) {
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kMaxSmemMacros * 8);
+      attr_done = true;
+    }
+    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 8, s>>>(C, P<int32_t>(g->n_ovl),
+                                                           P<int32_t>(g->cmem), Mm, ntile,
+                                                           P<int64_t>(g->mtoff),
+                                                           P<uint32_t>(g->mlist));
+    note_launch();
+  } else if (Mm) {
     TRY(ensure(g->mcur, (size_t)(Mm + 1) * 4));
     k_u64_to_u32<<<grid_for(Mm, 256), 256, 0, s>>>(P<uint64_t>(g->moff), P<uint32_t>(g->mcur), Mm);
     note_launch();

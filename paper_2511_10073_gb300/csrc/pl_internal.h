@@ -98,6 +98,8 @@ struct pl_graph {
   pl::Buf n_ovl;       // int32 [C]
   pl::Buf bcnt, boff, blist, bcur;  // bucket sort of movable cells by (bin, hint)
   pl::Buf mcnt, moff, mlist, mcur;  // cells overlapping each macro
+  pl::Buf mtc, mtoff;  // per (macro, cell tile) counts and their scan (tiled macro lists)
+  pl::Buf cmem;        // int32 [C * 8] each hint cell's macros (tiled macro lists)
   pl::Buf Db, phi;     // double [NB]
   pl::Buf hlen;        // int64 [N] augmented row length
   pl::Buf slen;        // uint32 [N] short-region length (0 for hub rows)
