@@ -227,17 +227,28 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
   const int t = blockIdx.x, i0 = t * kBinTile, i1 = min(C, i0 + kBinTile);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  // a round's cell memberships are loaded during the round before
+  int nn = i0 + (int)threadIdx.x < i1 ? min(n_ovl[i0 + threadIdx.x], kMacroSlots) : 0;
+  int32_t mn[kMacroSlots];
+#pragma unroll
+  for (int j = 0; j < kMacroSlots; ++j)
+    mn[j] = j < nn ? cmem[(long long)(i0 + threadIdx.x) * kMacroSlots + j] : 0;
   for (int base = i0; base < i1; base += blockDim.x) {
     const int i = base + threadIdx.x;
     // n_ovl is 0 for cells other than movable hint cells
-    const int n = i < i1 ? min(n_ovl[i], kMacroSlots) : 0;
+    const int n = nn;
     int32_t mk[kMacroSlots];
     long long tst[kMacroSlots];
 #pragma unroll
     for (int j = 0; j < kMacroSlots; ++j) {
-      mk[j] = j < n ? cmem[(long long)i * kMacroSlots + j] : 0;
+      mk[j] = mn[j];
       tst[j] = j < n ? off[(long long)mk[j] * ntile + t] : 0;
     }
+    const int inext = i + (int)blockDim.x;
+    nn = inext < i1 ? min(n_ovl[inext], kMacroSlots) : 0;
+#pragma unroll
+    for (int j = 0; j < kMacroSlots; ++j)
+      mn[j] = j < nn ? cmem[(long long)inext * kMacroSlots + j] : 0;
     for (int w = 0; w < nw; ++w) {
       if (wid == w) {
 #pragma unroll
@@ -637,8 +648,8 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     const int32_t *n_ovl, const float2 *xy, const float *cw, const float *ch,
     const int64_t *gptr, const uint32_t *glist, const float4 *ggeo, const double *base_w,
     const float *phif, const double *phid, const uint64_t *tpos, int W, const int32_t *crank,
-    const int64_t *boff, int32_t *col, void *w, dfl *dsum, dfl *psum, uint64_t *mac_base,
-    uint64_t *bin_base) {
+    const int64_t *boff, const int32_t *cmem, const float4 *mgeo, int32_t *col, void *w,
+    dfl *dsum, dfl *psum, uint64_t *mac_base, uint64_t *bin_base) {
   const bool bf = wdtype == PL_W_BF16;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.Nst;
        v += (long long)gridDim.x * blockDim.x) {
@@ -651,31 +662,42 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       const double bw = base_w[v];
       const float bwf = __double2float_rn(bw);
       // macro entries, ascending macro id (grid bucket lists are sorted)
-      const int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
-      const long long gk = (long long)ky * G.gnx + kx;
       uint64_t k = mb;
-      const float cwv = cw[v], chv = ch[v];
-      const long long qa = gptr[gk], qb = gptr[gk + 1];
-      for (long long q0 = qa; q0 < qb; q0 += 4) {
-        float4 mgs[4];  // four grid entries' geometry loaded at once
+      auto mac_entry = [&](int m, float4 mg) {
+        const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
+        const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
+        const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
+        col[k] = (int32_t)(G.mv0 + m);
+        if (bf && near_bf16_tie(wv))
+          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
+                                                                 mg.w, bw))));
+        else
+          acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+        ++k;
+      };
+      if (cmem) {
+        // the cell's macros as the cell pass found them (same geometry values)
+        const int n = n_ovl[v];
+        for (int j = 0; j < n; ++j) {
+          const int m = cmem[(long long)v * kMacroSlots + j];
+          mac_entry(m, mgeo[m]);
+        }
+      } else {
+        const int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
+        const long long gk = (long long)ky * G.gnx + kx;
+        const float cwv = cw[v], chv = ch[v];
+        const long long qa = gptr[gk], qb = gptr[gk + 1];
+        for (long long q0 = qa; q0 < qb; q0 += 4) {
+          float4 mgs[4];  // four grid entries' geometry loaded at once
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mgs[u] = q0 + u < qb ? ggeo[q0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int u = 0; u < 4; ++u) mgs[u] = q0 + u < qb ? ggeo[q0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const long long q = q0 + u;
-          const float4 mg = mgs[u];
-          if (q >= qb || !overlaps(p.x, p.y, cwv, chv, mg.x, mg.y, mg.z, mg.w)) continue;
-          const int m = (int)glist[q];
-          const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
-          const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
-          const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
-          col[k] = (int32_t)(G.mv0 + m);
-          if (bf && near_bf16_tie(wv))
-            acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
-                                                                   mg.w, bw))));
-          else
-            acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
-          ++k;
+          for (int u = 0; u < 4; ++u) {
+            const long long q = q0 + u;
+            const float4 mg = mgs[u];
+            if (q >= qb || !overlaps(p.x, p.y, cwv, chv, mg.x, mg.y, mg.z, mg.w)) continue;
+            mac_entry((int)glist[q], mg);
+          }
         }
       }
       const uint64_t bb0 = mb + n_ovl[v];
@@ -1218,7 +1240,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->blist), P<int64_t>(g->boff), nbk,
                                              nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
   }
-  if (tiledm && !(hst[0] & ST_MANY_OVL)) {
+  const bool cmem_ok = tiledm && !(hst[0] & ST_MANY_OVL);  // every hint cell's macros recorded
+  if (cmem_ok) {
     static bool attr_done = false;
     if (!attr_done) {
       cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1313,7 +1336,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
       P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<int64_t>(g->gptr),
       P<uint32_t>(g->glist), P<float4>(g->ggeo), P<double>(g->base_w), phif, P<double>(g->phi),
-      tpos, W, tiled ? P<int32_t>(g->crank) : nullptr, P<int64_t>(g->boff), P<int32_t>(m.col),
+      tpos, W, tiled ? P<int32_t>(g->crank) : nullptr, P<int64_t>(g->boff),
+      cmem_ok ? P<int32_t>(g->cmem) : nullptr, P<float4>(g->mgeo), P<int32_t>(m.col),
       m.w.p, P<dfl>(m.dsum),
       P<dfl>(m.psum), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
   note_launch();
