@@ -109,7 +109,8 @@ void pl_params_default(pl_params *p);
  * With xy_nodes (device, N pairs) it also builds the area-hint graph for that
  * placement (as pl_build_hints).  Synchronizes `stream`.
  * Errors: INVALID_ARG (netlist or params), UNSUPPORTED (a net with more than
- * 32768 pins, a graph row beyond 2^31 entries), OOM, CUDA, NONFINITE. */
+ * 32768 pins, 2^28 or more static nodes (cells, macro pins and stars), a graph
+ * row beyond 2^31 entries), OOM, CUDA, NONFINITE. */
 pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *xy_nodes,
                          pl_stream stream, pl_graph **g);
 

@@ -309,11 +309,22 @@ cudaError_t exclusive_scan(const Tin *in, Tout *out, long long n, void *tmp, cud
 //   MODE_SORT   : sort only (keys unique or order of equal keys irrelevant)
 //   MODE_UNIQUE : sort, then move the distinct keys to the segment start and
 //                 write their count to cnt[s]
-//   MODE_MERGE  : keys are (col << 32 | uint32 value); sort, then for each
-//                 distinct col write (col, sum of values as int64; a negative
-//                 value is kept as is) to mcol/mval at the segment start and
-//                 the count to cnt[s]
+//   MODE_MERGE  : keys are (col << 32 | uint32 value) (64-bit keys) or
+//                 (col << 4 | code) (32-bit keys, values decoded by the merge
+//                 context below); sort, then for each distinct col write
+//                 (col, sum of values as int64; a negative value is kept as
+//                 is) to mcol/mval at the segment start and the count to cnt[s]
 enum { MODE_SORT = 0, MODE_UNIQUE = 1, MODE_MERGE = 2 };
+// Value of a 32-bit merge key's code in segment (row) s: code c >= 1 is a
+// clique pair of weight 1/c in lattice units (lattice / c); code 0 is a star
+// edge, value -p for the star's net of p nodes, the star node being the row
+// when the row is one, else the column.
+struct MergeCtx {
+  long long lattice, star0;
+  int32_t nstar;
+  const int32_t *star_net, *net_p;
+};
+cudaError_t set_merge_ctx(const MergeCtx &c, cudaStream_t s);
 size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes);
 template <typename K, int MODE>
 cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long long nkeys,

@@ -182,14 +182,16 @@ __global__ void k_row_count(const int64_t *ptr, const uint32_t *nd, const int32_
 
 constexpr int kScatterRegs = 8;  // clique nets up to this size kept in registers
 
-// Unmerged entries as (col << 32 | value): value = 360360/(p-1) for a clique
-// pair, -p for a star edge.  Star rows are written in node order directly.
+// Unmerged entries as 32-bit keys (col << 4 | code): code p - 1 (1..15) for a
+// clique pair of a p-node net (value 360360/(p-1) in lattice units), code 0
+// for a star edge (value -p, p taken from the star node when merging).  Star
+// rows are written in node order directly.
 // A thread takes a clique net (each node reserves its p - 1 slots with one
 // atomic, all of a small net's reservations in flight at once); star nets are
 // taken by the whole warp in turn.
 __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
                           const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
-                          const int64_t *row_off, unsigned long long *cursor, uint64_t *keys) {
+                          const int64_t *row_off, unsigned long long *cursor, uint32_t *keys) {
   const int lane = threadIdx.x & 31;
   for (long long e0 = (blockIdx.x * (long long)blockDim.x) + (threadIdx.x & ~31); e0 < M;
        e0 += (long long)gridDim.x * blockDim.x) {
@@ -201,7 +203,7 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
       b = ptr[e];
     }
     if (p >= 2 && p <= cmax) {
-      const uint32_t lat = (uint32_t)(kLattice / (p - 1));
+      const uint32_t lat = (uint32_t)(p - 1);  // code
       if (p <= kScatterRegs) {
         uint32_t node[kScatterRegs];
         unsigned long long slot[kScatterRegs];
@@ -218,7 +220,7 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
 #pragma unroll
           for (int c = 0; c < kScatterRegs; ++c) {
             if (c >= p) break;
-            if (c != a) keys[k++] = ((uint64_t)node[c] << 32) | lat;
+            if (c != a) keys[k++] = (node[c] << 4) | lat;
           }
         }
       } else {
@@ -227,7 +229,7 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
           unsigned long long k = atomicAdd(&cursor[ra], (unsigned long long)(p - 1));
           for (int c = 0; c < p; ++c) {
             if (c == a) continue;
-            keys[k++] = ((uint64_t)nd[b + c] << 32) | lat;
+            keys[k++] = (nd[b + c] << 4) | lat;
           }
         }
       }
@@ -240,13 +242,12 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
       const int pp = __shfl_sync(0xffffffffu, p, src);
       const long long bb = __shfl_sync(0xffffffffu, b, src);
       const long long st = star0 + star_of[ee];
-      const uint32_t code = (uint32_t)(-pp);
       const long long so = row_off[st];
       for (int k = lane; k < pp; k += 32) {
         const uint32_t v = nd[bb + k];
         const unsigned long long slot = atomicAdd(&cursor[v], 1ull);
-        keys[slot] = ((uint64_t)(uint32_t)st << 32) | code;
-        keys[so + k] = ((uint64_t)v << 32) | code;
+        keys[slot] = (uint32_t)st << 4;
+        keys[so + k] = v << 4;
       }
     }
   }
@@ -794,10 +795,15 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   int64_t npre;
   TRY(d2h(&npre, row_off + Nst, 1, s));
 
-  // scatter, sort, merge
-  TRY(ensure(g->tmp[6], (size_t)npre * 8 + (size_t)(Nst + 1) * 8 + 512));
-  uint64_t *keys = P<uint64_t>(g->tmp[6]);
-  unsigned long long *cursor = reinterpret_cast<unsigned long long *>(keys + npre + 1);
+  // scatter, sort, merge (32-bit keys: node ids below 2^28)
+  if (Nst >= (1LL << 28)) {
+    set_error("too many static nodes (%lld) for the expansion's 28-bit columns", (long long)Nst);
+    return PL_ERR_UNSUPPORTED;
+  }
+  const size_t kbytes = ((size_t)(npre + 4) * 4 + 15) & ~size_t(15);
+  TRY(ensure(g->tmp[6], kbytes + (size_t)(Nst + 1) * 8 + 512));
+  uint32_t *keys = P<uint32_t>(g->tmp[6]);
+  unsigned long long *cursor = reinterpret_cast<unsigned long long *>(P<char>(g->tmp[6]) + kbytes);
   TRY(cudaMemcpyAsync(cursor, row_off, (size_t)Nst * 8, cudaMemcpyDeviceToDevice, s));
   k_scatter<<<grid_for((long long)M, 256), 256, 0, s>>>(
       P<int64_t>(g->net_ptr), P<uint32_t>(g->nd), P<int32_t>(g->net_p), P<int32_t>(g->star_of),
@@ -806,8 +812,17 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->tmp[1], (size_t)npre * 12 + 512));  // merged col (int32) + value (int64)
   int64_t *mval = P<int64_t>(g->tmp[1]);
   int32_t *mcol = reinterpret_cast<int32_t *>(mval + npre + 1);
-  TRY(ensure(g->tmp[3], segsort_tmp_bytes(Nst, npre, 8)));
-  TRY((segmented_sort<uint64_t, MODE_MERGE>(keys, row_off, Nst, npre, cnt, mcol, mval,
+  TRY(ensure(g->tmp[3], segsort_tmp_bytes(Nst, npre, 4)));
+  {
+    MergeCtx mc;
+    mc.lattice = kLattice;
+    mc.star0 = star0;
+    mc.nstar = g->S;
+    mc.star_net = P<int32_t>(g->star_net);
+    mc.net_p = P<int32_t>(g->net_p);
+    TRY(set_merge_ctx(mc, s));
+  }
+  TRY((segmented_sort<uint32_t, MODE_MERGE>(keys, row_off, Nst, npre, cnt, mcol, mval,
                                             g->tmp[3].p, s)));
   TRY(ensure(g->srp, (size_t)(Nst + 1) * 8));
   TRY((exclusive_scan<int32_t, int64_t>(cnt, P<int64_t>(g->srp), Nst, stmp, s)));
@@ -840,7 +855,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
       return PL_ERR_UNSUPPORTED;
     }
     unsigned long long *nlist = reinterpret_cast<unsigned long long *>(keys);
-    uint32_t *list = reinterpret_cast<uint32_t *>(keys + 2);
+    uint32_t *list = keys + 4;
     TRY(cudaMemsetAsync(nlist, 0, 8, s));
     k_static_weights<<<grid_for(Nst * 32, 256), 256, 0, s>>>(row_off, mval, P<int64_t>(g->srp),
                                                             Nst, P<double>(g->star_w), list,

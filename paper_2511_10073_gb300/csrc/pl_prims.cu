@@ -175,9 +175,30 @@ constexpr int SEG_CAP = 4096;  // keys sorted in shared memory at once
 
 template <typename K>
 __device__ __forceinline__ K key_max() { return ~K(0); }
-// Column half of a (col << 32 | value) key; 32-bit keys have none.
+// Merge keys: (col << 32 | value) for 64-bit keys, (col << 4 | code) for
+// 32-bit keys with the value decoded from the merge context.
+__constant__ MergeCtx c_merge;
+static MergeCtx h_merge;  // source of the asynchronous copy (kept alive)
+
+cudaError_t set_merge_ctx(const MergeCtx &c, cudaStream_t s) {
+  h_merge = c;
+  return cudaMemcpyToSymbolAsync(c_merge, &h_merge, sizeof(MergeCtx), 0, cudaMemcpyHostToDevice, s);
+}
+
 template <typename K>
-__device__ __forceinline__ int32_t key_col(K k) { return (int32_t)((uint64_t)k >> 32); }
+__device__ __forceinline__ int32_t key_col(K k) {
+  if (sizeof(K) == 8) return (int32_t)((uint64_t)k >> 32);
+  return (int32_t)((uint32_t)k >> 4);
+}
+template <typename K>
+__device__ __forceinline__ long long key_val(K k, long long s) {
+  if (sizeof(K) == 8) return (long long)(int32_t)(uint32_t)((uint64_t)k & 0xffffffffu);
+  const uint32_t code = (uint32_t)k & 15u;
+  if (code) return c_merge.lattice / code;
+  const long long col = (long long)((uint32_t)k >> 4);
+  const long long st = (s >= c_merge.star0 && s < c_merge.star0 + c_merge.nstar) ? s : col;
+  return -(long long)c_merge.net_p[c_merge.star_net[st - c_merge.star0]];
+}
 
 // Segments are sorted by size class: up to 8, 16 and 32 keys by groups of 8,
 // 16 or 32 lanes (several segments per warp); up to 64..512 keys by one warp
@@ -205,7 +226,7 @@ __device__ __forceinline__ void write_single(K key, long long o, int32_t *cnt, l
                                              int32_t *mcol, int64_t *mval) {
   if (MODE == MODE_MERGE) {
     mcol[o] = key_col<K>(key);
-    mval[o] = (int64_t)(int32_t)(uint32_t)((uint64_t)key & 0xffffffffu);
+    mval[o] = key_val<K>(key, s);
   }
   if (MODE != MODE_SORT) cnt[s] = 1;
 }
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(256) k_seg_group(K *keys, const int64_t *off, 
     }
     // MODE_MERGE: sum the values of equal columns
     const int32_t col = key_col<K>(key);
-    long long val = (long long)(int32_t)(uint32_t)((uint64_t)key & 0xffffffffu);
+    long long val = sub < n ? key_val<K>(key, s) : 0;
     const int32_t pcol = __shfl_up_sync(0xffffffffu, col, 1);
     const bool head = sub < n && (sub == 0 || pcol != col);
     const unsigned hm = __ballot_sync(0xffffffffu, head) & gmask;
@@ -392,8 +413,7 @@ __global__ void __launch_bounds__(256) k_seg_regs(K *keys, const int64_t *off, i
         if (!(e == 0 || key_col<K>(a[e]) != key_col<K>(a[e - 1]))) continue;
         const int32_t col = key_col<K>(a[e]);
         long long v = 0;
-        for (int q = e; q < n && key_col<K>(a[q]) == col; ++q)
-          v += (long long)(int32_t)(uint32_t)((uint64_t)a[q] & 0xffffffffu);
+        for (int q = e; q < n && key_col<K>(a[q]) == col; ++q) v += key_val<K>(a[q], s);
         mcol[o + w] = col;
         mval[o + w] = v;
       } else {
@@ -441,8 +461,7 @@ __device__ void cta_compact(K *a, long long n, long long o, long long s, int32_t
       if (MODE == MODE_MERGE) {
         int32_t col = key_col<K>(a[q]);
         long long v = 0;
-        for (long long r = q; r < n && key_col<K>(a[r]) == col; ++r)
-          v += (long long)(int32_t)(uint32_t)((uint64_t)a[r] & 0xffffffffu);
+        for (long long r = q; r < n && key_col<K>(a[r]) == col; ++r) v += key_val<K>(a[r], s);
         mcol[o + w] = col;
         mval[o + w] = v;
       } else {
@@ -699,5 +718,6 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
 template cudaError_t segmented_sort<uint32_t, MODE_SORT>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
 template cudaError_t segmented_sort<uint32_t, MODE_UNIQUE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
 template cudaError_t segmented_sort<uint64_t, MODE_MERGE>(uint64_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
+template cudaError_t segmented_sort<uint32_t, MODE_MERGE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
 
 }  // namespace pl
