@@ -267,7 +267,8 @@ __device__ __forceinline__ bool lattice_easy(long long val, const double *star_w
     return true;
   }
   if (val >= kLattice / 15 && val <= kLattice) {
-    const int d = (int)((float)kLattice / (float)val + 0.5f);
+    // 32-bit conversions (a 64-bit integer conversion would take the FP64 pipe)
+    const int d = (int)((float)kLattice / (float)(int)val + 0.5f);
     if (d >= 1 && d <= 15 && (long long)d * val == kLattice) {
       *w = c_recip[d];
       return true;

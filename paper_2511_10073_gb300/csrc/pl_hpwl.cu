@@ -3,12 +3,12 @@
 // offset.  A thread takes a net of up to 32 pins (a warp stages the pins of 32
 // consecutive nets when they fit), a warp a net of up to 1024; each block then
 // spans the larger nets of its own range of nets, one at a time with all its
-// threads.  Pin positions
-// and extrema are FP32 (min/max are exact), each net's span is formed and
-// summed in FP64.  Per-block FP64 sums go to the caller's workspace; the last
-// block to finish (ticket) adds them in a fixed order (strided over its
-// threads, then a fixed tree), so the result does not depend on scheduling.
-// A pin whose cell index is out of range makes the result NaN (it is not
+// threads.  Pin positions and extrema are FP32 (min/max are exact); each net's
+// span is formed exactly and summed in double-float per thread, the threads'
+// sums in FP64.  Per-block sums go to the caller's workspace; the last block
+// to finish (ticket) adds them in a fixed order (strided over its threads,
+// then a fixed tree), so the result does not depend on scheduling.  A pin
+// whose cell index is out of range makes the result NaN (it is not
 // dereferenced).
 #include <mutex>
 
@@ -37,6 +37,16 @@ __device__ __forceinline__ float2 pin_pos(const float2 *xy, const int32_t *pin_c
   return c;
 }
 
+// A net's span (x1 - x0) + (y1 - y0) added to a double-float sum: each
+// difference is exact as a TwoSum pair (FP32 arithmetic only).
+__device__ __forceinline__ void span_add(dfl &acc, float x0, float x1, float y0, float y1) {
+  dfl dx{x1, 0.f}, dy{y1, 0.f};
+  df_add(dx, -x0);
+  df_add(dy, -y0);
+  df_add_df(acc, dx);
+  df_add_df(acc, dy);
+}
+
 __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
                                                        const int32_t *pin_cell, const float *dx,
                                                        const float *dy, const float2 *xy,
@@ -50,7 +60,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
   __shared__ float4 mm[kHpwlThreads / 32];
   float2 *stg = stage_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double acc = 0.0;
+  dfl acc{0.f, 0.f};
   // each warp takes batches of 32 consecutive nets (warp-uniform loop): a
   // staged batch spans every net in it from shared memory; otherwise a lane
   // spans each net of at most 32 pins and the warp each one of at most
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
             x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
             y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
           }
-          acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+          span_add(acc, x0, x1, y0, y1);
         }
       }
       __syncwarp();
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
           x0 = fminf(x0, p.x); x1 = fmaxf(x1, p.x);
           y0 = fminf(y0, p.y); y1 = fmaxf(y1, p.y);
         }
-        acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+        span_add(acc, x0, x1, y0, y1);
       }
       mid = n > 32 && n <= kHpwlWarpMax;
     }
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
         y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, m));
         y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, m));
       }
-      if (lane == src) acc += ((double)x1 - (double)x0) + ((double)y1 - (double)y0);
+      if (lane == src) span_add(acc, x0, x1, y0, y1);
     }
   }
   // nets of more than kHpwlWarpMax pins in this block's range of nets, in
@@ -177,8 +187,8 @@ __global__ void __launch_bounds__(kHpwlThreads) k_hpwl(const int64_t *net_ptr,
       __syncthreads();
     }
   }
-  acc = warp_sum(acc);
-  if (lane == 0) red[wid] = acc;
+  const double accd = warp_sum(df_to_d(df_norm(acc)));
+  if (lane == 0) red[wid] = accd;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
