@@ -642,6 +642,7 @@ __device__ __forceinline__ dfl df_ratio(float x, float c, float h) {
 // = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u (double-float, once
 // per cell) as exact double-float differences; macro ratios are double-float
 // quotients.  FP64 only recomputes weights near a bf16 rounding midpoint.
+constexpr int kAsmStage = 768;  // own entries of a warp's 32 rows staged in shared memory
 __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     HintGeo G, int wdtype, const uint32_t *hrp, const int32_t *longidx, const uint64_t *lptr,
     const dfl *sdsum, const dfl *spsum, const uint8_t *hflag, const int32_t *cell_bin,
@@ -650,13 +651,38 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     const float *phif, const double *phid, const uint64_t *tpos, int W, const int32_t *crank,
     const int64_t *boff, const int32_t *cmem, const float4 *mgeo, int32_t *col, void *w,
     dfl *dsum, dfl *psum, uint64_t *mac_base, uint64_t *bin_base) {
+  __shared__ int32_t stage_col[8][kAsmStage];
+  __shared__ uint32_t stage_w[8][kAsmStage];
   const bool bf = wdtype == PL_W_BF16;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.Nst;
-       v += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  int32_t *scol = stage_col[threadIdx.x >> 5];
+  uint32_t *sw = stage_w[threadIdx.x >> 5];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); v0 < G.Nst;
+       v0 += stride) {
+    const long long v = v0 + lane;
+    // the warp's rows own a contiguous short-region range [rb, re)
+    const uint64_t rb = hrp[v0] & kOffMask;
+    const uint64_t re = hrp[v0 + 32 < G.Nst ? v0 + 32 : G.Nst] & kOffMask;
+    const bool staged = re - rb <= (uint64_t)kAsmStage;  // warp-uniform
+    if (v >= G.Nst) goto flush;
+    {
     dfl Dl = sdsum[v], Pl = spsum[v];
     if (v < G.C && hflag[v]) {
       const int li = longidx[v];
       const uint64_t mb = li >= 0 ? lptr[li] : (uint64_t)(hrp[v] & kOffMask);
+      const bool use_s = staged && li < 0;
+      // an own entry: to the warp's stage (short rows) or straight to memory
+      auto put = [&](uint64_t kk, int32_t c, uint32_t bits) {
+        if (use_s) {
+          scol[kk - rb] = c;
+          sw[kk - rb] = bits;
+        } else {
+          col[kk] = c;
+          if (bf) reinterpret_cast<uint16_t *>(w)[kk] = (uint16_t)bits;
+          else reinterpret_cast<uint32_t *>(w)[kk] = bits;
+        }
+      };
       float2 p = xy[v];
       if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
       const double bw = base_w[v];
@@ -667,12 +693,20 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
         const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
         const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
         const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
-        col[k] = (int32_t)(G.mv0 + m);
-        if (bf && near_bf16_tie(wv))
-          acc_deg(Dl, Pl, store_bits(w, k, d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z,
-                                                                 mg.w, bw))));
-        else
-          acc_deg(Dl, Pl, store_w(w, wdtype, k, wv));
+        uint32_t bits;
+        float sv;
+        if (bf) {
+          const uint16_t h = near_bf16_tie(wv)
+                                 ? d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z, mg.w, bw))
+                                 : f2bf16(wv);
+          bits = h;
+          sv = bf16_to_f(h);
+        } else {
+          bits = __float_as_uint(wv);
+          sv = wv;
+        }
+        put(k, (int32_t)(G.mv0 + m), bits);
+        acc_deg(Dl, Pl, sv);
         ++k;
       };
       if (cmem) {
@@ -736,15 +770,28 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
             const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
             const int bb = yy * G.nbx + xx;
             const float wv = -((e * ph[u]) * bwf);
-            col[k] = (int32_t)(G.bn0 + bb);
+            uint32_t bits;
+            float sv;
+            if (bf) {
+              const uint16_t h = near_bf16_tie(wv)
+                                     ? d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))
+                                     : f2bf16(wv);
+              bits = h;
+              sv = bf16_to_f(h);
+            } else {
+              bits = __float_as_uint(wv);
+              sv = wv;
+            }
+            put(k, (int32_t)(G.bn0 + bb), bits);
             // the same entry in the row of bin bb: this cell's bucket run
             // inside bb's window, at the cell's rank
             const uint64_t k2 = tp[u];
-            if (k2 != ~0ull) col[k2] = (int32_t)v;
-            if (bf && near_bf16_tie(wv))
-              acc_deg(Dl, Pl, store_bits2(w, k, k2, d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))));
-            else
-              acc_deg(Dl, Pl, store_w2(w, wdtype, k, k2, wv));
+            if (k2 != ~0ull) {
+              col[k2] = (int32_t)v;
+              if (bf) reinterpret_cast<uint16_t *>(w)[k2] = (uint16_t)bits;
+              else reinterpret_cast<uint32_t *>(w)[k2] = bits;
+            }
+            acc_deg(Dl, Pl, sv);
             ++k;
           }
         }
@@ -754,6 +801,18 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     }
     dsum[v] = df_norm(Dl);
     psum[v] = df_norm(Pl);
+    }
+  flush:
+    // the staged range, written with coalesced stores
+    if (staged) {
+      __syncwarp();
+      for (uint64_t i = lane; i < re - rb; i += 32) {
+        col[rb + i] = scol[i];
+        if (bf) reinterpret_cast<uint16_t *>(w)[rb + i] = (uint16_t)sw[i];
+        else reinterpret_cast<uint32_t *>(w)[rb + i] = sw[i];
+      }
+      __syncwarp();
+    }
   }
 }
 
