@@ -136,6 +136,36 @@ def test_hints_crossfed(cfg, seed, kw):
     assert frac > 0.5  # most weights bit-identical
 
 
+def test_hints_stacked_macros():
+    # ten macros on one site: the cells on it overlap all ten, more than the
+    # cell pass records per cell, so the round falls back to an atomic
+    # scatter and a segmented sort of the macro lists
+    nl = netgen.make_netlist("tiny", 5)
+    kind = np.asarray(nl.cell_kind)
+    cw, ch = np.asarray(nl.cell_w), np.asarray(nl.cell_h)
+    macros = np.flatnonzero(kind == netgen.KIND_MACRO)
+    m = int(macros[np.argmax(cw[macros] * ch[macros])])
+    rep = lambda a: np.r_[np.asarray(a), np.repeat(np.asarray(a)[m], 9)].astype(np.asarray(a).dtype)
+    nl2 = netgen.Netlist(nl.net_ptr, nl.pin_cell, nl.pin_dx, nl.pin_dy, rep(nl.cell_w), rep(nl.cell_h),
+                         rep(nl.cell_kind), rep(nl.fixed_x), rep(nl.fixed_y), nl.region)
+    s = Side(nl2, **cfg_params("tiny"))
+    _, xy = s.gpu_signal(5)
+    # put a block of cells on the stacked site
+    a = to_np(xy)
+    movable = np.flatnonzero(kind == netgen.KIND_MOVABLE)[:200]
+    rng = np.random.default_rng(5)
+    fx, fy = float(np.asarray(nl.fixed_x)[m]), float(np.asarray(nl.fixed_y)[m])
+    a[movable, 0] = fx + rng.uniform(-0.4, 0.4, len(movable)) * cw[m]
+    a[movable, 1] = fy + rng.uniform(-0.4, 0.4, len(movable)) * ch[m]
+    t = torch.tensor(a.astype(np.float32).reshape(-1), device="cuda")
+    pl().pl_build_hints(s.g, s.prm, t)
+    ge = s.g.export()
+    b = to_np(t)
+    s.o.build_hints(b[:, 0], b[:, 1])
+    oe = s.o.merged()
+    _compare_hints(s, ge, oe)
+
+
 # ------------------------------------------------------------ A0 / A4
 @pytest.mark.parametrize("cfg,seed,kw", [
     ("micro", 2, {}), ("small", 1, {}), ("tiny", 1, {}), ("tiny", 2, dict(wdtype=2)),
