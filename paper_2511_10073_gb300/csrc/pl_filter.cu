@@ -126,6 +126,41 @@ __device__ __forceinline__ void epilogue_k(const StepArgs &A, int64_t v, uint8_t
   }
 }
 
+// The same epilogue for one coordinate c (0: x, 1: y) of node v, so that the
+// two lanes of a row share its FP64 work.
+__device__ __forceinline__ void epilogue_c(const StepArgs &A, int64_t v, uint8_t kd, int c,
+                                           double acv, float yv) {
+  const float *fixc = reinterpret_cast<const float *>(A.fixedp) + 2 * v + c;
+  if (A.pin && kd == 2) yv = *fixc;
+  if (!A.fin) reinterpret_cast<float *>(A.y)[2 * v + c] = yv;
+  double t = 0.0;
+  if (A.tap) {
+    double sc = A.tscale ? (double)A.tscale[v] : 1.0;
+    acv += A.alpha * ((double)yv * sc);
+    reinterpret_cast<double *>(A.acc)[2 * v + c] = acv;
+    t = acv;
+  }
+  if (A.fin) {
+    double gv = A.single ? (double)yv : t;
+    gv += c ? A.cy : A.cx;
+    float o;
+    if (kd == 2) {
+      o = *fixc;
+    } else {
+      if (A.relax) {
+        const float g = reinterpret_cast<const float *>(A.g0)[2 * v + c];
+        gv = (1.0 - A.gamma) * (double)g + A.gamma * gv;
+      }
+      o = __double2float_rn(gv);
+      if (A.clamp) {
+        const float4 bd = A.bounds[v];
+        o = c ? fminf(fmaxf(o, bd.y), bd.w) : fminf(fmaxf(o, bd.x), bd.z);
+      }
+    }
+    reinterpret_cast<float *>(A.gnext)[2 * v + c] = o;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T yy) {
   epilogue_k<T>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0), yx, yy);
@@ -209,7 +244,8 @@ __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
 // m + kRowLanes, ...; kRowUnroll index and weight loads in flight, then their
 // gathers of x), a butterfly over the group sums them, and the group's first
 // lane applies the epilogue.  Hub rows are skipped (their own launches).
-constexpr int kRowLanes = 2;
+constexpr int kRowLanes = 2;  // the epilogue takes one coordinate per lane
+static_assert(kRowLanes == 2, "the row epilogue splits x and y over the row's two lanes");
 constexpr int kRowUnroll = 8;
 constexpr int kRowThreads = 256;
 
@@ -271,12 +307,13 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
       sx += __shfl_xor_sync(0xffffffffu, sx, d);
       sy += __shfl_xor_sync(0xffffffffu, sy, d);
     }
-    if (live && m == 0) {
+    if (live) {
+      // lane m of the pair finishes coordinate m
       const float av = A.a[v];
       const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
-      const float2 xr = A.x[v];
-      epilogue_k<float>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0),
-                        av * xr.x + bv * sx, av * xr.y + bv * sy);
+      const float xr = reinterpret_cast<const float *>(A.x)[2 * v + m];
+      const double acv = A.tap ? reinterpret_cast<const double *>(A.acc)[2 * v + m] : 0.0;
+      epilogue_c(A, v, A.nkind[v], m, acv, av * xr + bv * (m ? sy : sx));
     }
   }
 }
@@ -572,7 +609,15 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
   for (int q = 0; q < nch; ++q)
     if (kmax[q] > 0) last_chain = q;
   bool any = false;
-  for (int q = 0; q < nch; ++q) {
+  // chains without steps first: their bands (k = 0) only add to the sum,
+  // which the final step of the last chain with steps reads
+  int order[3], no = 0;
+  for (int q = 0; q < nch; ++q)
+    if (kmax[q] == 0) order[no++] = q;
+  for (int q = 0; q < nch; ++q)
+    if (kmax[q] > 0) order[no++] = q;
+  for (int oi = 0; oi < nch; ++oi) {
+    const int q = order[oi];
     k_gift_prep<<<grid_for(N, 256), 256, 0, s>>>(N, g->Nst, P<double>(g->sdeg), sig[q], gin, cx,
                                                  cy, ga, gb, gq, P<float2>(g->ua));
     note_launch();

@@ -170,6 +170,8 @@ def test_hints_stacked_macros():
 @pytest.mark.parametrize("cfg,seed,kw", [
     ("micro", 2, {}), ("small", 1, {}), ("tiny", 1, {}), ("tiny", 2, dict(wdtype=2)),
     ("tiny", 3, dict(gift_center=1, gift_k=(3, 1, 0), gift_sigma=(1.5, 3.0, 3.0))),
+    # a sigma whose only band has k = 0, after the chain with steps
+    ("tiny", 4, dict(gift_center=1, gift_k=(3, 1, 0), gift_sigma=(1.5, 1.5, 3.0))),
     ("medium", 1, {})])
 def test_init_and_gift_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
