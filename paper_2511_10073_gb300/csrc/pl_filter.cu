@@ -61,7 +61,8 @@ struct StepArgs {
   const float *tscale;   // GIFT: band value = u * tscale (sqrt(d_v)); nullptr: 1
   // epilogue
   int pin, tap, fin, relax, clamp;
-  double alpha, gamma, cx, cy;
+  double alpha, gamma, omg, cx, cy;  // omg = 1 - gamma
+  int addc;                          // cx or cy is not zero
   int single;            // final value is y itself (one tap, alpha 1)
   double2 *acc;
   const float2 *g0;
@@ -133,23 +134,26 @@ __device__ __forceinline__ void epilogue_c(const StepArgs &A, int64_t v, uint8_t
   const float *fixc = reinterpret_cast<const float *>(A.fixedp) + 2 * v + c;
   if (A.pin && kd == 2) yv = *fixc;
   if (!A.fin) reinterpret_cast<float *>(A.y)[2 * v + c] = yv;
+  // (FP64 is slow: no product by a unit scale, no sum with a zero centre,
+  // 1 - gamma from the host, no store of the last tap sum)
   double t = 0.0;
   if (A.tap) {
-    double sc = A.tscale ? (double)A.tscale[v] : 1.0;
-    acv += A.alpha * ((double)yv * sc);
-    reinterpret_cast<double *>(A.acc)[2 * v + c] = acv;
+    double pv = (double)yv;
+    if (A.tscale) pv *= (double)A.tscale[v];
+    acv += A.alpha * pv;
+    if (!A.fin) reinterpret_cast<double *>(A.acc)[2 * v + c] = acv;
     t = acv;
   }
   if (A.fin) {
     double gv = A.single ? (double)yv : t;
-    gv += c ? A.cy : A.cx;
+    if (A.addc) gv += c ? A.cy : A.cx;
     float o;
     if (kd == 2) {
       o = *fixc;
     } else {
       if (A.relax) {
         const float g = reinterpret_cast<const float *>(A.g0)[2 * v + c];
-        gv = (1.0 - A.gamma) * (double)g + A.gamma * gv;
+        gv = A.omg * (double)g + A.gamma * gv;
       }
       o = __double2float_rn(gv);
       if (A.clamp) {
@@ -642,6 +646,7 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
       A.fin = (q == last_chain && t == kmax[q]) ? 1 : 0;
       A.cx = A.fin ? cx : 0.0;
       A.cy = A.fin ? cy : 0.0;
+      A.addc = (A.cx != 0.0 || A.cy != 0.0) ? 1 : 0;
       A.pin = 0;
       TRY(launch_step<MODE_GIFT>(A, bytes, g->wdtype, s));
       any = true;
@@ -697,6 +702,7 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   A.g0 = gin;
   A.gnext = gout;
   A.gamma = p->gamma;
+  A.omg = 1.0 - p->gamma;
   A.relax = 1;
   A.clamp = p->clamp;
   A.single = single ? 1 : 0;
