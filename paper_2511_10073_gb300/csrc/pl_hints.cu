@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
                                                             const int32_t *cmem, int Mm,
                                                             int ntile, const int64_t *off,
                                                             uint32_t *mlist) {
-  extern __shared__ int32_t run[];  // [Mm] runs, then [Mm] lane masks
-  uint32_t *lmask = reinterpret_cast<uint32_t *>(run + Mm);
+  extern __shared__ uint32_t lmask[];  // [Mm] lane masks, then [Mm] runs (at most kBinTile)
+  uint16_t *run = reinterpret_cast<uint16_t *>(lmask + Mm);
   for (int k = threadIdx.x; k < Mm; k += blockDim.x) {
     run[k] = 0;
     lmask[k] = 0u;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
           if (j < n) {
             const uint32_t msk = lmask[mk[j]];
             if (msk && lane == __ffs(msk) - 1) {
-              run[mk[j]] += __popc(msk);
+              run[mk[j]] = (uint16_t)(run[mk[j]] + __popc(msk));
               lmask[mk[j]] = 0u;
             }
           }
@@ -1304,10 +1304,10 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     static bool attr_done = false;
     if (!attr_done) {
       cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kMaxSmemMacros * 8);
+                           kMaxSmemMacros * 6);
       attr_done = true;
     }
-    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 8, s>>>(C, P<int32_t>(g->n_ovl),
+    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s>>>(C, P<int32_t>(g->n_ovl),
                                                            P<int32_t>(g->cmem), Mm, ntile,
                                                            P<int64_t>(g->mtoff),
                                                            P<uint32_t>(g->mlist));
