@@ -115,6 +115,12 @@ static pl_status same_layout(const pl_graph *g, const pl_params *p) {
 
 static void destroy(pl_graph *g) {
   if (!g) return;
+  if (g->side) {  // the side stream's work ends before its buffers go
+    cudaStreamSynchronize(g->side);
+    cudaStreamDestroy(g->side);
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
   Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
                  &g->net_p, &g->star_of, &g->star_net, &g->macro_cell, &g->cell_macro, &g->srp,
                  &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(256) k_dens_level(int NB, int L, const int64_t
 __global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uint32_t *blist,
                              const float *cw, const float *ch, LevelBufs lv, const double *amac,
                              double abin, double cap, double mu, double *Db, double *Cb,
-                             double *phi, float *phif, int64_t *hub_len) {
+                             double *phi, float *phif) {
   const int NB = G.nbx * G.nby;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
     int L = 0;
@@ -458,6 +458,13 @@ __global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uin
     Cb[b] = c;
     phi[b] = ph;
     phif[b] = __double2float_rn(ph);
+  }
+}
+
+// Length of each bin row: the hint buckets of the bin's window.
+__global__ void k_bin_hub_len(HintGeo G, const int64_t *boff, int64_t *hub_len) {
+  const int NB = G.nbx * G.nby;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
     const int bx = b % G.nbx, by = b / G.nbx;
     long long hl = 0;
     for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
@@ -1300,19 +1307,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
                                              nbl, nullptr, nullptr, nullptr, g->tmp[3].p, s)));
   }
   const bool cmem_ok = tiledm && !(hst[0] & ST_MANY_OVL);  // every hint cell's macros recorded
-  if (cmem_ok) {
-    static bool attr_done = false;
-    if (!attr_done) {
-      cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kMaxSmemMacros * 6);
-      attr_done = true;
-    }
-    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s>>>(C, P<int32_t>(g->n_ovl),
-                                                           P<int32_t>(g->cmem), Mm, ntile,
-                                                           P<int64_t>(g->mtoff),
-                                                           P<uint32_t>(g->mlist));
-    note_launch();
-  } else if (Mm) {
+  if (!cmem_ok && Mm) {
     TRY(ensure(g->mcur, (size_t)(Mm + 1) * 4));
     k_u64_to_u32<<<grid_for(Mm, 256), 256, 0, s>>>(P<uint64_t>(g->moff), P<uint32_t>(g->mcur), Mm);
     note_launch();
@@ -1325,13 +1320,37 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->mlist), P<int64_t>(g->moff), Mm, nml,
                                              nullptr, nullptr, nullptr, g->tmp[3].p, s)));
   }
-  // H5: densities, phi, hub lengths
+  // H5: densities and phi, and the tiled macro lists, on the side stream
+  // while the row lengths and the layout go on (joined before the assembly)
+  if (!g->side) {
+    TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+    TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+  }
+  cudaStream_t s2 = g->side;
   TRY(ensure(g->Db, (size_t)NB * 8 + 16));
   TRY(ensure(g->phi, (size_t)NB * 8 + 16));
   const size_t phib = ((size_t)NB * 4 + 255) & ~size_t(255);
   TRY(ensure(g->tmp[4], phib + (size_t)NB * 8 + 256));
   float *phif = P<float>(g->tmp[4]);
   int64_t *hub_len = reinterpret_cast<int64_t *>(P<char>(g->tmp[4]) + phib);
+  k_bin_hub_len<<<grid_for(NB, 128), 128, 0, s>>>(G, P<int64_t>(g->boff), hub_len);
+  note_launch();
+  TRY(cudaEventRecord(g->ev_fork, s));
+  TRY(cudaStreamWaitEvent(s2, g->ev_fork, 0));
+  if (cmem_ok) {
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kMaxSmemMacros * 6);
+      attr_done = true;
+    }
+    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s2>>>(C, P<int32_t>(g->n_ovl),
+                                                            P<int32_t>(g->cmem), Mm, ntile,
+                                                            P<int64_t>(g->mtoff),
+                                                            P<uint32_t>(g->mlist));
+    note_launch();
+  }
   LevelBufs lv;
   int nlev = 0;  // launches: level L exists while 64^(L+1) < the longest bin
   {
@@ -1354,17 +1373,18 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       span *= 64.0;
     }
     for (int L = 0; L < nlev; ++L) {
-      k_dens_level<<<grid_for((long long)sizes[L], 256, 152 * 16), 256, 0, s>>>(
+      k_dens_level<<<grid_for((long long)sizes[L], 256, 152 * 16), 256, 0, s2>>>(
           NB, L, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch),
           L ? lv.base[L - 1] : nullptr, lv.base[L], (long long)sizes[L]);
       note_launch();
     }
   }
-  k_dens_final<<<grid_for(NB, 128), 128, 0, s>>>(
+  k_dens_final<<<grid_for(NB, 128), 128, 0, s2>>>(
       G, nlev, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch), lv,
       P<double>(g->amac), g->abin, p->capacity, p->mu, P<double>(g->Db), P<double>(g->Cb),
-      P<double>(g->phi), phif, hub_len);
+      P<double>(g->phi), phif);
   note_launch();
+  TRY(cudaEventRecord(g->ev_join, s2));
   // H6-H7: row lengths and layout
   pl_status st = ensure_row_arrays(g);
   if (st != PL_OK) return st;
@@ -1390,6 +1410,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
                                                  P<uint64_t>(m.lptr), tpos);
     note_launch();
   }
+  TRY(cudaStreamWaitEvent(s, g->ev_join, 0));  // phi and the macro lists
   k_assemble_hints<<<grid_for(g->Nst, 256), 256, 0, s>>>(
       G, g->wdtype, P<uint32_t>(m.rp_s), P<int32_t>(m.longidx), P<uint64_t>(m.lptr),
       P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),

@@ -121,6 +121,8 @@ struct pl_graph {
   pl::Buf status;         // int32 [8]
   pl::Buf stage;          // staging words of batched device-to-host reads
   pl::Buf star_w;         // double [kMaxNetPins + 1] star edge weights p / (p - 1)
+  cudaStream_t side = nullptr;  // the hint build's second stream (forked from and joined
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // back to the caller's stream)
   bool star_w_ok = false;
   pl::Scratch scr;
   pl::Buf tmp[8];
