@@ -849,6 +849,9 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     TRY(cudaStreamSynchronize(s));  // rc lives on this stack frame
     g->star_w_ok = true;
   }
+  TRY(ensure_side(g));
+  TRY(cudaEventRecord(g->ev_fork, s));
+  TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
   {
     // keys are consumed by the merge: their buffer holds the division list
     if ((unsigned long long)npre >= (1ull << 32)) {
@@ -878,6 +881,9 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY(cudaGetLastError());
 
+  // node tables and the macro lookup grid, on the side stream (forked before
+  // the weights) while the weights and the compaction run
+  cudaStream_t s2 = g->side;
   // node tables
   const int64_t N = g->N;
   g->wb = (g->xh - g->xl) / (double)g->nbx;
@@ -891,14 +897,14 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->nkind, (size_t)N + 16));
   TRY(ensure(g->fixedp, (size_t)N * 8 + 16));
   TRY(ensure(g->bounds, (size_t)N * 16 + 16));
-  k_nodes<<<grid_for(N, 256), 256, 0, s>>>(N, C, g->Pm, S, g->Mm, g->nbx, P<uint8_t>(g->ckind),
+  k_nodes<<<grid_for(N, 256), 256, 0, s2>>>(N, C, g->Pm, S, g->Mm, g->nbx, P<uint8_t>(g->ckind),
                                            P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
                                            P<float>(g->cfy), P<int32_t>(g->macro_cell), g->xl,
                                            g->yl, g->xh, g->yh, g->wb, g->hb, P<uint8_t>(g->nkind),
                                            P<float2>(g->fixedp), P<float4>(g->bounds));
   note_launch();
   if (NP) {
-    k_pin_fixed<<<grid_for(NP, 256), 256, 0, s>>>(P<int32_t>(g->pin_node), nl->pin_cell, nl->pin_dx,
+    k_pin_fixed<<<grid_for(NP, 256), 256, 0, s2>>>(P<int32_t>(g->pin_node), nl->pin_cell, nl->pin_dx,
                                                  nl->pin_dy, P<float>(g->cfx), P<float>(g->cfy), NP,
                                                  C, P<float2>(g->fixedp));
     note_launch();
@@ -907,13 +913,13 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->Cb, (size_t)g->NB * 8 + 16));
   TRY(ensure(g->mgeo, (size_t)g->Mm * 16 + 16));
   if (g->Mm) {
-    k_macro_geo<<<grid_for(g->Mm, 256), 256, 0, s>>>(g->Mm, P<int32_t>(g->macro_cell),
+    k_macro_geo<<<grid_for(g->Mm, 256), 256, 0, s2>>>(g->Mm, P<int32_t>(g->macro_cell),
                                                      P<float>(g->cfx), P<float>(g->cfy),
                                                      P<float>(g->cw), P<float>(g->ch),
                                                      P<float4>(g->mgeo));
     note_launch();
   }
-  k_bin_macro_area<<<grid_for((long long)g->NB * 32, 256), 256, 0, s>>>(
+  k_bin_macro_area<<<grid_for((long long)g->NB * 32, 256), 256, 0, s2>>>(
       g->NB, g->nbx, g->Mm, P<float4>(g->mgeo), g->xl, g->yl, g->wb, g->hb, P<double>(g->amac));
   note_launch();
 
@@ -931,16 +937,16 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->gptr, (size_t)(ng + 1) * 8 + 16));
   TRY(ensure(g->tmp[4], (size_t)(ng + 1) * 4 + 256));
   int32_t *gcnt = P<int32_t>(g->tmp[4]);
-  TRY(cudaMemsetAsync(gcnt, 0, (size_t)(ng + 1) * 4, s));
-  k_grid_count<<<grid_for(g->Mm, 128), 128, 0, s>>>(
+  TRY(cudaMemsetAsync(gcnt, 0, (size_t)(ng + 1) * 4, s2));
+  k_grid_count<<<grid_for(g->Mm, 128), 128, 0, s2>>>(
       g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
       P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, mgx, mgy, g->gnx, g->gny, gcnt);
   note_launch();
   int64_t *gptr = P<int64_t>(g->gptr);
   TRY(scan_tmp(g, ng, &stmp));
-  TRY((exclusive_scan<int32_t, int64_t>(gcnt, gptr, ng, stmp, s)));
+  TRY((exclusive_scan<int32_t, int64_t>(gcnt, gptr, ng, stmp, s2)));
   int64_t nreg;
-  TRY(d2h(&nreg, gptr + ng, 1, s));
+  TRY(d2h(&nreg, gptr + ng, 1, s2));
   TRY(ensure(g->glist, (size_t)nreg * 4 + 16));
   if (nreg >= (1LL << 31)) {
     set_error("macro lookup grid too large");
@@ -948,19 +954,19 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY(ensure(g->tmp[2], (size_t)(ng + 1) * 4 + 256));
   int32_t *gcur = P<int32_t>(g->tmp[2]);
-  k_i64_to_i32<<<grid_for(ng, 256), 256, 0, s>>>(gptr, gcur, ng);
+  k_i64_to_i32<<<grid_for(ng, 256), 256, 0, s2>>>(gptr, gcur, ng);
   note_launch();
-  k_grid_fill<<<grid_for(g->Mm, 128), 128, 0, s>>>(
+  k_grid_fill<<<grid_for(g->Mm, 128), 128, 0, s2>>>(
       g->Mm, P<int32_t>(g->macro_cell), P<float>(g->cw), P<float>(g->ch), P<float>(g->cfx),
       P<float>(g->cfy), wmax, hmax, g->xl, g->yl, sx, sy, mgx, mgy, g->gnx, g->gny, gcur,
       P<uint32_t>(g->glist));
   note_launch();
   TRY(ensure(g->tmp[3], segsort_tmp_bytes(ng, nreg, 4)));
   TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->glist), gptr, ng, nreg, nullptr,
-                                           nullptr, nullptr, g->tmp[3].p, s)));
+                                           nullptr, nullptr, g->tmp[3].p, s2)));
   TRY(ensure(g->ggeo, (size_t)nreg * 16 + 16));
   if (nreg) {
-    k_grid_geo<<<grid_for(nreg, 256), 256, 0, s>>>(nreg, P<uint32_t>(g->glist),
+    k_grid_geo<<<grid_for(nreg, 256), 256, 0, s2>>>(nreg, P<uint32_t>(g->glist),
                                                    P<int32_t>(g->macro_cell), P<float>(g->cfx),
                                                    P<float>(g->cfy), P<float>(g->cw),
                                                    P<float>(g->ch), P<float4>(g->ggeo));
@@ -969,6 +975,8 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   g->gsz = gs;
   g->gsx = sx;
   g->gsy = sy;
+  TRY(cudaEventRecord(g->ev_join, s2));
+  TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
   TRY(cudaGetLastError());
   TRY(cudaStreamSynchronize(s));
   (void)kMaxNetPins;

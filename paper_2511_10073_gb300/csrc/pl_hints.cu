@@ -1322,11 +1322,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   }
   // H5: densities and phi, and the tiled macro lists, on the side stream
   // while the row lengths and the layout go on (joined before the assembly)
-  if (!g->side) {
-    TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
-    TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
-    TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
-  }
+  TRY(ensure_side(g));
   cudaStream_t s2 = g->side;
   TRY(ensure(g->Db, (size_t)NB * 8 + 16));
   TRY(ensure(g->phi, (size_t)NB * 8 + 16));

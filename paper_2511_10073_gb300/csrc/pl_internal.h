@@ -144,3 +144,14 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
 pl_status read_status(pl_graph *g, cudaStream_t s);
 
 }  // namespace pl
+
+namespace pl {
+// The graph's second stream and its fork/join events, created on first use.
+inline cudaError_t ensure_side(pl_graph *g) {
+  if (g->side) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
+  return e;
+}
+}  // namespace pl
