@@ -326,9 +326,13 @@ struct MergeCtx {
 };
 cudaError_t set_merge_ctx(const MergeCtx &c, cudaStream_t s);
 size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes);
+// maxlen: a bound on the longest segment when the caller knows one (< 0:
+// nkeys), which bounds the merge passes of segments beyond shared memory.
 template <typename K, int MODE>
 cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long long nkeys,
                            int32_t *cnt, int32_t *mcol, int64_t *mval, void *tmp,
-                           cudaStream_t s);
+                           cudaStream_t s, long long maxlen = -1);
+// Largest of n int32 values, combined into *out with atomicMax (*out >= 0).
+cudaError_t max_i32(const int32_t *a, long long n, int *out, cudaStream_t s);
 
 }  // namespace pl

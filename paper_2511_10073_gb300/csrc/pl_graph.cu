@@ -95,6 +95,12 @@ __global__ void k_validate_nets(const int64_t *ptr, int32_t M, int64_t P, int *s
       if (d < 0) flag(status, ST_BAD_NET);
       if (d > kMaxNetPins) flag(status, ST_TOO_BIG);
     }
+    // the largest net beyond 1024 pins (status[13], else 0) bounds the merge
+    // passes of the net sort
+    if (e < M) {
+      const long long d = ptr[e + 1] - ptr[e];
+      if (d > 1024) atomicMax(&status[13], (int)min(d, (long long)INT32_MAX));
+    }
   }
 }
 
@@ -715,6 +721,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     return PL_ERR_UNSUPPORTED;
   }
   g->nmov = hst[12];
+  const int maxnet = hst[13];  // 0: no net above 1024 pins
   float wmax, hmax, mwmax, mhmax;
   memcpy(&wmax, &hst[8], 4);
   memcpy(&hmax, &hst[9], 4);
@@ -759,7 +766,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(ensure(g->tmp[3], segsort_tmp_bytes(M, NP, 4)));
   TRY((segmented_sort<uint32_t, MODE_UNIQUE>(P<uint32_t>(g->nd), P<int64_t>(g->net_ptr), M, NP,
                                              P<int32_t>(g->net_p), nullptr, nullptr,
-                                             g->tmp[3].p, s)));
+                                             g->tmp[3].p, s, maxnet > 0 ? maxnet : 1024)));
   // star nodes
   TRY(ensure(g->star_of, (size_t)(M + 1) * 4));
   k_star_flag<<<grid_for(M, 256), 256, 0, s>>>(P<int32_t>(g->net_p), M, p->clique_max, pflag);
@@ -793,8 +800,16 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   int64_t *row_off = P<int64_t>(g->tmp[5]);
   TRY(scan_tmp(g, Nst, &stmp));
   TRY((exclusive_scan<int32_t, int64_t>(cnt, row_off, Nst, stmp, s)));
+  // the longest unmerged row bounds the merge passes of the row sort
+  int *rowmax = P<int>(g->status) + 14;
+  TRY(cudaMemsetAsync(rowmax, 0, 4, s));
+  TRY(max_i32(cnt, Nst, rowmax, s));
   int64_t npre;
-  TRY(d2h(&npre, row_off + Nst, 1, s));
+  int32_t maxrow = 0;
+  {
+    const D2H it[2] = {{&npre, row_off + Nst, 8}, {&maxrow, rowmax, 4}};
+    TRY(d2h_many(g->stage, it, 2, s));
+  }
 
   // scatter, sort, merge (32-bit keys: node ids below 2^28)
   if (Nst >= (1LL << 28)) {
@@ -824,7 +839,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     TRY(set_merge_ctx(mc, s));
   }
   TRY((segmented_sort<uint32_t, MODE_MERGE>(keys, row_off, Nst, npre, cnt, mcol, mval,
-                                            g->tmp[3].p, s)));
+                                            g->tmp[3].p, s, maxrow)));
   TRY(ensure(g->srp, (size_t)(Nst + 1) * 8));
   TRY((exclusive_scan<int32_t, int64_t>(cnt, P<int64_t>(g->srp), Nst, stmp, s)));
   int64_t nnz;

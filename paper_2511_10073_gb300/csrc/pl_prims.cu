@@ -648,10 +648,26 @@ size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes) {
          (size_t)nkeys * key_bytes + 512;
 }
 
+__global__ void k_max_i32(const int32_t *a, long long n, int *out) {
+  int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = max(m, a[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+cudaError_t max_i32(const int32_t *a, long long n, int *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_max_i32<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(a, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename K, int MODE>
 cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long long nkeys,
                            int32_t *cnt, int32_t *mcol, int64_t *mval, void *tmp,
-                           cudaStream_t s) {
+                           cudaStream_t s, long long maxlen) {
   if (nseg <= 0) return cudaSuccess;
   char *t = static_cast<char *>(tmp);
   SegLists *lists = reinterpret_cast<SegLists *>(t);
@@ -683,7 +699,7 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   }
   k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, cl + 7 * nseg, lists);
   note_launch();
-  if (nkeys > SEG_CAP) {
+  if (nkeys > SEG_CAP && (maxlen < 0 || maxlen > SEG_CAP)) {
     // The unit prefix overwrites the lists of the small classes (consumed by
     // the launches above): (nbig + 1) 8-byte entries fit below the list of
     // class 8 at byte 32 * nseg, since nbig <= nseg.
@@ -694,9 +710,10 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
     note_launch();
     note_launch();
     // passes while R < the longest segment (a pass past it returns at once);
-    // nkeys bounds that length
+    // maxlen, else nkeys, bounds that length
+    const long long bound = maxlen >= 0 && maxlen < nkeys ? maxlen : nkeys;
     int npass = 0;
-    for (long long R = SEG_CAP; R < nkeys; R <<= 1) {
+    for (long long R = SEG_CAP; R < bound; R <<= 1) {
       k_big_merge<K><<<152 * 4, SEG_T, 0, s>>>(npass & 1 ? scratch : keys, npass & 1 ? keys : scratch,
                                                big, lists, bpre, off, R);
       note_launch();
@@ -715,9 +732,9 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   return cudaGetLastError();
 }
 
-template cudaError_t segmented_sort<uint32_t, MODE_SORT>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
-template cudaError_t segmented_sort<uint32_t, MODE_UNIQUE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
-template cudaError_t segmented_sort<uint64_t, MODE_MERGE>(uint64_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
-template cudaError_t segmented_sort<uint32_t, MODE_MERGE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t);
+template cudaError_t segmented_sort<uint32_t, MODE_SORT>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t, long long);
+template cudaError_t segmented_sort<uint32_t, MODE_UNIQUE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t, long long);
+template cudaError_t segmented_sort<uint64_t, MODE_MERGE>(uint64_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t, long long);
+template cudaError_t segmented_sort<uint32_t, MODE_MERGE>(uint32_t *, const int64_t *, long long, long long, int32_t *, int32_t *, int64_t *, void *, cudaStream_t, long long);
 
 }  // namespace pl
