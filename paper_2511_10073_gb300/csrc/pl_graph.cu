@@ -394,10 +394,33 @@ __device__ __forceinline__ void fix_add_double(Fix128 &a, double w) {
   a.hi += hi + (t < a.lo ? 1ull : 0ull);
   a.lo = t;
 }
+// RN(x) * 2^e for x > 0 with a normal result, in integer arithmetic (the
+// conversion and scaling instructions of FP64 would take the slow FP64 pipe):
+// round the top 53 bits to nearest, ties to even, and assemble the bits.
+__device__ __forceinline__ double u64_rn_scaled(unsigned long long x, int e) {
+  int nb = 64 - __clzll((long long)x);
+  unsigned long long m;
+  if (nb <= 53) {
+    m = x << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    m = x >> sh;
+    const unsigned long long rem = x & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++nb;
+    }
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(nb - 1 + e + 1023) << 52) | (m & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
 // The fixed-point value rounded once to the nearest double (ties to even):
 // the top 64 bits with a sticky bit, then one correctly rounded conversion.
 __device__ __forceinline__ double fix_to_double(const Fix128 &a) {
-  if (a.hi == 0) return ldexp(__ull2double_rn(a.lo), -67);
+  if (a.hi == 0) return a.lo ? u64_rn_scaled(a.lo, -67) : 0.0;
   const int sh = 64 - __clzll((long long)a.hi);  // bits of hi, 1..64
   unsigned long long top, rest;
   if (sh == 64) {
@@ -408,7 +431,7 @@ __device__ __forceinline__ double fix_to_double(const Fix128 &a) {
     rest = a.lo & ((1ull << sh) - 1ull);
   }
   if (rest) top |= 1ull;
-  return ldexp(__ull2double_rn(top), sh - 67);
+  return u64_rn_scaled(top, sh - 67);
 }
 
 // Final static matrix, written straight into its split layout, from the FP64
@@ -450,7 +473,7 @@ __global__ void __launch_bounds__(256) k_static_compact(
     if (cell) {
       const double bw = m > 0 ? __ddiv_rn(fix_to_double(fl), (double)m) : 0.0;
       base_w[v] = bw;
-      hflag[v] = (ckind[v] == 0 && bw > 0.0) ? 1 : 0;
+      hflag[v] = (ckind[v] == 0 && __double_as_longlong(bw) > 0) ? 1 : 0;  // bw > 0 (integer test)
     }
   }
 }
