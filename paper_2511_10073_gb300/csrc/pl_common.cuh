@@ -322,7 +322,8 @@ enum { MODE_SORT = 0, MODE_UNIQUE = 1, MODE_MERGE = 2 };
 struct MergeCtx {
   long long lattice, star0;
   int32_t nstar;
-  const int32_t *star_net, *net_p;
+  int32_t latq[16];  // lattice / c for c = 1..15 (no integer division per key)
+  const int32_t *star_p;  // node count of each star's net
 };
 cudaError_t set_merge_ctx(const MergeCtx &c, cudaStream_t s);
 size_t segsort_tmp_bytes(long long nseg, long long nkeys, int key_bytes);

@@ -143,6 +143,12 @@ __global__ void k_star_flag(const int32_t *net_p, int32_t M, int32_t cmax, uint8
     f[e] = net_p[e] > cmax;
 }
 
+__global__ void k_star_p(int32_t S, const int32_t *star_net, const int32_t *net_p,
+                         int32_t *star_p) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < S; q += gridDim.x * blockDim.x)
+    star_p[q] = net_p[star_net[q]];
+}
+
 __global__ void k_star_list(const uint8_t *f, const int32_t *scan, int32_t M, int32_t *star_net) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x)
     if (f[e]) star_net[scan[e]] = e;
@@ -803,6 +809,12 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   k_star_list<<<grid_for(M, 256), 256, 0, s>>>(pflag, P<int32_t>(g->star_of), M,
                                                P<int32_t>(g->star_net));
   note_launch();
+  TRY(ensure(g->star_p, (size_t)S * 4 + 16));
+  if (S) {
+    k_star_p<<<grid_for(S, 256), 256, 0, s>>>(S, P<int32_t>(g->star_net), P<int32_t>(g->net_p),
+                                             P<int32_t>(g->star_p));
+    note_launch();
+  }
   g->Nst = (int64_t)C + g->Pm + S;
   g->N = g->Nst + g->Mm + g->NB;
   if (g->N >= (1LL << 31) - 1) {
@@ -855,10 +867,11 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   {
     MergeCtx mc;
     mc.lattice = kLattice;
+    mc.latq[0] = 0;
+    for (int c = 1; c < 16; ++c) mc.latq[c] = (int32_t)(kLattice / c);
     mc.star0 = star0;
     mc.nstar = g->S;
-    mc.star_net = P<int32_t>(g->star_net);
-    mc.net_p = P<int32_t>(g->net_p);
+    mc.star_p = P<int32_t>(g->star_p);
     TRY(set_merge_ctx(mc, s));
   }
   TRY((segmented_sort<uint32_t, MODE_MERGE>(keys, row_off, Nst, npre, cnt, mcol, mval,

@@ -77,6 +77,7 @@ struct pl_graph {
   pl::Buf net_p;       // int32 [M] distinct node count
   pl::Buf star_of;     // int32 [M+1] scan of star flags
   pl::Buf star_net;    // int32 [S]
+  pl::Buf star_p;      // int32 [S] node count of each star's net
   pl::Buf macro_cell;  // int32 [Mm]
   pl::Buf cell_macro;  // int32 [C+1] scan of macro flags
   pl::Buf srp;         // int64 [Nst+1] static row pointers (entries live in st)

@@ -194,10 +194,10 @@ template <typename K>
 __device__ __forceinline__ long long key_val(K k, long long s) {
   if (sizeof(K) == 8) return (long long)(int32_t)(uint32_t)((uint64_t)k & 0xffffffffu);
   const uint32_t code = (uint32_t)k & 15u;
-  if (code) return c_merge.lattice / code;
+  if (code) return c_merge.latq[code];
   const long long col = (long long)((uint32_t)k >> 4);
   const long long st = (s >= c_merge.star0 && s < c_merge.star0 + c_merge.nstar) ? s : col;
-  return -(long long)c_merge.net_p[c_merge.star_net[st - c_merge.star0]];
+  return -(long long)c_merge.star_p[st - c_merge.star0];
 }
 
 // Segments are sorted by size class: up to 8, 16 and 32 keys by groups of 8,
