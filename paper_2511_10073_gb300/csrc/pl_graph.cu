@@ -366,39 +366,48 @@ __global__ void k_static_div(const uint32_t *list, const unsigned long long *nli
   }
 }
 
-__device__ __forceinline__ float stored(double w, int wdtype, uint16_t *bits) {
-  if (wdtype == PL_W_BF16) {
-    uint16_t h = d2bf16(w);
-    *bits = h;
-    return bf16_to_f(h);
+// BF16 bits of a double, rounded to nearest even, from the double's high word
+// with 32-bit integer operations when the result is a normal number (the
+// exponent rebias and the mantissa carry are one integer addition); other
+// values take d2bf16.
+__device__ __forceinline__ uint16_t d2bf16_normal(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t ah = hi & 0x7fffffffu;
+  if ((ah >> 20) - 897u < 254u) {  // unbiased exponent in [-126, 127]
+    const uint32_t t = ah >> 13;    // double exponent and the 7 kept mantissa bits
+    const uint32_t r = ah & 0x1fffu;  // the next 13 mantissa bits; 0x1000 is half
+    const uint32_t inc = (r > 0x1000u || (r == 0x1000u && (lo != 0u || (t & 1u)))) ? 1u : 0u;
+    return (uint16_t)(((hi >> 16) & 0x8000u) | (t - (896u << 7) + inc));
   }
-  return __double2float_rn(w);
+  return d2bf16(d);
 }
 
 // A positive double of at least 2^-15 in 128-bit fixed point with 2^-67
-// resolution (exact: its last mantissa bit is worth at least 2^-67).
+// resolution (exact: its last mantissa bit is worth at least 2^-67), as four
+// 32-bit limbs, least significant first.
 struct Fix128 {
-  unsigned long long lo, hi;
+  uint32_t a0, a1, a2, a3;
 };
 __device__ __forceinline__ void fix_add_double(Fix128 &a, double w) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(w);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;  // w = M 2^(e - 52)
-  const unsigned long long M = (b & 0xfffffffffffffull) | 0x10000000000000ull;
-  const int sh = e + 15;                            // w 2^67 = M << (e + 15)
-  unsigned long long lo, hi;
-  if (sh >= 64) {
-    lo = 0;
-    hi = M << (sh - 64);
-  } else if (sh > 0) {
-    lo = M << sh;
-    hi = M >> (64 - sh);
-  } else {
-    lo = M >> (-sh);  // not reached for weights >= 2^-15
-    hi = 0;
-  }
-  const unsigned long long t = a.lo + lo;
-  a.hi += hi + (t < a.lo ? 1ull : 0ull);
-  a.lo = t;
+  const uint32_t hi = (uint32_t)(b >> 32), Ml = (uint32_t)b;
+  const uint32_t Mh = (hi & 0xfffffu) | 0x100000u;  // w = M 2^(e - 52), M = Mh:Ml
+  const int sh = (int)((hi >> 20) & 0x7ffu) - 1008;  // w 2^67 = M << (e + 15), 0 <= sh < 75
+  const int q = sh >> 5, r = sh & 31;
+  // M << r as three limbs, then moved up by q limbs
+  const uint32_t c0 = Ml << r, c1 = __funnelshift_l(Ml, Mh, r), c2 = __funnelshift_l(Mh, 0u, r);
+  const bool q0 = q == 0, q1 = q == 1;
+  const uint32_t A0 = q0 ? c0 : 0u;
+  const uint32_t A1 = q0 ? c1 : (q1 ? c0 : 0u);
+  const uint32_t A2 = q0 ? c2 : (q1 ? c1 : c0);
+  const uint32_t A3 = q0 ? 0u : (q1 ? c2 : c1);
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(a.a0), "+r"(a.a1), "+r"(a.a2), "+r"(a.a3)
+      : "r"(A0), "r"(A1), "r"(A2), "r"(A3));
 }
 // RN(x) * 2^e for x > 0 with a normal result, in integer arithmetic (the
 // conversion and scaling instructions of FP64 would take the slow FP64 pipe):
@@ -425,59 +434,131 @@ __device__ __forceinline__ double u64_rn_scaled(unsigned long long x, int e) {
 
 // The fixed-point value rounded once to the nearest double (ties to even):
 // the top 64 bits with a sticky bit, then one correctly rounded conversion.
-__device__ __forceinline__ double fix_to_double(const Fix128 &a) {
-  if (a.hi == 0) return a.lo ? u64_rn_scaled(a.lo, -67) : 0.0;
-  const int sh = 64 - __clzll((long long)a.hi);  // bits of hi, 1..64
+__device__ __forceinline__ double fix_to_double(const Fix128 &f) {
+  const unsigned long long lo = ((unsigned long long)f.a1 << 32) | f.a0;
+  const unsigned long long hi = ((unsigned long long)f.a3 << 32) | f.a2;
+  if (hi == 0) return lo ? u64_rn_scaled(lo, -67) : 0.0;
+  const int sh = 64 - __clzll((long long)hi);  // bits of hi, 1..64
   unsigned long long top, rest;
   if (sh == 64) {
-    top = a.hi;
-    rest = a.lo;
+    top = hi;
+    rest = lo;
   } else {
-    top = (a.hi << (64 - sh)) | (a.lo >> sh);
-    rest = a.lo & ((1ull << sh) - 1ull);
+    top = (hi << (64 - sh)) | (lo >> sh);
+    rest = lo & ((1ull << sh) - 1ull);
   }
   if (rest) top |= 1ull;
   return u64_rn_scaled(top, sh - 67);
 }
 
 // Final static matrix, written straight into its split layout, from the FP64
-// weights (in place of the merged values), a thread per row: it writes the
-// row's columns and stored weights at the row's place (short region or hub
-// region), sums its static degree (double-float, in entry order, over the
-// stored weights; every static weight is positive, so it is also the
-// positive sum) and, for a cell, the exact sum of its FP64 weights (128-bit
-// fixed point, order-free) for baseWeight = RN(sum) / count.
+// weights (in place of the merged values): each row's columns and stored
+// weights go to the row's place (short region or hub region); its static
+// degree is summed in double-float over the stored weights (every static
+// weight is positive, so it is also the positive sum) and, for a cell, the
+// FP64 weights are summed exactly (128-bit fixed point, order-free) for
+// baseWeight = RN(sum) / count.  A thread takes a short row (entry order);
+// the warp takes each of its hub rows in turn (lanes over the entries, then
+// a fixed butterfly), so that a row of thousands of entries is no serial tail.
+struct CompactRow {
+  dfl dl{0.f, 0.f};
+  Fix128 fl{0u, 0u, 0u, 0u};
+};
+// One entry: its stored bits (BF16 or FP32), added to the degree (stored
+// value) and, for a cell, to the exact sum (FP64 value).
+template <bool BF>
+__device__ __forceinline__ uint32_t compact_entry(CompactRow &r, double w, bool cell) {
+  float f;
+  uint32_t bits;
+  if (BF) {
+    const uint16_t h = d2bf16_normal(w);
+    f = bf16_to_f(h);
+    bits = h;
+  } else {
+    f = __double2float_rn(w);
+    bits = __float_as_uint(f);
+  }
+  df_add(r.dl, f);
+  if (cell) fix_add_double(r.fl, w);
+  return bits;
+}
+// Exact sum of the lanes' fixed-point values (a butterfly; every lane gets it).
+__device__ __forceinline__ Fix128 warp_sum_fix(Fix128 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t b0 = __shfl_xor_sync(0xffffffffu, a.a0, o);
+    const uint32_t b1 = __shfl_xor_sync(0xffffffffu, a.a1, o);
+    const uint32_t b2 = __shfl_xor_sync(0xffffffffu, a.a2, o);
+    const uint32_t b3 = __shfl_xor_sync(0xffffffffu, a.a3, o);
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(a.a0), "+r"(a.a1), "+r"(a.a2), "+r"(a.a3)
+        : "r"(b0), "r"(b1), "r"(b2), "r"(b3));
+  }
+  return a;
+}
+
+template <bool BF>
 __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
-    int64_t Nst, int32_t C, int wdtype, const uint8_t *ckind, const uint32_t *rp_s,
-    const int32_t *longidx, const uint64_t *lptr, int32_t *scol, void *sw, dfl *dsum, dfl *psum,
-    double *base_w, uint8_t *hflag, double *sdeg) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nst;
-       v += (long long)gridDim.x * blockDim.x) {
-    const long long src = row_off[v];
-    const int m = (int)(srp[v + 1] - srp[v]);
-    const int li = longidx[v];
-    const long long dst = li >= 0 ? (long long)lptr[li] : (long long)(rp_s[v] & kOffMask);
-    const double *w64 = reinterpret_cast<const double *>(mval) + src;
-    const bool cell = v < C;
-    dfl dl{0.f, 0.f};
-    Fix128 fl{0ull, 0ull};
-    for (int k = 0; k < m; ++k) {
-      const double w = w64[k];
-      scol[dst + k] = mcol[src + k];
-      uint16_t hb = 0;
-      const float f = stored(w, wdtype, &hb);
-      if (wdtype == PL_W_BF16) reinterpret_cast<uint16_t *>(sw)[dst + k] = hb;
-      else reinterpret_cast<float *>(sw)[dst + k] = f;
-      df_add(dl, f);
-      if (cell) fix_add_double(fl, w);
+    int64_t Nst, int32_t C, const uint8_t *ckind, const uint32_t *rp_s, const int32_t *longidx,
+    const uint64_t *lptr, int32_t *scol, void *sw, dfl *dsum, dfl *psum, double *base_w,
+    uint8_t *hflag, double *sdeg) {
+  const int lane = threadIdx.x & 31;
+  const double *w64 = reinterpret_cast<const double *>(mval);
+  auto put = [&](long long k, uint32_t b) {
+    if (BF) reinterpret_cast<uint16_t *>(sw)[k] = (uint16_t)b;
+    else reinterpret_cast<uint32_t *>(sw)[k] = b;
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); v0 < Nst;
+       v0 += stride) {
+    const long long v = v0 + lane;
+    long long src = 0, dst = 0;
+    int m = 0, li = -1;
+    if (v < Nst) {
+      src = row_off[v];
+      m = (int)(srp[v + 1] - srp[v]);
+      li = longidx[v];
+      dst = li >= 0 ? (long long)lptr[li] : (long long)(rp_s[v] & kOffMask);
     }
-    dl = df_norm(dl);
+    const bool cell = v < C;
+    CompactRow r;
+    if (v < Nst && li < 0) {
+      for (int k = 0; k < m; ++k) {
+        put(dst + k, compact_entry<BF>(r, w64[src + k], cell));
+        scol[dst + k] = mcol[src + k];
+      }
+    }
+    unsigned hubs = __ballot_sync(0xffffffffu, v < Nst && li >= 0);
+    while (hubs) {
+      const int j = __ffs(hubs) - 1;
+      hubs &= hubs - 1;
+      const long long sj = __shfl_sync(0xffffffffu, src, j);
+      const long long dj = __shfl_sync(0xffffffffu, dst, j);
+      const int mj = __shfl_sync(0xffffffffu, m, j);
+      const bool cj = v0 + j < C;
+      CompactRow h;
+      for (int k = lane; k < mj; k += 32) {
+        put(dj + k, compact_entry<BF>(h, w64[sj + k], cj));
+        scol[dj + k] = mcol[sj + k];
+      }
+      const dfl d = warp_sum_df(h.dl);
+      const Fix128 f = warp_sum_fix(h.fl);
+      if (lane == j) {
+        r.dl = d;
+        r.fl = f;
+      }
+    }
+    if (v >= Nst) continue;
+    const dfl dl = df_norm(r.dl);
     sdeg[v] = df_to_d(dl);
     dsum[v] = dl;
     psum[v] = dl;
     if (cell) {
-      const double bw = m > 0 ? __ddiv_rn(fix_to_double(fl), (double)m) : 0.0;
+      const double bw = m > 0 ? __ddiv_rn(fix_to_double(r.fl), (double)m) : 0.0;
       base_w[v] = bw;
       hflag[v] = (ckind[v] == 0 && __double_as_longlong(bw) > 0) ? 1 : 0;  // bw > 0 (integer test)
     }
@@ -920,11 +1001,12 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     note_launch();
   }
   SpMat &sm = g->st;
-  k_static_compact<<<grid_for(Nst, 256), 256, 0, s>>>(
-      row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, p->wdtype, P<uint8_t>(g->ckind),
-      P<uint32_t>(sm.rp_s), P<int32_t>(sm.longidx), P<uint64_t>(sm.lptr), P<int32_t>(sm.col),
-      sm.w.p, P<dfl>(sm.dsum), P<dfl>(sm.psum), P<double>(g->base_w), P<uint8_t>(g->hflag),
-      P<double>(g->sdeg));
+  (p->wdtype == PL_W_BF16 ? k_static_compact<true> : k_static_compact<false>)
+      <<<grid_for(Nst, 256), 256, 0, s>>>(
+          row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, P<uint8_t>(g->ckind),
+          P<uint32_t>(sm.rp_s), P<int32_t>(sm.longidx), P<uint64_t>(sm.lptr),
+          P<int32_t>(sm.col), sm.w.p, P<dfl>(sm.dsum), P<dfl>(sm.psum), P<double>(g->base_w),
+          P<uint8_t>(g->hflag), P<double>(g->sdeg));
   note_launch();
   if (g->N > Nst) {
     TRY(cudaMemsetAsync(P<dfl>(sm.dsum) + Nst, 0, (size_t)(g->N - Nst) * sizeof(dfl), s));
