@@ -280,7 +280,9 @@ __device__ __forceinline__ bool lattice_easy(long long val, const double *star_w
   }
   if (val >= kLattice / 15 && val <= kLattice) {
     // 32-bit conversions (a 64-bit integer conversion would take the FP64 pipe)
-    const int d = (int)((float)kLattice / (float)(int)val + 0.5f);
+    // d = kLattice / val to within 2 ulp: exact d is recovered for val =
+    // kLattice / d, and every candidate is confirmed in integers
+    const int d = (int)(__fdividef((float)kLattice, (float)(int)val) + 0.5f);
     if (d >= 1 && d <= 15 && (long long)d * val == kLattice) {
       *w = c_recip[d];
       return true;
@@ -302,8 +304,10 @@ __global__ void k_star_weights(double *star_w) {
     star_w[p] = p >= 2 ? __ddiv_rn((double)p, (double)(p - 1)) : 0.0;
 }
 
-// Table weights in place of the merged values (warp per 32 rows, lanes over a
-// row's entries); entries that need a division are listed, so that the
+// Table weights in place of the merged values.  A warp takes 32 rows and
+// walks their entries as one flat sequence, a lane per entry (the row of an
+// entry is found from the rows' length prefix sums), so that short rows keep
+// every lane busy; entries that need a division are listed, so that the
 // divisions run together in k_static_div instead of stalling whole warps.
 constexpr int kDivBuf = 256;  // listed entries a warp buffers before one global append
 
@@ -328,29 +332,37 @@ __global__ void __launch_bounds__(256) k_static_weights(const int64_t *row_off, 
   for (long long v0 = wg * 32; v0 < Nst; v0 += nwarp * 32) {
     const long long v = v0 + lane;
     long long src = 0;
-    int m = 0;
+    uint32_t m = 0;
     if (v < Nst) {
       src = row_off[v];
-      m = (int)(srp[v + 1] - srp[v]);
+      m = (uint32_t)(srp[v + 1] - srp[v]);
     }
-    const int nv = (int)min((long long)32, Nst - v0);
-    for (int j = 0; j < nv; ++j) {
-      const long long sj = __shfl_sync(0xffffffffu, src, j);
-      const int mj = __shfl_sync(0xffffffffu, m, j);
-      for (int k0 = 0; k0 < mj; k0 += 32) {
-        const int k = k0 + lane;
-        bool hard = false;
-        if (k < mj) {
-          double w;
-          if (lattice_easy(mval[sj + k], star_w, &w)) reinterpret_cast<double *>(mval)[sj + k] = w;
-          else hard = true;
-        }
-        const unsigned hm = __ballot_sync(0xffffffffu, hard);
-        if (nb + 32 > kDivBuf) flush();
-        if (hard) buf[nb + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)(sj + k);
-        nb += __popc(hm);
-        __syncwarp();
+    uint32_t incl = m;  // inclusive prefix sum of the lengths (< 2^32 entries in all)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const long long rb = src - (long long)(incl - m);  // entry e of the warp is at rb_j + e
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t e0 = 0; e0 < T; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      int j = 0;  // the row holding entry e: rows whose prefix ends at or before e
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, j + st - 1) <= e) j += st;
+      const long long q = __shfl_sync(0xffffffffu, rb, j) + e;
+      bool hard = false;
+      if (e < T) {
+        double w;
+        if (lattice_easy(mval[q], star_w, &w)) reinterpret_cast<double *>(mval)[q] = w;
+        else hard = true;
       }
+      const unsigned hm = __ballot_sync(0xffffffffu, hard);
+      if (nb + 32 > kDivBuf) flush();
+      if (hard) buf[nb + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)q;
+      nb += __popc(hm);
+      __syncwarp();
     }
   }
   if (nb) flush();
