@@ -502,10 +502,12 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
-// One sparse product: the hub chunks, the hub rows, then the short rows
-// (same stream).
+// One sparse product: the hub chunks and then the hub rows on the graph's
+// side stream, the short rows on the caller's stream at the same time (they
+// write disjoint rows of y); the caller's stream waits for both.
 template <int MODE>
-static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s) {
+static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s,
+                               pl_graph *g) {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -524,14 +526,22 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   }
   const bool prof = prof_on();
   if (prof) prof_begin(s, MODE == MODE_HR ? PROF_HR : PROF_GIFT, bytes);
-  if (A.nchunks > 0) {
+  const bool fork = A.nchunks > 0;
+  if (fork) {
+    cudaError_t e = ensure_side(g);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    cudaStream_t sh = g->side;
     const long long want = ((long long)A.nchunks + 7) / 8;
     const int hgrid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
-    if (wi) k_spmm_hub<1, MODE><<<hgrid, 256, 0, s>>>(A);
-    else k_spmm_hub<0, MODE><<<hgrid, 256, 0, s>>>(A);
-    k_hub_rows<MODE><<<(int)(((long long)A.nlong + kHubRows - 1) / kHubRows), kHubRows * 32, 0, s>>>(A);
+    if (wi) k_spmm_hub<1, MODE><<<hgrid, 256, 0, sh>>>(A);
+    else k_spmm_hub<0, MODE><<<hgrid, 256, 0, sh>>>(A);
+    k_hub_rows<MODE><<<(int)(((long long)A.nlong + kHubRows - 1) / kHubRows), kHubRows * 32, 0, sh>>>(A);
     note_launch();
     note_launch();
+    e = cudaEventRecord(g->ev_join, sh);
+    if (e != cudaSuccess) return e;
   }
   const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
   const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
@@ -540,6 +550,10 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
   else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
   note_launch();
+  if (fork) {
+    const cudaError_t e = cudaStreamWaitEvent(s, g->ev_join, 0);
+    if (e != cudaSuccess) return e;
+  }
   if (prof) prof_end(s);
   return cudaGetLastError();
 }
@@ -648,7 +662,7 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
       A.cy = A.fin ? cy : 0.0;
       A.addc = (A.cx != 0.0 || A.cy != 0.0) ? 1 : 0;
       A.pin = 0;
-      TRY(launch_step<MODE_GIFT>(A, bytes, g->wdtype, s));
+      TRY(launch_step<MODE_GIFT>(A, bytes, g->wdtype, s, g));
       any = true;
       float2 *tt = x;
       x = y;
@@ -722,7 +736,7 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
           A.alpha = p->tap_alpha[j];
         }
     A.fin = t == kmax;
-    TRY(launch_step<MODE_HR>(A, bytes, g->wdtype, s));
+    TRY(launch_step<MODE_HR>(A, bytes, g->wdtype, s, g));
     x = bufs[t & 1];
   }
   return PL_OK;
