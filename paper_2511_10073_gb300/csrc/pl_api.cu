@@ -123,7 +123,7 @@ static void destroy(pl_graph *g) {
   if (g->ev_join) cudaEventDestroy(g->ev_join);
   Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
                  &g->net_p, &g->star_of, &g->star_net, &g->star_p, &g->macro_cell, &g->cell_macro, &g->srp,
-                 &g->base_w, &g->hflag, &g->sdeg, &g->nkind, &g->fixedp,
+                 &g->base_w, &g->hflag, &g->nkind, &g->fixedp,
                  &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
                  &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem,
                  &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->clen, &g->lflag,

@@ -423,21 +423,28 @@ __global__ void k_clamp(int64_t N, const uint8_t *nkind, const float2 *fixedp,
 }
 
 // GiFt per-node coefficients of one sigma: a = sigma/d, b = 1/d, band scale
-// sqrt(d), and u0 = (g - centre)/sqrt(d), d = D_vv + sigma.  d is formed in
-// FP64 and the rest in FP32, the precision the sparse products run in.
-__global__ void k_gift_prep(int64_t N, int64_t Nst, const double *sdeg, double sigma,
-                            const float2 *g, double cx, double cy, float *a, float *b,
-                            float *sq, float2 *u0) {
-  const float sf = (float)sigma;
+// sqrt(d), and u0 = (g - centre)/sqrt(d), d = D_vv + sigma.  d is the static
+// degree (double-float) plus sigma, rounded once to FP32; the rest is FP32,
+// the precision the sparse products run in (a centre is subtracted in FP64).
+__global__ void k_gift_prep(int64_t N, const dfl *deg, double sigma, const float2 *g,
+                            int center, double cx, double cy, float *a, float *b, float *sq,
+                            float2 *u0) {
+  const float sh = (float)sigma, sl = (float)(sigma - (double)sh);  // sigma as a double-float
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
-    const float d = (float)((v < Nst ? sdeg[v] : 0.0) + sigma);
+    dfl t = deg[v];
+    df_add(t, sh);
+    df_add(t, sl);
+    const float d = df_norm(t).hi;
     const float r = sqrtf(d);
-    a[v] = sf / d;
+    a[v] = sh / d;
     b[v] = 1.0f / d;
     sq[v] = r;
     const float2 q = g[v];
-    u0[v] = make_float2((float)((double)q.x - cx) / r, (float)((double)q.y - cy) / r);
+    if (center)
+      u0[v] = make_float2((float)((double)q.x - cx) / r, (float)((double)q.y - cy) / r);
+    else
+      u0[v] = make_float2(q.x / r, q.y / r);
   }
 }
 
@@ -636,8 +643,9 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
     if (kmax[q] > 0) order[no++] = q;
   for (int oi = 0; oi < nch; ++oi) {
     const int q = order[oi];
-    k_gift_prep<<<grid_for(N, 256), 256, 0, s>>>(N, g->Nst, P<double>(g->sdeg), sig[q], gin, cx,
-                                                 cy, ga, gb, gq, P<float2>(g->ua));
+    k_gift_prep<<<grid_for(N, 256), 256, 0, s>>>(N, P<dfl>(g->st.dsum), sig[q], gin,
+                                                 p->gift_center ? 1 : 0, cx, cy, ga, gb, gq,
+                                                 P<float2>(g->ua));
     note_launch();
     // bands with k = 0 contribute alpha * (g - centre)
     for (int bnd = 0; bnd < 3; ++bnd) {

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
     int64_t Nst, int32_t C, const uint8_t *ckind, const uint32_t *rp_s, const int32_t *longidx,
     const uint64_t *lptr, int32_t *scol, void *sw, dfl *dsum, dfl *psum, double *base_w,
-    uint8_t *hflag, double *sdeg) {
+    uint8_t *hflag) {
   const int lane = threadIdx.x & 31;
   const double *w64 = reinterpret_cast<const double *>(mval);
   auto put = [&](long long k, uint32_t b) {
@@ -566,7 +566,6 @@ __global__ void __launch_bounds__(256) k_static_compact(
     }
     if (v >= Nst) continue;
     const dfl dl = df_norm(r.dl);
-    sdeg[v] = df_to_d(dl);
     dsum[v] = dl;
     psum[v] = dl;
     if (cell) {
@@ -980,7 +979,6 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   }
   TRY(ensure(g->base_w, (size_t)C * 8 + 16));
   TRY(ensure(g->hflag, (size_t)C + 16));
-  TRY(ensure(g->sdeg, (size_t)Nst * 8 + 16));
   if (!g->star_w_ok) {
     // weight tables, once per graph: 1/d (host IEEE division) and p / (p - 1)
     double rc[16];
@@ -1018,7 +1016,7 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
           row_off, mcol, mval, P<int64_t>(g->srp), Nst, C, P<uint8_t>(g->ckind),
           P<uint32_t>(sm.rp_s), P<int32_t>(sm.longidx), P<uint64_t>(sm.lptr),
           P<int32_t>(sm.col), sm.w.p, P<dfl>(sm.dsum), P<dfl>(sm.psum), P<double>(g->base_w),
-          P<uint8_t>(g->hflag), P<double>(g->sdeg));
+          P<uint8_t>(g->hflag));
   note_launch();
   if (g->N > Nst) {
     TRY(cudaMemsetAsync(P<dfl>(sm.dsum) + Nst, 0, (size_t)(g->N - Nst) * sizeof(dfl), s));

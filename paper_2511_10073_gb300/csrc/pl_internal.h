@@ -83,7 +83,6 @@ struct pl_graph {
   pl::Buf srp;         // int64 [Nst+1] static row pointers (entries live in st)
   pl::Buf base_w;      // double [C]
   pl::Buf hflag;       // uint8 [C] movable with baseWeight > 0
-  pl::Buf sdeg;        // double [Nst] static degree (stored weights)
   pl::Buf nkind;       // uint8 [N] 0 movable cell, 1 star, 2 fixed
   pl::Buf fixedp;      // float2 [N]
   pl::Buf bounds;      // float4 [N] clamp box of the centre
