@@ -129,7 +129,7 @@ static void destroy(pl_graph *g) {
                  &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->clen, &g->lflag,
                  &g->crank, &g->tpos, &g->mac_base,
                  &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,
-                 &g->acc, &g->gsc, &g->status, &g->stage, &g->star_w, &g->scr.buf};
+                 &g->acc, &g->gsc, &g->q4a, &g->q4b, &g->status, &g->stage, &g->star_w, &g->scr.buf};
   for (Buf *b : bufs) release(*b);
   for (Buf &b : g->tmp) release(b);
   SpMat *ms[] = {&g->st, &g->hm};

@@ -71,19 +71,29 @@ struct StepArgs {
   const float2 *fixedp;
   const float4 *bounds;
   int *status;
+  // GiFt hub passes: stride of x and y in float2 units (2 for one chain's
+  // half of an interleaved chain pair, else 1)
+  int xs;
+  // GiFt chain pair (k_spmm_rows4): the second chain's coefficients and tap,
+  // and x and y of both chains interleaved as (x1, y1, x2, y2) per node
+  const float *a2, *b2, *tscale2;
+  int tap2;
+  double alpha2;
+  const float4 *x4;
+  float4 *y4;
 };
 
 // Epilogue of node v with its kind kd and (tap steps) accumulator ac loaded
 // by the caller.
 template <typename T>
 __device__ __forceinline__ void epilogue_k(const StepArgs &A, int64_t v, uint8_t kd, double2 ac,
-                                           T yx, T yy) {
+                                           T yx, T yy, int64_t yi) {
   if (A.pin && kd == 2) {
     float2 f = A.fixedp[v];
     yx = (T)f.x;
     yy = (T)f.y;
   }
-  if (!A.fin) A.y[v] = make_float2((float)yx, (float)yy);
+  if (!A.fin) A.y[yi] = make_float2((float)yx, (float)yy);
   double tx = 0.0, ty = 0.0;
   if (A.tap) {
     double sc = A.tscale ? (double)A.tscale[v] : 1.0;
@@ -127,12 +137,33 @@ __device__ __forceinline__ void epilogue_k(const StepArgs &A, int64_t v, uint8_t
   }
 }
 
-// The same epilogue for one coordinate c (0: x, 1: y) of node v, so that the
-// two lanes of a row share its FP64 work.
+// Final value of coordinate c (0: x, 1: y) of node v from its filter sum gv:
+// centre, relaxation, FP32 rounding, clamping; fixed nodes keep their place.
+__device__ __forceinline__ void finish_c(const StepArgs &A, int64_t v, uint8_t kd, int c,
+                                         double gv) {
+  if (A.addc) gv += c ? A.cy : A.cx;
+  float o;
+  if (kd == 2) {
+    o = reinterpret_cast<const float *>(A.fixedp)[2 * v + c];
+  } else {
+    if (A.relax) {
+      const float g = reinterpret_cast<const float *>(A.g0)[2 * v + c];
+      gv = A.omg * (double)g + A.gamma * gv;
+    }
+    o = __double2float_rn(gv);
+    if (A.clamp) {
+      const float4 bd = A.bounds[v];
+      o = c ? fminf(fmaxf(o, bd.y), bd.w) : fminf(fmaxf(o, bd.x), bd.z);
+    }
+  }
+  reinterpret_cast<float *>(A.gnext)[2 * v + c] = o;
+}
+
+// The same epilogue for one coordinate c of node v, so that the two lanes of
+// a row share its FP64 work.
 __device__ __forceinline__ void epilogue_c(const StepArgs &A, int64_t v, uint8_t kd, int c,
                                            double acv, float yv) {
-  const float *fixc = reinterpret_cast<const float *>(A.fixedp) + 2 * v + c;
-  if (A.pin && kd == 2) yv = *fixc;
+  if (A.pin && kd == 2) yv = reinterpret_cast<const float *>(A.fixedp)[2 * v + c];
   if (!A.fin) reinterpret_cast<float *>(A.y)[2 * v + c] = yv;
   // (FP64 is slow: no product by a unit scale, no sum with a zero centre,
   // 1 - gamma from the host, no store of the last tap sum)
@@ -144,30 +175,37 @@ __device__ __forceinline__ void epilogue_c(const StepArgs &A, int64_t v, uint8_t
     if (!A.fin) reinterpret_cast<double *>(A.acc)[2 * v + c] = acv;
     t = acv;
   }
-  if (A.fin) {
-    double gv = A.single ? (double)yv : t;
-    if (A.addc) gv += c ? A.cy : A.cx;
-    float o;
-    if (kd == 2) {
-      o = *fixc;
-    } else {
-      if (A.relax) {
-        const float g = reinterpret_cast<const float *>(A.g0)[2 * v + c];
-        gv = A.omg * (double)g + A.gamma * gv;
-      }
-      o = __double2float_rn(gv);
-      if (A.clamp) {
-        const float4 bd = A.bounds[v];
-        o = c ? fminf(fmaxf(o, bd.y), bd.w) : fminf(fmaxf(o, bd.x), bd.z);
-      }
-    }
-    reinterpret_cast<float *>(A.gnext)[2 * v + c] = o;
+  if (A.fin) finish_c(A, v, kd, c, A.single ? (double)yv : t);
+}
+
+// Epilogue of coordinate c of node v for a GiFt chain pair: both chains'
+// values (y1, y2) are stored interleaved and their taps added to the one
+// band sum, the first chain's first.
+__device__ __forceinline__ void epilogue_c2(const StepArgs &A, int64_t v, uint8_t kd, int c,
+                                            double acv, float y1, float y2) {
+  if (A.pin && kd == 2) y1 = y2 = reinterpret_cast<const float *>(A.fixedp)[2 * v + c];
+  if (!A.fin) {
+    float *yp = reinterpret_cast<float *>(A.y4) + 4 * v + c;
+    yp[0] = y1;
+    yp[2] = y2;
   }
+  if (A.tap) {
+    double pv = (double)y1;
+    if (A.tscale) pv *= (double)A.tscale[v];
+    acv += A.alpha * pv;
+  }
+  if (A.tap2) {
+    double pv = (double)y2;
+    if (A.tscale2) pv *= (double)A.tscale2[v];
+    acv += A.alpha2 * pv;
+  }
+  if ((A.tap || A.tap2) && !A.fin) reinterpret_cast<double *>(A.acc)[2 * v + c] = acv;
+  if (A.fin) finish_c(A, v, kd, c, acv);
 }
 
 template <typename T>
-__device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T yy) {
-  epilogue_k<T>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0), yx, yy);
+__device__ __forceinline__ void epilogue(const StepArgs &A, int64_t v, T yx, T yy, int64_t yi) {
+  epilogue_k<T>(A, v, A.nkind[v], A.tap ? A.acc[v] : make_double2(0.0, 0.0), yx, yy, yi);
 }
 
 // ------------------------------------------------------- work units
@@ -189,7 +227,8 @@ __device__ __forceinline__ float wload(const void *w, uint64_t k) {
 
 template <int WT>
 __device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp, uint64_t b,
-                                            uint64_t e, const float2 *x, dfl &sx, dfl &sy) {
+                                            uint64_t e, const float2 *x, int xs, dfl &sx,
+                                            dfl &sy) {
   const int lane = threadIdx.x & 31;
   for (uint64_t k0 = b; k0 < e; k0 += 32 * kChunkBatch) {
     int cc[kChunkBatch];
@@ -204,7 +243,7 @@ __device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp,
 #pragma unroll
     for (int q = 0; q < kChunkBatch; ++q) {
       const uint64_t k = k0 + q * 32 + lane;
-      xv[q] = k < e ? __ldg(x + cc[q]) : make_float2(0.f, 0.f);
+      xv[q] = k < e ? __ldg(x + (size_t)cc[q] * xs) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < kChunkBatch; ++q) {
@@ -216,19 +255,21 @@ __device__ __forceinline__ void chunk_piece(const int32_t *colp, const void *wp,
 
 // A hub chunk covers positions [q0, q1) of the row's st piece followed by its
 // hm piece; its double-float sums over the warp are the chunk's partial.
-template <int WT>
+template <int WT, int MODE>
 __device__ void warp_chunk(const StepArgs &A, int c) {
   const int lane = threadIdx.x & 31;
+  const int xs = MODE == MODE_GIFT ? A.xs : 1;
   const int l = A.chunk_lr[c];
   const int c0 = A.lchunk[l];
   const uint64_t sl = A.lsl[l], hl = A.lhl[l];
   const uint64_t q0 = (uint64_t)(c - c0) * kChunk;
   const uint64_t q1 = q0 + kChunk < sl + hl ? q0 + kChunk : sl + hl;
   dfl sx{0.f, 0.f}, sy{0.f, 0.f};
-  if (q0 < sl) chunk_piece<WT>(A.scol, A.sw, A.lsb[l] + q0, A.lsb[l] + (q1 < sl ? q1 : sl), A.x, sx, sy);
+  if (q0 < sl)
+    chunk_piece<WT>(A.scol, A.sw, A.lsb[l] + q0, A.lsb[l] + (q1 < sl ? q1 : sl), A.x, xs, sx, sy);
   if (q1 > sl) {
     const uint64_t hb = A.lhb[l];
-    chunk_piece<WT>(A.hcol, A.hw, hb + (q0 > sl ? q0 - sl : 0), hb + (q1 - sl), A.x, sx, sy);
+    chunk_piece<WT>(A.hcol, A.hw, hb + (q0 > sl ? q0 - sl : 0), hb + (q1 - sl), A.x, xs, sx, sy);
   }
   sx = warp_sum_df(sx);
   sy = warp_sum_df(sy);
@@ -240,7 +281,7 @@ template <int WT, int MODE>
 __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT>(A, (int)c);
+  for (long long c = gw; c < A.nchunks; c += nw) warp_chunk<WT, MODE>(A, (int)c);
 }
 
 // Short rows, row-split: a group of kRowLanes lanes per row reads the row's
@@ -322,6 +363,70 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
   }
 }
 
+// A GiFt chain pair over the short rows of the static matrix: the same
+// row-split walk, one gather of (x1, y1, x2, y2) per entry for both chains
+// (the indices, weights and gathers of one product serve two).
+template <int WT>
+__device__ __forceinline__ void row_piece4(const int32_t *col, const void *w, uint32_t k,
+                                           uint32_t e, const float4 *x, float4 &s) {
+  for (; k < e; k += kRowUnroll * kRowLanes) {
+    int c[kRowUnroll];
+    float wv[kRowUnroll];
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      const uint32_t kk = k + u * kRowLanes;
+      c[u] = kk < e ? __ldcs(col + kk) : -1;
+      wv[u] = kk < e ? wload<WT>(w, kk) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      if (c[u] >= 0) {
+        const float4 xv = __ldg(x + c[u]);
+        s.x = fmaf(wv[u], xv.x, s.x);
+        s.y = fmaf(wv[u], xv.y, s.y);
+        s.z = fmaf(wv[u], xv.z, s.z);
+        s.w = fmaf(wv[u], xv.w, s.w);
+      }
+    }
+  }
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kRowThreads) k_spmm_rows4(StepArgs A) {
+  const int64_t N = A.nrows;
+  constexpr int L = kRowLanes, RPW = 32 / L;
+  const int lane = threadIdx.x & 31, m = lane & (L - 1);
+  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
+  for (long long base = gw * RPW; base < N; base += nw * RPW) {
+    const long long v = base + lane / L;
+    bool live = false;
+    uint32_t sa = 0, sb = 0;
+    if (v < N) {
+      const uint32_t f0 = A.srp[v];
+      sa = f0 & kOffMask;
+      sb = A.srp[v + 1] & kOffMask;
+      live = !(f0 & kHubFlag);
+    }
+    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) row_piece4<WT>(A.scol, A.sw, sa + m, sb, A.x4, sm);
+    sm.x += __shfl_xor_sync(0xffffffffu, sm.x, 1);
+    sm.y += __shfl_xor_sync(0xffffffffu, sm.y, 1);
+    sm.z += __shfl_xor_sync(0xffffffffu, sm.z, 1);
+    sm.w += __shfl_xor_sync(0xffffffffu, sm.w, 1);
+    if (live) {
+      // lane m of the pair finishes coordinate m of both chains
+      const float *xr = reinterpret_cast<const float *>(A.x4) + 4 * v + m;
+      const float y1 = A.a[v] * xr[0] + A.b[v] * (m ? sm.y : sm.x);
+      const float y2 = A.a2[v] * xr[2] + A.b2[v] * (m ? sm.w : sm.z);
+      const double acv = (A.tap || A.tap2 || A.fin)
+                             ? reinterpret_cast<const double *>(A.acc)[2 * v + m]
+                             : 0.0;
+      epilogue_c2(A, v, A.nkind[v], m, acv, y1, y2);
+    }
+  }
+}
+
 // Hub rows, after the chunk launch: a block takes kHubRows rows, a warp per
 // row adding the row's partials in a fixed order (lane-strided over the
 // chunks, then a fixed tree); one warp then does the combines in FP64, a lane
@@ -358,8 +463,9 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
     av = (double)A.a[v];
     bv = (double)A.b[v];
   }
-  const float2 xv = A.x[v];
-  epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty);
+  const int64_t xi = MODE == MODE_GIFT ? v * A.xs : v;
+  const float2 xv = A.x[xi];
+  epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty, xi);
 }
 
 // ------------------------------------------------------------- helpers
@@ -565,6 +671,99 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   return cudaGetLastError();
 }
 
+// Algorithmic bytes of one product of a GiFt chain pair: indices and weights
+// once, row pointers, the four signals read and written, two coefficients.
+static double spmm_bytes_pair(double nnz, double N, int wdtype) {
+  return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 +
+         N * (16.0 + 16.0 + 8.0);
+}
+
+// One product of a GiFt chain pair: the hub rows of each chain in turn (its
+// half of the interleaved signals, stride 2) on the side stream, the short
+// rows of both chains in one launch on the caller's stream.
+static cudaError_t launch_pair(const StepArgs &A, double bytes, int wdtype, cudaStream_t s,
+                               pl_graph *g) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+  }
+  static int occ[2] = {0, 0};
+  const int wi = wdtype == PL_W_BF16 ? 1 : 0;
+  if (!occ[wi]) {
+    int b = 0;
+    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows4<1>, kRowThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows4<0>, kRowThreads, 0);
+    occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
+  }
+  const bool prof = prof_on();
+  if (prof) prof_begin(s, PROF_GIFT, bytes);
+  const bool fork = A.nchunks > 0;
+  if (fork) {
+    cudaError_t e = ensure_side(g);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    cudaStream_t sh = g->side;
+    const long long want = ((long long)A.nchunks + 7) / 8;
+    const int hgrid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
+    const int rgrid = (int)(((long long)A.nlong + kHubRows - 1) / kHubRows);
+    for (int h = 0; h < 2; ++h) {
+      StepArgs H = A;
+      H.x = reinterpret_cast<const float2 *>(A.x4) + h;
+      H.y = reinterpret_cast<float2 *>(A.y4) + h;
+      H.xs = 2;
+      if (h == 0) {  // the first chain never finishes: its tap goes to the sum
+        H.fin = 0;
+        H.cx = H.cy = 0.0;
+        H.addc = 0;
+      } else {
+        H.a = A.a2;
+        H.b = A.b2;
+        H.tscale = A.tscale2;
+        H.tap = A.tap2;
+        H.alpha = A.alpha2;
+        if (H.fin && !H.tap) {  // the final value reads the sum
+          H.tap = 1;
+          H.alpha = 0.0;
+        }
+      }
+      if (wi) k_spmm_hub<1, MODE_GIFT><<<hgrid, 256, 0, sh>>>(H);
+      else k_spmm_hub<0, MODE_GIFT><<<hgrid, 256, 0, sh>>>(H);
+      k_hub_rows<MODE_GIFT><<<rgrid, kHubRows * 32, 0, sh>>>(H);
+      note_launch();
+      note_launch();
+    }
+    e = cudaEventRecord(g->ev_join, sh);
+    if (e != cudaSuccess) return e;
+  }
+  const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
+  const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
+  const long long cap = (long long)occ[wi] * nsm;
+  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  if (wi) k_spmm_rows4<1><<<grid, kRowThreads, 0, s>>>(A);
+  else k_spmm_rows4<0><<<grid, kRowThreads, 0, s>>>(A);
+  note_launch();
+  if (fork) {
+    const cudaError_t e = cudaStreamWaitEvent(s, g->ev_join, 0);
+    if (e != cudaSuccess) return e;
+  }
+  if (prof) prof_end(s);
+  return cudaGetLastError();
+}
+
+// The pair's interleaved start: (x1, y1) of the first chain, (x2, y2) of the
+// second.
+__global__ void k_pack_pair(int64_t N, const float2 *a, const float2 *b, float4 *q) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    const float2 u = a[v], w = b[v];
+    q[v] = make_float4(u.x, u.y, w.x, w.y);
+  }
+}
+
 static void fill_nodes(StepArgs &A, pl_graph *g) {
   A.status = P<int>(g->status);
   A.nkind = P<uint8_t>(g->nkind);
@@ -612,71 +811,124 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
   }
   TRY(ensure(g->acc, (size_t)N * 16 + 16));
   TRY(cudaMemsetAsync(g->acc.p, 0, (size_t)N * 16, s));
-  TRY(ensure(g->gsc, (size_t)N * 12 + 64));
+  TRY(ensure(g->gsc, (size_t)N * 24 + 64));
   TRY(ensure(g->ua, (size_t)N * 8 + 64));
   TRY(ensure(g->ub, (size_t)N * 8 + 64));
   TRY(ensure(g->xa, (size_t)N * 8 + 64));
   float *ga = P<float>(g->gsc), *gb = ga + N, *gq = gb + N;
+  float *ga2 = gq + N, *gb2 = ga2 + N, *gq2 = gb2 + N;
   StepArgs A{};
   fill_matrix(A, g->st, nullptr);
   const double bytes = spmm_bytes((double)(g->st.nnz_s + g->st.nnz_l), (double)N, g->wdtype);
   fill_nodes(A, g);
   A.acc = P<double2>(g->acc);
-  A.tscale = gq;
-  A.a = ga;
-  A.b = gb;
   A.relax = 0;
   A.clamp = p->clamp;
   A.gnext = gout;
   A.single = 0;
-  // find the chain that finishes last (the final step)
-  int last_chain = -1;
-  for (int q = 0; q < nch; ++q)
-    if (kmax[q] > 0) last_chain = q;
-  bool any = false;
-  // chains without steps first: their bands (k = 0) only add to the sum,
-  // which the final step of the last chain with steps reads
-  int order[3], no = 0;
-  for (int q = 0; q < nch; ++q)
-    if (kmax[q] == 0) order[no++] = q;
-  for (int q = 0; q < nch; ++q)
-    if (kmax[q] > 0) order[no++] = q;
-  for (int oi = 0; oi < nch; ++oi) {
-    const int q = order[oi];
+  A.pin = 0;
+  A.xs = 1;
+  // tap of chain q at step t: the summed alpha of its bands with k = t
+  auto tap_of = [&](int q, int t, double *alpha) {
+    *alpha = 0.0;
+    int tap = 0;
+    for (int bnd = 0; bnd < 3; ++bnd)
+      if (chain_of[bnd] == q && p->gift_k[bnd] == t) {
+        tap = 1;
+        *alpha += p->gift_alpha[bnd];
+      }
+    return tap;
+  };
+  // per-node coefficients of chain q, its start u0, and its bands with k = 0
+  // (they contribute alpha * (g - centre))
+  auto prep = [&](int q, float *a, float *b, float *sq, float2 *u0) -> cudaError_t {
     k_gift_prep<<<grid_for(N, 256), 256, 0, s>>>(N, P<dfl>(g->st.dsum), sig[q], gin,
-                                                 p->gift_center ? 1 : 0, cx, cy, ga, gb, gq,
-                                                 P<float2>(g->ua));
+                                                 p->gift_center ? 1 : 0, cx, cy, a, b, sq, u0);
     note_launch();
-    // bands with k = 0 contribute alpha * (g - centre)
     for (int bnd = 0; bnd < 3; ++bnd) {
       if (chain_of[bnd] != q || p->gift_k[bnd] != 0) continue;
-      k_acc_add<<<grid_for(N, 256), 256, 0, s>>>(N, P<float2>(g->ua), gq, p->gift_alpha[bnd],
+      k_acc_add<<<grid_for(N, 256), 256, 0, s>>>(N, u0, sq, p->gift_alpha[bnd],
                                                  P<double2>(g->acc));
       note_launch();
     }
-    float2 *x = P<float2>(g->ua), *y = P<float2>(g->ub);
-    for (int t = 1; t <= kmax[q]; ++t) {
+    return cudaGetLastError();
+  };
+  auto set_final = [&](bool fin) {
+    A.fin = fin ? 1 : 0;
+    A.cx = fin ? cx : 0.0;
+    A.cy = fin ? cy : 0.0;
+    A.addc = (A.cx != 0.0 || A.cy != 0.0) ? 1 : 0;
+  };
+  // Chains without steps first (their bands only add to the sum that the
+  // final step reads), then the chains with steps: all but the last two
+  // alone, the last two as a pair.  The longer chain of the pair runs alone
+  // until the two have equal steps left, then both advance in one product
+  // per step (interleaved signals); the pair's last step is the final one.
+  int qs[3], ns = 0;
+  for (int q = 0; q < nch; ++q)
+    if (kmax[q] == 0) TRY(prep(q, ga, gb, gq, P<float2>(g->ua)));
+  for (int q = 0; q < nch; ++q)
+    if (kmax[q] > 0) qs[ns++] = q;
+  const bool pair = ns >= 2;
+  const int nsolo = pair ? ns - 2 : ns;
+  // one chain alone from x for steps t0 + 1 .. t1 (ping-pong x, y)
+  auto run_chain = [&](int q, float2 *&x, float2 *&y, int t0, int t1, bool last) -> cudaError_t {
+    A.a = ga;
+    A.b = gb;
+    A.tscale = gq;
+    for (int t = t0 + 1; t <= t1; ++t) {
       A.x = x;
       A.y = y;
-      A.tap = 0;
-      A.alpha = 0.0;
-      for (int bnd = 0; bnd < 3; ++bnd)
-        if (chain_of[bnd] == q && p->gift_k[bnd] == t) {
-          A.tap = 1;
-          A.alpha += p->gift_alpha[bnd];
-        }
-      A.fin = (q == last_chain && t == kmax[q]) ? 1 : 0;
-      A.cx = A.fin ? cx : 0.0;
-      A.cy = A.fin ? cy : 0.0;
-      A.addc = (A.cx != 0.0 || A.cy != 0.0) ? 1 : 0;
-      A.pin = 0;
-      TRY(launch_step<MODE_GIFT>(A, bytes, g->wdtype, s, g));
-      any = true;
+      A.tap = tap_of(q, t, &A.alpha);
+      set_final(last && t == t1);
+      const cudaError_t e = launch_step<MODE_GIFT>(A, bytes, g->wdtype, s, g);
+      if (e != cudaSuccess) return e;
       float2 *tt = x;
       x = y;
       y = tt;
     }
+    return cudaSuccess;
+  };
+  for (int i = 0; i < nsolo; ++i) {
+    const int q = qs[i];
+    TRY(prep(q, ga, gb, gq, P<float2>(g->ua)));
+    float2 *x = P<float2>(g->ua), *y = P<float2>(g->ub);
+    TRY(run_chain(q, x, y, 0, kmax[q], i == ns - 1));
   }
+  if (pair) {
+    const int q1 = qs[ns - 2], q2 = qs[ns - 1];
+    const int qL = kmax[q1] >= kmax[q2] ? q1 : q2, qS = qL == q1 ? q2 : q1;
+    const int d = kmax[qL] - kmax[qS];
+    TRY(prep(qL, ga, gb, gq, P<float2>(g->ua)));
+    TRY(prep(qS, ga2, gb2, gq2, P<float2>(g->xa)));
+    float2 *x = P<float2>(g->ua), *y = P<float2>(g->ub);
+    TRY(run_chain(qL, x, y, 0, d, false));
+    TRY(ensure(g->q4a, (size_t)N * 16 + 64));
+    TRY(ensure(g->q4b, (size_t)N * 16 + 64));
+    float4 *x4 = P<float4>(g->q4a), *y4 = P<float4>(g->q4b);
+    k_pack_pair<<<grid_for(N, 256), 256, 0, s>>>(N, x, P<float2>(g->xa), x4);
+    note_launch();
+    const double bytes4 = spmm_bytes_pair((double)(g->st.nnz_s + g->st.nnz_l), (double)N,
+                                          g->wdtype);
+    A.a = ga;
+    A.b = gb;
+    A.tscale = gq;
+    A.a2 = ga2;
+    A.b2 = gb2;
+    A.tscale2 = gq2;
+    for (int t = 1; t <= kmax[qS]; ++t) {
+      A.tap = tap_of(qL, d + t, &A.alpha);
+      A.tap2 = tap_of(qS, t, &A.alpha2);
+      A.x4 = x4;
+      A.y4 = y4;
+      set_final(t == kmax[qS]);
+      TRY(launch_pair(A, bytes4, g->wdtype, s, g));
+      float4 *tt = x4;
+      x4 = y4;
+      y4 = tt;
+    }
+  }
+  const bool any = ns > 0;
   if (!any) {
     // every band has k = 0: the filter is sum(alpha) * g
     k_acc_final<<<grid_for(N, 256), 256, 0, s>>>(N, P<double2>(g->acc), cx, cy, P<uint8_t>(g->nkind),

@@ -117,7 +117,8 @@ struct pl_graph {
   pl::Buf xa, xb, xc, g0; // float2 [N]
   pl::Buf ua, ub;         // float [N * 2 * nchain]
   pl::Buf acc;            // double2 [N]
-  pl::Buf gsc;            // float [3 * N] GiFt scales (1/sqrt(D+sigma))
+  pl::Buf gsc;            // float [6 * N] GiFt coefficients (a, b, sqrt(d)) of two chains
+  pl::Buf q4a, q4b;       // float4 [N] GiFt chain pair, (x1, y1, x2, y2) per node
   pl::Buf status;         // int32 [8]
   pl::Buf stage;          // staging words of batched device-to-host reads
   pl::Buf star_w;         // double [kMaxNetPins + 1] star edge weights p / (p - 1)

@@ -95,6 +95,40 @@ def test_static_graph_bitexact(cfg, seed, wd, perm):
     assert np.array_equal(ge["base_w"], oe["base_w"])
 
 
+@pytest.mark.parametrize("wd", [1, 2])
+def test_static_graph_hub_cells(wd):
+    # cells with more than 128 static entries (hub rows summed by a whole
+    # warp, one with over a thousand), repeated nets (summed lattice values
+    # that need a division), star nets through the hub cells, and many small
+    # nets around them
+    rng = np.random.default_rng(11)
+    cells = 4000
+    nets = []
+    for h, reps in [(0, 90), (1, 12), (2, 9), (3, 30)]:
+        for _ in range(reps):
+            nets.append(np.r_[h, rng.choice(np.arange(10, cells), 15, replace=False)])
+    nets += [nets[3], nets[3], nets[100], nets[101]]  # parallel edges
+    for h in (0, 2):
+        nets.append(np.r_[h, rng.choice(np.arange(10, cells), 40, replace=False)])
+    for _ in range(6000):
+        nets.append(rng.choice(cells, rng.integers(2, 5), replace=False))
+    ptr = np.r_[0, np.cumsum([len(n) for n in nets])].astype(np.int64)
+    pins = np.concatenate(nets).astype(np.int32)
+    z = np.zeros(len(pins), np.float32)
+    nl = netgen.Netlist(ptr, pins, z, z, np.ones(cells, np.float32), np.ones(cells, np.float32),
+                        np.zeros(cells, np.uint8), np.zeros(cells, np.float32),
+                        np.zeros(cells, np.float32), (0.0, 0.0, 100.0, 100.0))
+    s = Side(nl, **cfg_params("tiny", wdtype=wd))
+    ge = s.g.export_static()
+    oe = s.o.static_csr()
+    lens = np.diff(oe["rp"])
+    assert lens[:4].min() > 128 and lens[0] > 1000  # the hub cells
+    assert np.array_equal(ge["rp"], oe["rp"])
+    assert np.array_equal(ge["col"], oe["col"])
+    assert np.array_equal(ge["w"], oe["w_store"])
+    assert np.array_equal(ge["base_w"], oe["base_w"])
+
+
 # -------------------------------------------------------- A2/A3 hints
 def _compare_hints(s, ge, oe):
     assert np.array_equal(ge["cell_bin"], oe["cell_bin"])
@@ -172,6 +206,12 @@ def test_hints_stacked_macros():
     ("tiny", 3, dict(gift_center=1, gift_k=(3, 1, 0), gift_sigma=(1.5, 3.0, 3.0))),
     # a sigma whose only band has k = 0, after the chain with steps
     ("tiny", 4, dict(gift_center=1, gift_k=(3, 1, 0), gift_sigma=(1.5, 1.5, 3.0))),
+    # three chains with steps: one alone, then a pair of unequal lengths
+    ("tiny", 5, dict(gift_k=(2, 3, 1), gift_sigma=(1.0, 2.0, 3.0), gift_alpha=(0.5, 0.3, 0.2))),
+    # a pair of equal lengths, two bands sharing the last step of one chain
+    ("small", 3, dict(gift_center=1, gift_k=(2, 2, 2), gift_sigma=(4.0, 2.0, 4.0), wdtype=2)),
+    # one chain only
+    ("tiny", 6, dict(gift_k=(1, 3, 2), gift_sigma=(2.0, 2.0, 2.0))),
     ("medium", 1, {})])
 def test_init_and_gift_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
