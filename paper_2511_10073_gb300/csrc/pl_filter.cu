@@ -491,25 +491,34 @@ __global__ void k_init_signal(int64_t N, int32_t C, uint64_t seed, const float2 
   }
 }
 
-// Star node = mean of its net's distinct nodes (warp per star, FP64).
+// Star node = mean of its net's distinct nodes (warp per star): double-float
+// sums (about 48 bits) over the lanes and a fixed butterfly, then the
+// quotient by p as a double-float in FP32 operations (the remainder of the
+// leading quotient is exact), rounded once to FP32.
+__device__ __forceinline__ float df_div_int(dfl s, int p) {
+  const float fp = (float)p;
+  const float q = __fdiv_rn(s.hi, fp);
+  const float r = __fmaf_rn(-q, fp, s.hi);
+  return __fadd_rn(q, __fdiv_rn(__fadd_rn(r, s.lo), fp));
+}
 __global__ void k_star_init(int32_t S, int64_t star0, const int32_t *star_net,
                             const int64_t *net_ptr, const uint32_t *nd, const int32_t *net_p,
                             float2 *g) {
   const int lane = threadIdx.x & 31;
   for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < S;
        s += ((long long)gridDim.x * blockDim.x) >> 5) {
-    int e = star_net[s];
-    long long b = net_ptr[e];
-    int p = net_p[e];
-    double sx = 0.0, sy = 0.0;
+    const int e = star_net[s];
+    const long long b = net_ptr[e];
+    const int p = net_p[e];
+    dfl sx{0.f, 0.f}, sy{0.f, 0.f};
     for (int k = lane; k < p; k += 32) {
-      float2 q = g[nd[b + k]];
-      sx += q.x;
-      sy += q.y;
+      const float2 q = g[nd[b + k]];
+      df_add(sx, q.x);
+      df_add(sy, q.y);
     }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) g[star0 + s] = make_float2(__double2float_rn(sx / p), __double2float_rn(sy / p));
+    sx = warp_sum_df(sx);
+    sy = warp_sum_df(sy);
+    if (lane == 0) g[star0 + s] = make_float2(df_div_int(sx, p), df_div_int(sy, p));
   }
 }
 

@@ -512,6 +512,8 @@ __device__ __forceinline__ Fix128 warp_sum_fix(Fix128 a) {
   return a;
 }
 
+constexpr int kCompactUnroll = 4;  // entries of a short row loaded at once
+
 template <bool BF>
 __global__ void __launch_bounds__(256) k_static_compact(
     const int64_t *row_off, const int32_t *mcol, const int64_t *mval, const int64_t *srp,
@@ -539,7 +541,22 @@ __global__ void __launch_bounds__(256) k_static_compact(
     const bool cell = v < C;
     CompactRow r;
     if (v < Nst && li < 0) {
-      for (int k = 0; k < m; ++k) {
+      int k = 0;
+      for (; k + kCompactUnroll <= m; k += kCompactUnroll) {  // loads in flight, then the entries
+        double wv[kCompactUnroll];
+        int32_t cv[kCompactUnroll];
+#pragma unroll
+        for (int u = 0; u < kCompactUnroll; ++u) {
+          wv[u] = w64[src + k + u];
+          cv[u] = mcol[src + k + u];
+        }
+#pragma unroll
+        for (int u = 0; u < kCompactUnroll; ++u) {
+          put(dst + k + u, compact_entry<BF>(r, wv[u], cell));
+          scol[dst + k + u] = cv[u];
+        }
+      }
+      for (; k < m; ++k) {
         put(dst + k, compact_entry<BF>(r, w64[src + k], cell));
         scol[dst + k] = mcol[src + k];
       }
