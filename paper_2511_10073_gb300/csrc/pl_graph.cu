@@ -192,15 +192,15 @@ __global__ void k_row_count(const int64_t *ptr, const uint32_t *nd, const int32_
   }
 }
 
-constexpr int kScatterRegs = 8;  // clique nets up to this size kept in registers
+constexpr int kScatterRegs = 4;  // clique nets up to this size kept in registers
 
 // Unmerged entries as 32-bit keys (col << 4 | code): code p - 1 (1..15) for a
 // clique pair of a p-node net (value 360360/(p-1) in lattice units), code 0
 // for a star edge (value -p, p taken from the star node when merging).  Star
 // rows are written in node order directly.
-// A thread takes a clique net (each node reserves its p - 1 slots with one
-// atomic, all of a small net's reservations in flight at once); star nets are
-// taken by the whole warp in turn.
+// A thread takes a clique net of up to kScatterRegs nodes (each node reserves
+// its p - 1 slots with one atomic, all of the net's reservations in flight at
+// once); larger clique nets and star nets are taken by the whole warp in turn.
 __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t *net_p,
                           const int32_t *star_of, int32_t M, int32_t cmax, int64_t star0,
                           const int64_t *row_off, unsigned long long *cursor, uint32_t *keys) {
@@ -235,15 +235,31 @@ __global__ void k_scatter(const int64_t *ptr, const uint32_t *nd, const int32_t 
             if (c != a) keys[k++] = (node[c] << 4) | lat;
           }
         }
-      } else {
-        for (int a = 0; a < p; ++a) {
-          const uint32_t ra = nd[b + a];
-          unsigned long long k = atomicAdd(&cursor[ra], (unsigned long long)(p - 1));
-          for (int c = 0; c < p; ++c) {
-            if (c == a) continue;
-            keys[k++] = (nd[b + c] << 4) | lat;
-          }
-        }
+      }
+    }
+    // larger clique nets (up to 16 nodes) by the whole warp in turn: lane a
+    // holds node a and its slots, lanes then write the p (p - 1) keys
+    unsigned bc = __ballot_sync(0xffffffffu, p > kScatterRegs && p <= cmax);
+    while (bc) {
+      const int src = __ffs(bc) - 1;
+      bc &= bc - 1;
+      const int pp = __shfl_sync(0xffffffffu, p, src);
+      const long long bb = __shfl_sync(0xffffffffu, b, src);
+      uint32_t node = 0;
+      unsigned long long slot = 0;
+      if (lane < pp) {
+        node = nd[bb + lane];
+        slot = atomicAdd(&cursor[node], (unsigned long long)(pp - 1));
+      }
+      const uint32_t lat = (uint32_t)(pp - 1);
+      const int tot = pp * (pp - 1);
+      for (int t0 = 0; t0 < tot; t0 += 32) {
+        const int t = t0 + lane;
+        const int a = t / (pp - 1), cq = t - a * (pp - 1);  // key cq of node a's run
+        const int c = cq + (cq >= a ? 1 : 0);                // the other node (a skipped)
+        const uint32_t nc = __shfl_sync(0xffffffffu, node, c & 31);
+        const unsigned long long sa = __shfl_sync(0xffffffffu, slot, a & 31);
+        if (t < tot) keys[sa + cq] = (nc << 4) | lat;
       }
     }
     unsigned bm = __ballot_sync(0xffffffffu, p > cmax);
