@@ -166,6 +166,19 @@ def run_reference(args):
     }), flush=True)
 
 
+def whole_job_rate(ms_local, units_per_rank, steps, dist=None, device="cpu"):
+    """Whole-job throughput of a replica run: the slowest rank's time (MAX over
+    ranks) for the units all ranks processed.  Returns (units/s, max ms)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return world * units_per_rank * steps / (ms_max / 1e3), ms_max
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,12 +269,8 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     prof = pl.pl_prof_read()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     movable = nl.num_movable
-    value = world * movable * args.steps / (ms_max / 1e3)
+    value, ms_max = whole_job_rate(ms, movable, args.steps, dist, dev)
 
     # end to end through the C ABI from host buffers: netlist H2D, results D2H
     host = {k: getattr(dnl, k).cpu().pin_memory() for k in
@@ -289,10 +298,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * movable * ke / (float(t.item()) / 1e3)
+    e2e_value, _ = whole_job_rate(e0.elapsed_time(e1), movable, ke, dist, dev)
 
     # phase breakdown (untimed pass, CUDA events around each call)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
