@@ -283,6 +283,31 @@ def test_full_initializer_from_given_placement():
     assert err <= 1e-4 * s.die
 
 
+def test_full_initializer_net_through_every_cell():
+    # one net through every cell (macros and I/O included): a star row of
+    # every node, a star entry in every cell row, on top of a tiny netlist
+    nl = netgen.make_netlist("tiny", 7)
+    C = nl.num_cells
+    z = np.zeros(C, np.float32)
+    nl2 = netgen.Netlist(np.r_[nl.net_ptr, nl.net_ptr[-1] + C].astype(np.int64),
+                         np.r_[nl.pin_cell, np.arange(C)].astype(np.int32),
+                         np.r_[nl.pin_dx, z].astype(np.float32), np.r_[nl.pin_dy, z].astype(np.float32),
+                         nl.cell_w, nl.cell_h, nl.cell_kind, nl.fixed_x, nl.fixed_y, nl.region)
+    for wd in (1, 2):
+        s = Side(nl2, **cfg_params("tiny", wdtype=wd))
+        ge = s.g.export_static()
+        oe = s.o.static_csr()
+        assert np.array_equal(ge["col"], oe["col"]) and np.array_equal(ge["w"], oe["w_store"])
+        assert np.array_equal(ge["base_w"], oe["base_w"])
+        out = torch.empty(C * 2, dtype=torch.float32, device="cuda")
+        pl().pl_filter_init(s.g, s.prm, 3, None, out)
+        torch.cuda.synchronize()
+        gx, gy = s.o.run(3)
+        b = to_np(out)
+        err = max(np.abs(b[:, 0] - gx[:C]).max(), np.abs(b[:, 1] - gy[:C]).max())
+        assert err <= 1e-4 * s.die, err
+
+
 # --------------------------------------------------------------- A5 HPWL
 @pytest.mark.parametrize("cfg,seed", [("micro", 1), ("tiny", 2), ("medium", 1)])
 def test_hpwl(cfg, seed):
