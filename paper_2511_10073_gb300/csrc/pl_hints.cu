@@ -675,9 +675,25 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     if (v >= G.Nst) goto flush;
     {
     dfl Dl = sdsum[v], Pl = spsum[v];
-    if (v < G.C && hflag[v]) {
-      const int li = longidx[v];
-      const uint64_t mb = li >= 0 ? lptr[li] : (uint64_t)(hrp[v] & kOffMask);
+    // a cell's inputs, loaded before its hint test so that they are in flight
+    // together rather than one dependent round after another
+    uint8_t hf = 0;
+    int li = -1, cb = 0, cr = 0, nov = 0;
+    uint32_t hr = 0;
+    float2 p = make_float2(0.f, 0.f);
+    double bw = 0.0;
+    if (v < G.C) {
+      hf = hflag[v];
+      li = longidx[v];
+      hr = hrp[v];
+      p = xy[v];
+      bw = base_w[v];
+      cb = cell_bin[v];
+      nov = n_ovl[v];
+      if (tpos) cr = crank[v];
+    }
+    if (hf) {
+      const uint64_t mb = li >= 0 ? lptr[li] : (uint64_t)(hr & kOffMask);
       const bool use_s = staged && li < 0;
       // an own entry: to the warp's stage (short rows) or straight to memory
       auto put = [&](uint64_t kk, int32_t c, uint32_t bits) {
@@ -690,9 +706,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
           else reinterpret_cast<uint32_t *>(w)[kk] = bits;
         }
       };
-      float2 p = xy[v];
       if (!isfinite(p.x) || !isfinite(p.y)) p = make_float2(0.f, 0.f);
-      const double bw = base_w[v];
       const float bwf = __double2float_rn(bw);
       // macro entries, ascending macro id (grid bucket lists are sorted)
       uint64_t k = mb;
@@ -718,8 +732,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       };
       if (cmem) {
         // the cell's macros as the cell pass found them (same geometry values)
-        const int n = n_ovl[v];
-        for (int j = 0; j < n; ++j) {
+        for (int j = 0; j < nov; ++j) {
           const int m = cmem[(long long)v * kMacroSlots + j];
           mac_entry(m, mgeo[m]);
         }
@@ -741,13 +754,13 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
           }
         }
       }
-      const uint64_t bb0 = mb + n_ovl[v];
-      const int b = cell_bin[v], bx = b % G.nbx, by = b / G.nbx;
+      const uint64_t bb0 = mb + nov;
+      const int b = cb, bx = b % G.nbx, by = b / G.nbx;
       const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
       const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
       const dfl ux = df_offset_scale(p.x, G.xlh, G.xll, G.iwh, G.iwl);
       const dfl uy = df_offset_scale(p.y, G.ylh, G.yll, G.ihh, G.ihl);
-      const uint64_t rk = tpos ? (uint64_t)(crank[v] - boff[2 * b]) : 0ull;
+      const uint64_t rk = tpos ? (uint64_t)(cr - boff[2 * b]) : 0ull;
       k = bb0;
       for (int yy = y0; yy <= y1; ++yy) {
         // e^{-max(rx, ry)} is e^{-rx} or e^{-ry}
