@@ -147,12 +147,16 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
                              int32_t *cell_bin, int32_t *n_ovl, int32_t *bcnt, int32_t *mcnt,
                              int32_t *mtc, int ntile, int32_t *cmem, int *status) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.C; i += gridDim.x * blockDim.x) {
-    if (ckind[i] != 0) {
+    // the cell's inputs in flight together, before the kind test
+    const uint8_t kd = ckind[i];
+    float2 p = xy[i];
+    const bool hint = hflag[i] != 0;
+    const float cwi = cw[i], chi = ch[i];
+    if (kd != 0) {
       cell_bin[i] = -1;
       n_ovl[i] = 0;
       continue;
     }
-    float2 p = xy[i];
     if (!isfinite(p.x) || !isfinite(p.y)) {
       flag(status, ST_NONFINITE);
       p = make_float2(0.f, 0.f);
@@ -160,13 +164,11 @@ __global__ void k_hint_cells(HintGeo G, const float2 *xy, const uint8_t *ckind,
     int bx = bin_of(p.x, G.xlf, G.sxf, G.nbx), by = bin_of(p.y, G.ylf, G.syf, G.nby);
     int b = by * G.nbx + bx;
     cell_bin[i] = b;
-    bool hint = hflag[i] != 0;
     if (bcnt) atomicAdd(&bcnt[2 * b + (hint ? 0 : 1)], 1);
     int n = 0;
     if (hint) {
       int kx = grid_of(p.x, G.gxf, G.gsxf, G.gnx), ky = grid_of(p.y, G.gyf, G.gsyf, G.gny);
       long long k = (long long)ky * G.gnx + kx;
-      const float cwi = cw[i], chi = ch[i];
       for (long long q = gptr[k]; q < gptr[k + 1]; ++q) {
         const float4 mg = ggeo[q];
         if (overlaps(p.x, p.y, cwi, chi, mg.x, mg.y, mg.z, mg.w)) {
