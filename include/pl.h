@@ -26,6 +26,10 @@
  *     the device (graph builds) synchronize that stream; pl_filter_init reads
  *     the device status once at its end.  No call aborts, traps or spins
  *     without bound; failures come back as a pl_status and pl_last_error().
+ *   - Each pl_graph owns a second stream.  Graph builds and sparse products
+ *     fork part of their work onto it (an event recorded on the given stream)
+ *     and join it back (the given stream waits on an event), so every call
+ *     still completes in the order of the given stream.
  *   - The library owns the pl_graph object and the device memory inside it
  *     (allocated with cudaMalloc, freed by pl_graph_destroy).
  *   - One pl_graph must not be used from two host threads at once.
