@@ -54,7 +54,8 @@ typedef enum {
   PL_ERR_OOM = 4,         /* device allocation failed */
   PL_ERR_SPECTRUM = 5,    /* lambda_up <= 0 or not finite: no refinement filter */
   PL_ERR_NONFINITE = 6,   /* a coordinate given to the library is NaN or infinite */
-  PL_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+  PL_ERR_TIMEOUT = 7,     /* reserved: a bounded device-side wait gave up (no kernel of
+                             this library waits on another block, so none returns it) */
   PL_ERR_UNSUPPORTED = 8  /* input beyond a documented size limit */
 } pl_status;
 
@@ -136,7 +137,7 @@ pl_status pl_build_hints(pl_graph *g, const pl_params *p, const float *xy_nodes,
  * g~ = sum_t alpha_t H_r^{k_t} g, fixed nodes re-pinned, then
  * g' = (1 - gamma) g + gamma g~, re-pinned, movable centres clamped.
  * xy_in, xy_out: device, N pairs each, distinct buffers.  Synchronizes
- * `stream` to read the device status (TIMEOUT if a bounded wait gave up). */
+ * `stream` to read the device status. */
 pl_status pl_filter_apply(pl_graph *g, const pl_params *p, const float *xy_in, float *xy_out,
                           pl_stream stream);
 

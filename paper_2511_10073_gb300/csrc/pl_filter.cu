@@ -627,18 +627,25 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
 // One sparse product: the hub chunks and then the hub rows on the graph's
 // side stream, the short rows on the caller's stream at the same time (they
 // write disjoint rows of y); the caller's stream waits for both.
+// SM count of the graph's device, looked up once per graph (a graph is used
+// from one host thread at a time and stays on the device it was built on).
+static int graph_nsm(pl_graph *g) {
+  if (!g->nsm) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+    g->nsm = n;
+  }
+  return g->nsm;
+}
+
 template <int MODE>
 static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cudaStream_t s,
                                pl_graph *g) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 152;
-  }
+  const int nsm = graph_nsm(g);
   // short rows: one wave of resident blocks, row groups dealt round robin
-  static int occ[2] = {0, 0};
+  int *occ = g->occ_rows[MODE];
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
     int b = 0;
@@ -692,14 +699,8 @@ static double spmm_bytes_pair(double nnz, double N, int wdtype) {
 // rows of both chains in one launch on the caller's stream.
 static cudaError_t launch_pair(const StepArgs &A, double bytes, int wdtype, cudaStream_t s,
                                pl_graph *g) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 152;
-  }
-  static int occ[2] = {0, 0};
+  const int nsm = graph_nsm(g);
+  int *occ = g->occ_rows4;
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
     int b = 0;

@@ -8,8 +8,12 @@
 //  * L_hint = D - A with signed D_ii; lambda_up = max_i (D_ii + sum_j |w_ij|)
 //    (Gershgorin), which equals max_i 2 * (sum of positive w_ij).
 // Decisions (bin of a centre, overlap) are FP32 with one stated operation
-// sequence; D_b and phi_b are FP64; edge weights are FP32 with the exponent
-// argument carried in FP64; degree sums are double-float.
+// sequence; D_b and phi_b are FP64; degree sums are double-float.  Edge
+// weights are the FP64 value of the definition rounded once to the storage
+// type: for BF16 storage an FP32 value (exponent argument carried in FP64)
+// rounds to the same bf16 except within a few FP32 ulps of a bf16 rounding
+// midpoint, where the FP64 value is computed; FP32 storage, whose rounding
+// step an FP32 estimate cannot decide, always takes the FP64 value.
 #include <cmath>
 #include <cstring>
 
@@ -650,7 +654,9 @@ __device__ __forceinline__ dfl df_ratio(float x, float c, float h) {
 // static ones plus the hint entries.  The window ratios |x - x_b| / (w_b / 2)
 // = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u (double-float, once
 // per cell) as exact double-float differences; macro ratios are double-float
-// quotients.  FP64 only recomputes weights near a bf16 rounding midpoint.
+// quotients.  With BF16 storage FP64 only recomputes weights near a bf16
+// rounding midpoint; with FP32 storage every weight is the FP64 value of the
+// definition rounded once.
 constexpr int kAsmStage = 768;  // own entries of a warp's 32 rows staged in shared memory
 __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     HintGeo G, int wdtype, const uint32_t *hrp, const int32_t *longidx, const uint64_t *lptr,
@@ -713,20 +719,20 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       // macro entries, ascending macro id (grid bucket lists are sorted)
       uint64_t k = mb;
       auto mac_entry = [&](int m, float4 mg) {
-        const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
-        const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
-        const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
         uint32_t bits;
         float sv;
         if (bf) {
+          const dfl rx = df_ratio(p.x, mg.x, __fmul_rn(0.5f, mg.z));
+          const dfl ry = df_ratio(p.y, mg.y, __fmul_rn(0.5f, mg.w));
+          const float wv = -(exp_neg_df(df_ge(rx, ry) ? rx : ry) * bwf);
           const uint16_t h = near_bf16_tie(wv)
                                  ? d2bf16(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z, mg.w, bw))
                                  : f2bf16(wv);
           bits = h;
           sv = bf16_to_f(h);
         } else {
-          bits = __float_as_uint(wv);
-          sv = wv;
+          sv = __double2float_rn(macro_w_exact(p.x, p.y, mg.x, mg.y, mg.z, mg.w, bw));
+          bits = __float_as_uint(sv);
         }
         put(k, (int32_t)(G.mv0 + m), bits);
         acc_deg(Dl, Pl, sv);
@@ -788,21 +794,21 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
           for (int u = 0; u < 4; ++u) {
             const int xx = xc + u;
             if (xx > x1) break;
-            const dfl rx = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
-            const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
             const int bb = yy * G.nbx + xx;
-            const float wv = -((e * ph[u]) * bwf);
             uint32_t bits;
             float sv;
             if (bf) {
+              const dfl rx = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
+              const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
+              const float wv = -((e * ph[u]) * bwf);
               const uint16_t h = near_bf16_tie(wv)
                                      ? d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))
                                      : f2bf16(wv);
               bits = h;
               sv = bf16_to_f(h);
             } else {
-              bits = __float_as_uint(wv);
-              sv = wv;
+              sv = __double2float_rn(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw));
+              bits = __float_as_uint(sv);
             }
             put(k, (int32_t)(G.bn0 + bb), bits);
             // the same entry in the row of bin bb: this cell's bucket run

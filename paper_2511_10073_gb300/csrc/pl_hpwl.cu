@@ -269,6 +269,7 @@ static cudaError_t noalloc_scratch(void **out) {
 extern "C" pl_status pl_hpwl_noalloc(const pl_netlist *nl, const float *xy_cells, double *hpwl,
                                      pl_stream stream) {
   using namespace pl;
+  clear_error();
   if (!nl || !xy_cells || !hpwl) {
     set_error("NULL argument");
     return PL_ERR_INVALID_ARG;

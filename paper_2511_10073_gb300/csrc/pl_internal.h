@@ -125,6 +125,12 @@ struct pl_graph {
   cudaStream_t side = nullptr;  // the hint build's second stream (forked from and joined
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // back to the caller's stream)
   bool star_w_ok = false;
+  // launch shapes of the sparse products on the graph's device (0 = not yet
+  // looked up): SM count, resident blocks per SM of the short-row kernels by
+  // [mode][weight type] and of the chain-pair kernel by weight type
+  int nsm = 0;
+  int occ_rows[2][2] = {{0, 0}, {0, 0}};
+  int occ_rows4[2] = {0, 0};
   pl::Scratch scr;
   pl::Buf tmp[8];
   pl::Buf lay[4];         // layout scratch (scans of row lengths, chunk counts)
@@ -134,6 +140,7 @@ struct pl_graph {
 namespace pl {
 
 void set_error(const char *fmt, ...);
+void clear_error();
 pl_status cuda_fail(cudaError_t e, const char *what);
 
 pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cudaStream_t s);

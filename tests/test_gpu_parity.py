@@ -5,9 +5,8 @@ coordinates, both sides get the same FP32 node coordinates (produced by the
 GPU path itself), so each step is checked on its own:
   * static graph (A1): CSR bit-exact (columns, stored weights, baseWeight);
   * area hints (A2/A3): topology bit-exact (row pointers, columns, bins),
-    D_b / C_b / phi_b bit-exact (FP64), hint weights within 8 FP32 ulps
-    (FP32 storage) or 1 bf16 ulp (BF16 storage), degrees and lambda_up within
-    the resulting weight tolerance;
+    D_b / C_b / phi_b bit-exact (FP64), hint weights bit-exact (FP32 and BF16
+    storage), degrees and lambda_up within 1e-12 relative;
   * filters (A0, A4) and the whole initializer: coordinates within 1e-4 of the
     die width;
   * HPWL (A5): within 1e-5 relative.
@@ -22,8 +21,6 @@ from paper_2511_10073_gb300 import netgen
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-F32_ULP_TOL = 8
 
 
 def pl():
@@ -65,16 +62,10 @@ def to_np(t):
     return t.view(-1, 2).double().cpu().numpy()
 
 
-def check_weights(wg, wo, wdtype, where):
-    wg = np.asarray(wg, np.float64)
-    wo = np.asarray(wo, np.float64)
-    if wdtype == pl().PL_W_BF16:
-        tol = np.where(wo != 0, 2.0 ** (np.floor(np.log2(np.abs(np.where(wo != 0, wo, 1.0)))) - 7), 1e-45)
-    else:
-        tol = F32_ULP_TOL * np.where(wo != 0, np.spacing(np.abs(wo).astype(np.float32)).astype(np.float64), 1e-45)
-    bad = np.abs(wg - wo) > tol
-    assert not bad.any(), f"{where}: {bad.sum()} weights beyond tolerance, e.g. {wg[bad][:5]} vs {wo[bad][:5]}"
-    return float(np.mean(wg == wo)) if wg.size else 1.0
+# Degrees and lambda_up: the summed weights are bit-identical on both sides;
+# the GPU adds them in double-float (about 48 significant bits, a few units of
+# 2^-48 of the running sum per addition), the oracle in FP64.
+DEG_REL = 1e-12
 
 
 # -------------------------------------------------------------- A1 static
@@ -131,23 +122,25 @@ def test_static_graph_hub_cells(wd):
 
 # -------------------------------------------------------- A2/A3 hints
 def _compare_hints(s, ge, oe):
+    """Augmented graph of one hint build against the oracle's: bins, D_b, C_b,
+    phi_b, row pointers, columns and stored weights bit-identical (FP32 and
+    BF16 storage both round the FP64 weight of the definition once); signed
+    degrees within DEG_REL of the row's sum of |w|, lambda_up within DEG_REL."""
     assert np.array_equal(ge["cell_bin"], oe["cell_bin"])
     assert np.array_equal(ge["Db"], oe["Db"])
     assert np.array_equal(ge["Cb"], oe["Cb"])
     assert np.array_equal(ge["phi"], oe["phi"])
     assert np.array_equal(ge["rp"], oe["rp"])
     assert np.array_equal(ge["col"], oe["col"])
-    frac = check_weights(ge["w"], oe["w"], s.kw.get("wdtype", 1), "augmented graph")
-    if s.kw.get("wdtype", 1) == 2:  # BF16 weights are rounded exactly: bit-identical
-        assert np.array_equal(ge["w"], oe["w"])
+    bad = ge["w"] != oe["w"]
+    assert not bad.any(), f"{bad.sum()} weights differ, e.g. {ge['w'][bad][:5]} vs {oe['w'][bad][:5]}"
     rp = oe["rp"]
     absw = np.bincount(np.repeat(np.arange(s.N), np.diff(rp)), weights=np.abs(oe["w"]),
                        minlength=s.N)
-    tol = (2e-6 if s.kw.get("wdtype", 1) == 1 else 1e-2) * absw + 1e-12
-    assert (np.abs(ge["deg"] - oe["deg"]) <= tol).all()
-    rel = 2e-6 if s.kw.get("wdtype", 1) == 1 else 1e-2
-    assert ge["lam_up"] == pytest.approx(oe["lam_up"], rel=rel)
-    return frac
+    derr = np.abs(ge["deg"] - oe["deg"])
+    assert (derr <= DEG_REL * absw + 1e-300).all(), float((derr / np.maximum(absw, 1e-300)).max())
+    assert abs(ge["lam_up"] - oe["lam_up"]) <= DEG_REL * abs(oe["lam_up"])
+    return float((derr / np.maximum(absw, 1e-300)).max())
 
 
 @pytest.mark.parametrize("cfg,seed,kw", [
@@ -166,8 +159,7 @@ def test_hints_crossfed(cfg, seed, kw):
     a = to_np(xy)
     s.o.build_hints(a[:, 0], a[:, 1])
     oe = s.o.merged()
-    frac = _compare_hints(s, ge, oe)
-    assert frac > 0.5  # most weights bit-identical
+    _compare_hints(s, ge, oe)
 
 
 def test_hints_stacked_macros():
