@@ -113,20 +113,20 @@ def oracle_params(config):
     return dict(WORKLOADS[config][1])
 
 
-def oracle_sample(nl, config):
-    """The FP64 oracle (single host thread) on one step of the bench workload
-    itself (the same netlist: static graph, GSP init, 3 refinement rounds,
-    HPWL); about 10-30 s on one core.  Returns movable cells per second and
-    the seconds it took."""
+def oracle_sample(nl, config, parallel=False):
+    """The FP64 oracle on one step of the bench workload itself (the same
+    netlist: static graph, GSP init, 3 refinement rounds, HPWL), on one host
+    thread or, with parallel, on all host cores (the OpenMP build, same
+    results).  Returns movable cells per second, seconds, threads used."""
     import oracle
-    oracle.build()
     kw = oracle_params(config)
+    threads = oracle.host_cores() if parallel else 1
     t0 = time.perf_counter()
-    o = oracle.Oracle(nl, **kw)
+    o = oracle.Oracle(nl, parallel=parallel, **kw)
     gx, gy = o.run(1)
-    oracle.hpwl(nl, gx[:nl.num_cells], gy[:nl.num_cells])
+    oracle.hpwl(nl, gx[:nl.num_cells], gy[:nl.num_cells], parallel=parallel)
     dt = time.perf_counter() - t0
-    return nl.num_movable / dt, dt
+    return nl.num_movable / dt, dt, threads
 
 
 def run_reference(args):
@@ -136,15 +136,17 @@ def run_reference(args):
     import oracle
     from paper_2511_10073_gb300 import netgen
     oracle.build()
-    # each step: the half-size netlist of the workload's recipe with its parameters
-    sample = "half" if args.config == "large" else args.config
-    nl = netgen.make_netlist(WORKLOADS[sample][0], args.seed)
+    oracle.build_parallel()
+    cores = oracle.host_cores()
+    # each step: the oracle (OpenMP build, all host cores) on the workload's
+    # own netlist: static graph, GSP init, T_hint rounds, HPWL
+    nl = netgen.make_netlist(WORKLOADS[args.config][0], args.seed)
     kw = oracle_params(args.config)
 
     def step():
-        o = oracle.Oracle(nl, **kw)
+        o = oracle.Oracle(nl, parallel=True, **kw)
         gx, gy = o.run(args.seed)
-        oracle.hpwl(nl, gx[:nl.num_cells], gy[:nl.num_cells])
+        oracle.hpwl(nl, gx[:nl.num_cells], gy[:nl.num_cells], parallel=True)
 
     for _ in range(args.warmup):
         step()
@@ -158,10 +160,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.config, "sample": f"{sample} netlist of the same recipe"},
-        "cpu_baseline": {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one {sample} netlist of the workload's recipe per step "
-                                   "(full path: static graph, GSP init, 3 refinement rounds, HPWL)"},
+        "config": {"workload": args.config, "netlist": DESCR[args.config]},
+        "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                         "sample": f"the {args.config} workload's netlist each step (full path: "
+                                   "static graph, GSP init, refinement rounds, HPWL), OpenMP "
+                                   f"build on {cores} host cores"},
         "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -374,11 +377,18 @@ def main():
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_sample(nl, args.config)
-        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one step of the bench workload itself ({args.config}: "
-                                          f"static graph, GSP init, 3 refinement rounds, HPWL), "
-                                          f"{dt:.1f} s single-threaded"}
+        import oracle
+        oracle.build()
+        oracle.build_parallel()
+        v1, dt1, _ = oracle_sample(nl, args.config)
+        vp, dtp, cores = oracle_sample(nl, args.config, parallel=True)
+        what = (f"one step of the bench workload itself ({args.config}: static graph, GSP init, "
+                f"3 refinement rounds, HPWL)")
+        line["cpu_baseline"] = {"value": vp, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{what}, {dtp:.1f} s on {cores} host cores (OpenMP "
+                                          "build, same results as the single-threaded oracle)",
+                                "single_thread": {"value": v1, "unit": "cells/s", "cores": 1,
+                                                  "sample": f"{what}, {dt1:.1f} s"}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liborc.so")
+_SO_OMP = os.path.join(_HERE, "liborc_omp.so")
 _SRC = os.path.join(_HERE, "orc.c")
 
 W_FP64, W_FP32, W_BF16 = 0, 1, 2
@@ -30,15 +31,35 @@ DEFAULTS = dict(
 )
 
 
-def build(force: bool = False) -> str:
-    """Compile orc.c into liborc.so next to it (no FMA contraction)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+def _compile(so: str, extra: list, force: bool) -> str:
+    if force or not os.path.exists(so) or os.path.getmtime(so) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "orc.h"))):
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", _SO + ".tmp", _SRC, "-lm"]
+               *extra, "-shared", "-o", so + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(_SO + ".tmp", _SO)
-    return _SO
+        os.replace(so + ".tmp", so)
+    return so
+
+
+def build(force: bool = False) -> str:
+    """Compile orc.c into liborc.so next to it (single-threaded, no FMA
+    contraction): the oracle every test compares with."""
+    return _compile(_SO, [], force)
+
+
+def build_parallel(force: bool = False) -> str:
+    """The same source built with OpenMP (liborc_omp.so): its parallel loops
+    write disjoint outputs with unchanged arithmetic, so it returns the same
+    bits as liborc.so.  Used only to time the oracle on all host cores."""
+    return _compile(_SO_OMP, ["-fopenmp"], force)
+
+
+def host_cores() -> int:
+    """Host cores this process may run on (the OpenMP build's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class _Netlist(C.Structure):
@@ -62,14 +83,19 @@ class _Params(C.Structure):
                 ("clamp", C.c_int32)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = C.CDLL(_SO)
+def lib(parallel: bool = False):
+    """The loaded oracle library: liborc.so, or with parallel=True the OpenMP
+    build liborc_omp.so (same results, all host cores)."""
+    L = _libs.get(parallel)
+    if L is None:
+        if parallel:
+            os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
+            L = C.CDLL(build_parallel())
+        else:
+            L = C.CDLL(build())
         vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
         L.orc_create.restype = vp
         L.orc_create.argtypes = [vp, vp, vp]
@@ -94,8 +120,8 @@ def lib():
         L.orc_store.restype = dbl
         L.orc_store.argtypes = [dbl, C.c_int]
         _ = i64
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return L
 
 
 def _p(a):
@@ -150,28 +176,29 @@ class OracleError(RuntimeError):
 class Oracle:
     """One netlist's static graph plus the current augmented graph."""
 
-    def __init__(self, nl, **params):
+    def __init__(self, nl, parallel=False, **params):
         self.nl = nl
+        self._L = lib(parallel)
         self._arr = _NetlistArrays(nl)
         self.params = make_params(**params)
         err = C.c_int(0)
-        self._g = lib().orc_create(C.byref(self._arr.struct), C.byref(self.params), C.byref(err))
+        self._g = self._L.orc_create(C.byref(self._arr.struct), C.byref(self.params), C.byref(err))
         if not self._g:
             raise OracleError(err.value, "create")
         s = np.zeros(16, np.int64)
-        lib().orc_sizes(self._g, s.ctypes.data)
+        self._L.orc_sizes(self._g, s.ctypes.data)
         (self.C, self.Pm, self.S, self.Mm, self.NB, self.Nst, self.N, self.nnz_static) = \
             (int(v) for v in s[:8])
         self.hx, self.hy = int(s[9]), int(s[10])
 
     def __del__(self):
         if getattr(self, "_g", None):
-            lib().orc_destroy(self._g)
+            self._L.orc_destroy(self._g)
             self._g = None
 
     def sizes(self):
         s = np.zeros(16, np.int64)
-        lib().orc_sizes(self._g, s.ctypes.data)
+        self._L.orc_sizes(self._g, s.ctypes.data)
         return s
 
     def static_csr(self):
@@ -181,7 +208,7 @@ class Oracle:
         we = np.zeros(max(nnz, 1), np.float64)
         ws = np.zeros(max(nnz, 1), np.float64)
         bw = np.zeros(max(self.C, 1), np.float64)
-        lib().orc_static_export(self._g, rp.ctypes.data, col.ctypes.data, we.ctypes.data,
+        self._L.orc_static_export(self._g, rp.ctypes.data, col.ctypes.data, we.ctypes.data,
                                 ws.ctypes.data, bw.ctypes.data)
         return dict(rp=rp, col=col[:nnz], w_exact=we[:nnz], w_store=ws[:nnz], base_w=bw[:self.C])
 
@@ -190,14 +217,14 @@ class Oracle:
         nk = np.zeros(N, np.uint8)
         fx, fy, hw, hh = (np.zeros(N) for _ in range(4))
         pn = np.zeros(max(self.nl.num_pins, 1), np.int32)
-        lib().orc_nodes_export(self._g, nk.ctypes.data, fx.ctypes.data, fy.ctypes.data,
+        self._L.orc_nodes_export(self._g, nk.ctypes.data, fx.ctypes.data, fy.ctypes.data,
                                hw.ctypes.data, hh.ctypes.data, pn.ctypes.data)
         return dict(nkind=nk, fx=fx, fy=fy, hw=hw, hh=hh, pin_node=pn[:self.nl.num_pins])
 
     def build_hints(self, gx, gy, check=True):
         gx = np.ascontiguousarray(gx, np.float64)
         gy = np.ascontiguousarray(gy, np.float64)
-        err = lib().orc_build_hints(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data)
+        err = self._L.orc_build_hints(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data)
         if err and check:
             raise OracleError(err, "build_hints")
         return err
@@ -214,7 +241,7 @@ class Oracle:
         nb = max(self.NB, 1)
         Db, Cb, phi = np.zeros(nb), np.zeros(nb), np.zeros(nb)
         cb = np.zeros(max(self.C, 1), np.int32)
-        lib().orc_merged_export(self._g, rp.ctypes.data, col.ctypes.data, w.ctypes.data,
+        self._L.orc_merged_export(self._g, rp.ctypes.data, col.ctypes.data, w.ctypes.data,
                                 deg.ctypes.data, C.byref(lam), Db.ctypes.data, Cb.ctypes.data,
                                 phi.ctypes.data, cb.ctypes.data)
         return dict(rp=rp, col=col[:nnz], w=w[:nnz], deg=deg, lam_up=lam.value,
@@ -223,21 +250,21 @@ class Oracle:
     def hr_steps(self, k, x):
         x = np.ascontiguousarray(x, np.float64)
         y = np.zeros(self.N)
-        lib().orc_hr_steps(self._g, int(k), x.ctypes.data, y.ctypes.data)
+        self._L.orc_hr_steps(self._g, int(k), x.ctypes.data, y.ctypes.data)
         return y
 
     def filter(self, gx, gy):
         gx = np.ascontiguousarray(gx, np.float64)
         gy = np.ascontiguousarray(gy, np.float64)
         ox, oy = np.zeros(self.N), np.zeros(self.N)
-        lib().orc_filter(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data,
+        self._L.orc_filter(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data,
                          ox.ctypes.data, oy.ctypes.data)
         return ox, oy
 
     def gift_band(self, sigma, k, x):
         x = np.ascontiguousarray(x, np.float64)
         y = np.zeros(self.N)
-        err = lib().orc_gift_band(self._g, float(sigma), int(k), x.ctypes.data, y.ctypes.data)
+        err = self._L.orc_gift_band(self._g, float(sigma), int(k), x.ctypes.data, y.ctypes.data)
         if err:
             raise OracleError(err, "gift_band")
         return y
@@ -246,7 +273,7 @@ class Oracle:
         gx = np.ascontiguousarray(gx, np.float64)
         gy = np.ascontiguousarray(gy, np.float64)
         ox, oy = np.zeros(self.N), np.zeros(self.N)
-        err = lib().orc_gift(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data,
+        err = self._L.orc_gift(self._g, C.byref(self.params), gx.ctypes.data, gy.ctypes.data,
                              ox.ctypes.data, oy.ctypes.data)
         if err:
             raise OracleError(err, "gift")
@@ -255,24 +282,24 @@ class Oracle:
     def init_signal(self, seed, xy0=None):
         gx, gy = np.zeros(self.N), np.zeros(self.N)
         x0 = None if xy0 is None else np.ascontiguousarray(xy0, np.float32)
-        lib().orc_init_signal(self._g, C.c_uint64(seed), _p(x0), gx.ctypes.data, gy.ctypes.data)
+        self._L.orc_init_signal(self._g, C.c_uint64(seed), _p(x0), gx.ctypes.data, gy.ctypes.data)
         return gx, gy
 
     def run(self, seed, xy0=None, check=True):
         gx, gy = np.zeros(self.N), np.zeros(self.N)
         x0 = None if xy0 is None else np.ascontiguousarray(xy0, np.float32)
-        err = lib().orc_run(self._g, C.byref(self.params), C.c_uint64(seed), _p(x0),
+        err = self._L.orc_run(self._g, C.byref(self.params), C.c_uint64(seed), _p(x0),
                             gx.ctypes.data, gy.ctypes.data)
         if err and check:
             raise OracleError(err, "run")
         return gx, gy
 
 
-def hpwl(nl, cx, cy) -> float:
+def hpwl(nl, cx, cy, parallel=False) -> float:
     a = _NetlistArrays(nl)
     cx = np.ascontiguousarray(cx, np.float64)
     cy = np.ascontiguousarray(cy, np.float64)
-    return lib().orc_hpwl(C.byref(a.struct), cx.ctypes.data, cy.ctypes.data)
+    return lib(parallel).orc_hpwl(C.byref(a.struct), cx.ctypes.data, cy.ctypes.data)
 
 
 def exp(x: float) -> float:

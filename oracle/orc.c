@@ -13,6 +13,18 @@
  */
 #include "orc.h"
 
+/* Built twice: without OpenMP (liborc.so, the single-threaded oracle the
+ * tests compare with) and with it (liborc_omp.so, timed as the all-cores CPU
+ * baseline).  OMP_FOR marks only loops whose iterations write disjoint outputs
+ * with the same arithmetic per element, so both builds give the same bits. */
+#ifdef _OPENMP
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#define OMP_FOR_DYN _Pragma("omp parallel for schedule(dynamic, 64)")
+#else
+#define OMP_FOR
+#define OMP_FOR_DYN
+#endif
+
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -619,6 +631,7 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
     int64_t k = 2 * (int64_t)g->cell_bin[i] + (g->base_w[i] > 0.0 ? 0 : 1);
     area[bcnt[k] + fillp[k]++] = (double)g->cw[i] * (double)g->ch[i];
   }
+  OMP_FOR_DYN
   for (int32_t b = 0; b < g->NB; ++b) {
     int64_t a0 = bcnt[2 * (int64_t)b], a1 = bcnt[2 * (int64_t)b + 2];
     g->Db[b] = blocked_sum(area + a0, a1 - a0) / g->abin;
@@ -660,6 +673,7 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
   g->w = (double *)xcalloc(nnz, sizeof(double));
   g->deg = (double *)xcalloc(N, sizeof(double));
   int64_t *cur = (int64_t *)xcalloc(N, sizeof(int64_t));
+  OMP_FOR_DYN
   for (int64_t v = 0; v < N; ++v) {
     cur[v] = g->rp[v];
     if (v < Nst)
@@ -708,7 +722,8 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
   free(cur);
   free(hcnt);
 
-  double lam = 0.0;
+  double *gersh = (double *)xcalloc(N, sizeof(double));
+  OMP_FOR_DYN
   for (int64_t v = 0; v < N; ++v) {
     double d = 0.0, a = 0.0;
     for (int64_t k = g->rp[v]; k < g->rp[v + 1]; ++k) {
@@ -716,9 +731,12 @@ int orc_build_hints(orc_graph *g, const orc_params *pr, const double *gx, const 
       a += fabs(g->w[k]);
     }
     g->deg[v] = d;
-    double gb = d + a;
-    if (gb > lam || v == 0) lam = gb;
+    gersh[v] = d + a;
   }
+  double lam = 0.0;
+  for (int64_t v = 0; v < N; ++v)
+    if (gersh[v] > lam || v == 0) lam = gersh[v];
+  free(gersh);
   g->lam_up = lam;
   g->have_hints = 1;
   if (!(lam > 0.0) || !isfinite(lam)) return ORC_ERR_SPECTRUM;
@@ -745,6 +763,7 @@ void orc_merged_export(const orc_graph *g, int64_t *rp, int32_t *col, double *w,
  * refinement filter H_r = ((lambda_up I - L_hint)/lambda_up)^k, Sec. V). */
 static void hr_step(const orc_graph *g, const double *x, double *y) {
   const double lam = g->lam_up;
+  OMP_FOR_DYN
   for (int64_t v = 0; v < g->N; ++v) {
     double s = 0.0;
     for (int64_t k = g->rp[v]; k < g->rp[v + 1]; ++k) s += g->w[k] * x[g->col[k]];
@@ -800,11 +819,13 @@ void orc_filter(const orc_graph *g, const orc_params *pr, const double *gx, cons
     s = ay; ay = by; by = s;
     if (pr->pin_every_step) repin(g, ax, ay);
     for (int j = 0; j < pr->ntaps; ++j)
-      if (pr->tap_k[j] == t)
+      if (pr->tap_k[j] == t) {
+        OMP_FOR
         for (int64_t v = 0; v < N; ++v) {
           tx[v] += pr->tap_alpha[j] * ax[v];
           ty[v] += pr->tap_alpha[j] * ay[v];
         }
+      }
   }
   repin(g, tx, ty);
   for (int64_t v = 0; v < N; ++v) {
@@ -832,6 +853,7 @@ int orc_gift_band(const orc_graph *g, double sigma, int k, const double *x, doub
   }
   memcpy(a, x, sizeof(double) * N);
   for (int t = 0; t < k; ++t) {
+    OMP_FOR_DYN
     for (int64_t v = 0; v < N; ++v) {
       double s = sigma * a[v] / rs[v];
       if (v < g->Nst)
@@ -941,7 +963,8 @@ out:
  * paper uses HPWL as its quality metric (Sec. VII, VIII) without restating
  * the standard definition. */
 double orc_hpwl(const orc_netlist *nl, const double *cx, const double *cy) {
-  double total = 0.0;
+  double *span = (double *)xcalloc(nl->num_nets, sizeof(double));
+  OMP_FOR_DYN
   for (int32_t e = 0; e < nl->num_nets; ++e) {
     int64_t b = nl->net_ptr[e], n = nl->net_ptr[e + 1] - b;
     if (n < 1) continue;
@@ -953,7 +976,10 @@ double orc_hpwl(const orc_netlist *nl, const double *cx, const double *cy) {
       x0 = fmin(x0, px); x1 = fmax(x1, px);
       y0 = fmin(y0, py); y1 = fmax(y1, py);
     }
-    total += (x1 - x0) + (y1 - y0);
+    span[e] = (x1 - x0) + (y1 - y0);
   }
+  double total = 0.0;
+  for (int32_t e = 0; e < nl->num_nets; ++e) total += span[e];
+  free(span);
   return total;
 }
