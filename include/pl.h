@@ -30,8 +30,11 @@
  *     fork part of their work onto it (an event recorded on the given stream)
  *     and join it back (the given stream waits on an event), so every call
  *     still completes in the order of the given stream.
- *   - The library owns the pl_graph object and the device memory inside it
- *     (allocated with cudaMalloc, freed by pl_graph_destroy).
+ *   - The library allocates no device memory.  A graph's device buffers are
+ *     carved from a workspace the caller passes to pl_build_graph (sized by
+ *     pl_workspace_size); pl_hpwl takes its own small workspace.  The
+ *     library owns only the host-side pl_graph object, freed by
+ *     pl_graph_destroy.
  *   - One pl_graph must not be used from two host threads at once.
  */
 #ifndef PL_H
@@ -108,28 +111,50 @@ typedef struct pl_graph pl_graph;
  * detection ratio 0.1, capacity 1, mu 4, one tap of order 8, clamping on. */
 void pl_params_default(pl_params *p);
 
+/* Device bytes that a graph of `nl` built with `p` may take from its
+ * workspace: an upper bound computed on the host from the netlist's sizes and
+ * the parameters (no device access).  It covers the static build (A1), any
+ * number of hint builds (each reuses the same part of the workspace), GiFt and
+ * the refinement filter, given that the macro-cell overlaps of one hint build
+ * are at most 16 per movable cell on average.  0 for a NULL or negative-size
+ * argument. */
+size_t pl_workspace_size(const pl_netlist *nl, const pl_params *p);
+
 /* A1 (+ A2/A3 when xy_nodes != NULL).  Builds the static instance graph of
- * `nl` into *g: creates the graph when *g == NULL, otherwise rebuilds it in
- * place (buffers are reused when large enough; the netlist may differ).
- * With xy_nodes (device, N pairs) it also builds the area-hint graph for that
- * placement (as pl_build_hints).  Synchronizes `stream`.
- * Errors: INVALID_ARG (netlist or params), UNSUPPORTED (a net with more than
- * 32768 pins, 2^28 or more static nodes (cells, macro pins and stars), a graph
- * row beyond 2^31 entries), OOM, CUDA, NONFINITE. */
+ * `nl` (Sec. IV problem statement, Sec. V macro pin expansion) into *g:
+ * creates the graph when *g == NULL, otherwise rebuilds it in place (the
+ * netlist may differ).  ws: device memory of ws_bytes bytes, 256-byte aligned,
+ * owned by the caller, holding every device buffer of the graph; it needs no
+ * initialisation, must stay allocated and untouched while the graph is in use,
+ * and may be released after pl_graph_destroy or after a rebuild with another
+ * workspace.  pl_workspace_size(nl, p) bytes always suffice.  With xy_nodes
+ * (device, N pairs) it also builds the area-hint graph for that placement (as
+ * pl_build_hints).  Synchronizes `stream`.
+ * Errors: INVALID_ARG (netlist, params or workspace pointer), WORKSPACE (ws_bytes
+ * too small; the message gives the bytes needed so far), UNSUPPORTED (a net
+ * with more than 32768 pins, 2^28 or more static nodes (cells, macro pins and
+ * stars), a graph row beyond 2^31 entries), OOM (host), CUDA, NONFINITE. */
 pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *xy_nodes,
-                         pl_stream stream, pl_graph **g);
+                         void *ws, size_t ws_bytes, pl_stream stream, pl_graph **g);
 
 /* Sizes of a built graph, written to host out[16]:
  *   0 num_cells  1 macro pin nodes  2 star nodes  3 macros  4 bins
  *   5 static nodes  6 N (all nodes)  7 static nnz  8 augmented nnz (0 before
  *   the first hint build)  9 window half-width x  10 half-width y
- *   11 long (hub-path) rows  12 movable cells */
+ *   11 long (hub-path) rows  12 movable cells  13 workspace bytes used at
+ *   most so far  14 workspace bytes given  15 bytes held by the static build
+ *   (hint builds start above them) */
 pl_status pl_graph_info(const pl_graph *g, int64_t *out);
 
 /* A2 + A3 for the node placement xy_nodes (device, N pairs): bin densities
  * and phi_b, macro and bin hint edges, the augmented signed graph, degrees and
- * lambda_up.  Synchronizes `stream`.  Errors: NONFINITE (a movable cell
- * coordinate), SPECTRUM (lambda_up <= 0), OOM, CUDA. */
+ * lambda_up (Sec. V).  The bin hints are kept without stored columns: each
+ * hint cell's detection-window weights as one block, the bin rows as their
+ * transpose (pl_graph_export writes them out as ordinary entries).  Its
+ * buffers come from the graph's workspace, above the static build's part.
+ * Synchronizes `stream`.  Errors: NONFINITE (a movable cell coordinate),
+ * SPECTRUM (lambda_up <= 0), UNSUPPORTED (more than 16 macro-cell overlaps
+ * per movable cell), WORKSPACE, CUDA. */
 pl_status pl_build_hints(pl_graph *g, const pl_params *p, const float *xy_nodes,
                          pl_stream stream);
 

@@ -70,7 +70,8 @@ def lib():
                                       C.c_size_t)
         sigs = {
             "pl_params_default": (None, [vp]),
-            "pl_build_graph": (C.c_int, [vp, vp, vp, vp, vp]),
+            "pl_workspace_size": (sz, [vp, vp]),
+            "pl_build_graph": (C.c_int, [vp, vp, vp, vp, sz, vp, vp]),
             "pl_graph_info": (C.c_int, [vp, vp]),
             "pl_build_hints": (C.c_int, [vp, vp, vp, vp]),
             "pl_filter_apply": (C.c_int, [vp, vp, vp, vp, vp]),
@@ -157,11 +158,13 @@ class DeviceNetlist:
 
 
 class Graph:
-    """A pl_graph handle (library-owned device memory)."""
+    """A pl_graph handle and the workspace tensor that holds its device
+    memory (the library allocates none)."""
 
-    def __init__(self, handle: C.c_void_p, netlist: DeviceNetlist):
+    def __init__(self, handle: C.c_void_p, netlist: DeviceNetlist, ws=None):
         self._h = handle
         self.netlist = netlist
+        self.ws = ws
 
     def __del__(self):
         self.destroy()
@@ -179,7 +182,8 @@ class Graph:
         out = np.zeros(16, np.int64)
         _check(lib().pl_graph_info(self._h, out.ctypes.data))
         keys = ["num_cells", "macro_pins", "stars", "macros", "bins", "static_nodes", "N",
-                "static_nnz", "nnz", "hx", "hy", "hub_rows", "movable"]
+                "static_nnz", "nnz", "hx", "hy", "hub_rows", "movable", "ws_peak", "ws_bytes",
+                "ws_static"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def export_static(self) -> dict:
@@ -210,16 +214,37 @@ class Graph:
                     phi=phi, cell_bin=cb[:c])
 
 
+def pl_workspace_size(dnl: DeviceNetlist, prm: PlParams) -> int:
+    return int(lib().pl_workspace_size(C.byref(dnl.struct), C.byref(prm)))
+
+
+def workspace(nbytes: int, device="cuda"):
+    """A device workspace (a torch allocation, 256-byte aligned)."""
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
 def pl_build_graph(dnl: DeviceNetlist, prm: PlParams, xy_nodes=None, stream=None,
-                   graph: Graph | None = None) -> Graph:
+                   graph: Graph | None = None, ws=None) -> Graph:
+    """Builds (or, given `graph`, rebuilds in place) a graph in the device
+    workspace `ws`: by default the graph's current one when large enough,
+    else a new torch allocation of pl_workspace_size bytes."""
+    if ws is None:
+        need = pl_workspace_size(dnl, prm)
+        if graph is not None and graph.ws is not None and graph.ws.numel() >= need:
+            ws = graph.ws
+        else:
+            ws = workspace(need, dnl.cell_w.device)
     h = graph.handle if graph is not None else C.c_void_p(None)
-    _check(lib().pl_build_graph(C.byref(dnl.struct), C.byref(prm), _ptr(xy_nodes), _stream(stream),
+    _check(lib().pl_build_graph(C.byref(dnl.struct), C.byref(prm), _ptr(xy_nodes), _ptr(ws),
+                                C.c_size_t(ws.numel() * ws.element_size()), _stream(stream),
                                 C.byref(h)))
     if graph is not None:
         graph._h = h
         graph.netlist = dnl
+        graph.ws = ws
         return graph
-    return Graph(h, dnl)
+    return Graph(h, dnl, ws)
 
 
 def pl_build_hints(g: Graph, prm: PlParams, xy_nodes, stream=None):

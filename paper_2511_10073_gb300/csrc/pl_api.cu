@@ -64,9 +64,22 @@ void set_error(const char *fmt, ...) {
 }
 
 pl_status cuda_fail(cudaError_t e, const char *what) {
+  const Arena *a = current_arena();
+  if (e == cudaErrorMemoryAllocation && a && a->short_need) {
+    set_error("workspace too small: %zu bytes needed so far, %zu given (%s)", a->short_need,
+              a->cap, what);
+    return PL_ERR_WORKSPACE;
+  }
   set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
   return e == cudaErrorMemoryAllocation ? PL_ERR_OOM : PL_ERR_CUDA;
 }
+
+// An entry point's use of a graph's workspace: the arena becomes the calling
+// thread's current one, with no shortfall recorded yet.
+struct GraphScope {
+  ArenaScope scope;
+  explicit GraphScope(pl_graph *g) : scope(&g->arena) { g->arena.short_need = 0; }
+};
 
 int hpwl_blocks(int32_t M);
 size_t hpwl_ws_bytes(int32_t M);
@@ -123,25 +136,7 @@ static void destroy(pl_graph *g) {
   }
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
-  Buf *bufs[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node, &g->nd,
-                 &g->net_p, &g->star_of, &g->star_net, &g->star_p, &g->macro_cell, &g->cell_macro, &g->srp,
-                 &g->base_w, &g->hflag, &g->nkind, &g->fixedp,
-                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo, &g->hubf, &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3], &g->cell_bin, &g->n_ovl,
-                 &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff, &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem,
-                 &g->Db, &g->phi, &g->hlen, &g->slen, &g->llen, &g->clen, &g->lflag,
-                 &g->crank, &g->tpos, &g->mac_base,
-                 &g->bin_base, &g->hubtmp, &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub,
-                 &g->acc, &g->gsc, &g->q4a, &g->q4b, &g->status, &g->stage, &g->star_w, &g->scr.buf};
-  for (Buf *b : bufs) release(*b);
-  for (Buf &b : g->tmp) release(b);
-  SpMat *ms[] = {&g->st, &g->hm};
-  for (SpMat *m : ms) {
-    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
-                 &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->longidx,
-                 &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part};
-    for (Buf *b : mb) release(*b);
-  }
-  delete g;
+  delete g;  // its device memory is the caller's workspace
 }
 
 pl_status read_status(pl_graph *g, cudaStream_t s) {
@@ -191,9 +186,10 @@ void pl_params_default(pl_params *p) {
 const char *pl_last_error(void) { return pl::g_err; }
 
 pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *xy_nodes,
-                         pl_stream stream, pl_graph **gp) {
+                         void *ws, size_t ws_bytes, pl_stream stream, pl_graph **gp) {
   pl::g_err[0] = 0;
   if (!gp) { set_error("graph out-pointer is NULL"); return PL_ERR_INVALID_ARG; }
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) { set_error("workspace must be a 256-byte aligned device pointer"); return PL_ERR_INVALID_ARG; }
   pl_status st = check_netlist(nl);
   if (st == PL_OK) st = check_params(p);
   if (st != PL_OK) return st;
@@ -203,9 +199,21 @@ pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *
     *gp = new (std::nothrow) pl_graph();
     if (!*gp) { set_error("host allocation failed"); return PL_ERR_OOM; }
     created = true;
+  } else if ((*gp)->stream) {
+    // the previous build's work on its streams ends before its memory is reused
+    cudaStreamSynchronize((*gp)->stream);
+    if ((*gp)->side) cudaStreamSynchronize((*gp)->side);
   }
-  st = build_static(*gp, nl, p, s);
-  if (st == PL_OK && xy_nodes) st = build_hints(*gp, p, xy_nodes, s);
+  pl_graph *g = *gp;
+  for_each_buf(g, 0, [](Buf &b) { release(b); });
+  g->arena = Arena{};
+  g->arena.base = static_cast<char *>(ws);
+  g->arena.cap = ws_bytes;
+  g->hint_mark = 0;
+  g->star_w_ok = false;
+  GraphScope scope(g);
+  st = build_static(g, nl, p, s);
+  if (st == PL_OK && xy_nodes) st = build_hints(g, p, xy_nodes, s);
   if (st == PL_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_fail(e, "pl_build_graph");
@@ -222,9 +230,14 @@ pl_status pl_graph_info(const pl_graph *g, int64_t *out) {
   for (int k = 0; k < 16; ++k) out[k] = 0;
   out[0] = g->C; out[1] = g->Pm; out[2] = g->S; out[3] = g->Mm; out[4] = g->NB;
   out[5] = g->Nst; out[6] = g->N; out[7] = (int64_t)g->nnz_static;
-  out[8] = g->have_hints ? (int64_t)(g->st.nnz_s + g->st.nnz_l + g->hm.nnz_s + g->hm.nnz_l) : 0;
+  out[8] = g->have_hints
+               ? (int64_t)(g->st.nnz_s + g->st.nnz_l + g->hm.nnz_s + g->hm.nnz_l) + 2 * g->nslot
+               : 0;
   out[9] = g->hx; out[10] = g->hy; out[11] = g->have_hints ? g->hm.nlong : 0;
   out[12] = g->nmov;
+  out[13] = (int64_t)g->arena.peak;
+  out[14] = (int64_t)g->arena.cap;
+  out[15] = (int64_t)g->hint_mark;
   return PL_OK;
 }
 
@@ -235,6 +248,7 @@ pl_status pl_build_hints(pl_graph *g, const pl_params *p, const float *xy_nodes,
   pl_status st = check_params(p);
   if (st == PL_OK) st = same_layout(g, p);
   if (st != PL_OK) return st;
+  GraphScope scope(g);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
   return build_hints(g, p, xy_nodes, s);
@@ -248,6 +262,7 @@ pl_status pl_filter_apply(pl_graph *g, const pl_params *p, const float *xy_in, f
   if (st == PL_OK) st = same_layout(g, p);
   if (st != PL_OK) return st;
   if (!g->have_hints) { set_error("no augmented graph: call pl_build_hints first"); return PL_ERR_INVALID_ARG; }
+  GraphScope scope(g);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
   cudaError_t e = cudaMemsetAsync(g->status.p, 0, 32, s);
@@ -263,6 +278,7 @@ pl_status pl_gift(pl_graph *g, const pl_params *p, const float *xy_in, float *xy
   pl_status st = check_params(p);
   if (st == PL_OK) st = same_layout(g, p);
   if (st != PL_OK) return st;
+  GraphScope scope(g);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
   cudaError_t e = cudaMemsetAsync(g->status.p, 0, 32, s);
@@ -275,6 +291,7 @@ pl_status pl_init_signal(pl_graph *g, uint64_t seed, const float *xy0_cells, flo
                          pl_stream stream) {
   pl::g_err[0] = 0;
   if (!g || !xy_nodes) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
+  GraphScope scope(g);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
   return run_init_signal(g, seed, xy0_cells, xy_nodes, s);
@@ -292,6 +309,7 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
   pl_status st = check_params(p);
   if (st == PL_OK) st = same_layout(g, p);
   if (st != PL_OK) return st;
+  GraphScope scope(g);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   g->stream = s;
   const int64_t N = g->N;
@@ -396,16 +414,60 @@ static void row_range(const HostSplit &h, int64_t v, uint64_t *a, uint64_t *b) {
 // Rows in canonical order: the st piece, then (augmented graph) the hm piece;
 // a row kept in another order on the device (bin rows are the concatenation
 // of their window bins' lists) is sorted by column.
+// The augmented graph's bin entries are stored without columns: each hint
+// cell's window block of W slots (slot s = (dy + hy)(2 hx + 1) + (dx + hx)
+// for the bin at offset (dx, dy) from the cell's bin), and the bin rows are
+// its transpose.  The export writes them out as explicit entries.
+struct HostWindows {
+  std::vector<int32_t> hbin;            // bin of each hint cell, -1 otherwise
+  std::vector<float> w;                 // [C * W] slot weights
+  std::vector<std::vector<std::pair<int32_t, float>>> bins;  // bin rows, ascending cell
+};
+
+static cudaError_t fetch_windows(const pl_graph *g, HostWindows &hw) {
+  const size_t C = (size_t)g->C, W = (size_t)g->W;
+  hw.hbin.resize(C);
+  hw.w.assign(C * W, 0.f);
+  cudaError_t e = C ? cudaMemcpy(hw.hbin.data(), g->hbin.p, C * 4, cudaMemcpyDeviceToHost)
+                    : cudaSuccess;
+  if (e != cudaSuccess || !C || !W) return e;
+  if (g->wdtype == PL_W_BF16) {
+    std::vector<uint16_t> b(C * W);
+    e = cudaMemcpy(b.data(), g->hbw.p, C * W * 2, cudaMemcpyDeviceToHost);
+    for (size_t k = 0; k < C * W; ++k) {
+      const uint32_t u = (uint32_t)b[k] << 16;
+      memcpy(&hw.w[k], &u, 4);
+    }
+  } else {
+    e = cudaMemcpy(hw.w.data(), g->hbw.p, C * W * 4, cudaMemcpyDeviceToHost);
+  }
+  hw.bins.assign((size_t)g->NB, {});
+  for (size_t i = 0; i < C; ++i) {
+    const int hb = hw.hbin[i];
+    if (hb < 0) continue;
+    const int bx = hb % g->nbx, by = hb / g->nbx, wx = 2 * g->hx + 1;
+    for (size_t sl = 0; sl < W; ++sl) {
+      const int xx = bx + (int)(sl % wx) - g->hx, yy = by + (int)(sl / wx) - g->hy;
+      if (xx < 0 || yy < 0 || xx >= g->nbx || yy >= g->nby) continue;
+      hw.bins[(size_t)yy * g->nbx + xx].emplace_back((int32_t)i, hw.w[i * W + sl]);
+    }
+  }
+  return e;
+}
+
 static pl_status export_matrix(const pl_graph *g, const SpMat &st, const SpMat *hm, int64_t rows,
                                int64_t *rp, int32_t *col, double *w, double *deg) {
   cudaStream_t s = g->stream;
   HostSplit hs, hh;
+  HostWindows hw;
   cudaError_t e = fetch_split(g, st, hs, s);
   if (e == cudaSuccess && hm) e = fetch_split(g, *hm, hh, s);
+  if (e == cudaSuccess && hm) e = fetch_windows(g, hw);
   std::vector<dfl> ds(st.N);
   if (e == cudaSuccess && deg)
     e = cudaMemcpy(ds.data(), (hm ? hm->dsum : st.dsum).p, st.N * 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "export");
+  const int64_t bn0 = g->Nst + g->Mm;
   std::vector<std::pair<int32_t, float>> ent;
   int64_t o = 0;
   for (int64_t v = 0; v < rows; ++v) {
@@ -416,6 +478,16 @@ static pl_status export_matrix(const pl_graph *g, const SpMat &st, const SpMat *
     if (hm) {
       row_range(hh, v, &a, &b);
       for (uint64_t k = a; k < b; ++k) ent.emplace_back(hh.col[k], hh.w[k]);
+      if (v < g->C && hw.hbin[v] >= 0) {
+        const int hb = hw.hbin[v], bx = hb % g->nbx, by = hb / g->nbx, wx = 2 * g->hx + 1;
+        for (int sl = 0; sl < g->W; ++sl) {
+          const int xx = bx + sl % wx - g->hx, yy = by + sl / wx - g->hy;
+          if (xx < 0 || yy < 0 || xx >= g->nbx || yy >= g->nby) continue;
+          ent.emplace_back((int32_t)(bn0 + (int64_t)yy * g->nbx + xx), hw.w[(size_t)v * g->W + sl]);
+        }
+      } else if (v >= bn0 && v < bn0 + g->NB) {
+        for (auto &pr : hw.bins[v - bn0]) ent.push_back(pr);
+      }
     }
     auto by_col = [](const std::pair<int32_t, float> &x, const std::pair<int32_t, float> &y) {
       return x.first < y.first;

@@ -263,11 +263,30 @@ bool prof_on();
 void prof_begin(cudaStream_t s, int kind, double bytes);
 void prof_end(cudaStream_t s);
 
+// Device memory of a graph comes from the caller's workspace: an arena that
+// hands out 256-byte aligned pieces in order and never frees one.  A Buf
+// grows by taking a new piece (its old piece is abandoned until the arena is
+// reset).  The arena in use is the calling thread's current one, set by
+// ArenaScope for the duration of an entry point.
 struct Buf {
   void *p = nullptr;
   size_t bytes = 0;
 };
-cudaError_t ensure(Buf &b, size_t bytes);  // grow-only (contents not kept)
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, used = 0, peak = 0;
+  size_t short_need = 0;  // offset + bytes of a request that did not fit (0: none)
+};
+Arena *&current_arena();
+struct ArenaScope {
+  Arena *prev;
+  explicit ArenaScope(Arena *a) : prev(current_arena()) { current_arena() = a; }
+  ~ArenaScope() { current_arena() = prev; }
+};
+// Gives b at least `bytes` (contents not kept when it grows).  Fails with
+// cudaErrorMemoryAllocation, and records the shortfall in the arena, when the
+// workspace is too small.
+cudaError_t ensure(Buf &b, size_t bytes);
 
 // Several small device values to the host with one synchronisation: each is
 // copied device to device (asynchronously) into the staging buffer, then one
@@ -278,19 +297,12 @@ struct D2H {
   size_t n;  // bytes, at most 64 each
 };
 cudaError_t d2h_many(Buf &stage, const D2H *items, int count, cudaStream_t s);
-void release(Buf &b);
+void release(Buf &b);  // forgets the piece (the arena's memory is the caller's)
 template <typename T>
 inline T *P(Buf &b) { return reinterpret_cast<T *>(b.p); }
 template <typename T>
 inline const T *P(const Buf &b) { return reinterpret_cast<const T *>(b.p); }
 
-// Scratch arena for scans and sorts (grow-only).
-struct Scratch {
-  Buf buf;
-  size_t used = 0;
-  void reset() { used = 0; }
-  void *take(size_t bytes);  // 256-byte aligned; nullptr if it does not fit
-};
 
 inline int grid_for(long long n, int per_block, int cap = 152 * 64) {
   long long g = (n + per_block - 1) / per_block;

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "pl_bins.cuh"
 #include "pl_internal.h"
 
 namespace pl {
@@ -81,6 +82,21 @@ struct StepArgs {
   double alpha2;
   const float4 *x4;
   float4 *y4;
+  // refinement filter: bin hints without stored columns.  A hint cell v
+  // (hbin[v] >= 0) has W window-slot weights hbw[v W + s] towards the bin
+  // nodes bn0 + hbin[v] + offset(s); bin rows are the transposes, summed from
+  // chunk partials (bpart) of the bins' hint buckets.
+  const void *hbw;
+  const void *hbwq;  // the same blocks in bucket-list order
+  const int32_t *hbin;
+  int32_t C;
+  int64_t bn0;
+  BinGeo B;
+  const int32_t *bchunk;
+  const int32_t *cown;
+  const int64_t *boff;
+  const uint32_t *blist;
+  float4 *bpart;
 };
 
 // Epilogue of node v with its kind kd and (tap steps) accumulator ac loaded
@@ -317,6 +333,53 @@ __device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uin
   }
 }
 
+// Window slots of hint cell v (refinement filter): lane m of the row's group
+// takes slots m, m + L, ...; the column of a slot is the bin node at the
+// cell's bin plus the slot's offset, skipped outside the bin grid.  Like the
+// stored entries, kRowUnroll weights are loaded before their gathers of x.
+template <int WT, int L>
+__device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int m, float &sx,
+                                           float &sy) {
+  const int hb = A.hbin[v];
+  if (hb < 0) return;
+  const int nbx = A.B.nbx, wx = 2 * A.B.hx + 1, W = A.B.W;
+  const int bx = hb % nbx, by = hb / nbx;
+  // window position (ix, iy) of slot s, advanced by L slots at a time
+  int iy = m / wx, ix = m - iy * wx;
+  const float *wf = reinterpret_cast<const float *>(A.hbw) + (size_t)v * W;
+  const unsigned short *wh = reinterpret_cast<const unsigned short *>(A.hbw) + (size_t)v * W;
+  for (int s0 = m; s0 < W; s0 += kRowUnroll * L) {
+    int cb[kRowUnroll];
+    float wv[kRowUnroll];
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      const int sl = s0 + u * L;
+      cb[u] = -1;
+      wv[u] = 0.f;
+      if (sl < W) {
+        const int xx = bx + ix - A.B.hx, yy = by + iy - A.B.hy;
+        if (xx >= 0 && yy >= 0 && xx < nbx && yy < A.B.nby) {
+          cb[u] = yy * nbx + xx;
+          wv[u] = WT == 0 ? __ldcs(wf + sl) : __uint_as_float((uint32_t)__ldcs(wh + sl) << 16);
+        }
+        ix += L;
+        while (ix >= wx) {
+          ix -= wx;
+          ++iy;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      if (cb[u] >= 0) {
+        const float2 xv = __ldg(A.x + A.bn0 + cb[u]);
+        sx = fmaf(wv[u], xv.x, sx);
+        sy = fmaf(wv[u], xv.y, sy);
+      }
+    }
+  }
+}
+
 template <int WT, int MODE>
 __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
   const int64_t N = A.nrows;
@@ -345,7 +408,10 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
     float sx = 0.f, sy = 0.f;
     if (live) {
       row_piece<WT, L>(A.scol, A.sw, sa + m, sb, A.x, sx, sy);
-      if (two) row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
+      if (two) {
+        row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
+        if (MODE == MODE_HR && v < A.C) slot_piece<WT, L>(A, v, m, sx, sy);
+      }
     }
 #pragma unroll
     for (int d = 1; d < L; d <<= 1) {
@@ -360,6 +426,124 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
       const double acv = A.tap ? reinterpret_cast<const double *>(A.acc)[2 * v + m] : 0.0;
       epilogue_c(A, v, A.nkind[v], m, acv, av * xr + bv * (m ? sy : sx));
     }
+  }
+}
+
+// Short rows, streamed: a warp takes a tile of 32 consecutive rows.  Their
+// static entries are contiguous in st's short region, so the warp walks them
+// 32 at a time with coalesced index and weight loads (one entry per lane),
+// gathers x, and adds each row's products with a segmented scan over the
+// lanes; the last lane of a row's run in the window adds the run to the row's
+// sum in shared memory (runs in window order, so the sums are a fixed
+// function of the inputs).  Then lane j finishes row j of the tile: its hint
+// entries and window slots (refinement filter), the combine, and the epilogue
+// for both coordinates.  Hub rows are skipped (their own launches).
+constexpr int kTileRows = 32;
+constexpr int kTileWin = 4;  // windows of 32 entries whose loads are in flight together
+
+template <int WT, int MODE>
+__global__ void __launch_bounds__(kRowThreads) k_spmm_tiles(StepArgs A) {
+  __shared__ int32_t s_rid[kRowThreads / 32][32];
+  __shared__ float2 s_acc[kRowThreads / 32][kTileRows];
+  const int64_t N = A.nrows;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t *rid = s_rid[wid];
+  float2 *acc = s_acc[wid];
+  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
+  const bool two = A.hrp != nullptr;
+  for (long long r0 = gw * kTileRows; r0 < N; r0 += nw * kTileRows) {
+    const long long v = r0 + lane;
+    const bool inr = v < N;
+    // row j's static range (lane j), and the tile's whole range
+    const uint32_t a0 = inr ? (A.srp[v] & kOffMask) : 0u;
+    const uint32_t a1 = inr ? (A.srp[v + 1] & kOffMask) : 0u;
+    const long long rl = N - r0 < kTileRows ? N - r0 : kTileRows;
+    const uint32_t e0 = __shfl_sync(0xffffffffu, a0, 0);
+    const uint32_t e1 = __shfl_sync(0xffffffffu, a1, (int)rl - 1);
+    acc[lane] = make_float2(0.f, 0.f);
+    int carry = 0;  // row of the window's first entry when no row starts there
+    for (uint32_t k00 = e0; k00 < e1; k00 += 32 * kTileWin) {
+      // kTileWin windows' index and weight loads in flight, then their gathers
+      int cc[kTileWin];
+      float wv[kTileWin];
+#pragma unroll
+      for (int u = 0; u < kTileWin; ++u) {
+        const uint32_t k = k00 + 32 * u + lane;
+        cc[u] = k < e1 ? __ldcs(A.scol + k) : -1;
+        wv[u] = k < e1 ? wload<WT>(A.sw, k) : 0.f;
+      }
+      float2 xv[kTileWin];
+#pragma unroll
+      for (int u = 0; u < kTileWin; ++u)
+        xv[u] = cc[u] >= 0 ? __ldg(A.x + cc[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kTileWin; ++u) {
+        const uint32_t k0 = k00 + 32 * u;
+        if (k0 >= e1) break;
+        // rows starting in this window: a head bit at their first entry, and
+        // the row's index at that lane
+        const bool head = inr && a1 > a0 && a0 >= k0 && a0 < k0 + 32;
+        if (head) rid[a0 - k0] = lane;
+        const unsigned hm = __reduce_or_sync(0xffffffffu, head ? (1u << (a0 - k0)) : 0u);
+        __syncwarp();
+        const uint32_t k = k0 + lane;
+        float px = wv[u] * xv[u].x, py = wv[u] * xv[u].y;
+        // this lane's run: from its last head at or before it (or lane 0)
+        const unsigned le = hm & (0xffffffffu >> (31 - lane));
+        const int st = le ? 31 - __clz(le) : 0;
+        const int row = le ? rid[st] : carry;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const float ux = __shfl_up_sync(0xffffffffu, px, d);
+          const float uy = __shfl_up_sync(0xffffffffu, py, d);
+          if (lane - d >= st) {
+            px += ux;
+            py += uy;
+          }
+        }
+        // the run's last lane (the next lane starts a row, or the entries end)
+        const bool last = k < e1 && (lane == 31 || k + 1 == e1 || ((hm >> (lane + 1)) & 1u));
+        if (last) {
+          float2 t = acc[row];
+          t.x += px;
+          t.y += py;
+          acc[row] = t;
+        }
+        carry = __shfl_sync(0xffffffffu, row, 31);
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    // lane j finishes row r0 + j
+    bool live = false;
+    uint32_t ha = 0, hb = 0;
+    if (inr) {
+      if (two) {
+        const uint32_t h0 = A.hrp[v];
+        ha = h0 & kOffMask;
+        hb = A.hrp[v + 1] & kOffMask;
+        live = !(h0 & kHubFlag);
+      } else {
+        live = !(A.srp[v] & kHubFlag);
+      }
+    }
+    float2 sm = acc[lane];
+    if (live && two) {
+      row_piece<WT, 1>(A.hcol, A.hw, ha, hb, A.x, sm.x, sm.y);
+      if (MODE == MODE_HR && v < A.C) slot_piece<WT, 1>(A, v, 0, sm.x, sm.y);
+    }
+    if (live) {
+      const float av = A.a[v];
+      const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
+      const float2 xr = A.x[v];
+      const uint8_t kd = A.nkind[v];
+      double2 ac = make_double2(0.0, 0.0);
+      if (A.tap) ac = A.acc[v];
+      epilogue_c(A, v, kd, 0, ac.x, av * xr.x + bv * sm.x);
+      epilogue_c(A, v, kd, 1, ac.y, av * xr.y + bv * sm.y);
+    }
+    __syncwarp();
   }
 }
 
@@ -432,7 +616,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows4(StepArgs A) {
 // chunks, then a fixed tree); one warp then does the combines in FP64, a lane
 // per row, so the FP64 work of kHubRows rows shares its instructions.
 constexpr int kHubRows = 8;
-template <int MODE>
+template <int WT, int MODE>
 __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
   __shared__ float4 sums[kHubRows];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -447,6 +631,32 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
     }
     px = warp_sum_df(px);
     py = warp_sum_df(py);
+    if (MODE == MODE_HR) {
+      const int64_t v = A.lrow[l];
+      if (v >= A.bn0) {
+        // a bin row: its window-slot partials over the source buckets
+        dfl bx, by;
+        bin_row_sums(A.B, (int)(v - A.bn0), A.bchunk, A.bpart, &bx, &by);
+        df_add_df(px, bx);
+        df_add_df(py, by);
+      } else if (v < A.C && A.hbin[v] >= 0) {
+        // a hint cell with a hub row: its window slots, exact products
+        const int hb = A.hbin[v], bxc = hb % A.B.nbx, byc = hb / A.B.nbx;
+        dfl qx{0.f, 0.f}, qy{0.f, 0.f};
+        for (int sl = lane; sl < A.B.W; sl += 32) {
+          int dx, dy;
+          slot_off(A.B, sl, &dx, &dy);
+          const int xx = bxc + dx, yy = byc + dy;
+          if (xx < 0 || yy < 0 || xx >= A.B.nbx || yy >= A.B.nby) continue;
+          const float wv = bw_load<WT>(A.hbw, (size_t)v * A.B.W + sl);
+          const float2 xv = A.x[A.bn0 + yy * A.B.nbx + xx];
+          df_add_prod(qx, wv, xv.x);
+          df_add_prod(qy, wv, xv.y);
+        }
+        df_add_df(px, warp_sum_df(qx));
+        df_add_df(py, warp_sum_df(qy));
+      }
+    }
     if (lane == 0) sums[w] = make_float4(px.hi, px.lo, py.hi, py.lo);
   }
   __syncthreads();
@@ -624,6 +834,18 @@ static double spmm_bytes(double nnz, double N, int wdtype) {
   return nnz * (4.0 + (wdtype == PL_W_BF16 ? 2.0 : 4.0)) + (N + 1.0) * 4.0 + N * (8.0 + 8.0 + 4.0);
 }
 
+// Algorithmic bytes of one refinement product with column-free bin hints:
+// the stored entries (static, macro) once, each hint cell's window block
+// twice (its own row, and the bin rows' pass over the buckets) with the
+// bucket list once, row pointers, x read, y written, one coefficient per row.
+static double spmm_bytes_hint(const pl_graph *g) {
+  const double sw = g->wdtype == PL_W_BF16 ? 2.0 : 4.0;
+  const double stored = (double)(g->st.nnz_s + g->st.nnz_l + g->hm.nnz_s + g->hm.nnz_l);
+  const double nh = (double)g->nhint;
+  return stored * (4.0 + sw) + nh * (2.0 * g->W * sw + 4.0) + ((double)g->N + 1.0) * 4.0 +
+         (double)g->N * (8.0 + 8.0 + 4.0);
+}
+
 // One sparse product: the hub chunks and then the hub rows on the graph's
 // side stream, the short rows on the caller's stream at the same time (they
 // write disjoint rows of y); the caller's stream waits for both.
@@ -649,8 +871,8 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
     int b = 0;
-    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<1, MODE>, kRowThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<0, MODE>, kRowThreads, 0);
+    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_tiles<1, MODE>, kRowThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_tiles<0, MODE>, kRowThreads, 0);
     occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
   }
   const bool prof = prof_on();
@@ -666,18 +888,27 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     const int hgrid = (int)(want < 8LL * nsm ? want : 8LL * nsm);
     if (wi) k_spmm_hub<1, MODE><<<hgrid, 256, 0, sh>>>(A);
     else k_spmm_hub<0, MODE><<<hgrid, 256, 0, sh>>>(A);
-    k_hub_rows<MODE><<<(int)(((long long)A.nlong + kHubRows - 1) / kHubRows), kHubRows * 32, 0, sh>>>(A);
     note_launch();
+    if (MODE == MODE_HR && A.bpart) {
+      // bin rows: chunk partials of the window blocks times the cells' x
+      const int bgrid = (int)(g->nbc_max < 152LL * 8 ? g->nbc_max : 152LL * 8);
+      if (wi) k_bin_partials<1, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
+      else k_bin_partials<0, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
+      note_launch();
+    }
+    const int rgrid = (int)(((long long)A.nlong + kHubRows - 1) / kHubRows);
+    if (wi) k_hub_rows<1, MODE><<<rgrid, kHubRows * 32, 0, sh>>>(A);
+    else k_hub_rows<0, MODE><<<rgrid, kHubRows * 32, 0, sh>>>(A);
     note_launch();
     e = cudaEventRecord(g->ev_join, sh);
     if (e != cudaSuccess) return e;
   }
-  const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
+  const long long rows_per_block = (long long)(kRowThreads / 32) * kTileRows;
   const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
   const long long cap = (long long)occ[wi] * nsm;
   const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-  if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
-  else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  if (wi) k_spmm_tiles<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  else k_spmm_tiles<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
   note_launch();
   if (fork) {
     const cudaError_t e = cudaStreamWaitEvent(s, g->ev_join, 0);
@@ -742,7 +973,8 @@ static cudaError_t launch_pair(const StepArgs &A, double bytes, int wdtype, cuda
       }
       if (wi) k_spmm_hub<1, MODE_GIFT><<<hgrid, 256, 0, sh>>>(H);
       else k_spmm_hub<0, MODE_GIFT><<<hgrid, 256, 0, sh>>>(H);
-      k_hub_rows<MODE_GIFT><<<rgrid, kHubRows * 32, 0, sh>>>(H);
+      if (wi) k_hub_rows<1, MODE_GIFT><<<rgrid, kHubRows * 32, 0, sh>>>(H);
+      else k_hub_rows<0, MODE_GIFT><<<rgrid, kHubRows * 32, 0, sh>>>(H);
       note_launch();
       note_launch();
     }
@@ -973,8 +1205,23 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   const SpMat &m = g->hm;
   StepArgs A{};
   fill_matrix(A, g->st, &m);
-  const double bytes = spmm_bytes((double)(g->st.nnz_s + g->st.nnz_l + m.nnz_s + m.nnz_l),
-                                  (double)N, g->wdtype);
+  const double bytes = spmm_bytes_hint(g);
+  A.hbw = g->hbw.p;
+  A.hbwq = g->hbwq.p;
+  A.hbin = P<int32_t>(g->hbin);
+  A.C = g->C;
+  A.bn0 = g->Nst + g->Mm;
+  A.B.nbx = g->nbx;
+  A.B.nby = g->nby;
+  A.B.hx = g->hx;
+  A.B.hy = g->hy;
+  A.B.W = g->W;
+  A.B.NB = g->NB;
+  A.bchunk = P<int32_t>(g->bchunk);
+  A.cown = P<int32_t>(g->cown);
+  A.boff = P<int64_t>(g->boff);
+  A.blist = P<uint32_t>(g->blist);
+  A.bpart = P<float4>(g->bpart);
   fill_nodes(A, g);
   A.a = P<float>(m.c32);
   A.b = nullptr;

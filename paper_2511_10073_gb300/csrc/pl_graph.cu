@@ -1100,7 +1100,9 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   note_launch();
 
   // macro lookup grid
-  double gs = fmax(1.0, fmax((double)mwmax, (double)mhmax));
+  // buckets at least as large as any macro or movable cell side, so a macro
+  // is listed in at most 6 x 6 buckets (the workspace bound counts on it)
+  double gs = fmax(1.0, fmax(fmax((double)mwmax, (double)mhmax), fmax((double)wmax, (double)hmax)));
   g->gnx = (int)fmin(2048.0, fmax(1.0, ceil((g->xh - g->xl) / gs)));
   g->gny = (int)fmin(2048.0, fmax(1.0, ceil((g->yh - g->yl) / gs)));
   const long long ng = (long long)g->gnx * g->gny;
@@ -1123,6 +1125,10 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY((exclusive_scan<int32_t, int64_t>(gcnt, gptr, ng, stmp, s2)));
   int64_t nreg;
   TRY(d2h(&nreg, gptr + ng, 1, s2));
+  if (nreg > 36LL * g->Mm) {
+    set_error("macro lookup grid: %lld entries for %d macros", (long long)nreg, g->Mm);
+    return PL_ERR_UNSUPPORTED;
+  }
   TRY(ensure(g->glist, (size_t)nreg * 4 + 16));
   if (nreg >= (1LL << 31)) {
     set_error("macro lookup grid too large");
@@ -1156,6 +1162,11 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(cudaGetLastError());
   TRY(cudaStreamSynchronize(s));
   (void)kMaxNetPins;
+  {
+    pl_status fs = take_filter_buffers(g);
+    if (fs != PL_OK) return fs;
+  }
+  g->hint_mark = g->arena.used;
   return PL_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "pl_bins.cuh"
 #include "pl_internal.h"
 
 namespace pl {
@@ -306,13 +307,11 @@ __global__ void __launch_bounds__(256) k_bin_tile_count(int32_t C, int nbk, int 
 
 // Rounds of blockDim cells; inside a round the warps take turns (so equal
 // buckets keep cell order), lanes of a warp rank themselves with match_any.
-// A hint cell's place in the list goes to crank.
 __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, int ntile,
                                                           const uint8_t *ckind,
                                                           const uint8_t *hflag,
                                                           const int32_t *cell_bin,
-                                                          const int64_t *off, uint32_t *blist,
-                                                          int32_t *crank) {
+                                                          const int64_t *off, uint32_t *blist) {
   extern __shared__ int32_t run[];
   for (int k = threadIdx.x; k < nbk; k += blockDim.x) run[k] = 0;
   __syncthreads();
@@ -337,9 +336,6 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
         if (mv) {
           const long long pos = tst + before + __popc(grp & lt);
           blist[pos] = (uint32_t)i;
-          // a hint cell's place in the bucket list (its rank once the
-          // bucket's start is taken off)
-          if (!(key & 1)) crank[i] = (int32_t)pos;
         }
       }
       __syncthreads();
@@ -467,21 +463,6 @@ __global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uin
   }
 }
 
-// Length of each bin row: the hint buckets of the bin's window.
-__global__ void k_bin_hub_len(HintGeo G, const int64_t *boff, int64_t *hub_len) {
-  const int NB = G.nbx * G.nby;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
-    const int bx = b % G.nbx, by = b / G.nbx;
-    long long hl = 0;
-    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
-      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx) {
-        const int bb = yy * G.nbx + xx;
-        hl += boff[2 * bb + 1] - boff[2 * bb];
-      }
-    hub_len[b] = hl;
-  }
-}
-
 // ------------------------------------------------------- H6: row lengths
 __device__ __forceinline__ int win_count(int bx, int by, const HintGeo &G) {
   int nx = min(G.nbx - 1, bx + G.hx) - max(0, bx - G.hx) + 1;
@@ -490,13 +471,14 @@ __device__ __forceinline__ int win_count(int bx, int by, const HintGeo &G) {
 }
 
 // Per-row lengths of a split matrix.  Static mode: the st rows (hub when
-// longer than kLong).  Hint mode: the hm rows; a row is a hub row when it is a
-// virtual node or its static plus hint entries exceed kLong.  clen is the
-// length the hub chunks cover (st part + hm part).
+// longer than kLong).  Hint mode: the stored hm part of each row (a hint
+// cell's macro entries, a macro row's cells; bin rows store nothing, their
+// sums come from the window blocks); a row is a hub row when it is a virtual
+// node or its static entries, macro entries and window slots exceed kLong.
+// clen is the stored length the hub chunks cover (st part + hm part).
 __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const uint8_t *hflag,
                           const int32_t *cell_bin, const int32_t *n_ovl, const int64_t *moff,
-                          const int64_t *hub_len, uint32_t *slen, uint64_t *llen, uint8_t *lflag,
-                          uint64_t *clen) {
+                          uint32_t *slen, uint64_t *llen, uint8_t *lflag, uint64_t *clen) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < G.N;
        v += (long long)gridDim.x * blockDim.x) {
     const long long sl = v < G.Nst ? srp[v + 1] - srp[v] : 0;
@@ -508,19 +490,19 @@ __global__ void k_row_len(HintGeo G, int with_hints, const int64_t *srp, const u
       clen[v] = hub ? (uint64_t)sl : 0ull;
       continue;
     }
-    long long hl = 0;
+    long long hl = 0, ws = 0;
     bool virt = false;
     if (v < G.C && hflag[v]) {
       int b = cell_bin[v];
-      hl = n_ovl[v] + win_count(b % G.nbx, b / G.nbx, G);
+      hl = n_ovl[v];
+      ws = win_count(b % G.nbx, b / G.nbx, G);
     } else if (v >= G.mv0 && v < G.bn0) {
       hl = moff[v - G.mv0 + 1] - moff[v - G.mv0];
       virt = true;
     } else if (v >= G.bn0) {
-      hl = hub_len[v - G.bn0];
       virt = true;
     }
-    const bool hub = virt || sl + hl > kLong;
+    const bool hub = virt || sl + hl + ws > kLong;
     slen[v] = hub ? 0u : (uint32_t)hl;
     llen[v] = hub ? (uint64_t)hl : 0ull;
     lflag[v] = hub ? 1 : 0;
@@ -648,24 +630,27 @@ __device__ __forceinline__ dfl df_ratio(float x, float c, float h) {
 }
 
 // Hint part of the rows of cells, macro pins and stars (thread per row): for a
-// hint cell its macro entries (ascending macro) and window bin entries
-// (row-major), written to the row's hm place, and (tpos given) the same bin
-// entries in the bin rows; the degree sums of the whole augmented row are the
-// static ones plus the hint entries.  The window ratios |x - x_b| / (w_b / 2)
-// = |u - (2 xx + 1)|, u = 2 (x - x_l) / w_b, come from u (double-float, once
-// per cell) as exact double-float differences; macro ratios are double-float
-// quotients.  With BF16 storage FP64 only recomputes weights near a bf16
-// rounding midpoint; with FP32 storage every weight is the FP64 value of the
-// definition rounded once.
+// hint cell its macro entries (ascending macro), written to the row's hm
+// place, and the weights of its detection-window bins as a dense block of W
+// slots, slot s = (yy - by + hy) (2 hx + 1) + (xx - bx + hx) for window bin
+// (xx, yy) around the cell's bin (bx, by); slots outside the bin grid hold 0.
+// The column of a slot is implicit (the bin node of that window position), and
+// the bin rows are the transpose of these blocks (k_bin_partials).  The degree
+// sums of the whole augmented row are the static ones plus the hint entries.
+// The window ratios |x - x_b| / (w_b / 2) = |u - (2 xx + 1)|, u = 2 (x - x_l) /
+// w_b, come from u (double-float, once per cell) as exact double-float
+// differences; macro ratios are double-float quotients.  With BF16 storage FP64
+// only recomputes weights near a bf16 rounding midpoint; with FP32 storage
+// every weight is the FP64 value of the definition rounded once.
 constexpr int kAsmStage = 768;  // own entries of a warp's 32 rows staged in shared memory
 __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     HintGeo G, int wdtype, const uint32_t *hrp, const int32_t *longidx, const uint64_t *lptr,
     const dfl *sdsum, const dfl *spsum, const uint8_t *hflag, const int32_t *cell_bin,
     const int32_t *n_ovl, const float2 *xy, const float *cw, const float *ch,
     const int64_t *gptr, const uint32_t *glist, const float4 *ggeo, const double *base_w,
-    const float *phif, const double *phid, const uint64_t *tpos, int W, const int32_t *crank,
-    const int64_t *boff, const int32_t *cmem, const float4 *mgeo, int32_t *col, void *w,
-    dfl *dsum, dfl *psum, uint64_t *mac_base, uint64_t *bin_base) {
+    const float *phif, const double *phid, int W, const int32_t *cmem, const float4 *mgeo,
+    int32_t *col, void *w, void *bwin, void *bwinq, const int32_t *crank, int32_t *hbin,
+    dfl *dsum, dfl *psum, uint64_t *mac_base, unsigned long long *counts) {
   __shared__ int32_t stage_col[8][kAsmStage];
   __shared__ uint32_t stage_w[8][kAsmStage];
   const bool bf = wdtype == PL_W_BF16;
@@ -673,6 +658,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
   int32_t *scol = stage_col[threadIdx.x >> 5];
   uint32_t *sw = stage_w[threadIdx.x >> 5];
   const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long slots = 0, hints = 0;  // this thread's window slots in the grid, hint cells
   for (long long v0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); v0 < G.Nst;
        v0 += stride) {
     const long long v = v0 + lane;
@@ -686,7 +672,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     // a cell's inputs, loaded before its hint test so that they are in flight
     // together rather than one dependent round after another
     uint8_t hf = 0;
-    int li = -1, cb = 0, cr = 0, nov = 0;
+    int li = -1, cb = 0, nov = 0;
     uint32_t hr = 0;
     float2 p = make_float2(0.f, 0.f);
     double bw = 0.0;
@@ -698,9 +684,10 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       bw = base_w[v];
       cb = cell_bin[v];
       nov = n_ovl[v];
-      if (tpos) cr = crank[v];
     }
+    if (v < G.C) hbin[v] = hf ? cb : -1;
     if (hf) {
+      ++hints;
       const uint64_t mb = li >= 0 ? lptr[li] : (uint64_t)(hr & kOffMask);
       const bool use_s = staged && li < 0;
       // an own entry: to the warp's stage (short rows) or straight to memory
@@ -762,70 +749,65 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
           }
         }
       }
-      const uint64_t bb0 = mb + nov;
-      const int b = cb, bx = b % G.nbx, by = b / G.nbx;
-      const int x0 = max(0, bx - G.hx), x1 = min(G.nbx - 1, bx + G.hx);
-      const int y0 = max(0, by - G.hy), y1 = min(G.nby - 1, by + G.hy);
+      // window slots, row-major over the full window
+      const int b = cb, bx = b % G.nbx, by = b / G.nbx, wx = 2 * G.hx + 1;
       const dfl ux = df_offset_scale(p.x, G.xlh, G.xll, G.iwh, G.iwl);
       const dfl uy = df_offset_scale(p.y, G.ylh, G.yll, G.ihh, G.ihl);
-      const uint64_t rk = tpos ? (uint64_t)(cr - boff[2 * b]) : 0ull;
-      k = bb0;
-      for (int yy = y0; yy <= y1; ++yy) {
+      uint16_t *wb16 = reinterpret_cast<uint16_t *>(bwin) + (size_t)v * W;
+      uint32_t *wb32 = reinterpret_cast<uint32_t *>(bwin) + (size_t)v * W;
+      const size_t q = (size_t)crank[v] * W;  // the bucket-order copy
+      uint16_t *wq16 = reinterpret_cast<uint16_t *>(bwinq) + q;
+      uint32_t *wq32 = reinterpret_cast<uint32_t *>(bwinq) + q;
+      int sidx = 0;
+      for (int yy = by - G.hy; yy <= by + G.hy; ++yy) {
+        const bool yin = yy >= 0 && yy < G.nby;
         // e^{-max(rx, ry)} is e^{-rx} or e^{-ry}
         const dfl ry = df_absdiff(uy.hi, uy.lo, (float)(2 * yy + 1));
-        const float ey = exp_neg_df(ry);
-        const int y0b = max(0, yy - G.hy);
-        for (int xc = x0; xc <= x1; xc += 4) {
-          // four window bins' phi and bin-row places loaded at once
-          float ph[4];
-          uint64_t tp[4];
+        const float ey = (bf && yin) ? exp_neg_df(ry) : 0.f;
+        for (int xc = bx - G.hx; xc <= bx + G.hx; xc += 4) {
+          float ph[4];  // four window bins' phi loaded at once
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int xx = xc + u, bb = yy * G.nbx + xx;
-            ph[u] = xx <= x1 ? phif[bb] : 0.f;
-            tp[u] = ~0ull;
-            if (tpos && xx <= x1) {
-              const int x0b = max(0, xx - G.hx);
-              const int nxb = min(G.nbx - 1, xx + G.hx) - x0b + 1;
-              tp[u] = tpos[(long long)bb * W + (by - y0b) * nxb + (bx - x0b)] + rk;
-            }
+            const int xx = xc + u;
+            ph[u] = (yin && xx >= 0 && xx < G.nbx && xx <= bx + G.hx) ? phif[yy * G.nbx + xx] : 0.f;
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int xx = xc + u;
-            if (xx > x1) break;
-            const int bb = yy * G.nbx + xx;
-            uint32_t bits;
-            float sv;
+            if (xx > bx + G.hx) break;
+            uint32_t bits = 0;
+            if (yin && xx >= 0 && xx < G.nbx) {
+              const int bb = yy * G.nbx + xx;
+              float sv;
+              if (bf) {
+                const dfl rx = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
+                const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
+                const float wv = -((e * ph[u]) * bwf);
+                const uint16_t h = near_bf16_tie(wv)
+                                       ? d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))
+                                       : f2bf16(wv);
+                bits = h;
+                sv = bf16_to_f(h);
+              } else {
+                sv = __double2float_rn(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw));
+                bits = __float_as_uint(sv);
+              }
+              acc_deg(Dl, Pl, sv);
+              ++slots;
+            }
             if (bf) {
-              const dfl rx = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
-              const float e = df_ge(rx, ry) ? exp_neg_df(rx) : ey;
-              const float wv = -((e * ph[u]) * bwf);
-              const uint16_t h = near_bf16_tie(wv)
-                                     ? d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw))
-                                     : f2bf16(wv);
-              bits = h;
-              sv = bf16_to_f(h);
+              wb16[sidx] = (uint16_t)bits;
+              wq16[sidx] = (uint16_t)bits;
             } else {
-              sv = __double2float_rn(bin_w_exact(p.x, p.y, xx, yy, G, phid[bb], bw));
-              bits = __float_as_uint(sv);
+              wb32[sidx] = bits;
+              wq32[sidx] = bits;
             }
-            put(k, (int32_t)(G.bn0 + bb), bits);
-            // the same entry in the row of bin bb: this cell's bucket run
-            // inside bb's window, at the cell's rank
-            const uint64_t k2 = tp[u];
-            if (k2 != ~0ull) {
-              col[k2] = (int32_t)v;
-              if (bf) reinterpret_cast<uint16_t *>(w)[k2] = (uint16_t)bits;
-              else reinterpret_cast<uint32_t *>(w)[k2] = bits;
-            }
-            acc_deg(Dl, Pl, sv);
-            ++k;
+            ++sidx;
           }
         }
       }
+      (void)wx;
       mac_base[v] = mb;
-      bin_base[v] = bb0;
     }
     dsum[v] = df_norm(Dl);
     psum[v] = df_norm(Pl);
@@ -842,120 +824,38 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       __syncwarp();
     }
   }
+  slots = warp_sum(slots);
+  hints = warp_sum(hints);
+  if (lane == 0 && slots) atomicAdd(counts, slots);
+  if (lane == 0 && hints) atomicAdd(counts + 1, hints);
 }
 
-// Where the cells of each window bin start in a bin row: the row of bin b is
-// the concatenation of the hint buckets of its window bins in row-major
-// order, so window position j of b starts at the row's first entry plus the
-// sizes of the buckets before it.
-__global__ void k_bin_tpos(HintGeo G, int W, const int64_t *boff, const int32_t *longidx,
-                           const uint64_t *lptr, uint64_t *tpos) {
-  const int NB = G.nbx * G.nby;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
-    const int bx = b % G.nbx, by = b / G.nbx;
-    uint64_t o = lptr[longidx[G.bn0 + b]];
-    int j = 0;
-    for (int yy = max(0, by - G.hy); yy <= min(G.nby - 1, by + G.hy); ++yy)
-      for (int xx = max(0, bx - G.hx); xx <= min(G.nbx - 1, bx + G.hx); ++xx, ++j) {
-        const int bb = yy * G.nbx + xx;
-        tpos[(long long)b * W + j] = o;
-        o += (uint64_t)(boff[2 * bb + 1] - boff[2 * bb]);
-      }
-  }
-}
-
-// Degree partials of the chunks of bin rows (entries written by the cells'
-// assembly), one warp per chunk, double-float, in entry order per lane then
-// a fixed tree.
-__global__ void k_bin_sums(HintGeo G, int wdtype, int32_t nchunks, const int32_t *chunk_lr,
-                           const int32_t *lrow, const uint64_t *lptr, const int32_t *lchunk,
-                           const void *w, dfl *cpart) {
-  const int lane = threadIdx.x & 31;
-  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nchunks;
-       c += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const int l = chunk_lr[c];
-    if (lrow[l] < G.bn0) continue;
-    const uint64_t base = lptr[l], len = lptr[l + 1] - base;
-    const uint64_t q0 = (uint64_t)(c - lchunk[l]) * kChunk;
-    const uint64_t q1 = q0 + kChunk < len ? q0 + kChunk : len;
-    dfl D{0.f, 0.f}, Pp{0.f, 0.f};
-    for (uint64_t q = q0 + lane; q < q1; q += 32) acc_deg(D, Pp, load_w(w, wdtype, base + q));
-    D = warp_sum_df(D);
-    Pp = warp_sum_df(Pp);
-    if (lane == 0) {
-      cpart[2 * c] = D;
-      cpart[2 * c + 1] = Pp;
-    }
-  }
-}
-
-// Virtual rows, in the hub chunks of the sparse-product layout (one CTA per
-// chunk of kChunk entries).  A macro row lists the cells overlapping it (sorted
-// by id); a bin row is the concatenation of its window bins' hint buckets in
-// row-major window order, each ascending (the canonical column order is
-// restored when the graph is exported).  Weights are copied from the cells'
-// own entries, so the matrix is exactly symmetric.  Degree partials per chunk.
+// Macro rows, in the hub chunks of the sparse-product layout (one CTA per
+// chunk of kChunk entries): a macro row lists the cells overlapping it
+// (sorted by id), with the weights copied from the cells' own entries, so the
+// matrix is exactly symmetric.  Degree partials per chunk.
 __global__ void __launch_bounds__(256) k_hub_chunks(
     HintGeo G, int wdtype, int32_t nchunks, const int32_t *chunk_lr, const int32_t *lrow,
     const uint64_t *lptr, const int32_t *lchunk, const int64_t *moff, const uint32_t *mlist,
-    const int64_t *boff, const uint32_t *blist, const int32_t *cell_bin, const int32_t *n_ovl,
-    const uint64_t *mac_base, const uint64_t *bin_base, int skip_bins, int32_t *col, void *w,
-    dfl *cpart) {
-  __shared__ long long roff[1025];
-  __shared__ int rbin[1024];
-  __shared__ int nrun;
+    const int32_t *n_ovl, const uint64_t *mac_base, int32_t *col, void *w, dfl *cpart) {
   __shared__ dfl red[2][8];
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int l = chunk_lr[c];
     const int64_t v = lrow[l];
-    if (v < G.mv0) continue;  // long rows of real nodes are assembled elsewhere
-    if (skip_bins && v >= G.bn0) continue;  // written by the cells' assembly
+    if (v < G.mv0 || v >= G.bn0) continue;  // macro rows only
     const uint64_t base = lptr[l];
     const long long len = (long long)(lptr[l + 1] - base);
     const long long q0 = (long long)(c - lchunk[l]) * kChunk;
     const long long q1 = min(len, q0 + (long long)kChunk);
-    const bool is_bin = v >= G.bn0;
-    const int b = is_bin ? (int)(v - G.bn0) : 0, m = is_bin ? 0 : (int)(v - G.mv0);
-    const int bxb = b % G.nbx, byb = b / G.nbx;
-    if (is_bin) {
-      if (threadIdx.x == 0) {
-        int nr = 0;
-        long long o = 0;
-        for (int yy = max(0, byb - G.hy); yy <= min(G.nby - 1, byb + G.hy); ++yy)
-          for (int xx = max(0, bxb - G.hx); xx <= min(G.nbx - 1, bxb + G.hx); ++xx) {
-            int bb = yy * G.nbx + xx;
-            roff[nr] = o;
-            rbin[nr] = bb;
-            o += boff[2 * bb + 1] - boff[2 * bb];
-            ++nr;
-          }
-        roff[nr] = o;
-        nrun = nr;
-      }
-      __syncthreads();
-    }
+    const int m = (int)(v - G.mv0);
     dfl D{0.f, 0.f}, Pp{0.f, 0.f};
     for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      int i;
-      uint64_t src;
-      if (!is_bin) {
-        i = (int)mlist[moff[m] + q];
-        const uint64_t mb = mac_base[i];
-        const int n = n_ovl[i];
-        int j = 0;
-        while (j < n - 1 && col[mb + j] != (int32_t)v) ++j;
-        src = mb + j;
-      } else {
-        int lo = 0, hi = nrun - 1;  // run r with roff[r] <= q < roff[r+1]
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (roff[mid] <= q) lo = mid; else hi = mid - 1;
-        }
-        i = (int)blist[boff[2 * rbin[lo]] + (q - roff[lo])];
-        const int ci = cell_bin[i], bxi = ci % G.nbx, byi = ci / G.nbx;
-        const int x0 = max(0, bxi - G.hx), x1 = min(G.nbx - 1, bxi + G.hx), y0 = max(0, byi - G.hy);
-        src = bin_base[i] + (uint64_t)((byb - y0) * (x1 - x0 + 1) + (bxb - x0));
-      }
+      const int i = (int)mlist[moff[m] + q];
+      const uint64_t mb = mac_base[i];
+      const int n = n_ovl[i];
+      int j = 0;
+      while (j < n - 1 && col[mb + j] != (int32_t)v) ++j;
+      const uint64_t src = mb + j;
       col[base + q] = i;
       copy_w(w, w, wdtype, base + q, src);
       acc_deg(D, Pp, load_w(w, wdtype, src));
@@ -981,21 +881,27 @@ __global__ void __launch_bounds__(256) k_hub_chunks(
   }
 }
 
-// Degrees of virtual rows from their chunk partials (warp per row).
-__global__ void k_hub_finalize(HintGeo G, int32_t nlong, const int32_t *lrow,
-                               const int32_t *lchunk, const dfl *cpart, dfl *dsum, dfl *psum) {
+// Degrees of virtual rows (warp per row): a macro row from its chunk
+// partials, a bin row from the window blocks' degree partials.
+__global__ void k_hub_finalize(HintGeo G, BinGeo B, int32_t nlong, const int32_t *lrow,
+                               const int32_t *lchunk, const dfl *cpart, const int32_t *bchunk,
+                               const float4 *bdeg, dfl *dsum, dfl *psum) {
   const int lane = threadIdx.x & 31;
   for (long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; l < nlong;
        l += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int64_t v = lrow[l];
     if (v < G.mv0) continue;
     dfl D{0.f, 0.f}, Pp{0.f, 0.f};
-    for (int c = lchunk[l] + lane; c < lchunk[l + 1]; c += 32) {
-      df_add_df(D, cpart[2 * (long long)c]);
-      df_add_df(Pp, cpart[2 * (long long)c + 1]);
+    if (v >= G.bn0) {
+      bin_row_sums(B, (int)(v - G.bn0), bchunk, bdeg, &D, &Pp);
+    } else {
+      for (int c = lchunk[l] + lane; c < lchunk[l + 1]; c += 32) {
+        df_add_df(D, cpart[2 * (long long)c]);
+        df_add_df(Pp, cpart[2 * (long long)c + 1]);
+      }
+      D = warp_sum_df(D);
+      Pp = warp_sum_df(Pp);
     }
-    D = warp_sum_df(D);
-    Pp = warp_sum_df(Pp);
     if (lane == 0) {
       dsum[v] = D;
       psum[v] = Pp;
@@ -1103,6 +1009,17 @@ static HintGeo make_geo(const pl_graph *g) {
   return G;
 }
 
+static BinGeo make_bingeo(const pl_graph *g) {
+  BinGeo B;
+  B.nbx = g->nbx;
+  B.nby = g->nby;
+  B.hx = g->hx;
+  B.hy = g->hy;
+  B.W = (2 * g->hx + 1) * (2 * g->hy + 1);
+  B.NB = g->NB;
+  return B;
+}
+
 // Layout of a split matrix from per-row lengths already in g->slen/llen/lflag.
 // Layout of a split matrix from per-row lengths in g->slen/llen/clen and
 // hub flags in g->hubf.
@@ -1208,7 +1125,7 @@ pl_status prepare_static_layout(pl_graph *g, cudaStream_t s) {
   pl_status st = ensure_row_arrays(g);
   if (st != PL_OK) return st;
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 0, P<int64_t>(g->srp), nullptr, nullptr, nullptr,
-                                             nullptr, nullptr, P<uint32_t>(g->slen),
+                                             nullptr, P<uint32_t>(g->slen),
                                              P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
                                              P<uint64_t>(g->clen));
   note_launch();
@@ -1221,6 +1138,10 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   const float2 *xy = reinterpret_cast<const float2 *>(xy_in);
   HintGeo G = make_geo(g);
   g->have_hints = false;
+  // a hint build takes its buffers anew, above the static build's part of
+  // the workspace
+  for_each_buf(g, 1, [](Buf &b) { release(b); });
+  g->arena.used = g->hint_mark;
   if (g->hx * 2 + 1 > kMaxWin || g->hy * 2 + 1 > kMaxWin) {
     set_error("detection window larger than 31 x 31 bins");
     return PL_ERR_UNSUPPORTED;
@@ -1304,16 +1225,19 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     set_error("non-finite movable cell coordinate");
     return PL_ERR_NONFINITE;
   }
+  if (nml > (int64_t)g->nmov * kMaxCellMacros) {
+    set_error("%lld macro-cell overlaps, more than %d per movable cell", (long long)nml,
+              kMaxCellMacros);
+    return PL_ERR_UNSUPPORTED;
+  }
   // H3-H4: bin buckets (ascending cell id) and macro lists (sorted)
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
   if (tiled) {
-    TRY(ensure(g->crank, (size_t)C * 4 + 16));
     k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
                                                           P<uint8_t>(g->hflag),
                                                           P<int32_t>(g->cell_bin), cmo,
-                                                          P<uint32_t>(g->blist),
-                                                          P<int32_t>(g->crank));
+                                                          P<uint32_t>(g->blist));
     note_launch();
   } else {
     TRY(ensure(g->bcur, (size_t)(nbk + 1) * 4));
@@ -1347,12 +1271,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   cudaStream_t s2 = g->side;
   TRY(ensure(g->Db, (size_t)NB * 8 + 16));
   TRY(ensure(g->phi, (size_t)NB * 8 + 16));
-  const size_t phib = ((size_t)NB * 4 + 255) & ~size_t(255);
-  TRY(ensure(g->tmp[4], phib + (size_t)NB * 8 + 256));
+  TRY(ensure(g->tmp[4], (size_t)NB * 4 + 256));
   float *phif = P<float>(g->tmp[4]);
-  int64_t *hub_len = reinterpret_cast<int64_t *>(P<char>(g->tmp[4]) + phib);
-  k_bin_hub_len<<<grid_for(NB, 128), 128, 0, s>>>(G, P<int64_t>(g->boff), hub_len);
-  note_launch();
   TRY(cudaEventRecord(g->ev_fork, s));
   TRY(cudaStreamWaitEvent(s2, g->ev_fork, 0));
   if (cmem_ok) {
@@ -1407,56 +1327,72 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   if (st != PL_OK) return st;
   k_row_len<<<grid_for(N, 256), 256, 0, s>>>(G, 1, P<int64_t>(g->srp), P<uint8_t>(g->hflag),
                                              P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
-                                             P<int64_t>(g->moff), hub_len, P<uint32_t>(g->slen),
+                                             P<int64_t>(g->moff), P<uint32_t>(g->slen),
                                              P<uint64_t>(g->llen), P<uint8_t>(g->hubf),
                                              P<uint64_t>(g->clen));
   note_launch();
   st = layout(g, g->hm, 1, s);
   if (st != PL_OK) return st;
   SpMat &m = g->hm;
-  // H9: hint parts of cells (and degrees of every real node); with the
-  // tiled bucket sort the cells also write their entries of the bin rows
+  // H9: hint parts of cells (macro entries, window blocks) and degrees of
+  // every real node
   TRY(ensure(g->mac_base, (size_t)C * 8 + 16));
-  TRY(ensure(g->bin_base, (size_t)C * 8 + 16));
   const int W = (2 * g->hx + 1) * (2 * g->hy + 1);
-  uint64_t *tpos = nullptr;
-  if (tiled) {
-    TRY(ensure(g->tpos, (size_t)NB * W * 8 + 16));
-    tpos = P<uint64_t>(g->tpos);
-    k_bin_tpos<<<grid_for(NB, 128), 128, 0, s>>>(G, W, P<int64_t>(g->boff), P<int32_t>(m.longidx),
-                                                 P<uint64_t>(m.lptr), tpos);
-    note_launch();
-  }
+  g->W = W;
+  TRY(ensure(g->hbw, (size_t)C * W * m.wbytes + 64));
+  TRY(ensure(g->hbwq, (size_t)nbl * W * m.wbytes + 64));
+  TRY(ensure(g->hbin, (size_t)C * 4 + 16));
+  TRY(ensure(g->crank, (size_t)C * 4 + 16));
+  k_bucket_rank<<<grid_for(nbl, 256), 256, 0, s>>>(nbl, P<uint32_t>(g->blist), P<int32_t>(g->crank));
+  note_launch();
+  unsigned long long *counts = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 3);
+  TRY(cudaMemsetAsync(counts, 0, 16, s));
   TRY(cudaStreamWaitEvent(s, g->ev_join, 0));  // phi and the macro lists
   k_assemble_hints<<<grid_for(g->Nst, 256), 256, 0, s>>>(
       G, g->wdtype, P<uint32_t>(m.rp_s), P<int32_t>(m.longidx), P<uint64_t>(m.lptr),
       P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),
       P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<int64_t>(g->gptr),
       P<uint32_t>(g->glist), P<float4>(g->ggeo), P<double>(g->base_w), phif, P<double>(g->phi),
-      tpos, W, tiled ? P<int32_t>(g->crank) : nullptr, P<int64_t>(g->boff),
-      cmem_ok ? P<int32_t>(g->cmem) : nullptr, P<float4>(g->mgeo), P<int32_t>(m.col),
-      m.w.p, P<dfl>(m.dsum),
-      P<dfl>(m.psum), P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base));
+      W, cmem_ok ? P<int32_t>(g->cmem) : nullptr, P<float4>(g->mgeo), P<int32_t>(m.col), m.w.p,
+      g->hbw.p, g->hbwq.p, P<int32_t>(g->crank), P<int32_t>(g->hbin), P<dfl>(m.dsum),
+      P<dfl>(m.psum), P<uint64_t>(g->mac_base), counts);
   note_launch();
-  // H10: virtual rows
+  // H10: bin rows (degree partials of the window blocks, chunk by chunk) and
+  // macro rows (their entries and degree partials)
+  const BinGeo B = make_bingeo(g);
+  TRY(ensure(g->bchunk, (size_t)(NB + 1) * 4 + 256));
+  TRY(ensure(g->tmp[6], (size_t)(NB + 1) * 4 + 256));
+  k_bin_chunk_count<<<grid_for(NB, 256), 256, 0, s>>>(NB, P<int64_t>(g->boff), P<int32_t>(g->tmp[6]));
+  note_launch();
+  TRY((exclusive_scan<int32_t, int32_t>(P<int32_t>(g->tmp[6]), P<int32_t>(g->bchunk), NB, stmp, s)));
+  const long long nbc_max = nbl / kBinChunk + NB + 1;  // chunks at most (the grid size)
+  g->nbc_max = nbc_max;
+  TRY(ensure(g->cown, (size_t)nbc_max * 4 + 256));
+  k_chunk_bins<<<grid_for(NB, 128), 128, 0, s>>>(NB, P<int32_t>(g->bchunk), P<int32_t>(g->cown));
+  note_launch();
+  TRY(ensure(g->bdeg, (size_t)nbc_max * W * 16 + 256));
+  TRY(ensure(g->bpart, (size_t)nbc_max * W * 16 + 256));
+  const int bgrid = (int)(nbc_max < 152 * 8 ? nbc_max : 152 * 8);
+  if (g->wdtype == PL_W_BF16)
+    k_bin_partials<1, true><<<bgrid, kBinThreads, 0, s>>>(B, P<int32_t>(g->bchunk), P<int32_t>(g->cown), P<int64_t>(g->boff),
+                                                         P<uint32_t>(g->blist), g->hbwq.p, nullptr,
+                                                         P<float4>(g->bdeg));
+  else
+    k_bin_partials<0, true><<<bgrid, kBinThreads, 0, s>>>(B, P<int32_t>(g->bchunk), P<int32_t>(g->cown), P<int64_t>(g->boff),
+                                                         P<uint32_t>(g->blist), g->hbwq.p, nullptr,
+                                                         P<float4>(g->bdeg));
+  note_launch();
   TRY(ensure(g->tmp[5], (size_t)(m.nchunks + 1) * 2 * sizeof(dfl) + 256));
   dfl *cpart = P<dfl>(g->tmp[5]);
   if (m.nchunks) {
     k_hub_chunks<<<m.nchunks < 152 * 32 ? m.nchunks : 152 * 32, 256, 0, s>>>(
         G, g->wdtype, m.nchunks, P<int32_t>(m.chunk_lr), P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
-        P<int32_t>(m.lchunk), P<int64_t>(g->moff), P<uint32_t>(g->mlist), P<int64_t>(g->boff),
-        P<uint32_t>(g->blist), P<int32_t>(g->cell_bin), P<int32_t>(g->n_ovl),
-        P<uint64_t>(g->mac_base), P<uint64_t>(g->bin_base), tiled ? 1 : 0, P<int32_t>(m.col),
-        m.w.p, cpart);
+        P<int32_t>(m.lchunk), P<int64_t>(g->moff), P<uint32_t>(g->mlist), P<int32_t>(g->n_ovl),
+        P<uint64_t>(g->mac_base), P<int32_t>(m.col), m.w.p, cpart);
     note_launch();
-    if (tiled) {
-      k_bin_sums<<<grid_for((long long)m.nchunks * 32, 256), 256, 0, s>>>(
-          G, g->wdtype, m.nchunks, P<int32_t>(m.chunk_lr), P<int32_t>(m.lrow), P<uint64_t>(m.lptr),
-          P<int32_t>(m.lchunk), m.w.p, cpart);
-      note_launch();
-    }
     k_hub_finalize<<<grid_for((long long)m.nlong * 32, 256), 256, 0, s>>>(
-        G, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<dfl>(m.dsum), P<dfl>(m.psum));
+        G, B, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<int32_t>(g->bchunk),
+        P<float4>(g->bdeg), P<dfl>(m.dsum), P<dfl>(m.psum));
     note_launch();
   }
   // H11: lambda_up and coefficients
@@ -1474,7 +1410,13 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     note_launch();
   }
   TRY(cudaGetLastError());
-  TRY(d2h(hst, g->status.p, 8, s));
+  {
+    unsigned long long ns[2] = {0, 0};
+    const D2H it[2] = {{hst, g->status.p, 32}, {ns, counts, 16}};
+    TRY(d2h_many(g->stage, it, 2, s));
+    g->nslot = (int64_t)ns[0];
+    g->nhint = (int64_t)ns[1];
+  }
   memcpy(g->lam_h, hst + 4, sizeof(g->lam_h));
   g->have_hints = true;
   if (hst[0] & ST_SPECTRUM) {

@@ -20,6 +20,9 @@ constexpr int kPad = 16;  // spare entries after the last one
 constexpr int kRpPad = 8;  // spare row pointers after the last one
 constexpr uint32_t kHubFlag = 0x80000000u;  // rp_s bit 31: the row is a hub row
 constexpr uint32_t kOffMask = 0x7fffffffu;
+// Macro-cell overlap pairs of one hint build, at most this many per movable
+// cell on average (the workspace bound counts on it).
+constexpr int kMaxCellMacros = 16;
 
 // A split CSR matrix as the SpMM kernels read it.  Entries of short rows come
 // first (row pointers rp_s; hub rows have zero length there and bit 31 set),
@@ -49,7 +52,8 @@ struct SpMat {
   Buf psum;     // dfl [N] sum of positive weights
   Buf c32;      // float [N] 1 - D_ii / lambda_up
   Buf c64l;     // double [nlong] same, FP64, hub rows
-  Buf lam;      // double [4]: lambda_up, 1/lambda_up, and the raw max key
+  Buf lam;      // 8-byte words: lambda_up, 1/lambda_up (double), the raw max key, the
+                // count of window slots inside the grid and of hint cells (uint64)
   Buf part;     // float4 [nchunks] hub partial sums (two double-floats)
   int wbytes = 4;
 };
@@ -101,15 +105,26 @@ struct pl_graph {
   pl::Buf mtc, mtoff;  // per (macro, cell tile) counts and their scan (tiled macro lists)
   pl::Buf cmem;        // int32 [C * 8] each hint cell's macros (tiled macro lists)
   pl::Buf Db, phi;     // double [NB]
-  pl::Buf hlen;        // int64 [N] augmented row length
   pl::Buf slen;        // uint32 [N] short-region length (0 for hub rows)
   pl::Buf llen;        // uint64 [N] hub-region length (0 for short rows)
   pl::Buf clen;        // uint64 [N] chunked length of hub rows
   pl::Buf lflag;       // int32 [N+1] hub flag scan
-  pl::Buf crank;       // int32 [C] place of a hint cell in the bucket list
-  pl::Buf tpos;        // uint64 [NB * window] place of each window bin's cells in a bin row
   pl::Buf mac_base;    // uint64 [C] entry offset of a cell's first macro entry
-  pl::Buf bin_base;    // uint64 [C] entry offset of a cell's first bin entry
+  // bin hints without stored columns: each hint cell's window block and the
+  // bin rows as its transpose over the bucket lists
+  int W = 0;           // slots of a window, (2 hx + 1)(2 hy + 1)
+  int64_t nslot = 0;   // window slots inside the bin grid, over all hint cells
+  int64_t nhint = 0;   // hint cells (movable, baseWeight > 0)
+  long long nbc_max = 0;  // bin-row chunks at most (grid of the chunk kernels)
+  pl::Buf hbw;         // storage type [C * W] window-block weights of hint cells
+  pl::Buf hbwq;        // storage type [movable cells * W] the same blocks at each cell's
+                       // place in the bucket lists (read in list order by the bin rows)
+  pl::Buf crank;       // int32 [C] place of a movable cell in the bucket lists
+  pl::Buf hbin;        // int32 [C] bin of a hint cell, -1 for other cells
+  pl::Buf bchunk;      // int32 [NB + 1] first chunk of each bin's hint bucket
+  pl::Buf cown;        // int32 [chunks] bin of each chunk
+  pl::Buf bdeg;        // float4 [chunks * W] degree partials of the bin rows
+  pl::Buf bpart;       // float4 [chunks * W] product partials of the bin rows
   pl::Buf hubtmp;      // int32 scratch for merging bin rows
   pl::SpMat st;        // static matrix (A0)
   pl::SpMat hm;        // augmented matrix (A2-A4)
@@ -122,6 +137,10 @@ struct pl_graph {
   pl::Buf status;         // int32 [8]
   pl::Buf stage;          // staging words of batched device-to-host reads
   pl::Buf star_w;         // double [kMaxNetPins + 1] star edge weights p / (p - 1)
+  // device memory: the caller's workspace.  The static build takes the bottom
+  // of it (up to hint_mark); every hint build starts again at hint_mark.
+  pl::Arena arena;
+  size_t hint_mark = 0;
   cudaStream_t side = nullptr;  // the hint build's second stream (forked from and joined
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // back to the caller's stream)
   bool star_w_ok = false;
@@ -131,7 +150,6 @@ struct pl_graph {
   int nsm = 0;
   int occ_rows[2][2] = {{0, 0}, {0, 0}};
   int occ_rows4[2] = {0, 0};
-  pl::Scratch scr;
   pl::Buf tmp[8];
   pl::Buf lay[4];         // layout scratch (scans of row lengths, chunk counts)
   pl::Buf hubf;           // uint8 [N] hub flags of a layout
@@ -139,11 +157,43 @@ struct pl_graph {
 
 namespace pl {
 
+// Every device buffer of a graph.  kind 0: all; kind 1: those a hint build
+// takes anew (its own results and the scratch buffers every phase shares).
+template <typename F>
+void for_each_buf(pl_graph *g, int kind, F f) {
+  Buf *hint[] = {&g->tmp[0], &g->tmp[1], &g->tmp[2], &g->tmp[3], &g->tmp[4], &g->tmp[5],
+                 &g->tmp[6], &g->tmp[7], &g->lay[0], &g->lay[1], &g->lay[2], &g->lay[3],
+                 &g->hubf, &g->slen, &g->llen, &g->clen, &g->lflag, &g->hubtmp, &g->cell_bin,
+                 &g->n_ovl, &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff,
+                 &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem, &g->Db, &g->phi,
+                 &g->mac_base, &g->hbw, &g->hbwq, &g->crank, &g->hbin, &g->bchunk, &g->cown, &g->bdeg,
+                 &g->bpart};
+  for (Buf *b : hint) f(*b);
+  SpMat *ms[] = {&g->hm, &g->st};
+  for (int i = 0; i < (kind == 0 ? 2 : 1); ++i) {
+    SpMat *m = ms[i];
+    Buf *mb[] = {&m->rp_s, &m->col, &m->w, &m->lrow, &m->lptr, &m->lsb, &m->lhb,
+                 &m->lsl, &m->lhl, &m->lchunk, &m->chunk_lr, &m->longidx,
+                 &m->dsum, &m->psum, &m->c32, &m->c64l, &m->lam, &m->part};
+    for (Buf *b : mb) f(*b);
+  }
+  if (kind != 0) return;
+  Buf *rest[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node,
+                 &g->nd, &g->net_p, &g->star_of, &g->star_net, &g->star_p, &g->macro_cell,
+                 &g->cell_macro, &g->srp, &g->base_w, &g->hflag, &g->nkind, &g->fixedp,
+                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo,
+                 &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub, &g->acc, &g->gsc, &g->q4a,
+                 &g->q4b, &g->status, &g->stage, &g->star_w};
+  for (Buf *b : rest) f(*b);
+}
+
 void set_error(const char *fmt, ...);
 void clear_error();
 pl_status cuda_fail(cudaError_t e, const char *what);
 
 pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cudaStream_t s);
+pl_status take_filter_buffers(pl_graph *g);
+double workspace_bound(const pl_netlist *nl, const pl_params *p);
 pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy, cudaStream_t s);
 pl_status prepare_static_layout(pl_graph *g, cudaStream_t s);
 pl_status run_init_signal(pl_graph *g, uint64_t seed, const float *xy0, float *xy, cudaStream_t s);

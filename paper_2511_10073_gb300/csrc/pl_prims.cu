@@ -5,18 +5,24 @@
 
 namespace pl {
 
+Arena *&current_arena() {
+  static thread_local Arena *a = nullptr;
+  return a;
+}
+
 cudaError_t ensure(Buf &b, size_t bytes) {
   if (bytes <= b.bytes && b.p) return cudaSuccess;
-  size_t nb = bytes + bytes / 4 + 1024;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-  cudaError_t e = cudaMalloc(&b.p, nb);
-  if (e != cudaSuccess) {
-    b.p = nullptr;
-    return e;
+  Arena *a = current_arena();
+  if (!a || !a->base) return cudaErrorInvalidValue;
+  const size_t off = (a->used + 255) & ~size_t(255);
+  if (off > a->cap || bytes > a->cap - off) {
+    if (off + bytes > a->short_need) a->short_need = off + bytes;
+    return cudaErrorMemoryAllocation;
   }
-  b.bytes = nb;
+  b.p = a->base + off;
+  b.bytes = bytes;
+  a->used = off + bytes;
+  if (a->used > a->peak) a->peak = a->used;
   return cudaSuccess;
 }
 
@@ -40,16 +46,8 @@ cudaError_t d2h_many(Buf &stage, const D2H *items, int count, cudaStream_t s) {
 }
 
 void release(Buf &b) {
-  if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
-}
-
-void *Scratch::take(size_t bytes) {
-  size_t off = (used + 255) & ~size_t(255);
-  if (off + bytes > buf.bytes) return nullptr;
-  used = off + bytes;
-  return static_cast<char *>(buf.p) + off;
 }
 
 // ------------------------------------------------------------------- scan
