@@ -169,6 +169,75 @@ def run_reference(args):
     }), flush=True)
 
 
+BATCH_PARAMS = dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+                    tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))
+
+
+def run_batched(pl, netgen, dev, stream, args, n=64):
+    """The batched serving form: n designs of uneven size (std cells
+    log-uniform in 5k-500k), each built once; one step initializes all of
+    them.  The plain GPU form runs the designs one after another on one
+    stream; the batched form runs pl_filter_init_batch over S streams, S
+    chosen by timing S = 1, 2, 4, 8, 16 once each.  Both forms give the same
+    bits, so their HPWL differs by 0."""
+    import torch
+    cfgs = netgen.batch_configs(args.seed, n=n)
+    nls = [netgen.make_netlist(c, 1000 + i) for i, c in enumerate(cfgs)]
+    prm = pl.params(**BATCH_PARAMS)
+    dnls = [pl.DeviceNetlist(nl, dev) for nl in nls]
+    graphs = [pl.pl_build_graph(d, prm) for d in dnls]
+    outs = [torch.empty(nl.num_cells * 2, dtype=torch.float32, device=dev) for nl in nls]
+    seeds = [args.seed + i for i in range(n)]
+    movable = sum(nl.num_movable for nl in nls)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def plain():
+        for g, o, sd in zip(graphs, outs, seeds):
+            pl.pl_filter_init(g, prm, sd, None, o)
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    plain()
+    ref = [o.clone() for o in outs]
+    ms_plain = timed(plain, max(1, args.steps // 2))
+    tried = {}
+    pools = {}
+    for ns in (1, 2, 4, 8, 16):
+        pools[ns] = [torch.cuda.Stream(device=dev) for _ in range(ns)]
+        fn = lambda ns=ns: pl.pl_filter_init_batch(graphs, prm, seeds, outs, pools[ns])
+        fn()
+        tried[ns] = timed(fn, 1)
+    best = min(tried, key=tried.get)
+    ms_batch = timed(lambda: pl.pl_filter_init_batch(graphs, prm, seeds, outs, pools[best]),
+                     max(1, args.steps // 2))
+    same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    hws = [pl.hpwl_workspace(nl.num_nets, dev) for nl in nls]
+    h = torch.zeros(2 * n, dtype=torch.float64, device=dev)
+    for i, (d, o, w) in enumerate(zip(dnls, outs, hws)):
+        pl.pl_hpwl(d, o, h[i:i + 1], w)
+        pl.pl_hpwl(d, ref[i], h[n + i:n + i + 1], w)
+    hp = h.cpu().numpy()
+    rel = float(abs(hp[:n].sum() - hp[n:].sum()) / hp[n:].sum())
+    for g in graphs:
+        g.destroy()
+    return {"what": f"{n} designs, std cells log-uniform 5k-500k ({movable} movable cells), "
+                    "each initialized from its seed (GiFt + 3 rounds, BF16, taps {2,4,8})",
+            "unit": "cells/s", "value": movable / (ms_batch / 1e3),
+            "plain_gpu_value": movable / (ms_plain / 1e3), "speedup": ms_plain / ms_batch,
+            "ms_per_batch": ms_batch, "plain_ms_per_batch": ms_plain,
+            "autotune": {"streams_tried_ms": {str(k): v for k, v in tried.items()},
+                         "streams": best},
+            "same_bits_as_plain": same, "hpwl_rel_diff": rel,
+            "timing": "wall clock of whole batches after a synchronize (host threads drive "
+                      "the streams)"}
+
+
 def whole_job_rate(ms_local, units_per_rank, steps, dist=None, device="cpu"):
     """Whole-job throughput of a replica run: the slowest rank's time (MAX over
     ranks) for the units all ranks processed.  Returns (units/s, max ms)."""
@@ -191,6 +260,7 @@ def main():
     ap.add_argument("--config", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched serving form")
     ap.add_argument("--profile-one", action="store_true",
                     help="warm up, then run one step inside a CUDA profiler range and exit "
                          "(for ncu --profile-from-start off)")
@@ -339,6 +409,25 @@ def main():
               "hpwl_ms": ev[2].elapsed_time(ev[3])}
     info = g.info()
 
+    # macro charge-density schedules (Sec. VI) on this netlist's macros, over
+    # a 512 x 512 bin grid (a global-placement grid), one call per model
+    kind = np.asarray(nl.cell_kind)
+    mids = np.flatnonzero(kind == netgen.KIND_MACRO)
+    mgeo = [torch.tensor(np.asarray(a, np.float32)[mids], device=dev)
+            for a in (nl.fixed_x, nl.fixed_y, nl.cell_w, nl.cell_h)]
+    rho = torch.empty(512 * 512, dtype=torch.float64, device=dev)
+    rho_ms = {}
+    for model, name in enumerate(("gauss", "exp", "linear", "sigmoid")):
+        rp = pl.rho_params(model=model)
+        for _ in range(2):
+            pl.pl_macro_density(rp, 150, *mgeo, nl.region, 512, 512, rho)
+        e0.record(stream)
+        for _ in range(5):
+            pl.pl_macro_density(rp, 150, *mgeo, nl.region, 512, 512, rho)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rho_ms[name] = e0.elapsed_time(e1) / 5
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -363,7 +452,9 @@ def main():
                    "augmented_nnz": info["nnz"], "hub_rows": info["hub_rows"],
                    "l2": "inputs larger than L2 (each sparse product streams >400 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_spmm_hub + k_hub_rows + k_spmm_rows (one sparse product of the refinement filter, A4)",
+        "roofline": {"kernel": "one sparse product of the refinement filter (A4): k_spmm_rows (short rows, "
+                               "window slots) + k_spmm_hub, k_bin_partials, k_bin_bucket_sums, "
+                               "k_hub_rows (second stream)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -372,10 +463,15 @@ def main():
                      "algorithmic_bytes_per_launch": prof["hr_bytes"] / max(1, prof["hr_launches"])},
         "gpu_launches": prof["launches"],
         "phases": phases,
+        "macro_density": {"what": "pl_macro_density at t = 150 of T = 300 (Sec. VI), this netlist's "
+                                  f"{len(mids)} macros over 512 x 512 bins, FP64",
+                          "ms_per_call": rho_ms},
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
+    if not args.no_batch:
+        line["batched"] = run_batched(pl, netgen, dev, stream, args)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

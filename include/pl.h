@@ -35,7 +35,9 @@
  *     pl_workspace_size); pl_hpwl takes its own small workspace.  The
  *     library owns only the host-side pl_graph object, freed by
  *     pl_graph_destroy.
- *   - One pl_graph must not be used from two host threads at once.
+ *   - One pl_graph must not be used from two host threads at once; different
+ *     graphs may be (pl_filter_init_batch does), and static builds on several
+ *     threads take turns.
  */
 #ifndef PL_H
 #define PL_H
@@ -184,6 +186,21 @@ pl_status pl_init_signal(pl_graph *g, uint64_t seed, const float *xy0_cells, flo
 pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const float *xy0_cells,
                          float *xy_out_cells, pl_stream stream);
 
+/* The batched serving form: the whole initializer (as pl_filter_init, from
+ * the seed, no given placement) of n designs, each on its own built graph
+ * (Algorithm 1 runs per design, so designs are independent).  nstreams worker
+ * threads each drive one of the caller's streams and take the next design,
+ * largest first; the designs' kernels overlap on the GPU.  A design's result
+ * is the same bits as its pl_filter_init call on any stream.  xy_out_cells[i]:
+ * device, graphs[i]'s num_cells pairs.  Returns after every design is done
+ * (each worker synchronizes its stream).  Graph builds do not run here: build
+ * the graphs first (pl_build_graph calls on several threads take turns).
+ * Errors: INVALID_ARG, or the first failing design's status (its index in
+ * pl_last_error). */
+pl_status pl_filter_init_batch(int32_t n, pl_graph *const *graphs, const pl_params *p,
+                               const uint64_t *seeds, float *const *xy_out_cells,
+                               int32_t nstreams, const pl_stream *streams);
+
 /* A5: writes sum over nets of (max - min) pin x + (max - min) pin y, pin =
  * cell centre (xy_cells, device) + offset, as one double to *hpwl (device).
  * ws: device scratch of at least pl_hpwl_workspace_size(num_nets) bytes, 256-
@@ -212,6 +229,47 @@ pl_status pl_hpwl(const pl_netlist *nl, const float *xy_cells, double *hpwl, voi
  * CUDA. */
 pl_status pl_hpwl_noalloc(const pl_netlist *nl, const float *xy_cells, double *hpwl,
                           pl_stream stream);
+
+/* Sec. VI: macro charge densities scheduled over the T iterations of global
+ * placement, and their integrals over the bins (the macro part of each bin's
+ * density at iteration t).  Four models, as the paper defines them:
+ *   PL_RHO_GAUSS    charge redistribution: an area-normalized 2D Gaussian
+ *                   truncated to the footprint, eta(t) blended from scheme A
+ *                   (edge decay ratio r0 -> r1, log-linear) and scheme B (FWHM
+ *                   beta_min -> beta_max, linear) by a smoothstep between
+ *                   alpha0 and alpha1 of a = t / T;
+ *   PL_RHO_EXP      charge restoration, exponential-like, sigma(t) =
+ *                   -sigma_factor T ln(1 - t / T);
+ *   PL_RHO_LINEAR   linear-like, clamped at 0, k(t) = k_factor / tan(pi t / 2T);
+ *   PL_RHO_SIGMOID  sigmoid-like, the same k(t).
+ * The paper gives no values besides T = 300 for its figure; the defaults are
+ * readings.  panels x nodes: the composite Gauss-Legendre rule per axis of
+ * the models without a closed form. */
+typedef enum { PL_RHO_GAUSS = 0, PL_RHO_EXP = 1, PL_RHO_LINEAR = 2, PL_RHO_SIGMOID = 3 } pl_rho_model;
+typedef struct {
+  int32_t model;             /* pl_rho_model */
+  int32_t T;                 /* iterations of the schedule, >= 1 */
+  double r0, r1;             /* scheme A, in (0, 1) */
+  double beta_min, beta_max; /* scheme B, > 0 */
+  double alpha0, alpha1;     /* blend window, alpha0 < alpha1 */
+  double sigma_factor;       /* > 0 */
+  double k_factor;           /* > 0 */
+  int32_t panels, nodes;     /* 1..64 panels, 1..32 nodes */
+} pl_rho_params;
+
+/* Defaults: Gaussian, T 300, r 0.05 -> 0.9, beta 0.25 -> 1.5, blend 0.3..0.7,
+ * sigma_factor 0.002, k_factor 0.5, 4 panels of 8 nodes. */
+void pl_rho_params_default(pl_rho_params *p);
+
+/* rho[b] (device, nbx * nby doubles, bins row-major with x fastest over the
+ * region) = sum over macros, ascending, of the integral of macro m's density
+ * at iteration t (0 <= t <= T) over bin b, in area units.  mx, my, mw, mh:
+ * device, the macros' centres and sizes.  FP64.  Needs no workspace; does not
+ * synchronize.  Errors: INVALID_ARG, CUDA. */
+pl_status pl_macro_density(const pl_rho_params *rp, int32_t t, int32_t num_macros,
+                           const float *mx, const float *my, const float *mw, const float *mh,
+                           double xl, double yl, double xh, double yh, int32_t nbx, int32_t nby,
+                           double *rho, pl_stream stream);
 
 /* Copies of the graph for exact comparison (all HOST buffers):
  * static CSR: rp[static nodes + 1], col[static nnz], w[static nnz] (stored

@@ -119,6 +119,16 @@ def lib(parallel: bool = False):
         L.orc_u01.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_store.restype = dbl
         L.orc_store.argtypes = [dbl, C.c_int]
+        L.orc_gauss_legendre.argtypes = [C.c_int, vp, vp]
+        for f in ("orc_rho_eta", "orc_rho_sigma", "orc_rho_k"):
+            getattr(L, f).restype = dbl
+            getattr(L, f).argtypes = [vp, C.c_int]
+        L.orc_rho_value.restype = dbl
+        L.orc_rho_value.argtypes = [vp, C.c_int, dbl, dbl, dbl, dbl]
+        L.orc_rho_integral.restype = dbl
+        L.orc_rho_integral.argtypes = [vp, C.c_int, dbl, dbl, dbl, dbl, dbl, dbl]
+        L.orc_macro_density.argtypes = [vp, C.c_int, C.c_int32, vp, vp, vp, vp, dbl, dbl, dbl,
+                                         dbl, C.c_int32, C.c_int32, vp]
         _ = i64
         _libs[parallel] = L
     return L
@@ -312,3 +322,64 @@ def u01(seed: int, ctr: int) -> float:
 
 def store(w: float, dtype: int) -> float:
     return lib().orc_store(float(w), int(dtype))
+
+
+# ----------------------------------------------- Sec. VI charge schedules
+RHO_GAUSS, RHO_EXP, RHO_LINEAR, RHO_SIGMOID = 0, 1, 2, 3
+
+
+class RhoParams(C.Structure):
+    _fields_ = [("model", C.c_int32), ("T", C.c_int32), ("r0", C.c_double), ("r1", C.c_double),
+                ("beta_min", C.c_double), ("beta_max", C.c_double), ("alpha0", C.c_double),
+                ("alpha1", C.c_double), ("sigma_factor", C.c_double), ("k_factor", C.c_double),
+                ("panels", C.c_int32), ("nodes", C.c_int32)]
+
+
+# Readings (the paper gives T = 300 for its figure and no other value).
+RHO_DEFAULTS = dict(model=RHO_GAUSS, T=300, r0=0.05, r1=0.9, beta_min=0.25, beta_max=1.5,
+                    alpha0=0.3, alpha1=0.7, sigma_factor=0.002, k_factor=0.5, panels=4, nodes=8)
+
+
+def rho_params(**kw) -> RhoParams:
+    d = dict(RHO_DEFAULTS)
+    d.update(kw)
+    p = RhoParams()
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+def gauss_legendre(n):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gauss_legendre(int(n), x.ctypes.data, w.ctypes.data)
+    return x, w
+
+
+def rho_eta(rp, t):
+    return lib().orc_rho_eta(C.byref(rp), int(t))
+
+
+def rho_sigma(rp, t):
+    return lib().orc_rho_sigma(C.byref(rp), int(t))
+
+
+def rho_k(rp, t):
+    return lib().orc_rho_k(C.byref(rp), int(t))
+
+
+def rho_value(rp, t, dx, dy, w, h):
+    return lib().orc_rho_value(C.byref(rp), int(t), dx, dy, w, h)
+
+
+def rho_integral(rp, t, w, h, ax, bx, ay, by):
+    return lib().orc_rho_integral(C.byref(rp), int(t), w, h, ax, bx, ay, by)
+
+
+def macro_density(rp, t, mx, my, mw, mh, region, nbx, nby):
+    """Per-bin integral of the macros' scheduled charge (area units)."""
+    a = [np.ascontiguousarray(v, np.float64) for v in (mx, my, mw, mh)]
+    out = np.zeros(nbx * nby)
+    xl, yl, xh, yh = region
+    lib().orc_macro_density(C.byref(rp), int(t), len(a[0]), *(v.ctypes.data for v in a),
+                            xl, yl, xh, yh, int(nbx), int(nby), out.ctypes.data)
+    return out

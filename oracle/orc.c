@@ -983,3 +983,174 @@ double orc_hpwl(const orc_netlist *nl, const double *cx, const double *cy) {
   free(span);
   return total;
 }
+
+/* ------------------------------- Sec. VI: macro charge-density schedules */
+
+#define ORC_PI 3.14159265358979323846
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: the roots of P_n by Newton's
+ * method from the classical starting guesses cos(pi (i - 1/4) / (n + 1/2)),
+ * P_n and P_n' from the three-term recurrence; weights 2 / ((1 - x^2) P_n'^2). */
+void orc_gauss_legendre(int n, double *x, double *w) {
+  for (int i = 1; i <= n; ++i) {
+    double z = cos(ORC_PI * (i - 0.25) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i - 1] = -z;
+    w[i - 1] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* Blended concentration eta(t) of the charge-redistribution model:
+ * alpha = t / T; scheme A: log r = (1 - alpha) log r0 + alpha log r1,
+ * eta_A = sqrt(-2 log r); scheme B: beta = beta_min + (beta_max - beta_min)
+ * alpha, eta_B = sqrt(2 ln 2) / beta; smoothstep w(alpha) between alpha0 and
+ * alpha1; eta = eta_B^(1 - w) eta_A^w. */
+double orc_rho_eta(const orc_rho_params *rp, int t) {
+  double a = (double)t / (double)rp->T;
+  double lr = (1.0 - a) * log(rp->r0) + a * log(rp->r1);
+  double ea = sqrt(-2.0 * lr);
+  double beta = rp->beta_min + (rp->beta_max - rp->beta_min) * a;
+  double eb = sqrt(2.0 * log(2.0)) / beta;
+  double wgt;
+  if (a <= rp->alpha0) wgt = 0.0;
+  else if (a >= rp->alpha1) wgt = 1.0;
+  else {
+    double z = (a - rp->alpha0) / (rp->alpha1 - rp->alpha0);
+    wgt = 3.0 * z * z - 2.0 * z * z * z;
+  }
+  return pow(eb, 1.0 - wgt) * pow(ea, wgt);
+}
+
+/* sigma(t) = -sigma_factor T ln(1 - t / T) of the exponential-like model
+ * (infinite at t = T). */
+double orc_rho_sigma(const orc_rho_params *rp, int t) {
+  if (t >= rp->T) return INFINITY;
+  return -rp->sigma_factor * rp->T * log(1.0 - (double)t / (double)rp->T);
+}
+
+/* k(t) = k_factor / tan(pi t / (2 T)) of the linear- and sigmoid-like models
+ * (infinite at t = 0, 0 at t = T). */
+double orc_rho_k(const orc_rho_params *rp, int t) {
+  if (t <= 0) return INFINITY;
+  if (t >= rp->T) return 0.0;
+  return rp->k_factor / tan(0.5 * ORC_PI * (double)t / (double)rp->T);
+}
+
+/* The density rho_t at offset (dx, dy) from the centre of a w x h macro, zero
+ * outside the macro.  Readings where the paper is silent: the linear-like
+ * density is clamped at 0 (a charge density; the restored region is
+ * r <= 1 / k); with sigma = 0 or k = infinity the density is 0 away from the
+ * centre; with sigma = infinity or k = 0 it is 1. */
+double orc_rho_value(const orc_rho_params *rp, int t, double dx, double dy, double w, double h) {
+  if (fabs(dx) > 0.5 * w || fabs(dy) > 0.5 * h) return 0.0;
+  double u = dx / w, v = dy / h;
+  if (rp->model == ORC_RHO_GAUSS) {
+    double eta = orc_rho_eta(rp, t), e = erf(eta / sqrt(2.0));
+    return 2.0 * eta * eta / (ORC_PI * e * e) * exp(-2.0 * eta * eta * (u * u + v * v));
+  }
+  if (rp->model == ORC_RHO_EXP) {
+    double sg = orc_rho_sigma(rp, t);
+    if (isinf(sg)) return 1.0;
+    if (!(sg > 0.0)) return 0.0;
+    double tx = tan(ORC_PI * u), ty = tan(ORC_PI * v);
+    return exp(-(tx * tx + ty * ty) / (2.0 * sg * sg));
+  }
+  double k = orc_rho_k(rp, t), r = sqrt(2.0 * (u * u + v * v));
+  if (isinf(k)) return 0.0;
+  if (rp->model == ORC_RHO_LINEAR) return fmax(0.0, 1.0 - k * r);
+  return 2.0 / (1.0 + exp(k * r));
+}
+
+/* Composite Gauss-Legendre sum of f over [a, b]: `panels` equal panels,
+ * `nodes` points each. */
+static double gl_1d(double a, double b, int panels, int nodes, const double *gx, const double *gw,
+                    double (*f)(double, const void *), const void *ctx) {
+  double s = 0.0, hp = (b - a) / panels;
+  for (int p = 0; p < panels; ++p) {
+    double c = a + (p + 0.5) * hp;
+    for (int i = 0; i < nodes; ++i) s += 0.5 * hp * gw[i] * f(c + 0.5 * hp * gx[i], ctx);
+  }
+  return s;
+}
+
+typedef struct { double scale; double w; } exp_ctx;
+static double exp_1d(double d, const void *c) {
+  const exp_ctx *e = (const exp_ctx *)c;
+  double tv = tan(ORC_PI * d / e->w);
+  return exp(-tv * tv * e->scale);
+}
+
+/* Integral of rho_t over [ax, bx] x [ay, by] (offsets from the macro centre),
+ * the part inside the macro.  Gaussian: the separable closed form with erf;
+ * exponential-like: separable, a composite Gauss-Legendre rule per axis;
+ * linear- and sigmoid-like: the tensor rule on the rectangle. */
+double orc_rho_integral(const orc_rho_params *rp, int t, double w, double h, double ax, double bx,
+                        double ay, double by) {
+  ax = fmax(ax, -0.5 * w); bx = fmin(bx, 0.5 * w);
+  ay = fmax(ay, -0.5 * h); by = fmin(by, 0.5 * h);
+  if (!(bx > ax) || !(by > ay)) return 0.0;
+  if (rp->model == ORC_RHO_GAUSS) {
+    double eta = orc_rho_eta(rp, t), e = erf(eta / sqrt(2.0));
+    double A = 2.0 * eta * eta / (ORC_PI * e * e);
+    double c = sqrt(2.0) * eta;
+    /* int_a^b exp(-2 eta^2 d^2 / w^2) dd = w sqrt(pi) / (2 sqrt(2) eta) [erf(c b / w) - erf(c a / w)] */
+    double ix = w * sqrt(ORC_PI) / (2.0 * c) * (erf(c * bx / w) - erf(c * ax / w));
+    double iy = h * sqrt(ORC_PI) / (2.0 * c) * (erf(c * by / h) - erf(c * ay / h));
+    return A * ix * iy;
+  }
+  int n = rp->nodes, P = rp->panels;
+  double *gx = (double *)xcalloc(n, sizeof(double)), *gw = (double *)xcalloc(n, sizeof(double));
+  orc_gauss_legendre(n, gx, gw);
+  double r = 0.0;
+  if (rp->model == ORC_RHO_EXP) {
+    double sg = orc_rho_sigma(rp, t);
+    if (isinf(sg)) r = (bx - ax) * (by - ay);
+    else if (sg > 0.0) {
+      exp_ctx cx = {1.0 / (2.0 * sg * sg), w}, cy = {1.0 / (2.0 * sg * sg), h};
+      r = gl_1d(ax, bx, P, n, gx, gw, exp_1d, &cx) * gl_1d(ay, by, P, n, gx, gw, exp_1d, &cy);
+    }
+  } else {
+    double hx = (bx - ax) / P, hy = (by - ay) / P;
+    for (int px = 0; px < P; ++px)
+      for (int py = 0; py < P; ++py) {
+        double cx = ax + (px + 0.5) * hx, cy = ay + (py + 0.5) * hy;
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j)
+            r += 0.25 * hx * hy * gw[i] * gw[j] *
+                 orc_rho_value(rp, t, cx + 0.5 * hx * gx[i], cy + 0.5 * hy * gx[j], w, h);
+      }
+  }
+  free(gx);
+  free(gw);
+  return r;
+}
+
+/* Delta rho_b(t) summed over macros (ascending): for every bin b of the
+ * nbx x nby grid over the region, the integral over B_b of each macro's
+ * rho_t (Sec. VI), in area units. */
+void orc_macro_density(const orc_rho_params *rp, int t, int32_t nm, const double *mx,
+                       const double *my, const double *mw, const double *mh, double xl, double yl,
+                       double xh, double yh, int32_t nbx, int32_t nby, double *out) {
+  double wb = (xh - xl) / nbx, hb = (yh - yl) / nby;
+  for (int64_t b = 0; b < (int64_t)nbx * nby; ++b) out[b] = 0.0;
+  for (int32_t b = 0; b < nbx * nby; ++b) {
+    int32_t bx = b % nbx, by = b / nbx;
+    double x0 = xl + bx * wb, x1 = xl + (bx + 1) * wb, y0 = yl + by * hb, y1 = yl + (by + 1) * hb;
+    double s = 0.0;
+    for (int32_t m = 0; m < nm; ++m)
+      s += orc_rho_integral(rp, t, mw[m], mh[m], x0 - mx[m], x1 - mx[m], y0 - my[m], y1 - my[m]);
+    out[b] = s;
+  }
+}

@@ -78,6 +78,29 @@ void orc_init_signal(const orc_graph *g, uint64_t seed, const float *xy0,
 int  orc_run(orc_graph *g, const orc_params *pr, uint64_t seed, const float *xy0,
              double *gx, double *gy);
 double orc_hpwl(const orc_netlist *nl, const double *cx, const double *cy);
+
+/* Sec. VI: iteration-scheduled macro charge densities and their bin integrals */
+enum { ORC_RHO_GAUSS = 0, ORC_RHO_EXP = 1, ORC_RHO_LINEAR = 2, ORC_RHO_SIGMOID = 3 };
+typedef struct {
+  int32_t model;          /* ORC_RHO_* */
+  int32_t T;              /* iterations of the schedule */
+  double r0, r1;          /* scheme A: edge decay ratio at alpha = 0 and 1 */
+  double beta_min, beta_max; /* scheme B: normalized FWHM at alpha = 0 and 1 */
+  double alpha0, alpha1;  /* smoothstep blend between them */
+  double sigma_factor;    /* exponential-like model */
+  double k_factor;        /* linear-like and sigmoid-like models */
+  int32_t panels, nodes;  /* composite Gauss-Legendre rule per axis */
+} orc_rho_params;
+void orc_gauss_legendre(int n, double *x, double *w);
+double orc_rho_eta(const orc_rho_params *rp, int t);
+double orc_rho_sigma(const orc_rho_params *rp, int t);
+double orc_rho_k(const orc_rho_params *rp, int t);
+double orc_rho_value(const orc_rho_params *rp, int t, double dx, double dy, double w, double h);
+double orc_rho_integral(const orc_rho_params *rp, int t, double w, double h, double ax, double bx,
+                        double ay, double by);
+void orc_macro_density(const orc_rho_params *rp, int t, int32_t nm, const double *mx,
+                       const double *my, const double *mw, const double *mh, double xl, double yl,
+                       double xh, double yh, int32_t nbx, int32_t nby, double *out);
 double orc_exp(double x);
 double orc_u01(uint64_t seed, uint64_t ctr);
 double orc_store(double w, int dtype);

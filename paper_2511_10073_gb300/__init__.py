@@ -85,6 +85,10 @@ def lib():
             "pl_graph_export": (C.c_int, [vp] * 10),
             "pl_graph_destroy": (None, [vp]),
             "pl_last_error": (C.c_char_p, []),
+            "pl_filter_init_batch": (C.c_int, [i32, vp, vp, vp, vp, i32, vp]),
+            "pl_rho_params_default": (None, [vp]),
+            "pl_macro_density": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, dbl, dbl, dbl, dbl,
+                                           i32, i32, vp, vp]),
             "pl_prof_enable": (None, [C.c_int]),
             "pl_prof_read": (C.c_int, [vp]),
         }
@@ -270,6 +274,18 @@ def pl_filter_init(g: Graph, prm: PlParams, seed: int, xy0_cells, xy_out_cells, 
                                 _ptr(xy_out_cells), _stream(stream)))
 
 
+def pl_filter_init_batch(graphs, prm: PlParams, seeds, outs, streams):
+    """The initializer of every design of a batch, concurrently on `streams`
+    (torch CUDA streams, one worker thread each); outs[i]: device tensor of
+    graphs[i]'s num_cells pairs."""
+    n = len(graphs)
+    gh = (C.c_void_p * n)(*[g.handle.value for g in graphs])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    sp = (C.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
+    _check(lib().pl_filter_init_batch(n, gh, C.byref(prm), sd, op, len(streams), sp))
+
+
 def pl_hpwl_workspace_size(num_nets: int) -> int:
     return int(lib().pl_hpwl_workspace_size(int(num_nets)))
 
@@ -301,3 +317,33 @@ def pl_prof_read() -> dict:
     return dict(launches=int(out[0]), hr_launches=int(out[1]), hr_ms=float(out[2]),
                 hr_bytes=float(out[3]), gift_launches=int(out[4]), gift_ms=float(out[5]),
                 gift_bytes=float(out[6]))
+
+
+# ------------------------------------------- Sec. VI macro charge schedules
+PL_RHO_GAUSS, PL_RHO_EXP, PL_RHO_LINEAR, PL_RHO_SIGMOID = range(4)
+
+
+class PlRhoParams(C.Structure):
+    _fields_ = [("model", C.c_int32), ("T", C.c_int32), ("r0", C.c_double), ("r1", C.c_double),
+                ("beta_min", C.c_double), ("beta_max", C.c_double), ("alpha0", C.c_double),
+                ("alpha1", C.c_double), ("sigma_factor", C.c_double), ("k_factor", C.c_double),
+                ("panels", C.c_int32), ("nodes", C.c_int32)]
+
+
+def rho_params(**kw) -> PlRhoParams:
+    """pl_rho_params_default() with the given fields replaced."""
+    p = PlRhoParams()
+    lib().pl_rho_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def pl_macro_density(rp: PlRhoParams, t: int, mx, my, mw, mh, region, nbx: int, nby: int, out,
+                     stream=None):
+    """Per-bin integral (device doubles `out`) of the macros' charge at
+    iteration t; mx..mh are device float tensors."""
+    xl, yl, xh, yh = (float(v) for v in region)
+    _check(lib().pl_macro_density(C.byref(rp), int(t), int(mx.numel()), _ptr(mx), _ptr(my),
+                                  _ptr(mw), _ptr(mh), xl, yl, xh, yh, int(nbx), int(nby),
+                                  _ptr(out), _stream(stream)))

@@ -212,7 +212,13 @@ pl_status pl_build_graph(const pl_netlist *nl, const pl_params *p, const float *
   g->hint_mark = 0;
   g->star_w_ok = false;
   GraphScope scope(g);
-  st = build_static(g, nl, p, s);
+  {
+    // the static build's merge sort reads a process-wide constant (the merge
+    // context), so static builds on different threads take turns
+    static std::mutex build_mu;
+    std::lock_guard<std::mutex> lk(build_mu);
+    st = build_static(g, nl, p, s);
+  }
   if (st == PL_OK && xy_nodes) st = build_hints(g, p, xy_nodes, s);
   if (st == PL_OK) {
     cudaError_t e = cudaStreamSynchronize(s);

@@ -21,10 +21,9 @@
 
 namespace pl {
 
-constexpr int kBinThreads = 256;   // one CTA per chunk
-constexpr int kBinPer = 4;         // hint cells per thread
-constexpr int kBinChunk = kBinThreads * kBinPer;  // hint cells per chunk
-constexpr int kBinSlotTile = 10;   // slots per round of a chunk (a warp sums each)
+constexpr int kBinThreads = 256;   // 8 warps a CTA, each on its own chunks
+constexpr int kBinPer = 8;         // hint cells per lane
+constexpr int kBinChunk = 32 * kBinPer;  // hint cells per chunk (one warp)
 
 struct BinGeo {
   int nbx, nby, hx, hy, W;  // bin grid, window half widths, slots per window
@@ -47,105 +46,106 @@ __device__ __forceinline__ float bw_load(const void *bw, size_t k) {
 
 // Per chunk and slot, a float4 partial: with DEG, (sum w, sum of positive w)
 // as two double-floats; otherwise (sum w x_i, sum w y_i) with exact products.
-// bwq: the window blocks in bucket-list order (the block of the cell at list
-// position k at k W), so a warp reads consecutive blocks; x: coordinates of
+// A warp per chunk: lane j takes the chunk's cells j, j + 32, ... (all their
+// loads in flight together); per slot, each lane adds its cells in order and
+// a fixed tree adds the lanes, so every partial is a fixed function of the
+// inputs.  bwq: the window blocks in bucket-list order (the block of the cell
+// at list position k at k W), read as consecutive blocks; x: coordinates of
 // every node (the cells' ones are gathered).  The chunk count is bchunk[NB];
-// the grid may be any size.  Slots go in rounds of kBinSlotTile:
-// each thread forms its cells' sums for the round's slots (every weight load
-// of the round in flight at once) and leaves them in shared memory; warp j
-// then adds slot j's 256 thread sums, lane q taking threads q, q + 32, ...
-// in order, and a fixed tree over the lanes.
+// the grid may be any size.
 template <int WT, bool DEG>
-__global__ void __launch_bounds__(kBinThreads) k_bin_partials(BinGeo B, const int32_t *bchunk,
+__global__ void __launch_bounds__(kBinThreads, 4) k_bin_partials(BinGeo B, const int32_t *bchunk,
                                                               const int32_t *cown,
                                                               const int64_t *boff,
                                                               const uint32_t *blist,
                                                               const void *bwq, const float2 *x,
                                                               float4 *part) {
-  __shared__ float4 red[kBinSlotTile][kBinThreads];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int nchunk = bchunk[B.NB];
-  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nchunk;
+       c += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int b = cown[c];
     const long long k0 = boff[2 * b] + (long long)(c - bchunk[b]) * kBinChunk;
     const long long k1 = boff[2 * b + 1];
-    // thread t takes the chunk's cells t, t + kBinThreads, ...
-    uint32_t ci[kBinPer];
-    long long kp[kBinPer];
+    uint32_t kp[kBinPer];  // list positions (below 2^31: movable cells)
     bool cv[kBinPer];
+    uint32_t ci[kBinPer];
 #pragma unroll
     for (int u = 0; u < kBinPer; ++u) {
-      kp[u] = k0 + threadIdx.x + (long long)u * kBinThreads;
-      cv[u] = kp[u] < k1;
+      kp[u] = (uint32_t)(k0 + lane + 32LL * u);
+      cv[u] = k0 + lane + 32LL * u < k1;
       ci[u] = (!DEG && cv[u]) ? blist[kp[u]] : 0u;
     }
     float2 xi[kBinPer];
 #pragma unroll
     for (int u = 0; u < kBinPer; ++u) xi[u] = (!DEG && cv[u]) ? x[ci[u]] : make_float2(0.f, 0.f);
-    for (int s0 = 0; s0 < B.W; s0 += kBinSlotTile) {
-      const int ns = B.W - s0 < kBinSlotTile ? B.W - s0 : kBinSlotTile;
-      float w[kBinPer][kBinSlotTile];
+    for (int t = 0; t < B.W; ++t) {
+      float w[kBinPer];
 #pragma unroll
-      for (int u = 0; u < kBinPer; ++u)
+      for (int u = 0; u < kBinPer; ++u) w[u] = cv[u] ? bw_load<WT>(bwq, (size_t)kp[u] * B.W + t) : 0.f;
+      dfl a{0.f, 0.f}, e{0.f, 0.f};
 #pragma unroll
-        for (int t = 0; t < kBinSlotTile; ++t)
-          w[u][t] = (cv[u] && t < ns) ? bw_load<WT>(bwq, (size_t)kp[u] * B.W + s0 + t) : 0.f;
-#pragma unroll
-      for (int t = 0; t < kBinSlotTile; ++t) {
-        if (t >= ns) break;
-        dfl a{0.f, 0.f}, e{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < kBinPer; ++u) {
-          if (DEG) {
-            df_add(a, w[u][t]);
-            if (w[u][t] > 0.f) df_add(e, w[u][t]);
-          } else {
-            df_add_prod(a, w[u][t], xi[u].x);
-            df_add_prod(e, w[u][t], xi[u].y);
-          }
+      for (int u = 0; u < kBinPer; ++u) {
+        if (DEG) {
+          df_add(a, w[u]);
+          if (w[u] > 0.f) df_add(e, w[u]);
+        } else {
+          df_add_prod(a, w[u], xi[u].x);
+          df_add_prod(e, w[u], xi[u].y);
         }
-        red[t][threadIdx.x] = make_float4(a.hi, a.lo, e.hi, e.lo);
       }
-      __syncthreads();
-      for (int t = wid; t < ns; t += kBinThreads / 32) {
-        dfl a{0.f, 0.f}, e{0.f, 0.f};
-#pragma unroll
-        for (int q = lane; q < kBinThreads; q += 32) {
-          const float4 v = red[t][q];
-          df_add_df(a, dfl{v.x, v.y});
-          df_add_df(e, dfl{v.z, v.w});
-        }
-        a = warp_sum_df(a);
-        e = warp_sum_df(e);
-        if (lane == 0) part[(size_t)c * B.W + s0 + t] = make_float4(a.hi, a.lo, e.hi, e.lo);
-      }
-      __syncthreads();
+      a = warp_sum_df(a);
+      e = warp_sum_df(e);
+      if (lane == 0) part[(size_t)c * B.W + t] = make_float4(a.hi, a.lo, e.hi, e.lo);
     }
   }
 }
 
-// Sums of bin b's row by the lanes of one warp.  Its (slot, chunk) pairs are
-// taken in slot order, each slot's chunks of its source bucket in order, and
-// dealt round robin to the lanes (a hot bucket's chunks spread over the
-// warp); each lane adds its pairs in that order, then a fixed tree.  Returns
-// the two double-floats of the partials' layout.
-__device__ __forceinline__ void bin_row_sums(const BinGeo &B, int b, const int32_t *bchunk,
-                                             const float4 *part, dfl *a, dfl *e) {
+// Sums of each (bucket, slot) over the bucket's chunks: a warp per pair, the
+// lanes strided over the chunks in order, then a fixed tree (a hot bucket's
+// hundreds of chunks spread over the warp).
+static __global__ void k_bin_bucket_sums(BinGeo B, const int32_t *bchunk, const float4 *part,
+                                  float4 *bsum) {
+  const int lane = threadIdx.x & 31;
+  const long long npair = (long long)B.NB * B.W;
+  for (long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; q < npair;
+       q += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int b = (int)(q / B.W), s = (int)(q - (long long)b * B.W);
+    dfl a{0.f, 0.f}, e{0.f, 0.f};
+    const int c1 = bchunk[b + 1];
+    for (int c0 = bchunk[b] + lane; c0 < c1; c0 += 32 * 4) {
+      float4 v[4];  // four partials in flight, added in order
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = c0 + 32 * u < c1 ? __ldcg(&part[(size_t)(c0 + 32 * u) * B.W + s])
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        df_add_df(a, dfl{v[u].x, v[u].y});
+        df_add_df(e, dfl{v[u].z, v[u].w});
+      }
+    }
+    a = warp_sum_df(a);
+    e = warp_sum_df(e);
+    if (lane == 0) bsum[q] = make_float4(a.hi, a.lo, e.hi, e.lo);
+  }
+}
+
+// Sums of bin b's row by the lanes of one warp: for every slot s whose source
+// bucket b - offset(s) lies in the grid, that bucket's sum for s; lanes
+// strided over the slots, then a fixed tree.  Returns the two double-floats of
+// the partials' layout.
+__device__ __forceinline__ void bin_row_sums(const BinGeo &B, int b, const float4 *bsum, dfl *a,
+                                             dfl *e) {
   const int lane = threadIdx.x & 31;
   const int bx = b % B.nbx, by = b / B.nbx, wx = 2 * B.hx + 1;
   dfl sa{0.f, 0.f}, se{0.f, 0.f};
-  int flat = 0;  // pairs dealt before this slot
-  for (int s = 0; s < B.W; ++s) {
+  for (int s = lane; s < B.W; s += 32) {
     const int sx = bx - (s % wx - B.hx), sy = by - (s / wx - B.hy);
     if (sx < 0 || sy < 0 || sx >= B.nbx || sy >= B.nby) continue;
-    const int src = sy * B.nbx + sx;
-    const int c0 = bchunk[src], n = bchunk[src + 1] - c0;
-    for (int k = (lane - flat % 32 + 32) % 32; k < n; k += 32) {
-      const float4 q = __ldcg(&part[(size_t)(c0 + k) * B.W + s]);
-      df_add_df(sa, dfl{q.x, q.y});
-      df_add_df(se, dfl{q.z, q.w});
-    }
-    flat += n;
+    const float4 q = __ldcg(&bsum[(size_t)(sy * B.nbx + sx) * B.W + s]);
+    df_add_df(sa, dfl{q.x, q.y});
+    df_add_df(se, dfl{q.z, q.w});
   }
   *a = warp_sum_df(sa);
   *e = warp_sum_df(se);
@@ -163,14 +163,6 @@ static __global__ void k_bin_chunk_count(int NB, const int64_t *boff, int32_t *c
 static __global__ void k_chunk_bins(int NB, const int32_t *bchunk, int32_t *cown) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x)
     for (int c = bchunk[b]; c < bchunk[b + 1]; ++c) cown[c] = b;
-}
-
-// Place of each movable cell in the bucket lists (the bucket-order copies of
-// the window blocks are written at it).
-static __global__ void k_bucket_rank(long long n, const uint32_t *blist, int32_t *crank) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    crank[blist[k]] = (int32_t)k;
 }
 
 }  // namespace pl

@@ -97,6 +97,7 @@ struct StepArgs {
   const int64_t *boff;
   const uint32_t *blist;
   float4 *bpart;
+  float4 *bpartb;  // bpart summed per (bucket, slot)
 };
 
 // Epilogue of node v with its kind kd and (tap steps) accumulator ac loaded
@@ -335,44 +336,37 @@ __device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uin
 
 // Window slots of hint cell v (refinement filter): lane m of the row's group
 // takes slots m, m + L, ...; the column of a slot is the bin node at the
-// cell's bin plus the slot's offset, skipped outside the bin grid.  Like the
-// stored entries, kRowUnroll weights are loaded before their gathers of x.
+// cell's bin plus the slot's offset.  Slots outside the bin grid hold weight
+// 0, so their bin index is clamped into the grid instead of tested (a finite
+// coordinate times 0).  The weights are loaded before their gathers of x.
+constexpr int kSlotUnroll = 5;  // slots a lane loads at once (a 3 x 3 window over 2 lanes)
 template <int WT, int L>
-__device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int m, float &sx,
+__device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int hb, int m, float &sx,
                                            float &sy) {
-  const int hb = A.hbin[v];
   if (hb < 0) return;
-  const int nbx = A.B.nbx, wx = 2 * A.B.hx + 1, W = A.B.W;
+  const int nbx = A.B.nbx, nby = A.B.nby, wx = 2 * A.B.hx + 1, W = A.B.W;
   const int bx = hb % nbx, by = hb / nbx;
-  // window position (ix, iy) of slot s, advanced by L slots at a time
-  int iy = m / wx, ix = m - iy * wx;
+  const float iwx = 1.0f / (float)wx;  // row of a slot: (s + 1/2) / wx, exact below 2^12
   const float *wf = reinterpret_cast<const float *>(A.hbw) + (size_t)v * W;
   const unsigned short *wh = reinterpret_cast<const unsigned short *>(A.hbw) + (size_t)v * W;
-  for (int s0 = m; s0 < W; s0 += kRowUnroll * L) {
-    int cb[kRowUnroll];
-    float wv[kRowUnroll];
+  const float2 *xb = A.x + A.bn0;
+  for (int s0 = m; s0 < W; s0 += kSlotUnroll * L) {
+    float wv[kSlotUnroll];
+    int cb[kSlotUnroll];
 #pragma unroll
-    for (int u = 0; u < kRowUnroll; ++u) {
+    for (int u = 0; u < kSlotUnroll; ++u) {
       const int sl = s0 + u * L;
-      cb[u] = -1;
-      wv[u] = 0.f;
-      if (sl < W) {
-        const int xx = bx + ix - A.B.hx, yy = by + iy - A.B.hy;
-        if (xx >= 0 && yy >= 0 && xx < nbx && yy < A.B.nby) {
-          cb[u] = yy * nbx + xx;
-          wv[u] = WT == 0 ? __ldcs(wf + sl) : __uint_as_float((uint32_t)__ldcs(wh + sl) << 16);
-        }
-        ix += L;
-        while (ix >= wx) {
-          ix -= wx;
-          ++iy;
-        }
-      }
+      const bool ok = sl < W;
+      wv[u] = ok ? (WT == 0 ? __ldcs(wf + sl) : __uint_as_float((uint32_t)__ldcs(wh + sl) << 16)) : 0.f;
+      const int iy = (int)(((float)sl + 0.5f) * iwx);
+      const int xx = min(max(bx + sl - iy * wx - A.B.hx, 0), nbx - 1);
+      const int yy = min(max(by + iy - A.B.hy, 0), nby - 1);
+      cb[u] = ok ? yy * nbx + xx : -1;
     }
 #pragma unroll
-    for (int u = 0; u < kRowUnroll; ++u) {
+    for (int u = 0; u < kSlotUnroll; ++u) {
       if (cb[u] >= 0) {
-        const float2 xv = __ldg(A.x + A.bn0 + cb[u]);
+        const float2 xv = __ldg(xb + cb[u]);
         sx = fmaf(wv[u], xv.x, sx);
         sy = fmaf(wv[u], xv.y, sy);
       }
@@ -380,8 +374,61 @@ __device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int m
   }
 }
 
+// A short row's st piece [k, e) by the row's pair of lanes in aligned groups
+// of 4 entries: lane m takes groups m, m + 2, ... from the group holding k,
+// one 16-byte index load and one 8-byte (BF16) or 16-byte (FP32) weight load
+// per group, entries outside [k, e) masked.  kGroupUnroll groups' loads are in
+// flight before their gathers.
+constexpr int kGroupUnroll = 2;
+template <int WT>
+__device__ __forceinline__ void row_groups(const int32_t *col, const void *w, uint32_t k,
+                                           uint32_t e, int m, const float2 *x, float &sx,
+                                           float &sy) {
+  if (k >= e) return;
+  for (uint32_t g = (k & ~3u) + 4u * m; g < e; g += 8u * kGroupUnroll) {
+    int4 cc[kGroupUnroll];
+    float wv[kGroupUnroll][4];
+#pragma unroll
+    for (int u = 0; u < kGroupUnroll; ++u) {
+      const uint32_t gg = g + 8u * u;
+      if (gg < e) {
+        cc[u] = __ldcs(reinterpret_cast<const int4 *>(col + gg));
+        if (WT == 0) {
+          const float4 q = __ldcs(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(w) + gg));
+          wv[u][0] = q.x; wv[u][1] = q.y; wv[u][2] = q.z; wv[u][3] = q.w;
+        } else {
+          const uint2 q = __ldcs(reinterpret_cast<const uint2 *>(reinterpret_cast<const unsigned short *>(w) + gg));
+          wv[u][0] = __uint_as_float(q.x << 16);
+          wv[u][1] = __uint_as_float(q.x & 0xffff0000u);
+          wv[u][2] = __uint_as_float(q.y << 16);
+          wv[u][3] = __uint_as_float(q.y & 0xffff0000u);
+        }
+      } else {
+        cc[u] = make_int4(0, 0, 0, 0);
+        wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGroupUnroll; ++u) {
+      const uint32_t gg = g + 8u * u;
+      const int ci[4] = {cc[u].x, cc[u].y, cc[u].z, cc[u].w};
+      float2 xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool in = gg + q >= k && gg + q < e;
+        xv[q] = in ? __ldg(x + ci[q]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sx = fmaf(wv[u][q], xv[q].x, sx);
+        sy = fmaf(wv[u][q], xv[q].y, sy);
+      }
+    }
+  }
+}
+
 template <int WT, int MODE>
-__global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
+__global__ void __launch_bounds__(kRowThreads, 6) k_spmm_rows(StepArgs A) {
   const int64_t N = A.nrows;
   constexpr int L = kRowLanes, RPW = 32 / L;
   const int lane = threadIdx.x & 31, m = lane & (L - 1);
@@ -392,8 +439,10 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
     const long long v = base + lane / L;
     bool live = false;
     uint32_t sa = 0, sb = 0, ha = 0, hb = 0;
+    int hbv = -1;
     if (v < N) {
       const uint32_t f0 = A.srp[v], f1 = A.srp[v + 1];
+      if (MODE == MODE_HR && two && v < A.C) hbv = A.hbin[v];  // in flight with the row pointers
       sa = f0 & kOffMask;
       sb = f1 & kOffMask;
       if (two) {
@@ -407,10 +456,10 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
     }
     float sx = 0.f, sy = 0.f;
     if (live) {
-      row_piece<WT, L>(A.scol, A.sw, sa + m, sb, A.x, sx, sy);
+      row_groups<WT>(A.scol, A.sw, sa, sb, m, A.x, sx, sy);
       if (two) {
         row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
-        if (MODE == MODE_HR && v < A.C) slot_piece<WT, L>(A, v, m, sx, sy);
+        if (MODE == MODE_HR) slot_piece<WT, L>(A, v, hbv, m, sx, sy);
       }
     }
 #pragma unroll
@@ -426,124 +475,6 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows(StepArgs A) {
       const double acv = A.tap ? reinterpret_cast<const double *>(A.acc)[2 * v + m] : 0.0;
       epilogue_c(A, v, A.nkind[v], m, acv, av * xr + bv * (m ? sy : sx));
     }
-  }
-}
-
-// Short rows, streamed: a warp takes a tile of 32 consecutive rows.  Their
-// static entries are contiguous in st's short region, so the warp walks them
-// 32 at a time with coalesced index and weight loads (one entry per lane),
-// gathers x, and adds each row's products with a segmented scan over the
-// lanes; the last lane of a row's run in the window adds the run to the row's
-// sum in shared memory (runs in window order, so the sums are a fixed
-// function of the inputs).  Then lane j finishes row j of the tile: its hint
-// entries and window slots (refinement filter), the combine, and the epilogue
-// for both coordinates.  Hub rows are skipped (their own launches).
-constexpr int kTileRows = 32;
-constexpr int kTileWin = 4;  // windows of 32 entries whose loads are in flight together
-
-template <int WT, int MODE>
-__global__ void __launch_bounds__(kRowThreads) k_spmm_tiles(StepArgs A) {
-  __shared__ int32_t s_rid[kRowThreads / 32][32];
-  __shared__ float2 s_acc[kRowThreads / 32][kTileRows];
-  const int64_t N = A.nrows;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t *rid = s_rid[wid];
-  float2 *acc = s_acc[wid];
-  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
-  const bool two = A.hrp != nullptr;
-  for (long long r0 = gw * kTileRows; r0 < N; r0 += nw * kTileRows) {
-    const long long v = r0 + lane;
-    const bool inr = v < N;
-    // row j's static range (lane j), and the tile's whole range
-    const uint32_t a0 = inr ? (A.srp[v] & kOffMask) : 0u;
-    const uint32_t a1 = inr ? (A.srp[v + 1] & kOffMask) : 0u;
-    const long long rl = N - r0 < kTileRows ? N - r0 : kTileRows;
-    const uint32_t e0 = __shfl_sync(0xffffffffu, a0, 0);
-    const uint32_t e1 = __shfl_sync(0xffffffffu, a1, (int)rl - 1);
-    acc[lane] = make_float2(0.f, 0.f);
-    int carry = 0;  // row of the window's first entry when no row starts there
-    for (uint32_t k00 = e0; k00 < e1; k00 += 32 * kTileWin) {
-      // kTileWin windows' index and weight loads in flight, then their gathers
-      int cc[kTileWin];
-      float wv[kTileWin];
-#pragma unroll
-      for (int u = 0; u < kTileWin; ++u) {
-        const uint32_t k = k00 + 32 * u + lane;
-        cc[u] = k < e1 ? __ldcs(A.scol + k) : -1;
-        wv[u] = k < e1 ? wload<WT>(A.sw, k) : 0.f;
-      }
-      float2 xv[kTileWin];
-#pragma unroll
-      for (int u = 0; u < kTileWin; ++u)
-        xv[u] = cc[u] >= 0 ? __ldg(A.x + cc[u]) : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < kTileWin; ++u) {
-        const uint32_t k0 = k00 + 32 * u;
-        if (k0 >= e1) break;
-        // rows starting in this window: a head bit at their first entry, and
-        // the row's index at that lane
-        const bool head = inr && a1 > a0 && a0 >= k0 && a0 < k0 + 32;
-        if (head) rid[a0 - k0] = lane;
-        const unsigned hm = __reduce_or_sync(0xffffffffu, head ? (1u << (a0 - k0)) : 0u);
-        __syncwarp();
-        const uint32_t k = k0 + lane;
-        float px = wv[u] * xv[u].x, py = wv[u] * xv[u].y;
-        // this lane's run: from its last head at or before it (or lane 0)
-        const unsigned le = hm & (0xffffffffu >> (31 - lane));
-        const int st = le ? 31 - __clz(le) : 0;
-        const int row = le ? rid[st] : carry;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const float ux = __shfl_up_sync(0xffffffffu, px, d);
-          const float uy = __shfl_up_sync(0xffffffffu, py, d);
-          if (lane - d >= st) {
-            px += ux;
-            py += uy;
-          }
-        }
-        // the run's last lane (the next lane starts a row, or the entries end)
-        const bool last = k < e1 && (lane == 31 || k + 1 == e1 || ((hm >> (lane + 1)) & 1u));
-        if (last) {
-          float2 t = acc[row];
-          t.x += px;
-          t.y += py;
-          acc[row] = t;
-        }
-        carry = __shfl_sync(0xffffffffu, row, 31);
-        __syncwarp();
-      }
-    }
-    __syncwarp();
-    // lane j finishes row r0 + j
-    bool live = false;
-    uint32_t ha = 0, hb = 0;
-    if (inr) {
-      if (two) {
-        const uint32_t h0 = A.hrp[v];
-        ha = h0 & kOffMask;
-        hb = A.hrp[v + 1] & kOffMask;
-        live = !(h0 & kHubFlag);
-      } else {
-        live = !(A.srp[v] & kHubFlag);
-      }
-    }
-    float2 sm = acc[lane];
-    if (live && two) {
-      row_piece<WT, 1>(A.hcol, A.hw, ha, hb, A.x, sm.x, sm.y);
-      if (MODE == MODE_HR && v < A.C) slot_piece<WT, 1>(A, v, 0, sm.x, sm.y);
-    }
-    if (live) {
-      const float av = A.a[v];
-      const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
-      const float2 xr = A.x[v];
-      const uint8_t kd = A.nkind[v];
-      double2 ac = make_double2(0.0, 0.0);
-      if (A.tap) ac = A.acc[v];
-      epilogue_c(A, v, kd, 0, ac.x, av * xr.x + bv * sm.x);
-      epilogue_c(A, v, kd, 1, ac.y, av * xr.y + bv * sm.y);
-    }
-    __syncwarp();
   }
 }
 
@@ -636,7 +567,7 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
       if (v >= A.bn0) {
         // a bin row: its window-slot partials over the source buckets
         dfl bx, by;
-        bin_row_sums(A.B, (int)(v - A.bn0), A.bchunk, A.bpart, &bx, &by);
+        bin_row_sums(A.B, (int)(v - A.bn0), A.bpartb, &bx, &by);
         df_add_df(px, bx);
         df_add_df(py, by);
       } else if (v < A.C && A.hbin[v] >= 0) {
@@ -871,8 +802,8 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   const int wi = wdtype == PL_W_BF16 ? 1 : 0;
   if (!occ[wi]) {
     int b = 0;
-    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_tiles<1, MODE>, kRowThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_tiles<0, MODE>, kRowThreads, 0);
+    cudaError_t e = wi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<1, MODE>, kRowThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_rows<0, MODE>, kRowThreads, 0);
     occ[wi] = (e == cudaSuccess && b > 0) ? b : 1;
   }
   const bool prof = prof_on();
@@ -891,9 +822,13 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     note_launch();
     if (MODE == MODE_HR && A.bpart) {
       // bin rows: chunk partials of the window blocks times the cells' x
-      const int bgrid = (int)(g->nbc_max < 152LL * 8 ? g->nbc_max : 152LL * 8);
+      const long long bwant = (g->nbc_max + kBinThreads / 32 - 1) / (kBinThreads / 32);
+      const int bgrid = (int)(bwant < 152LL * 16 ? bwant : 152LL * 16);
       if (wi) k_bin_partials<1, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
       else k_bin_partials<0, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
+      k_bin_bucket_sums<<<grid_for((long long)A.B.NB * A.B.W * 32, 256), 256, 0, sh>>>(
+          A.B, A.bchunk, A.bpart, A.bpartb);
+      note_launch();
       note_launch();
     }
     const int rgrid = (int)(((long long)A.nlong + kHubRows - 1) / kHubRows);
@@ -903,12 +838,12 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
     e = cudaEventRecord(g->ev_join, sh);
     if (e != cudaSuccess) return e;
   }
-  const long long rows_per_block = (long long)(kRowThreads / 32) * kTileRows;
+  const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
   const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
   const long long cap = (long long)occ[wi] * nsm;
   const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-  if (wi) k_spmm_tiles<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
-  else k_spmm_tiles<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
+  else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
   note_launch();
   if (fork) {
     const cudaError_t e = cudaStreamWaitEvent(s, g->ev_join, 0);
@@ -1222,6 +1157,7 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   A.boff = P<int64_t>(g->boff);
   A.blist = P<uint32_t>(g->blist);
   A.bpart = P<float4>(g->bpart);
+  A.bpartb = P<float4>(g->bpartb);
   fill_nodes(A, g);
   A.a = P<float>(m.c32);
   A.b = nullptr;

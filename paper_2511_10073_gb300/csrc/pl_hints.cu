@@ -16,6 +16,7 @@
 // step an FP32 estimate cannot decide, always takes the FP64 value.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "pl_bins.cuh"
 #include "pl_internal.h"
@@ -649,8 +650,8 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
     const int32_t *n_ovl, const float2 *xy, const float *cw, const float *ch,
     const int64_t *gptr, const uint32_t *glist, const float4 *ggeo, const double *base_w,
     const float *phif, const double *phid, int W, const int32_t *cmem, const float4 *mgeo,
-    int32_t *col, void *w, void *bwin, void *bwinq, const int32_t *crank, int32_t *hbin,
-    dfl *dsum, dfl *psum, uint64_t *mac_base, unsigned long long *counts) {
+    int32_t *col, void *w, void *bwin, int32_t *hbin, dfl *dsum, dfl *psum, uint64_t *mac_base,
+    unsigned long long *counts) {
   __shared__ int32_t stage_col[8][kAsmStage];
   __shared__ uint32_t stage_w[8][kAsmStage];
   const bool bf = wdtype == PL_W_BF16;
@@ -755,9 +756,6 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       const dfl uy = df_offset_scale(p.y, G.ylh, G.yll, G.ihh, G.ihl);
       uint16_t *wb16 = reinterpret_cast<uint16_t *>(bwin) + (size_t)v * W;
       uint32_t *wb32 = reinterpret_cast<uint32_t *>(bwin) + (size_t)v * W;
-      const size_t q = (size_t)crank[v] * W;  // the bucket-order copy
-      uint16_t *wq16 = reinterpret_cast<uint16_t *>(bwinq) + q;
-      uint32_t *wq32 = reinterpret_cast<uint32_t *>(bwinq) + q;
       int sidx = 0;
       for (int yy = by - G.hy; yy <= by + G.hy; ++yy) {
         const bool yin = yy >= 0 && yy < G.nby;
@@ -795,13 +793,8 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
               acc_deg(Dl, Pl, sv);
               ++slots;
             }
-            if (bf) {
-              wb16[sidx] = (uint16_t)bits;
-              wq16[sidx] = (uint16_t)bits;
-            } else {
-              wb32[sidx] = bits;
-              wq32[sidx] = bits;
-            }
+            if (bf) wb16[sidx] = (uint16_t)bits;
+            else wb32[sidx] = bits;
             ++sidx;
           }
         }
@@ -828,6 +821,19 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
   hints = warp_sum(hints);
   if (lane == 0 && slots) atomicAdd(counts, slots);
   if (lane == 0 && hints) atomicAdd(counts + 1, hints);
+}
+
+// The window blocks in bucket-list order: a thread per list position copies
+// the block of the cell there (its W weights, one gathered block) to the
+// position's place.  Positions of non-hint cells copy blocks nobody reads.
+template <typename T>
+__global__ void k_blocks_to_lists(long long n, int W, const uint32_t *blist, const T *blk, T *out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const T *src = blk + (size_t)blist[k] * W;
+    T *dst = out + (size_t)k * W;
+    for (int s = 0; s < W; ++s) dst[s] = src[s];
+  }
 }
 
 // Macro rows, in the hub chunks of the sparse-product layout (one CTA per
@@ -884,8 +890,8 @@ __global__ void __launch_bounds__(256) k_hub_chunks(
 // Degrees of virtual rows (warp per row): a macro row from its chunk
 // partials, a bin row from the window blocks' degree partials.
 __global__ void k_hub_finalize(HintGeo G, BinGeo B, int32_t nlong, const int32_t *lrow,
-                               const int32_t *lchunk, const dfl *cpart, const int32_t *bchunk,
-                               const float4 *bdeg, dfl *dsum, dfl *psum) {
+                               const int32_t *lchunk, const dfl *cpart, const float4 *bdeg,
+                               dfl *dsum, dfl *psum) {
   const int lane = threadIdx.x & 31;
   for (long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; l < nlong;
        l += ((long long)gridDim.x * blockDim.x) >> 5) {
@@ -893,7 +899,7 @@ __global__ void k_hub_finalize(HintGeo G, BinGeo B, int32_t nlong, const int32_t
     if (v < G.mv0) continue;
     dfl D{0.f, 0.f}, Pp{0.f, 0.f};
     if (v >= G.bn0) {
-      bin_row_sums(B, (int)(v - G.bn0), bchunk, bdeg, &D, &Pp);
+      bin_row_sums(B, (int)(v - G.bn0), bdeg, &D, &Pp);
     } else {
       for (int c = lchunk[l] + lane; c < lchunk[l + 1]; c += 32) {
         df_add_df(D, cpart[2 * (long long)c]);
@@ -1276,12 +1282,11 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(cudaEventRecord(g->ev_fork, s));
   TRY(cudaStreamWaitEvent(s2, g->ev_fork, 0));
   if (cmem_ok) {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
       cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kMaxSmemMacros * 6);
-      attr_done = true;
-    }
+    });
     k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s2>>>(C, P<int32_t>(g->n_ovl),
                                                             P<int32_t>(g->cmem), Mm, ntile,
                                                             P<int64_t>(g->mtoff),
@@ -1342,9 +1347,6 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->hbw, (size_t)C * W * m.wbytes + 64));
   TRY(ensure(g->hbwq, (size_t)nbl * W * m.wbytes + 64));
   TRY(ensure(g->hbin, (size_t)C * 4 + 16));
-  TRY(ensure(g->crank, (size_t)C * 4 + 16));
-  k_bucket_rank<<<grid_for(nbl, 256), 256, 0, s>>>(nbl, P<uint32_t>(g->blist), P<int32_t>(g->crank));
-  note_launch();
   unsigned long long *counts = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 3);
   TRY(cudaMemsetAsync(counts, 0, 16, s));
   TRY(cudaStreamWaitEvent(s, g->ev_join, 0));  // phi and the macro lists
@@ -1354,8 +1356,16 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       P<int32_t>(g->n_ovl), xy, P<float>(g->cw), P<float>(g->ch), P<int64_t>(g->gptr),
       P<uint32_t>(g->glist), P<float4>(g->ggeo), P<double>(g->base_w), phif, P<double>(g->phi),
       W, cmem_ok ? P<int32_t>(g->cmem) : nullptr, P<float4>(g->mgeo), P<int32_t>(m.col), m.w.p,
-      g->hbw.p, g->hbwq.p, P<int32_t>(g->crank), P<int32_t>(g->hbin), P<dfl>(m.dsum),
-      P<dfl>(m.psum), P<uint64_t>(g->mac_base), counts);
+      g->hbw.p, P<int32_t>(g->hbin), P<dfl>(m.dsum), P<dfl>(m.psum), P<uint64_t>(g->mac_base),
+      counts);
+  note_launch();
+  // the bucket-order copy of the window blocks (read in list order by the bin rows)
+  if (g->wdtype == PL_W_BF16)
+    k_blocks_to_lists<uint16_t><<<grid_for(nbl, 256), 256, 0, s>>>(
+        nbl, W, P<uint32_t>(g->blist), P<uint16_t>(g->hbw), P<uint16_t>(g->hbwq));
+  else
+    k_blocks_to_lists<uint32_t><<<grid_for(nbl, 256), 256, 0, s>>>(
+        nbl, W, P<uint32_t>(g->blist), P<uint32_t>(g->hbw), P<uint32_t>(g->hbwq));
   note_launch();
   // H10: bin rows (degree partials of the window blocks, chunk by chunk) and
   // macro rows (their entries and degree partials)
@@ -1372,7 +1382,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   note_launch();
   TRY(ensure(g->bdeg, (size_t)nbc_max * W * 16 + 256));
   TRY(ensure(g->bpart, (size_t)nbc_max * W * 16 + 256));
-  const int bgrid = (int)(nbc_max < 152 * 8 ? nbc_max : 152 * 8);
+  const long long bwant = (nbc_max + kBinThreads / 32 - 1) / (kBinThreads / 32);
+  const int bgrid = (int)(bwant < 152 * 16 ? bwant : 152 * 16);
   if (g->wdtype == PL_W_BF16)
     k_bin_partials<1, true><<<bgrid, kBinThreads, 0, s>>>(B, P<int32_t>(g->bchunk), P<int32_t>(g->cown), P<int64_t>(g->boff),
                                                          P<uint32_t>(g->blist), g->hbwq.p, nullptr,
@@ -1382,6 +1393,12 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
                                                          P<uint32_t>(g->blist), g->hbwq.p, nullptr,
                                                          P<float4>(g->bdeg));
   note_launch();
+  // degree partials per (bucket, slot)
+  TRY(ensure(g->bdegb, (size_t)NB * W * 16 + 256));
+  k_bin_bucket_sums<<<grid_for((long long)NB * W * 32, 256), 256, 0, s>>>(
+      B, P<int32_t>(g->bchunk), P<float4>(g->bdeg), P<float4>(g->bdegb));
+  note_launch();
+  TRY(ensure(g->bpartb, (size_t)NB * W * 16 + 256));
   TRY(ensure(g->tmp[5], (size_t)(m.nchunks + 1) * 2 * sizeof(dfl) + 256));
   dfl *cpart = P<dfl>(g->tmp[5]);
   if (m.nchunks) {
@@ -1391,8 +1408,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
         P<uint64_t>(g->mac_base), P<int32_t>(m.col), m.w.p, cpart);
     note_launch();
     k_hub_finalize<<<grid_for((long long)m.nlong * 32, 256), 256, 0, s>>>(
-        G, B, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<int32_t>(g->bchunk),
-        P<float4>(g->bdeg), P<dfl>(m.dsum), P<dfl>(m.psum));
+        G, B, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<float4>(g->bdegb),
+        P<dfl>(m.dsum), P<dfl>(m.psum));
     note_launch();
   }
   // H11: lambda_up and coefficients

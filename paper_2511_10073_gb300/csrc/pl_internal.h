@@ -119,12 +119,12 @@ struct pl_graph {
   pl::Buf hbw;         // storage type [C * W] window-block weights of hint cells
   pl::Buf hbwq;        // storage type [movable cells * W] the same blocks at each cell's
                        // place in the bucket lists (read in list order by the bin rows)
-  pl::Buf crank;       // int32 [C] place of a movable cell in the bucket lists
   pl::Buf hbin;        // int32 [C] bin of a hint cell, -1 for other cells
   pl::Buf bchunk;      // int32 [NB + 1] first chunk of each bin's hint bucket
   pl::Buf cown;        // int32 [chunks] bin of each chunk
   pl::Buf bdeg;        // float4 [chunks * W] degree partials of the bin rows
   pl::Buf bpart;       // float4 [chunks * W] product partials of the bin rows
+  pl::Buf bdegb, bpartb;  // float4 [NB * W] the same summed per (bucket, slot)
   pl::Buf hubtmp;      // int32 scratch for merging bin rows
   pl::SpMat st;        // static matrix (A0)
   pl::SpMat hm;        // augmented matrix (A2-A4)
@@ -166,8 +166,8 @@ void for_each_buf(pl_graph *g, int kind, F f) {
                  &g->hubf, &g->slen, &g->llen, &g->clen, &g->lflag, &g->hubtmp, &g->cell_bin,
                  &g->n_ovl, &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff,
                  &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem, &g->Db, &g->phi,
-                 &g->mac_base, &g->hbw, &g->hbwq, &g->crank, &g->hbin, &g->bchunk, &g->cown, &g->bdeg,
-                 &g->bpart};
+                 &g->mac_base, &g->hbw, &g->hbwq, &g->hbin, &g->bchunk, &g->cown, &g->bdeg,
+                 &g->bpart, &g->bdegb, &g->bpartb};
   for (Buf *b : hint) f(*b);
   SpMat *ms[] = {&g->hm, &g->st};
   for (int i = 0; i < (kind == 0 ? 2 : 1); ++i) {

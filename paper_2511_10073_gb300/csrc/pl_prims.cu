@@ -1,5 +1,6 @@
 // Device-wide primitives: exclusive scan and segmented sort (+ unique / merge).
 #include <cstring>
+#include <mutex>
 
 #include "pl_common.cuh"
 
@@ -689,12 +690,11 @@ cudaError_t segmented_sort(K *keys, const int64_t *off, long long nseg, long lon
   k_seg_regs<K, MODE, 16><<<gb, 256, 0, s>>>(keys, off, cnt, mcol, mval, cl + 6 * nseg, lists, 6);
   for (int q = 0; q < 7; ++q) note_launch();
   size_t sm = SEG_CAP * sizeof(K);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [sm] {
     cudaFuncSetAttribute(k_seg_cta<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_big_units<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_done = true;
-  }
+  });
   k_seg_cta<K, MODE><<<152 * 4, SEG_T, sm, s>>>(keys, off, cnt, mcol, mval, cl + 7 * nseg, lists);
   note_launch();
   if (nkeys > SEG_CAP && (maxlen < 0 || maxlen > SEG_CAP)) {

@@ -186,12 +186,13 @@ double workspace_bound(const pl_netlist *nl, const pl_params *p) {
   h.add(C * W * sw + 64);            // window blocks, cell order
   h.add(nmov * W * sw + 64);         // window blocks, bucket order
   h.add(C * 4 + 16);
-  h.add(C * 4 + 16);
   h.add((NB + 1) * 4 + 256);
   h.add((NB + 1) * 4 + 256);
   const double nbc = std::floor(nmov / kBinChunk) + NB + 1;
   h.add(nbc * 4 + 256);
   h.add(nbc * W * 16 + 256);
+  h.add(NB * W * 16 + 256);
+  h.add(NB * W * 16 + 256);
   h.add(nbc * W * 16 + 256);
   h.add((nchunk_h + 1) * 2 * 8 + 256);
   return st.b + h.b + 4096.0;

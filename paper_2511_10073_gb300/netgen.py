@@ -49,6 +49,20 @@ CONFIGS = {
 }
 
 
+def batch_configs(seed: int, n: int = 64, lo: int = 5_000, hi: int = 500_000) -> list:
+    """A batch of n designs of uneven size: std cells log-uniform in [lo, hi],
+    macros 0.2-1% of the cells, I/O 0.5% (at least 16), nets 1.02 x the
+    cells, the medium recipe's degree law (cap 2,000) and macro share."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        c = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        out.append(dict(n_std=c, n_macro=max(1, int(round(c * rng.uniform(0.002, 0.01)))),
+                        n_io=max(16, int(round(0.005 * c))), n_nets=int(round(1.02 * c)),
+                        cap=2000, macro_mode="frac"))
+    return out
+
+
 @dataclass
 class Netlist:
     net_ptr: np.ndarray    # int64[M+1]
