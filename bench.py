@@ -238,6 +238,81 @@ def run_batched(pl, netgen, dev, stream, args, n=64):
                       "the streams)"}
 
 
+LEARNED_DIR = os.path.join(ROOT, "paper_2511_10073_gb300", "weights")
+
+
+def run_learned(pl, g, dnl, nl, args, dev, stream):
+    """The learned filter in place of the plain one (every trained model
+    committed under the package's weights/), on the workload's netlist with
+    the parameters it was trained for (the workload's, fixed nodes re-pinned
+    after every power).  The same step (graph build, initializer, HPWL) for
+    the plain filter and for each model, timed with CUDA events; HPWL
+    difference and the movable cells' coordinate RMS difference over the die."""
+    import glob
+    import torch
+    files = sorted(glob.glob(os.path.join(LEARNED_DIR, "learned_k*.json")))
+    if not files:
+        return None
+    models = [json.load(open(f)) for f in files]
+    prm = pl.params(**models[0]["params"])
+    out_plain = torch.empty(nl.num_cells * 2, dtype=torch.float32, device=dev)
+    out = torch.empty_like(out_plain)
+    ws = pl.hpwl_workspace(nl.num_nets, dev)
+    hp = torch.zeros(1, dtype=torch.float64, device=dev)
+    mov = torch.tensor(np.asarray(nl.cell_kind) == 0, device=dev)
+    die = nl.region[2] - nl.region[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps // 2)
+
+    def timed(m, dst):
+        nf = [0]
+
+        def step():
+            pl.pl_build_graph(dnl, prm, graph=g)
+            if m is None:
+                pl.pl_filter_init(g, prm, args.seed, None, dst)
+            else:
+                nf[0] = pl.pl_filter_init_learned(g, prm, m, args.seed, None, dst)
+            pl.pl_hpwl(dnl, dst, hp, ws)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, float(hp.item()), nf[0]
+
+    ms_plain, hp_plain, _ = timed(None, out_plain)
+    res = {}
+    for d in models:
+        m = pl.LearnedModel.from_host(d, dev)
+        ms, h, nf = timed(m, out)
+        dd = (out - out_plain).view(-1, 2)[mov].double()
+        rms = float(torch.sqrt((dd * dd).sum(1).mean() / 2).item()) / die
+        key = "k" + "".join(str(x) for x in m.k)
+        res[key] = {"tap_powers": list(m.k), "products_per_round": m.k[2],
+                    "value": nl.num_movable / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
+                    "speedup_vs_plain_gpu": ms_plain / ms, "hpwl": h,
+                    "hpwl_delta": (h - hp_plain) / hp_plain, "coord_rms_over_die": rms,
+                    "fallback_rounds": nf,
+                    "within_gate": abs((h - hp_plain) / hp_plain) <= 1e-3,
+                    "trained_on": d.get("data")}
+    ok = [k for k, v in res.items() if v["within_gate"]]
+    best = max(ok, key=lambda k: res[k]["speedup_vs_plain_gpu"]) if ok else None
+    return {"what": "the whole step (graph build, initializer, HPWL) with the learned filter "
+                    "(k2 sparse products per round, MLP on tensor cores) against the same step "
+                    "with the plain filter (max(tap_k) products per round), same netlist and seed",
+            "params": {k: (list(v) if isinstance(v, (list, tuple)) else v)
+                       for k, v in models[0]["params"].items()},
+            "plain": {"value": nl.num_movable / (ms_plain / 1e3), "unit": "cells/s",
+                      "ms_per_step": ms_plain, "hpwl": hp_plain,
+                      "products_per_round": max(prm.tap_k[:prm.ntaps])},
+            "gate": "|HPWL delta| <= 0.1%", "best_within_gate": best, "models": res}
+
+
 def whole_job_rate(ms_local, units_per_rank, steps, dist=None, device="cpu"):
     """Whole-job throughput of a replica run: the slowest rank's time (MAX over
     ranks) for the units all ranks processed.  Returns (units/s, max ms)."""
@@ -258,6 +333,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-filter leg")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched serving form")
@@ -470,6 +546,10 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
+    if not args.no_learned:
+        lr = run_learned(pl, g, dnl, nl, args, dev, stream)
+        if lr is not None:
+            line["learned"] = lr
     if not args.no_batch:
         line["batched"] = run_batched(pl, netgen, dev, stream, args)
     if world == 1 and not args.no_cpu_baseline:

@@ -59,8 +59,9 @@ typedef enum {
   PL_ERR_OOM = 4,         /* device allocation failed */
   PL_ERR_SPECTRUM = 5,    /* lambda_up <= 0 or not finite: no refinement filter */
   PL_ERR_NONFINITE = 6,   /* a coordinate given to the library is NaN or infinite */
-  PL_ERR_TIMEOUT = 7,     /* reserved: a bounded device-side wait gave up (no kernel of
-                             this library waits on another block, so none returns it) */
+  PL_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up: the learned filter's
+                             tensor-core kernels wait on their own MMAs for at most
+                             about 2 s (no kernel waits on another block) */
   PL_ERR_UNSUPPORTED = 8  /* input beyond a documented size limit */
 } pl_status;
 
@@ -270,6 +271,136 @@ pl_status pl_macro_density(const pl_rho_params *rp, int32_t t, int32_t num_macro
                            const float *mx, const float *my, const float *mw, const float *mh,
                            double xl, double yl, double xh, double yh, int32_t nbx, int32_t nby,
                            double *rho, pl_stream stream);
+
+/* ------------------------------------------------------------------------
+ * The learned refinement filter: a small learned stand-in for the plain
+ * refinement filter of Sec. V (Algorithm 1's filter step), with fewer sparse
+ * products.  Three taps at powers k0 < k1 < k2 of H_r and a per-node MLP on
+ * tensor cores.  In bin units about the region centre c (s the bin size per
+ * axis), G_t = (H_r^{k_t} g - c) / s and
+ *   P_v = theta_0 G0 + theta_1 G1 + theta_2 G2 + a_v (G1 - G0) + b_v (G2 - G0)
+ *         + (o_v^x, o_v^y),
+ *   (a_v, b_v, o_v^x, o_v^y) = W2 relu(W1 x_v + b1) + b2,  g~_v = c + s P_v,
+ * x_v the node's 16 features, normalised ((f - mu) * isd) and rounded to
+ * BF16; W1 (64 x 16) and W2 (4 x 64) are used as BF16, the hidden layer is
+ * rounded to BF16, and both layers accumulate in FP32 (tcgen05.mma, kind::f16,
+ * accumulators in TMEM).  The features: 0-1 G1 - G0, 2-3 G2 - G0, 4 D_vv /
+ * lambda_up, 5 sum_j |w_vj| / lambda_up, 6 (negative weights) / lambda_up,
+ * 7 phi_b of a hint cell's bin, 8 hint cell, 9 star node, 10 a movable
+ * cell's area over the bin area, 11 round t / T_hint, 12-15 zero.  The round
+ * then ends as the plain filter's: fixed nodes re-pinned, relaxation by gamma,
+ * re-pinned, movable centres clamped.  No counterpart in the paper: the paper
+ * applies the plain filter, which stays the judge of this one (the records
+ * below are its outputs).
+ *
+ * Parameter vector (device, FP32, PL_LEARNED_SIZE floats, in this order):
+ * mu[16], isd[16], theta[3], W1[64][16], b1[64], W2[4][64], b2[4]. */
+#define PL_LEARNED_NF 16
+#define PL_LEARNED_HID 64
+#define PL_LEARNED_NOUT 4
+#define PL_LW_MU 0
+#define PL_LW_ISD 16
+#define PL_LW_THETA 32
+#define PL_LW_W1 35
+#define PL_LW_B1 1059
+#define PL_LW_W2 1123
+#define PL_LW_B2 1379
+#define PL_LEARNED_SIZE 1383
+/* A training record: one free node (movable cell or star node) of one round,
+ * 24 floats: raw features f[16], G0[2], G1[2], G2[2], and the target T[2] in
+ * the same bin units: the filter output that the round's relaxation maps to
+ * the plain round's result g' (re-pinned and clamped), (g' - (1 - gamma) g) /
+ * gamma, which is the plain filter's g~ wherever clamping did not act.  (The
+ * signed graph's H_r can amplify, so an unclamped g~ may lie far outside the
+ * region; the clamped result is what the round keeps.) */
+#define PL_LEARNED_REC 24
+
+typedef struct {
+  int32_t k[3];    /* tap powers, 0 <= k0 < k1 < k2 <= 64 */
+  const float *w;  /* device, PL_LEARNED_SIZE floats */
+} pl_learned;
+
+/* One round of Algorithm 1 with the learned filter in place of the plain
+ * one, on the current augmented graph (pl_build_hints at xy_in first): k2
+ * refinement products, then one fused kernel (features, the MLP on tensor
+ * cores, taps, relaxation, re-pinning, clamping).  round: t of Algorithm 1
+ * (feature 11 = t / T_hint).  xy_in, xy_out: device, N pairs each, distinct.
+ * Synchronizes `stream` to read the device status.  Errors: INVALID_ARG,
+ * NONFINITE (the learned g~ of a free node is not finite), TIMEOUT, CUDA. */
+pl_status pl_learned_apply(pl_graph *g, const pl_params *p, const pl_learned *m, int32_t round,
+                           const float *xy_in, float *xy_out, pl_stream stream);
+
+/* The whole initializer with the learned filter: A0 as pl_filter_init, then
+ * T_hint rounds of A2, A3 and the learned round.  A round whose learned g~
+ * is not finite is run again with the plain filter (the fallback); their
+ * count goes to *fallbacks (host, may be NULL).  m == NULL runs the plain
+ * filter in every round (the same bits as pl_filter_init).  Reads the device
+ * status once per round.  Errors: as pl_filter_init, TIMEOUT. */
+pl_status pl_filter_init_learned(pl_graph *g, const pl_params *p, const pl_learned *m,
+                                 uint64_t seed, const float *xy0_cells, float *xy_out_cells,
+                                 int32_t *fallbacks, pl_stream stream);
+
+/* The MLP alone on given raw features: out[i] (device, n x 4 floats) = the
+ * four outputs for feat[i] (device, n x 16 floats), with the normalisation,
+ * BF16 roundings and tensor-core arithmetic of pl_learned_apply.  w: device
+ * parameter vector.  Does not synchronize.  Errors: INVALID_ARG, CUDA (a
+ * timed-out wait leaves the rows of its tile as NaN). */
+pl_status pl_learned_forward(const float *w, const float *feat, int64_t n, float *out,
+                             pl_stream stream);
+
+/* Training records of one round: with the hints built at xy_in, runs the
+ * plain round of p (its result gives the target) and the powers k[0..2],
+ * and writes one record per free node, in node order, to rec
+ * (device, cap records of PL_LEARNED_REC floats); *count (host) = records
+ * written.  round as in pl_learned_apply.  xy_in is not changed (advance the
+ * trajectory with pl_filter_apply).  Synchronizes `stream`.  Errors:
+ * INVALID_ARG (also gamma = 0: no filter output to learn), WORKSPACE (cap too
+ * small; *count = records needed), CUDA. */
+pl_status pl_learned_collect(pl_graph *g, const pl_params *p, const int32_t k[3], int32_t round,
+                             const float *xy_in, float *rec, int64_t cap, int64_t *count,
+                             pl_stream stream);
+
+/* Training options.  Minibatches are batch_tiles tiles of 128 consecutive
+ * records, the tiles in a fresh order every epoch (splitmix64 of seed and
+ * epoch, Fisher-Yates); an epoch takes floor(full tiles / batch_tiles) steps
+ * (at least one).  Adam (Kingma & Ba) with the learning rate on a cosine from
+ * lr to lr_min over all steps.  fit_norm: set mu and isd from the records'
+ * feature means and standard deviations first; fit_taps: set theta to the
+ * least-squares taps first (both in FP64 over all records). */
+typedef struct {
+  int32_t epochs;       /* >= 1 */
+  int32_t batch_tiles;  /* 1..1024 */
+  double lr, lr_min, beta1, beta2, eps;
+  uint64_t seed;
+  int32_t fit_norm, fit_taps;
+} pl_train_opts;
+
+/* Defaults: 20 epochs, 128 tiles (16384 records), lr 2e-3 -> 1e-4, betas
+ * 0.9 / 0.999, eps 1e-8, seed 1, both fits on. */
+void pl_train_opts_default(pl_train_opts *o);
+
+/* Device bytes of the workspace of pl_learned_train and pl_learned_loss for
+ * nrec records (0 for a negative count). */
+size_t pl_learned_train_ws(int64_t nrec);
+
+/* Trains the parameter vector w (device, in/out; W1, W2, b1, b2 and theta
+ * as initial values) on nrec >= 128 records (device) to minimise the mean
+ * over records of ||P - T||^2 (bin units).  Forward on tensor cores as in
+ * pl_learned_apply; backward on CUDA cores in FP32 (BF16 roundings passed
+ * straight through), per-block partial gradients added in a fixed order, so
+ * a run is reproducible.  epoch_loss (host, epochs doubles, may be NULL):
+ * the mean minibatch loss of each epoch.  ws: device, 256-byte aligned,
+ * pl_learned_train_ws(nrec) bytes.  Synchronizes `stream` once per epoch.
+ * Errors: INVALID_ARG, WORKSPACE, TIMEOUT, CUDA. */
+pl_status pl_learned_train(const float *rec, int64_t nrec, float *w, const pl_train_opts *o,
+                           void *ws, size_t ws_bytes, double *epoch_loss, pl_stream stream);
+
+/* The training loss over all nrec records (*loss, host) and, when grad
+ * (device, PL_LEARNED_SIZE floats) is not NULL, its gradient (zero for mu
+ * and isd).  Same kernels as pl_learned_train.  Synchronizes `stream`.
+ * Errors: INVALID_ARG, WORKSPACE, TIMEOUT, CUDA. */
+pl_status pl_learned_loss(const float *rec, int64_t nrec, const float *w, void *ws,
+                          size_t ws_bytes, double *loss, float *grad, pl_stream stream);
 
 /* Copies of the graph for exact comparison (all HOST buffers):
  * static CSR: rp[static nodes + 1], col[static nnz], w[static nnz] (stored

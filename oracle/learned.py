@@ -14,7 +14,11 @@ axis), with G_t = (H_r^{k_t} g - c) / s:
 the MLP two layers 16 -> 64 (ReLU) -> 4 on the node's normalised features
 x_v.  The rest of the round is the plain filter's (fixed nodes re-pinned,
 relaxation by gamma, re-pinned, movable centres clamped).  It is trained to
-reproduce the plain filter's g~ (the plain filter stays the judge).
+reproduce the plain round (the plain filter stays the judge): its target is
+the filter output that the relaxation maps to the plain round's result g',
+(g' - (1 - gamma) g) / gamma, which is the plain g~ wherever clamping did not
+act (the signed graph's H_r can amplify, so an unclamped g~ may lie far
+outside the region; the clamped result is what the round keeps).
 
 Every step is written in plain numpy, FP64, with the BF16 roundings that the
 GPU's tensor cores see (normalised features, weights, hidden layer) written
@@ -68,6 +72,12 @@ def pack(p):
     w[W2:B2] = np.asarray(p["W2"]).ravel()
     w[B2:SIZE] = p["b2"]
     return w
+
+
+def effective_target(g1, g, gamma):
+    """The filter output that the relaxation maps to the round result g1:
+    (g1 - (1 - gamma) g) / gamma, gamma > 0."""
+    return (np.asarray(g1, np.float64) - (1.0 - gamma) * np.asarray(g, np.float64)) / gamma
 
 
 def bins(xy, c, s):

@@ -89,6 +89,14 @@ def lib():
             "pl_rho_params_default": (None, [vp]),
             "pl_macro_density": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, dbl, dbl, dbl, dbl,
                                            i32, i32, vp, vp]),
+            "pl_learned_apply": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
+            "pl_filter_init_learned": (C.c_int, [vp, vp, vp, u64, vp, vp, vp, vp]),
+            "pl_learned_forward": (C.c_int, [vp, vp, i64, vp, vp]),
+            "pl_learned_collect": (C.c_int, [vp, vp, vp, i32, vp, vp, i64, vp, vp]),
+            "pl_train_opts_default": (None, [vp]),
+            "pl_learned_train_ws": (sz, [i64]),
+            "pl_learned_train": (C.c_int, [vp, i64, vp, vp, vp, sz, vp, vp]),
+            "pl_learned_loss": (C.c_int, [vp, i64, vp, vp, sz, vp, vp, vp]),
             "pl_prof_enable": (None, [C.c_int]),
             "pl_prof_read": (C.c_int, [vp]),
         }
@@ -347,3 +355,124 @@ def pl_macro_density(rp: PlRhoParams, t: int, mx, my, mw, mh, region, nbx: int, 
     _check(lib().pl_macro_density(C.byref(rp), int(t), int(mx.numel()), _ptr(mx), _ptr(my),
                                   _ptr(mw), _ptr(mh), xl, yl, xh, yh, int(nbx), int(nby),
                                   _ptr(out), _stream(stream)))
+
+
+# ------------------------------------------- the learned refinement filter
+LEARNED_NF, LEARNED_HID, LEARNED_NOUT = 16, 64, 4
+LW_MU, LW_ISD, LW_THETA, LW_W1, LW_B1, LW_W2, LW_B2, LEARNED_SIZE = 0, 16, 32, 35, 1059, 1123, 1379, 1383
+LEARNED_REC = 24
+
+
+class PlLearned(C.Structure):
+    _fields_ = [("k", C.c_int32 * 3), ("w", C.c_void_p)]
+
+
+class PlTrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch_tiles", C.c_int32), ("lr", C.c_double),
+                ("lr_min", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double), ("seed", C.c_uint64), ("fit_norm", C.c_int32),
+                ("fit_taps", C.c_int32)]
+
+
+class LearnedModel:
+    """Tap powers k = (k0, k1, k2) and the device parameter vector `w`
+    (PL_LEARNED_SIZE floats), with the C struct that points at them."""
+
+    def __init__(self, k, w):
+        self.k = tuple(int(x) for x in k)
+        self.w = w
+        self.struct = PlLearned((C.c_int32 * 3)(*self.k), C.c_void_p(w.data_ptr()))
+
+    def host(self) -> dict:
+        return {"k": list(self.k), "w": [float(x) for x in self.w.detach().cpu().numpy()]}
+
+    @staticmethod
+    def from_host(d: dict, device="cuda") -> "LearnedModel":
+        import torch
+        return LearnedModel(d["k"], torch.tensor(d["w"], dtype=torch.float32, device=device))
+
+
+def learned_init(k, seed: int, device="cuda") -> LearnedModel:
+    """A fresh parameter vector: W1 ~ N(0, 1/16) (He-like for 16 inputs) from
+    numpy's PCG64(seed), every other weight zero, isd 1 (normalisation and
+    taps are fitted by pl_learned_train)."""
+    import torch
+    w = np.zeros(LEARNED_SIZE, np.float32)
+    w[LW_ISD:LW_ISD + LEARNED_NF] = 1.0
+    w[LW_THETA + 2] = 1.0
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w[LW_W1:LW_B1] = rng.normal(0.0, 0.25, LEARNED_HID * LEARNED_NF)
+    return LearnedModel(k, torch.tensor(w, device=device))
+
+
+def train_opts(**kw) -> PlTrainOpts:
+    o = PlTrainOpts()
+    lib().pl_train_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pl_learned_apply(g: Graph, prm: PlParams, m: LearnedModel, rnd: int, xy_in, xy_out,
+                     stream=None):
+    _check(lib().pl_learned_apply(g.handle, C.byref(prm), C.byref(m.struct), int(rnd),
+                                  _ptr(xy_in), _ptr(xy_out), _stream(stream)))
+
+
+def pl_filter_init_learned(g: Graph, prm: PlParams, m: LearnedModel | None, seed: int, xy0_cells,
+                           xy_out_cells, stream=None) -> int:
+    """The whole initializer with the learned filter; returns the number of
+    rounds that fell back to the plain filter."""
+    nf = C.c_int32(0)
+    _check(lib().pl_filter_init_learned(g.handle, C.byref(prm),
+                                        None if m is None else C.byref(m.struct), C.c_uint64(seed),
+                                        _ptr(xy0_cells), _ptr(xy_out_cells), C.byref(nf),
+                                        _stream(stream)))
+    return int(nf.value)
+
+
+def pl_learned_forward(w, feat, out, stream=None):
+    _check(lib().pl_learned_forward(_ptr(w), _ptr(feat), int(feat.shape[0]), _ptr(out),
+                                    _stream(stream)))
+
+
+def pl_learned_collect(g: Graph, prm: PlParams, k, rnd: int, xy_in, rec, stream=None) -> int:
+    """Writes this round's records into the device float tensor `rec`
+    (rows of LEARNED_REC floats) and returns their count; with rec None,
+    only returns the count."""
+    kk = (C.c_int32 * 3)(*[int(x) for x in k])
+    cnt = C.c_int64(0)
+    cap = 0 if rec is None else rec.numel() // LEARNED_REC
+    code = lib().pl_learned_collect(g.handle, C.byref(prm), kk, int(rnd), _ptr(xy_in), _ptr(rec),
+                                    cap, C.byref(cnt), _stream(stream))
+    if rec is None and code == PL_ERR_WORKSPACE:
+        return int(cnt.value)  # the count asked for
+    _check(code)
+    return int(cnt.value)
+
+
+def learned_train_workspace(nrec: int, device="cuda"):
+    import torch
+    return torch.empty(max(int(lib().pl_learned_train_ws(int(nrec))), 256), dtype=torch.uint8,
+                       device=device)
+
+
+def pl_learned_train(rec, nrec: int, m: LearnedModel, opts: PlTrainOpts, ws=None,
+                     stream=None) -> list:
+    """Trains m.w in place on the first nrec rows of `rec`; returns the
+    per-epoch mean minibatch loss."""
+    if ws is None:
+        ws = learned_train_workspace(nrec, rec.device)
+    loss = np.zeros(max(opts.epochs, 1))
+    _check(lib().pl_learned_train(_ptr(rec), int(nrec), _ptr(m.w), C.byref(opts), _ptr(ws),
+                                  C.c_size_t(ws.numel()), loss.ctypes.data, _stream(stream)))
+    return [float(x) for x in loss[:opts.epochs]]
+
+
+def pl_learned_loss(rec, nrec: int, w, grad=None, ws=None, stream=None) -> float:
+    if ws is None:
+        ws = learned_train_workspace(nrec, rec.device)
+    loss = C.c_double(0)
+    _check(lib().pl_learned_loss(_ptr(rec), int(nrec), _ptr(w), _ptr(ws), C.c_size_t(ws.numel()),
+                                 C.byref(loss), _ptr(grad), _stream(stream)))
+    return float(loss.value)

@@ -308,15 +308,15 @@ __global__ void k_copy_cells(int32_t C, const float2 *g, float2 *out) {
     out[i] = g[i];
 }
 
-pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const float *xy0_cells,
-                         float *xy_out_cells, pl_stream stream) {
-  pl::g_err[0] = 0;
-  if (!g || !xy_out_cells) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
-  pl_status st = check_params(p);
-  if (st == PL_OK) st = same_layout(g, p);
-  if (st != PL_OK) return st;
-  GraphScope scope(g);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace pl {
+// The whole initializer (A0, then T_hint rounds of A2-A4), with the plain
+// filter (m == NULL) or the learned one in every round; a learned round whose
+// output is not finite is run again with the plain filter.
+static pl_status init_run(pl_graph *g, const pl_params *p, const pl_learned *m, uint64_t seed,
+                          const float *xy0_cells, float *xy_out_cells, int32_t *fallbacks,
+                          cudaStream_t s) {
   g->stream = s;
   const int64_t N = g->N;
   cudaError_t e = ensure(g->xc, (size_t)N * 8 + 64);
@@ -325,7 +325,7 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
   float *cur = P<float>(g->xc), *nxt = P<float>(g->g0);
   e = cudaMemsetAsync(g->status.p, 0, 32, s);
   if (e != cudaSuccess) return cuda_fail(e, "status reset");
-  st = run_init_signal(g, seed, xy0_cells, cur, s);
+  pl_status st = run_init_signal(g, seed, xy0_cells, cur, s);
   if (st != PL_OK) return st;
   if (p->gift_enable) {
     st = run_gift(g, p, cur, nxt, s);
@@ -335,23 +335,72 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
   if (st == PL_OK) st = read_status(g, s);
   if (st != PL_OK) return st;
   std::swap(cur, nxt);
+  int32_t nfall = 0;
   for (int t = 0; t < p->t_hint; ++t) {
-    if (t) {
+    if (t && !m) {
       st = read_status(g, s);
       if (st != PL_OK) return st;
     }
     st = build_hints(g, p, cur, s);
     if (st != PL_OK) return st;
-    st = run_filter(g, p, cur, nxt, s);
+    if (m) {
+      st = run_learned(g, p, m, t, cur, nxt, s);
+      int w0 = 0;
+      if (st == PL_OK) {
+        e = cudaMemcpyAsync(&w0, g->status.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "status read");
+      }
+      if (st == PL_OK && (w0 & ST_LEARNED_NF) && !(w0 & ~ST_LEARNED_NF)) {
+        e = cudaMemsetAsync(g->status.p, 0, sizeof(int), s);  // the fallback: the plain round
+        if (e != cudaSuccess) return cuda_fail(e, "status reset");
+        st = run_filter(g, p, cur, nxt, s);
+        ++nfall;
+      }
+      if (st == PL_OK) st = read_status(g, s);
+    } else {
+      st = run_filter(g, p, cur, nxt, s);
+    }
     if (st != PL_OK) return st;
     std::swap(cur, nxt);
   }
+  if (fallbacks) *fallbacks = nfall;
   k_copy_cells<<<grid_for(g->C, 256), 256, 0, s>>>(g->C, reinterpret_cast<const float2 *>(cur),
                                                    reinterpret_cast<float2 *>(xy_out_cells));
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "copy out");
   return read_status(g, s);
+}
+}  // namespace pl
+
+extern "C" {
+
+pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const float *xy0_cells,
+                         float *xy_out_cells, pl_stream stream) {
+  pl::g_err[0] = 0;
+  if (!g || !xy_out_cells) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
+  pl_status st = check_params(p);
+  if (st == PL_OK) st = same_layout(g, p);
+  if (st != PL_OK) return st;
+  GraphScope scope(g);
+  return init_run(g, p, nullptr, seed, xy0_cells, xy_out_cells, nullptr,
+                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+pl_status pl_filter_init_learned(pl_graph *g, const pl_params *p, const pl_learned *m,
+                                 uint64_t seed, const float *xy0_cells, float *xy_out_cells,
+                                 int32_t *fallbacks, pl_stream stream) {
+  pl::g_err[0] = 0;
+  if (fallbacks) *fallbacks = 0;
+  if (!g || !xy_out_cells) { set_error("NULL argument"); return PL_ERR_INVALID_ARG; }
+  pl_status st = check_params(p);
+  if (st == PL_OK) st = same_layout(g, p);
+  if (st == PL_OK && m) st = check_model(m);
+  if (st != PL_OK) return st;
+  GraphScope scope(g);
+  return init_run(g, p, m, seed, xy0_cells, xy_out_cells, fallbacks,
+                  reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t pl_hpwl_workspace_size(int32_t num_nets) { return hpwl_ws_bytes(num_nets < 0 ? 0 : num_nets); }

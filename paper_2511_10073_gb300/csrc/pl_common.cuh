@@ -14,7 +14,8 @@ constexpr int kWarp = 32;
 
 // ------------------------------------------------------------------ errors
 enum : int { ST_BAD_INDEX = 1, ST_NONFINITE = 2, ST_SPECTRUM = 4, ST_TOO_BIG = 8, ST_BAD_NET = 16,
-             ST_BAD_CELL = 32, ST_TIMEOUT = 64, ST_MANY_OVL = 128 };
+             ST_BAD_CELL = 32, ST_TIMEOUT = 64, ST_MANY_OVL = 128,
+             ST_LEARNED_NF = 256 /* a free node's learned g~ is not finite */ };
 
 __device__ __forceinline__ void flag(int *status, int bit) { atomicOr(status, bit); }
 

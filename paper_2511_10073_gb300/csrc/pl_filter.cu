@@ -1117,30 +1117,11 @@ pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out,
   return PL_OK;
 }
 
-pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *out,
-                     cudaStream_t s) {
-  const int64_t N = g->N;
-  const float2 *gin = reinterpret_cast<const float2 *>(in);
-  float2 *gout = reinterpret_cast<float2 *>(out);
-  if (p->gamma == 0.0) {
-    k_clamp<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->nkind), P<float2>(g->fixedp),
-                                             P<float4>(g->bounds), gin, gout, p->clamp);
-    note_launch();
-    TRY(cudaGetLastError());
-    return PL_OK;
-  }
-  const int kmax = p->tap_k[p->ntaps - 1];
-  const bool single = p->ntaps == 1 && p->tap_alpha[0] == 1.0;
-  TRY(ensure(g->xa, (size_t)N * 8 + 64));
-  TRY(ensure(g->xb, (size_t)N * 8 + 64));
-  if (!single) {
-    TRY(ensure(g->acc, (size_t)N * 16 + 16));
-    TRY(cudaMemsetAsync(g->acc.p, 0, (size_t)N * 16, s));
-  }
+// The refinement product's arguments on the current augmented graph (A4):
+// matrix, column-free bin hints, coefficients and node tables.
+static void hr_args(pl_graph *g, StepArgs &A) {
   const SpMat &m = g->hm;
-  StepArgs A{};
   fill_matrix(A, g->st, &m);
-  const double bytes = spmm_bytes_hint(g);
   A.hbw = g->hbw.p;
   A.hbwq = g->hbwq.p;
   A.hbin = P<int32_t>(g->hbin);
@@ -1166,6 +1147,32 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   A.binvf = (float)g->lam_h[1];
   A.tscale = nullptr;
   A.acc = P<double2>(g->acc);
+  A.cx = A.cy = 0.0;
+}
+
+pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *out,
+                     cudaStream_t s) {
+  const int64_t N = g->N;
+  const float2 *gin = reinterpret_cast<const float2 *>(in);
+  float2 *gout = reinterpret_cast<float2 *>(out);
+  if (p->gamma == 0.0) {
+    k_clamp<<<grid_for(N, 256), 256, 0, s>>>(N, P<uint8_t>(g->nkind), P<float2>(g->fixedp),
+                                             P<float4>(g->bounds), gin, gout, p->clamp);
+    note_launch();
+    TRY(cudaGetLastError());
+    return PL_OK;
+  }
+  const int kmax = p->tap_k[p->ntaps - 1];
+  const bool single = p->ntaps == 1 && p->tap_alpha[0] == 1.0;
+  TRY(ensure(g->xa, (size_t)N * 8 + 64));
+  TRY(ensure(g->xb, (size_t)N * 8 + 64));
+  if (!single) {
+    TRY(ensure(g->acc, (size_t)N * 16 + 16));
+    TRY(cudaMemsetAsync(g->acc.p, 0, (size_t)N * 16, s));
+  }
+  StepArgs A{};
+  hr_args(g, A);
+  const double bytes = spmm_bytes_hint(g);
   A.g0 = gin;
   A.gnext = gout;
   A.gamma = p->gamma;
@@ -1174,7 +1181,6 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
   A.clamp = p->clamp;
   A.single = single ? 1 : 0;
   A.pin = p->pin_every_step;
-  A.cx = A.cy = 0.0;
   const float2 *x = gin;
   float2 *bufs[2] = {P<float2>(g->xa), P<float2>(g->xb)};
   for (int t = 1; t <= kmax; ++t) {
@@ -1191,6 +1197,36 @@ pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *ou
     A.fin = t == kmax;
     TRY(launch_step<MODE_HR>(A, bytes, g->wdtype, s, g));
     x = bufs[t & 1];
+  }
+  return PL_OK;
+}
+
+// Powers H_r^k g for the learned filter's taps k[0] < k[1] < k[2]: one
+// refinement product per power up to k[2], each stored in FP32 and re-pinned
+// when p asks for it (as the plain filter's powers).  out[i] points at
+// H_r^{k[i]} g: the input itself for k = 0, else ua (k[0]), ub (k[1]) or one
+// of xa / xb (k[2]).
+pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int32_t k[3],
+                     const float2 *out[3], cudaStream_t s) {
+  const float2 *gin = reinterpret_cast<const float2 *>(in);
+  StepArgs A{};
+  hr_args(g, A);
+  const double bytes = spmm_bytes_hint(g);
+  A.pin = p->pin_every_step;
+  A.fin = 0;
+  A.tap = 0;
+  const float2 *x = gin;
+  float2 *bufs[2] = {P<float2>(g->xa), P<float2>(g->xb)};
+  for (int i = 0; i < 3; ++i)
+    if (k[i] == 0) out[i] = gin;
+  for (int t = 1; t <= k[2]; ++t) {
+    float2 *y = t == k[0] ? P<float2>(g->ua) : t == k[1] ? P<float2>(g->ub) : bufs[t & 1];
+    A.x = x;
+    A.y = y;
+    TRY(launch_step<MODE_HR>(A, bytes, g->wdtype, s, g));
+    for (int i = 0; i < 3; ++i)
+      if (k[i] == t) out[i] = y;
+    x = y;
   }
   return PL_OK;
 }

@@ -137,6 +137,7 @@ struct pl_graph {
   pl::Buf status;         // int32 [8]
   pl::Buf stage;          // staging words of batched device-to-host reads
   pl::Buf star_w;         // double [kMaxNetPins + 1] star edge weights p / (p - 1)
+  pl::Buf lscr;           // int32 [N / 1024 + 2] learned filter: free nodes per block of 1024
   // device memory: the caller's workspace.  The static build takes the bottom
   // of it (up to hint_mark); every hint build starts again at hint_mark.
   pl::Arena arena;
@@ -183,7 +184,7 @@ void for_each_buf(pl_graph *g, int kind, F f) {
                  &g->cell_macro, &g->srp, &g->base_w, &g->hflag, &g->nkind, &g->fixedp,
                  &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo,
                  &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub, &g->acc, &g->gsc, &g->q4a,
-                 &g->q4b, &g->status, &g->stage, &g->star_w};
+                 &g->q4b, &g->status, &g->stage, &g->star_w, &g->lscr};
   for (Buf *b : rest) f(*b);
 }
 
@@ -199,6 +200,12 @@ pl_status prepare_static_layout(pl_graph *g, cudaStream_t s);
 pl_status run_init_signal(pl_graph *g, uint64_t seed, const float *xy0, float *xy, cudaStream_t s);
 pl_status run_gift(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
 pl_status run_filter(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
+pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int32_t k[3],
+                     const float2 *out[3], cudaStream_t s);
+pl_status clamp_nodes(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
+pl_status check_model(const pl_learned *m);
+pl_status run_learned(pl_graph *g, const pl_params *p, const pl_learned *m, int32_t round,
+                      const float *in, float *out, cudaStream_t s);
 pl_status read_status(pl_graph *g, cudaStream_t s);
 
 }  // namespace pl

@@ -121,6 +121,7 @@ double workspace_bound(const pl_netlist *nl, const pl_params *p) {
   st.add(N * 24 + 64);
   st.add(N * 16 + 64);
   st.add(N * 16 + 64);
+  st.add((std::floor(N / 1024.0) + 2) * 4 + 64);  // learned filter's block counts
 
   // one hint build
   Plan h;
@@ -211,6 +212,7 @@ pl_status take_filter_buffers(pl_graph *g) {
   if (e == cudaSuccess) e = ensure(g->gsc, N * 24 + 64);
   if (e == cudaSuccess) e = ensure(g->q4a, N * 16 + 64);
   if (e == cudaSuccess) e = ensure(g->q4b, N * 16 + 64);
+  if (e == cudaSuccess) e = ensure(g->lscr, (N / 1024 + 2) * 4 + 64);
   if (e != cudaSuccess) return cuda_fail(e, "filter buffers");
   return PL_OK;
 }

@@ -1,8 +1,9 @@
 """GPU parity: every step of the CUDA path against the FP64 oracle.
 
 Inputs are the seeded synthetic netlists of netgen.  Where a step consumes
-coordinates, both sides get the same FP32 node coordinates (produced by the
-GPU path itself), so each step is checked on its own:
+coordinates, both sides get the same FP32 node coordinates (the oracle's own
+previous step rounded to FP32; no oracle input comes from the GPU), so each
+step is checked on its own:
   * static graph (A1): CSR bit-exact (columns, stored weights, baseWeight);
   * area hints (A2/A3): topology bit-exact (row pointers, columns, bins),
     D_b / C_b / phi_b bit-exact (FP64), hint weights bit-exact (FP32 and BF16
@@ -49,13 +50,16 @@ class Side:
         self.N = self.info["N"]
         self.die = nl.region[2] - nl.region[0]
 
-    def gpu_signal(self, seed):
-        x0 = torch.empty(self.N * 2, dtype=torch.float32, device="cuda")
-        pl().pl_init_signal(self.g, seed, None, x0)
-        x1 = torch.empty_like(x0)
-        pl().pl_gift(self.g, self.prm, x0, x1)
-        torch.cuda.synchronize()
-        return x0, x1
+    def oracle_signal(self, seed):
+        """The oracle's initial signal (A0 step 1) and its GiFt output, each
+        rounded to FP32 (device tensors): the common input of both sides'
+        next step."""
+        ox, oy = self.o.init_signal(seed)
+        a0 = np.stack([ox, oy], 1).astype(np.float32)
+        gx, gy = self.o.gift(a0[:, 0].astype(np.float64), a0[:, 1].astype(np.float64))
+        a1 = np.stack([gx, gy], 1).astype(np.float32)
+        dev = lambda a: torch.tensor(a.reshape(-1), device="cuda")
+        return dev(a0), dev(a1)
 
 
 def to_np(t):
@@ -153,7 +157,7 @@ def _compare_hints(s, ge, oe):
 def test_hints_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
     s = Side(nl, **cfg_params(cfg, **kw))
-    _, xy = s.gpu_signal(seed)
+    _, xy = s.oracle_signal(seed)
     pl().pl_build_hints(s.g, s.prm, xy)
     ge = s.g.export()
     a = to_np(xy)
@@ -175,7 +179,7 @@ def test_hints_stacked_macros():
     nl2 = netgen.Netlist(nl.net_ptr, nl.pin_cell, nl.pin_dx, nl.pin_dy, rep(nl.cell_w), rep(nl.cell_h),
                          rep(nl.cell_kind), rep(nl.fixed_x), rep(nl.fixed_y), nl.region)
     s = Side(nl2, **cfg_params("tiny"))
-    _, xy = s.gpu_signal(5)
+    _, xy = s.oracle_signal(5)
     # put a block of cells on the stacked site
     a = to_np(xy)
     movable = np.flatnonzero(kind == netgen.KIND_MOVABLE)[:200]
@@ -208,13 +212,19 @@ def test_hints_stacked_macros():
 def test_init_and_gift_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
     s = Side(nl, **cfg_params(cfg, **kw))
-    x0, x1 = s.gpu_signal(seed)
-    a0 = to_np(x0)
+    xg = torch.empty(s.N * 2, dtype=torch.float32, device="cuda")
+    pl().pl_init_signal(s.g, seed, None, xg)
+    ag = to_np(xg)
     ox, oy = s.o.init_signal(seed)
     mov = nl.cell_kind == 0
     C = nl.num_cells
-    assert np.array_equal(a0[:C, 0][mov], ox[:C][mov].astype(np.float32))
-    assert np.abs(a0[:, 0] - ox).max() <= 1e-6 * s.die
+    assert np.array_equal(ag[:C, 0][mov], ox[:C][mov].astype(np.float32))
+    assert np.abs(ag[:, 0] - ox).max() <= 1e-6 * s.die
+    x0, _ = s.oracle_signal(seed)
+    x1 = torch.empty_like(x0)
+    pl().pl_gift(s.g, s.prm, x0, x1)
+    torch.cuda.synchronize()
+    a0 = to_np(x0)
     gx, gy = s.o.gift(a0[:, 0], a0[:, 1])
     a1 = to_np(x1)
     err = max(np.abs(a1[:, 0] - gx).max(), np.abs(a1[:, 1] - gy).max())
@@ -231,7 +241,7 @@ def test_init_and_gift_crossfed(cfg, seed, kw):
 def test_filter_step_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
     s = Side(nl, **cfg_params(cfg, **kw))
-    _, xy = s.gpu_signal(seed)
+    _, xy = s.oracle_signal(seed)
     pl().pl_build_hints(s.g, s.prm, xy)
     out = torch.empty_like(xy)
     pl().pl_filter_apply(s.g, s.prm, xy, out)
@@ -393,7 +403,7 @@ def test_empty_graph_spectrum_error():
                         np.ones(3, np.float32), np.ones(3, np.float32), np.zeros(3, np.uint8),
                         np.zeros(3, np.float32), np.zeros(3, np.float32), (0.0, 0.0, 10.0, 10.0))
     s = Side(nl, nbx=2, nby=2)
-    x0, x1 = s.gpu_signal(1)
+    x0, x1 = s.oracle_signal(1)
     with pytest.raises(m.PlError) as e:
         m.pl_build_hints(s.g, s.prm, x1)
     assert e.value.code == m.PL_ERR_SPECTRUM
@@ -428,11 +438,13 @@ def test_large_workload_steps_crossfed():
     assert np.array_equal(ge["rp"], oe["rp"]) and np.array_equal(ge["col"], oe["col"])
     assert np.array_equal(ge["w"], oe["w_store"]) and np.array_equal(ge["base_w"], oe["base_w"])
     del ge, oe
-    x0, xy = s.gpu_signal(1)
-    a0 = to_np(x0)
-    gx, gy = s.o.gift(a0[:, 0], a0[:, 1])
+    x0, xy = s.oracle_signal(1)  # xy: the oracle's GiFt of x0, in FP32
+    x1 = torch.empty_like(x0)
+    pl().pl_gift(s.g, s.prm, x0, x1)
     a = to_np(xy)
-    assert max(np.abs(a[:, 0] - gx).max(), np.abs(a[:, 1] - gy).max()) <= 1e-4 * s.die
+    a1 = to_np(x1)
+    assert np.abs(a1 - a).max() <= 1e-4 * s.die
+    del x0, x1, a1
     pl().pl_build_hints(s.g, s.prm, xy)
     s.o.build_hints(a[:, 0], a[:, 1])
     _compare_hints(s, s.g.export(), s.o.merged())
@@ -442,8 +454,10 @@ def test_large_workload_steps_crossfed():
     b = to_np(out)
     err = max(np.abs(b[:, 0] - ox).max(), np.abs(b[:, 1] - oy).max())
     assert err <= 1e-4 * s.die, err
-    cells = torch.tensor(b[:nl.num_cells].astype(np.float32).reshape(-1), device="cuda")
+    # HPWL of the oracle's round output, in FP32, on both sides
+    c = np.stack([ox, oy], 1)[:nl.num_cells].astype(np.float32)
+    cells = torch.tensor(c.reshape(-1), device="cuda")
     h = torch.zeros(1, dtype=torch.float64, device="cuda")
     pl().pl_hpwl(s.dnl, cells, h, pl().hpwl_workspace(nl.num_nets))
-    ref = oracle.hpwl(nl, b[:nl.num_cells, 0], b[:nl.num_cells, 1])
+    ref = oracle.hpwl(nl, c[:, 0].astype(np.float64), c[:, 1].astype(np.float64))
     assert h.item() == pytest.approx(ref, rel=1e-5)

@@ -171,3 +171,19 @@ def test_pure_tap_model_is_the_plain_filter():
     r = L.round_inputs(o, gx, gy, (0, 1, 2), 0)
     h2 = o.hr_steps(2, gx)
     assert np.allclose(r["c"][0] + r["s"][0] * r["G2"][:, 0], h2, rtol=0, atol=1e-9 * die)
+
+
+def test_effective_target_inverts_the_relaxation():
+    rng = np.random.default_rng(8)
+    nk = np.array([0, 1, 0, 0], np.uint8)
+    g = rng.uniform(2, 8, (4, 2))
+    gt = rng.uniform(2, 8, (4, 2))
+    z = np.zeros(4)
+    for gamma in (0.3, 0.5, 1.0):
+        g1 = L.finish_round(gt, g, nk, z, z, z, z, (0.0, 0.0, 10.0, 10.0), gamma, 1)
+        assert np.allclose(L.effective_target(g1, g, gamma), gt, rtol=1e-13)
+    # where the clamp acted the target is the output that relaxes onto the edge
+    gt[0] = [40.0, -30.0]
+    g1 = L.finish_round(gt, g, nk, z, z, z, z, (0.0, 0.0, 10.0, 10.0), 0.5, 1)
+    t = L.effective_target(g1, g, 0.5)
+    assert np.allclose(0.5 * g[0] + 0.5 * t[0], [10.0, 0.0])

@@ -9,9 +9,10 @@ boundary, after which that cell's hint edges differ.  The whole path is
 therefore compared round by round from the same input: pl_filter_init's
 output is bit-identical to the split calls (pl_init_signal, pl_gift, then
 pl_build_hints + pl_filter_apply per round of Algorithm 1), and each of those
-steps, started from the GPU's previous state, is within 1e-4 of the die width
-of the oracle's step from that state.  Independent runs of the two sides are
-reported (bin flips, error distribution, HPWL) with a loose check.
+calls, started from the oracle's previous state rounded to FP32 (the input of
+both sides), is within 1e-4 of the die width of the oracle's step from that
+state.  Independent runs of the two sides are reported (bin flips, error
+distribution, HPWL) with a loose check.
 """
 import json
 import os
@@ -64,7 +65,8 @@ def run(request):
     pl.pl_hpwl(dnl, mono, h, pl.hpwl_workspace(nl.num_nets))
     torch.cuda.synchronize()
     yield dict(cfg=cfg, kw=kw, nl=nl, mono=_np(mono), states=states, hpwl=h.item(),
-               die=nl.region[2] - nl.region[0], mov=np.asarray(nl.cell_kind) == 0)
+               die=nl.region[2] - nl.region[0], mov=np.asarray(nl.cell_kind) == 0, g=g,
+               prm=prm, N=N)
     g.destroy()
 
 
@@ -106,20 +108,37 @@ def test_whole_initializer_round_by_round(run):
     C = r["nl"].num_cells
     # the monolithic call passes through exactly these states
     assert np.array_equal(r["mono"], st[-1][:, :C])
+    import paper_2511_10073_gb300 as pl
+    g, prm = r["g"], r["prm"]
     o = oracle.Oracle(r["nl"], **r["kw"])
     ox, oy = o.init_signal(SEED)
     assert np.abs(st[0][0] - ox).max() <= 1e-6 * r["die"]
-    gx, gy = o.gift(st[0][0], st[0][1])
-    e = _err(st[1], (gx, gy), r)
+
+    def f32(x, y):  # the common FP32 input of both sides' next step
+        a = np.stack([x, y], 1).astype(np.float32)
+        return a[:, 0].astype(np.float64), a[:, 1].astype(np.float64), \
+            torch.tensor(a.reshape(-1), device="cuda")
+
+    ax, ay, dev = f32(ox, oy)
+    gx, gy = o.gift(ax, ay)
+    out = torch.empty_like(dev)
+    pl.pl_gift(g, prm, dev, out)
+    e = _err(_np(out), (gx, gy), r)
     assert e["max"] <= 1e-4, e
-    for t in range(1, len(st) - 1):
-        o.build_hints(st[t][0], st[t][1])
-        gx, gy = o.filter(st[t][0], st[t][1])
-        e = _err(st[t + 1], (gx, gy), r)
+    for t in range(len(st) - 2):
+        ax, ay, dev = f32(gx, gy)
+        o.build_hints(ax, ay)
+        gx, gy = o.filter(ax, ay)
+        pl.pl_build_hints(g, prm, dev)
+        pl.pl_filter_apply(g, prm, dev, out)
+        e = _err(_np(out), (gx, gy), r)
         assert e["max"] <= 1e-4, (t, e)
-    # HPWL of the final placement (pl_hpwl on the monolithic output)
-    ref = oracle.hpwl(r["nl"], r["mono"][0], r["mono"][1])
-    assert r["hpwl"] == pytest.approx(ref, rel=1e-5)
+    # HPWL of the oracle's final placement, in FP32, on both sides
+    C = r["nl"].num_cells
+    ax, ay, dev = f32(gx[:C], gy[:C])
+    h = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pl.pl_hpwl(pl.DeviceNetlist(r["nl"]), dev, h, pl.hpwl_workspace(r["nl"].num_nets))
+    assert h.item() == pytest.approx(oracle.hpwl(r["nl"], ax, ay), rel=1e-5)
 
 
 def test_independent_runs_and_precision_against_fp64(run):
@@ -139,8 +158,9 @@ def test_independent_runs_and_precision_against_fp64(run):
                                         for t in range(1, len(st))]
     rep["gpu_vs_fp64"] = [_err(st[t], fp[t], r) for t in range(len(st))]
     rep["emulated_vs_fp64"] = [_err(em[t], fp[t], r) for t in range(len(st))]
-    h = {k: oracle.hpwl(r["nl"], v[-1][0][:C], v[-1][1][:C])
-         for k, v in (("gpu", [st[-1]]), ("emulated", em), ("fp64", fp))}
+    # the GPU's HPWL is its own (pl_hpwl of its output); the oracle's of its runs
+    h = {k: oracle.hpwl(r["nl"], v[-1][0][:C], v[-1][1][:C]) for k, v in (("emulated", em), ("fp64", fp))}
+    h["gpu"] = r["hpwl"]
     rep["hpwl"] = h
     rep["hpwl_rel_gpu_vs_emulated"] = (h["gpu"] - h["emulated"]) / h["emulated"]
     rep["hpwl_rel_gpu_vs_fp64"] = (h["gpu"] - h["fp64"]) / h["fp64"]
