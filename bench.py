@@ -249,6 +249,8 @@ def run_learned(pl, g, dnl, nl, args, dev, stream):
     the plain filter and for each model, timed with CUDA events; HPWL
     difference and the movable cells' coordinate RMS difference over the die."""
     import glob
+
+    import numpy as np
     import torch
     files = sorted(glob.glob(os.path.join(LEARNED_DIR, "learned_k*.json")))
     if not files:
@@ -337,6 +339,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched serving form")
+    ap.add_argument("--profile-learned", default=None, metavar="KEY",
+                    help="with --profile-one: profile the step with the committed learned model "
+                         "KEY (e.g. k012) instead of the plain filter")
     ap.add_argument("--profile-one", action="store_true",
                     help="warm up, then run one step inside a CUDA profiler range and exit "
                          "(for ncu --profile-from-start off)")
@@ -378,6 +383,17 @@ def main():
         pl.pl_build_graph(dnl, prm, graph=g)
         pl.pl_filter_init(g, prm, args.seed, None, out)
         pl.pl_hpwl(dnl, out, hp, ws)
+
+    if args.profile_one and args.profile_learned:
+        # the step with a committed learned model (and the parameters it was trained for)
+        d = json.load(open(os.path.join(LEARNED_DIR, f"learned_{args.profile_learned}.json")))
+        lm = pl.LearnedModel.from_host(d, dev)
+        prm = pl.params(**d["params"])
+
+        def step():
+            pl.pl_build_graph(dnl, prm, graph=g)
+            pl.pl_filter_init_learned(g, prm, lm, args.seed, None, out)
+            pl.pl_hpwl(dnl, out, hp, ws)
 
     for _ in range(max(3, args.warmup) if not args.profile_one else args.warmup):
         step()

@@ -340,6 +340,15 @@ pl_status pl_filter_init_learned(pl_graph *g, const pl_params *p, const pl_learn
                                  uint64_t seed, const float *xy0_cells, float *xy_out_cells,
                                  int32_t *fallbacks, pl_stream stream);
 
+/* Check of the bounded waits above (no counterpart in the paper): one CTA
+ * sets up as the learned kernels do (tensor memory, mbarrier), waits on an
+ * mbarrier phase that nothing completes for at most `cycles` clocks
+ * (1..4e9), frees its tensor memory and returns.  ws: device scratch of at
+ * least 8192 bytes, 256-byte aligned.  Returns PL_ERR_TIMEOUT when the wait
+ * gave up (the expected result; the context stays usable), PL_OK otherwise.
+ * Synchronizes `stream`.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+pl_status pl_learned_wait_check(int64_t cycles, void *ws, size_t ws_bytes, pl_stream stream);
+
 /* The MLP alone on given raw features: out[i] (device, n x 4 floats) = the
  * four outputs for feat[i] (device, n x 16 floats), with the normalisation,
  * BF16 roundings and tensor-core arithmetic of pl_learned_apply.  w: device

@@ -92,6 +92,7 @@ def lib():
             "pl_learned_apply": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
             "pl_filter_init_learned": (C.c_int, [vp, vp, vp, u64, vp, vp, vp, vp]),
             "pl_learned_forward": (C.c_int, [vp, vp, i64, vp, vp]),
+            "pl_learned_wait_check": (C.c_int, [i64, vp, sz, vp]),
             "pl_learned_collect": (C.c_int, [vp, vp, vp, i32, vp, vp, i64, vp, vp]),
             "pl_train_opts_default": (None, [vp]),
             "pl_learned_train_ws": (sz, [i64]),
@@ -429,6 +430,18 @@ def pl_filter_init_learned(g: Graph, prm: PlParams, m: LearnedModel | None, seed
                                         _ptr(xy0_cells), _ptr(xy_out_cells), C.byref(nf),
                                         _stream(stream)))
     return int(nf.value)
+
+
+def pl_learned_wait_check(cycles: int, ws=None, stream=None) -> int:
+    """Runs the bounded-wait check; returns its status code (PL_ERR_TIMEOUT
+    when the wait gave up, as it should)."""
+    import torch
+    if ws is None:
+        ws = torch.empty(8192, dtype=torch.uint8, device="cuda")
+    code = lib().pl_learned_wait_check(int(cycles), _ptr(ws), C.c_size_t(ws.numel()), _stream(stream))
+    if code not in (PL_OK, PL_ERR_TIMEOUT):
+        _check(code)
+    return int(code)
 
 
 def pl_learned_forward(w, feat, out, stream=None):

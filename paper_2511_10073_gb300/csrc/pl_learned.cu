@@ -47,8 +47,7 @@ static_assert(kW1 == kTH + 3 && kB1 == kW1 + kHid * kNF && kW2 == kB1 + kHid &&
                   kB2 == kW2 + kNOut * kHid && kLW == kB2 + kNOut,
               "parameter layout");
 constexpr int kTile = 128;      // nodes per tile (MMA M), threads per CTA
-constexpr int kTmemCols = 128;  // D1 in columns 0..63, D2 in 64..79
-constexpr int kD2 = 64;
+constexpr int kTmemCols = 64;   // D1 in columns 0..63; D2 reuses 0..15 once D1 is read
 constexpr int kN2 = 16;         // layer 2's N (4 outputs padded)
 constexpr int kPart = kLW + 1;  // per-block row: gradient at its weight's index, loss last
 constexpr int kMaxBatch = 1024; // tiles per training step at most
@@ -73,9 +72,12 @@ constexpr int SM_XS = SM_DH + kTile * kDhS * 4;      // [128][17]
 constexpr int SM_DO = SM_XS + kTile * kXsS * 4;      // [128][4]
 constexpr int SM_GT = SM_DO + kTile * 4 * 4;         // [128][4]: theta terms, loss
 constexpr int SM_TR = SM_GT + kTile * 4 * 4;
-constexpr int kSmemFwd = 51200;  // > 45 KB: at most 4 CTAs (4 x 128 TMEM columns) per SM
+// Shared memory per CTA also bounds the CTAs per SM, so that their tensor
+// memory (64 columns each) never exceeds the SM's 512 columns: at most 8
+// forward CTAs, at most 3 training CTAs, and no mix above 8 in total.
+constexpr int kSmemFwd = SM_TC + 1024;
 constexpr int kSmemTrain = SM_TR + 1024;
-static_assert(SM_TC + 1024 <= kSmemFwd && 5 * (kSmemFwd + 1024) > 233472, "forward smem");
+static_assert(9 * (kSmemFwd + 1024) > 233472 && 8 * (kSmemFwd + 1024) <= 233472, "forward smem");
 static_assert(4 * (kSmemTrain + 1024) > 233472, "training: at most 3 CTAs per SM");
 
 // instruction descriptors (kind::f16): D FP32 (bit 4), A and B BF16 (bits 7,
@@ -118,8 +120,9 @@ __device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Waits for phase `parity` of the mbarrier, for at most kWaitCycles clocks.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+// Waits for phase `parity` of the mbarrier, for at most `limit` clocks.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity,
+                                         long long limit = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -130,7 +133,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -160,6 +163,17 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 __device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+// Two floats rounded to BF16 (nearest even) in one conversion: lo in the low
+// half; with RELU, negative values become 0.
+template <bool RELU>
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+  uint32_t r;
+  if (RELU)
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 __device__ __forceinline__ uint8_t *smem_base() {
@@ -216,21 +230,34 @@ __device__ void tc_teardown(uint32_t tmem) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// The bounded wait's own check: set up as the learned kernels do, wait on
+// an mbarrier phase that nothing completes, for at most `limit` clocks, then
+// free the tensor memory and report.
+__global__ void __launch_bounds__(kTile) k_wait_check(long long limit, const float *w, int *status) {
+  uint8_t *sm = smem_base();
+  const uint32_t tmem = tc_setup(sm, w);
+  const bool ok = bar_wait(su32(sm + SM_BAR), 0u, limit);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) flag(status, ST_TIMEOUT);
+  tc_teardown(tmem);
+}
+
 // Normalised BF16 inputs of one node from its raw features.
 __device__ __forceinline__ void normalise(const uint8_t *sm, const float *f, uint32_t *xw) {
   const float *prm = reinterpret_cast<const float *>(sm + SM_PRM);
 #pragma unroll
   for (int k = 0; k < kNF; k += 2)
-    xw[k / 2] = pack2(f2bf16((f[k] - prm[k]) * prm[16 + k]),
-                      f2bf16((f[k + 1] - prm[k + 1]) * prm[16 + k + 1]));
+    xw[k / 2] = cvt_bf16x2<false>((f[k] - prm[k]) * prm[16 + k],
+                                  (f[k + 1] - prm[k + 1]) * prm[16 + k + 1]);
 }
 
 // One tile through both layers.  xw: this thread's row (8 words of BF16
-// pairs).  pre: the 64 pre-activations (with b1); out: the 4 outputs (with
-// b2).  ph: the mbarrier's next phase parity.  False (the same in every
-// thread) when a wait gave up.
-__device__ bool tc_tile(uint8_t *sm, uint32_t tmem, uint32_t &ph, const uint32_t *xw, float *pre,
-                        float *out) {
+// pairs).  out: the 4 outputs (with b2).  With MASK, *mask gets bit j set
+// where pre-activation j (with b1) is positive (the ReLU's derivative).  ph:
+// the mbarrier's next phase parity.  False (the same in every thread) when a
+// wait gave up.
+template <bool MASK>
+__device__ bool tc_tile(uint8_t *sm, uint32_t tmem, uint32_t &ph, const uint32_t *xw, float *out,
+                        uint64_t *mask) {
   const int r = threadIdx.x, warp = r >> 5;
   *reinterpret_cast<uint4 *>(sm + SM_XA + opnd_off(r, 0, 0)) = make_uint4(xw[0], xw[1], xw[2], xw[3]);
   *reinterpret_cast<uint4 *>(sm + SM_XA + opnd_off(r, 8, 0)) = make_uint4(xw[4], xw[5], xw[6], xw[7]);
@@ -248,22 +275,28 @@ __device__ bool tc_tile(uint8_t *sm, uint32_t tmem, uint32_t &ph, const uint32_t
   if (!__syncthreads_and(ok)) return false;
   tc_after();
   const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  tmem_ld32(lane_base, pre);
-  tmem_ld32(lane_base + 32, pre + 32);
-  tmem_wait_ld();
   const float *b1 = reinterpret_cast<const float *>(sm + SM_B1);
+  uint64_t msk = 0;
 #pragma unroll
-  for (int q = 0; q < kHid / 8; ++q) {
-    uint32_t h[4];
+  for (int half = 0; half < 2; ++half) {
+    float d[32];
+    tmem_ld32(lane_base + 32 * half, d);
+    tmem_wait_ld();
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = 8 * q + 2 * u;
-      pre[j] += b1[j];
-      pre[j + 1] += b1[j + 1];
-      h[u] = pack2(f2bf16(fmaxf(pre[j], 0.f)), f2bf16(fmaxf(pre[j + 1], 0.f)));
+    for (int q = 0; q < 4; ++q) {
+      uint32_t h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = 8 * q + 2 * u, j = 32 * half + jj;
+        const float a = d[jj] + b1[j], b = d[jj + 1] + b1[j + 1];
+        if (MASK) msk |= (uint64_t)(a > 0.f) << j | (uint64_t)(b > 0.f) << (j + 1);
+        h[u] = cvt_bf16x2<true>(a, b);
+      }
+      *reinterpret_cast<uint4 *>(sm + SM_HA + opnd_off(r, 32 * half + 8 * q, 4096)) =
+          make_uint4(h[0], h[1], h[2], h[3]);
     }
-    *reinterpret_cast<uint4 *>(sm + SM_HA + opnd_off(r, 8 * q, 4096)) = make_uint4(h[0], h[1], h[2], h[3]);
   }
+  if (MASK) *mask = msk;
   fence_async();
   tc_before();
   __syncthreads();
@@ -271,7 +304,7 @@ __device__ bool tc_tile(uint8_t *sm, uint32_t tmem, uint32_t &ph, const uint32_t
     tc_after();
 #pragma unroll
     for (int c = 0; c < kHid / 16; ++c)
-      mma(tmem + kD2, sdesc(su32(sm + SM_HA + c * 4096)), sdesc(su32(sm + SM_W2 + c * 512)), kIdesc2,
+      mma(tmem, sdesc(su32(sm + SM_HA + c * 4096)), sdesc(su32(sm + SM_W2 + c * 512)), kIdesc2,
           c > 0 ? 1u : 0u);
     commit(bar);
   }
@@ -279,7 +312,7 @@ __device__ bool tc_tile(uint8_t *sm, uint32_t tmem, uint32_t &ph, const uint32_t
   ph ^= 1u;
   if (!__syncthreads_and(ok)) return false;
   tc_after();
-  tmem_ld4(lane_base + kD2, out);
+  tmem_ld4(lane_base, out);
   tmem_wait_ld();
   const float *b2 = reinterpret_cast<const float *>(sm + SM_PRM) + 36;
 #pragma unroll
@@ -299,7 +332,8 @@ struct NodeArgs {
   const uint8_t *nkind;
   const float2 *fixedp;
   const float4 *bounds;
-  float sx, sy, cx, cy, ba, lamf, rnd, gamma, omg;
+  float sx, sy, cx, cy, rnd, gamma, omg;
+  float isx, isy, ilam, iba;  // 1 / bin width, 1 / bin height, 1 / lambda_up, 1 / bin area
   int clamp;
   const float *w;
   float2 *out;
@@ -320,8 +354,8 @@ __device__ __forceinline__ void node_in(const NodeArgs &A, int64_t v, NodeIn &q)
   const float2 t[3] = {A.t0[v], A.t1[v], A.t2[v]};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    q.G[i][0] = (t[i].x - A.cx) / A.sx;
-    q.G[i][1] = (t[i].y - A.cy) / A.sy;
+    q.G[i][0] = (t[i].x - A.cx) * A.isx;
+    q.G[i][1] = (t[i].y - A.cy) * A.isy;
   }
   const uint8_t kd = A.nkind[v];
   const dfl D = A.dsum[v], Pp = A.psum[v];
@@ -330,15 +364,15 @@ __device__ __forceinline__ void node_in(const NodeArgs &A, int64_t v, NodeIn &q)
   float area = 0.f;
   if (v < A.C) {
     hb = A.hbin[v];
-    if (kd == 0) area = (A.cw[v] * A.ch[v]) / A.ba;
+    if (kd == 0) area = (A.cw[v] * A.ch[v]) * A.iba;
   }
   q.f[0] = q.G[1][0] - q.G[0][0];
   q.f[1] = q.G[1][1] - q.G[0][1];
   q.f[2] = q.G[2][0] - q.G[0][0];
   q.f[3] = q.G[2][1] - q.G[0][1];
-  q.f[4] = d / A.lamf;
-  q.f[5] = (2.f * p - d) / A.lamf;
-  q.f[6] = (d - p) / A.lamf;
+  q.f[4] = d * A.ilam;
+  q.f[5] = (2.f * p - d) * A.ilam;
+  q.f[6] = (d - p) * A.ilam;
   q.f[7] = hb >= 0 ? (float)A.phi[hb] : 0.f;
   q.f[8] = hb >= 0 ? 1.f : 0.f;
   q.f[9] = kd == 1 ? 1.f : 0.f;
@@ -349,7 +383,7 @@ __device__ __forceinline__ void node_in(const NodeArgs &A, int64_t v, NodeIn &q)
 }
 
 // Persistent: CTA b takes tiles b, b + grid, ...
-__global__ void __launch_bounds__(kTile) k_learned_apply(NodeArgs A) {
+__global__ void __launch_bounds__(kTile, 8) k_learned_apply(NodeArgs A) {
   uint8_t *sm = smem_base();
   const uint32_t tmem = tc_setup(sm, A.w);
   const float *prm = reinterpret_cast<const float *>(sm + SM_PRM);
@@ -359,21 +393,27 @@ __global__ void __launch_bounds__(kTile) k_learned_apply(NodeArgs A) {
     const int64_t v = tile * kTile + threadIdx.x;
     const bool live = v < A.N;
     NodeIn q;
+    uint8_t kd = 2;
+    float2 g = make_float2(0.f, 0.f);
+    float4 bd = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
       node_in(A, v, q);
+      // the round's end reads these: loaded now, in flight during the MMAs
+      kd = A.nkind[v];
+      g = A.g[v];
+      if (A.clamp) bd = A.bounds[v];
     } else {
 #pragma unroll
       for (int k = 0; k < kNF; ++k) q.f[k] = 0.f;
     }
     uint32_t xw[8];
     normalise(sm, q.f, xw);
-    float pre[kHid], o[kNOut];
-    if (!tc_tile(sm, tmem, ph, xw, pre, o)) {
+    float o[kNOut];
+    if (!tc_tile<false>(sm, tmem, ph, xw, o, nullptr)) {
       if (threadIdx.x == 0) flag(A.status, ST_TIMEOUT);
       break;
     }
     if (!live) continue;
-    const uint8_t kd = A.nkind[v];
     float gt[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -390,11 +430,9 @@ __global__ void __launch_bounds__(kTile) k_learned_apply(NodeArgs A) {
       r = A.fixedp[v];
     } else {
       if (!isfinite(gt[0]) || !isfinite(gt[1])) flag(A.status, ST_LEARNED_NF);
-      const float2 g = A.g[v];
       r.x = A.omg * g.x + A.gamma * gt[0];
       r.y = A.omg * g.y + A.gamma * gt[1];
       if (A.clamp) {
-        const float4 bd = A.bounds[v];
         r.x = fminf(fmaxf(r.x, bd.x), bd.z);
         r.y = fminf(fmaxf(r.y, bd.y), bd.w);
       }
@@ -405,8 +443,8 @@ __global__ void __launch_bounds__(kTile) k_learned_apply(NodeArgs A) {
 }
 
 // The MLP alone on given raw features (n x 16 floats) -> n x 4 floats.
-__global__ void __launch_bounds__(kTile) k_learned_forward(const float *w, const float *feat,
-                                                           int64_t n, float *out) {
+__global__ void __launch_bounds__(kTile, 8) k_learned_forward(const float *w, const float *feat,
+                                                              int64_t n, float *out) {
   uint8_t *sm = smem_base();
   const uint32_t tmem = tc_setup(sm, w);
   uint32_t ph = 0;
@@ -430,8 +468,8 @@ __global__ void __launch_bounds__(kTile) k_learned_forward(const float *w, const
     }
     uint32_t xw[8];
     normalise(sm, f, xw);
-    float pre[kHid], o[kNOut];
-    const bool ok = tc_tile(sm, tmem, ph, xw, pre, o);
+    float o[kNOut];
+    const bool ok = tc_tile<false>(sm, tmem, ph, xw, o, nullptr);
     if (!ok) o[0] = o[1] = o[2] = o[3] = __int_as_float(0x7fc00000);
     if (i < n) reinterpret_cast<float4 *>(out)[i] = make_float4(o[0], o[1], o[2], o[3]);
     if (!ok) break;
@@ -570,9 +608,10 @@ __global__ void __launch_bounds__(kTile) k_train_tile(const float *rec, int64_t 
   }
   uint32_t xw[8];
   normalise(sm, q.f, xw);
-  float pre[kHid], o[kNOut];
+  float o[kNOut];
+  uint64_t pos = 0;
   uint32_t ph = 0;
-  const bool ok = tc_tile(sm, tmem, ph, xw, pre, o);
+  const bool ok = tc_tile<true>(sm, tmem, ph, xw, o, &pos);
   if (!ok) {
     if (t == 0) flag(status, ST_TIMEOUT);
     tc_teardown(tmem);
@@ -615,7 +654,7 @@ __global__ void __launch_bounds__(kTile) k_train_tile(const float *rec, int64_t 
     s += d[1] * w2f[kHid + j];
     s += d[2] * w2f[2 * kHid + j];
     s += d[3] * w2f[3 * kHid + j];
-    dh[t * kDhS + j] = pre[j] > 0.f ? s : 0.f;
+    dh[t * kDhS + j] = (pos >> j) & 1u ? s : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < kNF; k += 2) {
@@ -780,8 +819,10 @@ NodeArgs node_args(pl_graph *g, const pl_params *p, int32_t round) {
   A.sy = (float)g->hb;
   A.cx = (float)(0.5 * (g->xl + g->xh));
   A.cy = (float)(0.5 * (g->yl + g->yh));
-  A.ba = A.sx * A.sy;
-  A.lamf = (float)g->lam_h[0];
+  A.isx = (float)(1.0 / g->wb);
+  A.isy = (float)(1.0 / g->hb);
+  A.iba = (float)(1.0 / ((double)A.sx * (double)A.sy));
+  A.ilam = (float)g->lam_h[1];
   A.rnd = p->t_hint > 0 ? (float)round / (float)p->t_hint : 0.f;
   A.gamma = (float)p->gamma;
   A.omg = (float)(1.0 - p->gamma);
@@ -823,7 +864,7 @@ pl_status run_learned(pl_graph *g, const pl_params *p, const pl_learned *m, int3
   A.out = reinterpret_cast<float2 *>(out);
   TRY(smem_attrs());
   const long long ntiles = (g->N + kTile - 1) / kTile;
-  const long long cap = 4LL * device_sms();
+  const long long cap = 8LL * device_sms();
   const int grid = (int)std::max(1LL, std::min(ntiles, cap));
   k_learned_apply<<<grid, kTile, kSmemFwd, s>>>(A);
   note_launch();
@@ -861,6 +902,27 @@ pl_status pl_learned_apply(pl_graph *g, const pl_params *p, const pl_learned *m,
   return PL_OK;
 }
 
+pl_status pl_learned_wait_check(int64_t cycles, void *ws, size_t ws_bytes, pl_stream stream) {
+  clear_error();
+  if (cycles < 1 || cycles > kWaitCycles) { set_error("cycles must be in 1..4e9"); return PL_ERR_INVALID_ARG; }
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) { set_error("workspace must be non-NULL and 256-byte aligned"); return PL_ERR_INVALID_ARG; }
+  if (ws_bytes < 8192) { set_error("workspace too small: need 8192 bytes"); return PL_ERR_WORKSPACE; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TRY(cudaFuncSetAttribute(k_wait_check, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd));
+  // the workspace: a zero parameter vector, then the status word
+  float *w = static_cast<float *>(ws);
+  int *status = reinterpret_cast<int *>(static_cast<char *>(ws) + 6144);
+  TRY(cudaMemsetAsync(ws, 0, 8192, s));
+  k_wait_check<<<1, kTile, kSmemFwd, s>>>((long long)cycles, w, status);
+  note_launch();
+  TRY(cudaGetLastError());
+  int sw = 0;
+  TRY(cudaMemcpyAsync(&sw, status, 4, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (sw & ST_TIMEOUT) { set_error("a bounded device-side wait gave up"); return PL_ERR_TIMEOUT; }
+  return PL_OK;
+}
+
 pl_status pl_learned_forward(const float *w, const float *feat, int64_t n, float *out,
                              pl_stream stream) {
   clear_error();
@@ -869,7 +931,7 @@ pl_status pl_learned_forward(const float *w, const float *feat, int64_t n, float
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   TRY(smem_attrs());
   const long long ntiles = (n + kTile - 1) / kTile;
-  const int grid = (int)std::min(ntiles, 4LL * device_sms());
+  const int grid = (int)std::min(ntiles, 8LL * device_sms());
   k_learned_forward<<<grid, kTile, kSmemFwd, s>>>(w, feat, n, out);
   note_launch();
   TRY(cudaGetLastError());

@@ -329,3 +329,17 @@ def test_learned_argument_errors():
     with pytest.raises(m.PlError) as e:  # fewer than one tile of records
         m.pl_learned_train(R, 100, m.LearnedModel((0, 1, 2), dev(w)), m.train_opts())
     assert e.value.code == m.PL_ERR_INVALID_ARG
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The tensor-core kernels' mbarrier waits are bounded: a wait on a phase
+    that nothing completes gives up after the limit (about 1 ms here), the
+    CTA frees its tensor memory, and the host reads PL_ERR_TIMEOUT.  The
+    tensor-core path then still gives exact results."""
+    m = pl()
+    import time
+    t0 = time.perf_counter()
+    assert m.pl_learned_wait_check(2_000_000) == m.PL_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30
+    assert "gave up" in m.lib().pl_last_error().decode()
+    test_forward_exact_on_dyadic_inputs()
