@@ -177,9 +177,11 @@ def run_batched(pl, netgen, dev, stream, args, n=64):
     """The batched serving form: n designs of uneven size (std cells
     log-uniform in 5k-500k), each built once; one step initializes all of
     them.  The plain GPU form runs the designs one after another on one
-    stream; the batched form runs pl_filter_init_batch over S streams, S
-    chosen by timing S = 1, 2, 4, 8, 16 once each.  Both forms give the same
-    bits, so their HPWL differs by 0."""
+    stream.  The batched form is pl_filter_init_batch with the options the
+    library's autotuner (pl_batch_autotune) picks over 16 streams: the union
+    form (one launch per kernel and power over all designs) or the per-design
+    form, stream count, short-row CTAs per SM.  Every form gives the same
+    bits, so the HPWL differs by 0."""
     import torch
     cfgs = netgen.batch_configs(args.seed, n=n)
     nls = [netgen.make_netlist(c, 1000 + i) for i, c in enumerate(cfgs)]
@@ -189,7 +191,8 @@ def run_batched(pl, netgen, dev, stream, args, n=64):
     outs = [torch.empty(nl.num_cells * 2, dtype=torch.float32, device=dev) for nl in nls]
     seeds = [args.seed + i for i in range(n)]
     movable = sum(nl.num_movable for nl in nls)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(16)]
+    ws = pl.batch_workspace(n, prm, dev)
 
     def plain():
         for g, o, sd in zip(graphs, outs, seeds):
@@ -206,17 +209,13 @@ def run_batched(pl, netgen, dev, stream, args, n=64):
     plain()
     ref = [o.clone() for o in outs]
     ms_plain = timed(plain, max(1, args.steps // 2))
-    tried = {}
-    pools = {}
-    for ns in (1, 2, 4, 8, 16):
-        pools[ns] = [torch.cuda.Stream(device=dev) for _ in range(ns)]
-        fn = lambda ns=ns: pl.pl_filter_init_batch(graphs, prm, seeds, outs, pools[ns])
-        fn()
-        tried[ns] = timed(fn, 1)
-    best = min(tried, key=tried.get)
-    ms_batch = timed(lambda: pl.pl_filter_init_batch(graphs, prm, seeds, outs, pools[best]),
-                     max(1, args.steps // 2))
+    best, tune_ms = pl.pl_batch_autotune(graphs, prm, seeds, outs, streams, ws)
+    reps = max(1, args.steps // 2)
+    ms_batch = timed(lambda: pl.pl_filter_init_batch(graphs, prm, seeds, outs, streams, best, ws), reps)
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    other = pl.batch_opts(union_products=1 - best.union_products, streams=best.streams or 16)
+    ms_other = timed(lambda: pl.pl_filter_init_batch(graphs, prm, seeds, outs, streams, other, ws), reps)
+    same = same and all(torch.equal(a, b) for a, b in zip(ref, outs))
     hws = [pl.hpwl_workspace(nl.num_nets, dev) for nl in nls]
     h = torch.zeros(2 * n, dtype=torch.float64, device=dev)
     for i, (d, o, w) in enumerate(zip(dnls, outs, hws)):
@@ -226,13 +225,16 @@ def run_batched(pl, netgen, dev, stream, args, n=64):
     rel = float(abs(hp[:n].sum() - hp[n:].sum()) / hp[n:].sum())
     for g in graphs:
         g.destroy()
+    form = "union" if best.union_products else "per-design"
     return {"what": f"{n} designs, std cells log-uniform 5k-500k ({movable} movable cells), "
                     "each initialized from its seed (GiFt + 3 rounds, BF16, taps {2,4,8})",
             "unit": "cells/s", "value": movable / (ms_batch / 1e3),
             "plain_gpu_value": movable / (ms_plain / 1e3), "speedup": ms_plain / ms_batch,
             "ms_per_batch": ms_batch, "plain_ms_per_batch": ms_plain,
-            "autotune": {"streams_tried_ms": {str(k): v for k, v in tried.items()},
-                         "streams": best},
+            "autotune": {"form": form, "streams": best.streams,
+                         "rows_ctas_per_sm": best.rows_ctas_per_sm, "best_trial_ms": tune_ms},
+            "other_form": {"form": "per-design" if best.union_products else "union",
+                           "ms_per_batch": ms_other},
             "same_bits_as_plain": same, "hpwl_rel_diff": rel,
             "timing": "wall clock of whole batches after a synchronize (host threads drive "
                       "the streams)"}

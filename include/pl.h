@@ -189,18 +189,48 @@ pl_status pl_filter_init(pl_graph *g, const pl_params *p, uint64_t seed, const f
 
 /* The batched serving form: the whole initializer (as pl_filter_init, from
  * the seed, no given placement) of n designs, each on its own built graph
- * (Algorithm 1 runs per design, so designs are independent).  nstreams worker
- * threads each drive one of the caller's streams and take the next design,
- * largest first; the designs' kernels overlap on the GPU.  A design's result
- * is the same bits as its pl_filter_init call on any stream.  xy_out_cells[i]:
- * device, graphs[i]'s num_cells pairs.  Returns after every design is done
- * (each worker synchronizes its stream).  Graph builds do not run here: build
- * the graphs first (pl_build_graph calls on several threads take turns).
- * Errors: INVALID_ARG, or the first failing design's status (its index in
- * pl_last_error). */
+ * (Algorithm 1 runs per design, so designs are independent).  A design's
+ * result is the same bits as its pl_filter_init call.  Two forms (opts):
+ *  - union_products = 1 (the default): A0 and each round's hint build run
+ *    per design, on worker threads that each drive one of the caller's
+ *    streams (largest design first); each round's filter then runs as one
+ *    launch per kernel and power over all designs, a block-diagonal union of
+ *    the designs' matrices with each design's own lambda_up and coefficients
+ *    (on streams[0] and the first graph's second stream);
+ *  - union_products = 0: each worker runs whole initializers, one design at a
+ *    time.
+ * xy_out_cells[i]: device, graphs[i]'s num_cells pairs.  Returns after every
+ * design is done.  ws: device, 256-byte aligned, pl_batch_workspace_size(n, p)
+ * bytes (only the union form uses it; may be NULL for the other).  Graph
+ * builds do not run here: build the graphs first (pl_build_graph calls on
+ * several threads take turns).  The union form needs one weight type for all
+ * graphs.  Errors: INVALID_ARG, WORKSPACE, or the first failing design's
+ * status (its index in pl_last_error). */
+typedef struct {
+  int32_t union_products;   /* 1: one launch per kernel and power over all designs; 0: per design */
+  int32_t streams;          /* how many of the caller's streams to use, 1..nstreams (0: all) */
+  int32_t rows_ctas_per_sm; /* CTAs per SM of the union short-row kernel, 1..5 (0: 5) */
+} pl_batch_opts;
+
+/* Defaults: union form, all streams, 5 CTAs per SM. */
+void pl_batch_opts_default(pl_batch_opts *o);
+size_t pl_batch_workspace_size(int32_t n, const pl_params *p);
 pl_status pl_filter_init_batch(int32_t n, pl_graph *const *graphs, const pl_params *p,
                                const uint64_t *seeds, float *const *xy_out_cells,
-                               int32_t nstreams, const pl_stream *streams);
+                               int32_t nstreams, const pl_stream *streams,
+                               const pl_batch_opts *opts, void *ws, size_t ws_bytes);
+
+/* The batch form's autotuner: runs pl_filter_init_batch once for each
+ * candidate (per-design form on 1, 2, 4, 8, 16 streams; union form on 4, 8,
+ * 16 streams with 3, 4, 5 short-row CTAs per SM; streams at most nstreams),
+ * timing each call on the host clock after a device synchronisation, and
+ * writes the fastest to *best (and its time in ms to *best_ms, may be
+ * NULL).  Every candidate gives the same bits, so xy_out_cells holds the
+ * result.  Errors: as pl_filter_init_batch. */
+pl_status pl_batch_autotune(int32_t n, pl_graph *const *graphs, const pl_params *p,
+                            const uint64_t *seeds, float *const *xy_out_cells, int32_t nstreams,
+                            const pl_stream *streams, void *ws, size_t ws_bytes,
+                            pl_batch_opts *best, double *best_ms);
 
 /* A5: writes sum over nets of (max - min) pin x + (max - min) pin y, pin =
  * cell centre (xy_cells, device) + offset, as one double to *hpwl (device).

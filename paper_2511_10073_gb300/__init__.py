@@ -85,7 +85,10 @@ def lib():
             "pl_graph_export": (C.c_int, [vp] * 10),
             "pl_graph_destroy": (None, [vp]),
             "pl_last_error": (C.c_char_p, []),
-            "pl_filter_init_batch": (C.c_int, [i32, vp, vp, vp, vp, i32, vp]),
+            "pl_filter_init_batch": (C.c_int, [i32, vp, vp, vp, vp, i32, vp, vp, vp, sz]),
+            "pl_batch_opts_default": (None, [vp]),
+            "pl_batch_workspace_size": (sz, [i32, vp]),
+            "pl_batch_autotune": (C.c_int, [i32, vp, vp, vp, vp, i32, vp, vp, sz, vp, vp]),
             "pl_rho_params_default": (None, [vp]),
             "pl_macro_density": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, dbl, dbl, dbl, dbl,
                                            i32, i32, vp, vp]),
@@ -283,16 +286,61 @@ def pl_filter_init(g: Graph, prm: PlParams, seed: int, xy0_cells, xy_out_cells, 
                                 _ptr(xy_out_cells), _stream(stream)))
 
 
-def pl_filter_init_batch(graphs, prm: PlParams, seeds, outs, streams):
-    """The initializer of every design of a batch, concurrently on `streams`
-    (torch CUDA streams, one worker thread each); outs[i]: device tensor of
-    graphs[i]'s num_cells pairs."""
+class PlBatchOpts(C.Structure):
+    _fields_ = [("union_products", C.c_int32), ("streams", C.c_int32),
+                ("rows_ctas_per_sm", C.c_int32)]
+
+
+def batch_opts(**kw) -> PlBatchOpts:
+    o = PlBatchOpts()
+    lib().pl_batch_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def batch_workspace(n: int, prm: PlParams, device="cuda"):
+    import torch
+    nb = int(lib().pl_batch_workspace_size(int(n), C.byref(prm)))
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
+def _batch_args(graphs, seeds, outs, streams):
     n = len(graphs)
     gh = (C.c_void_p * n)(*[g.handle.value for g in graphs])
     sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
     op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
     sp = (C.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
-    _check(lib().pl_filter_init_batch(n, gh, C.byref(prm), sd, op, len(streams), sp))
+    return n, gh, sd, op, sp
+
+
+def pl_filter_init_batch(graphs, prm: PlParams, seeds, outs, streams, opts: PlBatchOpts | None = None,
+                         ws=None):
+    """The initializer of every design of a batch (see include/pl.h):
+    outs[i] is a device tensor of graphs[i]'s num_cells pairs; streams are
+    torch CUDA streams (one worker thread each).  The union form (the
+    default) takes a device workspace (allocated here when ws is None)."""
+    n, gh, sd, op, sp = _batch_args(graphs, seeds, outs, streams)
+    if opts is None:
+        opts = batch_opts()
+    if ws is None and opts.union_products:
+        ws = batch_workspace(n, prm, outs[0].device)
+    nb = 0 if ws is None else ws.numel()
+    _check(lib().pl_filter_init_batch(n, gh, C.byref(prm), sd, op, len(streams), sp,
+                                      C.byref(opts), _ptr(ws), C.c_size_t(nb)))
+
+
+def pl_batch_autotune(graphs, prm: PlParams, seeds, outs, streams, ws=None):
+    """Runs every candidate of the batch autotuner; returns (best options,
+    best ms)."""
+    n, gh, sd, op, sp = _batch_args(graphs, seeds, outs, streams)
+    if ws is None:
+        ws = batch_workspace(n, prm, outs[0].device)
+    best = PlBatchOpts()
+    ms = C.c_double(0)
+    _check(lib().pl_batch_autotune(n, gh, C.byref(prm), sd, op, len(streams), sp, _ptr(ws),
+                                   C.c_size_t(ws.numel()), C.byref(best), C.byref(ms)))
+    return best, float(ms.value)
 
 
 def pl_hpwl_workspace_size(num_nets: int) -> int:

@@ -88,7 +88,7 @@ cudaError_t launch_hpwl(const pl_netlist *nl, const float *xy, double *out, void
 
 static bool finite(double v) { return std::isfinite(v); }
 
-static pl_status check_params(const pl_params *p) {
+pl_status check_params(const pl_params *p) {
   if (!p) { set_error("params is NULL"); return PL_ERR_INVALID_ARG; }
   if (p->clique_max < 2 || p->clique_max > 16) { set_error("clique_max must be in 2..16"); return PL_ERR_INVALID_ARG; }
   if (p->wdtype != PL_W_FP32 && p->wdtype != PL_W_BF16) { set_error("wdtype must be PL_W_FP32 or PL_W_BF16"); return PL_ERR_INVALID_ARG; }
@@ -119,7 +119,7 @@ static pl_status check_netlist(const pl_netlist *nl) {
   return PL_OK;
 }
 
-static pl_status same_layout(const pl_graph *g, const pl_params *p) {
+pl_status same_layout(const pl_graph *g, const pl_params *p) {
   if (p->nbx != g->nbx || p->nby != g->nby || p->det_ratio != g->det_ratio ||
       p->wdtype != g->wdtype || p->clique_max != g->clique_max) {
     set_error("bins, detection ratio, weight type and clique_max must match the graph build");

@@ -54,81 +54,92 @@ __device__ __forceinline__ float bw_load(const void *bw, size_t k) {
 // every node (the cells' ones are gathered).  The chunk count is bchunk[NB];
 // the grid may be any size.
 template <int WT, bool DEG>
+__device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk,
+                                          const int32_t *cown, const int64_t *boff,
+                                          const uint32_t *blist, const void *bwq,
+                                          const float2 *x, float4 *part, long long c) {
+  const int lane = threadIdx.x & 31;
+  const int b = cown[c];
+  const long long k0 = boff[2 * b] + (long long)(c - bchunk[b]) * kBinChunk;
+  const long long k1 = boff[2 * b + 1];
+  uint32_t kp[kBinPer];  // list positions (below 2^31: movable cells)
+  bool cv[kBinPer];
+  uint32_t ci[kBinPer];
+#pragma unroll
+  for (int u = 0; u < kBinPer; ++u) {
+    kp[u] = (uint32_t)(k0 + lane + 32LL * u);
+    cv[u] = k0 + lane + 32LL * u < k1;
+    ci[u] = (!DEG && cv[u]) ? blist[kp[u]] : 0u;
+  }
+  float2 xi[kBinPer];
+#pragma unroll
+  for (int u = 0; u < kBinPer; ++u) xi[u] = (!DEG && cv[u]) ? x[ci[u]] : make_float2(0.f, 0.f);
+  for (int t = 0; t < B.W; ++t) {
+    float w[kBinPer];
+#pragma unroll
+    for (int u = 0; u < kBinPer; ++u) w[u] = cv[u] ? bw_load<WT>(bwq, (size_t)kp[u] * B.W + t) : 0.f;
+    dfl a{0.f, 0.f}, e{0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kBinPer; ++u) {
+      if (DEG) {
+        df_add(a, w[u]);
+        if (w[u] > 0.f) df_add(e, w[u]);
+      } else {
+        df_add_prod(a, w[u], xi[u].x);
+        df_add_prod(e, w[u], xi[u].y);
+      }
+    }
+    a = warp_sum_df(a);
+    e = warp_sum_df(e);
+    if (lane == 0) part[(size_t)c * B.W + t] = make_float4(a.hi, a.lo, e.hi, e.lo);
+  }
+}
+
+template <int WT, bool DEG>
 __global__ void __launch_bounds__(kBinThreads, 4) k_bin_partials(BinGeo B, const int32_t *bchunk,
                                                               const int32_t *cown,
                                                               const int64_t *boff,
                                                               const uint32_t *blist,
                                                               const void *bwq, const float2 *x,
                                                               float4 *part) {
-  const int lane = threadIdx.x & 31;
   const int nchunk = bchunk[B.NB];
   for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nchunk;
-       c += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const int b = cown[c];
-    const long long k0 = boff[2 * b] + (long long)(c - bchunk[b]) * kBinChunk;
-    const long long k1 = boff[2 * b + 1];
-    uint32_t kp[kBinPer];  // list positions (below 2^31: movable cells)
-    bool cv[kBinPer];
-    uint32_t ci[kBinPer];
-#pragma unroll
-    for (int u = 0; u < kBinPer; ++u) {
-      kp[u] = (uint32_t)(k0 + lane + 32LL * u);
-      cv[u] = k0 + lane + 32LL * u < k1;
-      ci[u] = (!DEG && cv[u]) ? blist[kp[u]] : 0u;
-    }
-    float2 xi[kBinPer];
-#pragma unroll
-    for (int u = 0; u < kBinPer; ++u) xi[u] = (!DEG && cv[u]) ? x[ci[u]] : make_float2(0.f, 0.f);
-    for (int t = 0; t < B.W; ++t) {
-      float w[kBinPer];
-#pragma unroll
-      for (int u = 0; u < kBinPer; ++u) w[u] = cv[u] ? bw_load<WT>(bwq, (size_t)kp[u] * B.W + t) : 0.f;
-      dfl a{0.f, 0.f}, e{0.f, 0.f};
-#pragma unroll
-      for (int u = 0; u < kBinPer; ++u) {
-        if (DEG) {
-          df_add(a, w[u]);
-          if (w[u] > 0.f) df_add(e, w[u]);
-        } else {
-          df_add_prod(a, w[u], xi[u].x);
-          df_add_prod(e, w[u], xi[u].y);
-        }
-      }
-      a = warp_sum_df(a);
-      e = warp_sum_df(e);
-      if (lane == 0) part[(size_t)c * B.W + t] = make_float4(a.hi, a.lo, e.hi, e.lo);
-    }
-  }
+       c += ((long long)gridDim.x * blockDim.x) >> 5)
+    bin_chunk<WT, DEG>(B, bchunk, cown, boff, blist, bwq, x, part, c);
 }
 
 // Sums of each (bucket, slot) over the bucket's chunks: a warp per pair, the
 // lanes strided over the chunks in order, then a fixed tree (a hot bucket's
 // hundreds of chunks spread over the warp).
+__device__ __forceinline__ void bucket_sum(const BinGeo &B, const int32_t *bchunk,
+                                           const float4 *part, float4 *bsum, long long q) {
+  const int lane = threadIdx.x & 31;
+  const int b = (int)(q / B.W), s = (int)(q - (long long)b * B.W);
+  dfl a{0.f, 0.f}, e{0.f, 0.f};
+  const int c1 = bchunk[b + 1];
+  for (int c0 = bchunk[b] + lane; c0 < c1; c0 += 32 * 4) {
+    float4 v[4];  // four partials in flight, added in order
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = c0 + 32 * u < c1 ? __ldcg(&part[(size_t)(c0 + 32 * u) * B.W + s])
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      df_add_df(a, dfl{v[u].x, v[u].y});
+      df_add_df(e, dfl{v[u].z, v[u].w});
+    }
+  }
+  a = warp_sum_df(a);
+  e = warp_sum_df(e);
+  if (lane == 0) bsum[q] = make_float4(a.hi, a.lo, e.hi, e.lo);
+}
+
 static __global__ void k_bin_bucket_sums(BinGeo B, const int32_t *bchunk, const float4 *part,
                                   float4 *bsum) {
-  const int lane = threadIdx.x & 31;
   const long long npair = (long long)B.NB * B.W;
   for (long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; q < npair;
-       q += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const int b = (int)(q / B.W), s = (int)(q - (long long)b * B.W);
-    dfl a{0.f, 0.f}, e{0.f, 0.f};
-    const int c1 = bchunk[b + 1];
-    for (int c0 = bchunk[b] + lane; c0 < c1; c0 += 32 * 4) {
-      float4 v[4];  // four partials in flight, added in order
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        v[u] = c0 + 32 * u < c1 ? __ldcg(&part[(size_t)(c0 + 32 * u) * B.W + s])
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        df_add_df(a, dfl{v[u].x, v[u].y});
-        df_add_df(e, dfl{v[u].z, v[u].w});
-      }
-    }
-    a = warp_sum_df(a);
-    e = warp_sum_df(e);
-    if (lane == 0) bsum[q] = make_float4(a.hi, a.lo, e.hi, e.lo);
-  }
+       q += ((long long)gridDim.x * blockDim.x) >> 5)
+    bucket_sum(B, bchunk, part, bsum, q);
 }
 
 // Sums of bin b's row by the lanes of one warp: for every slot s whose source

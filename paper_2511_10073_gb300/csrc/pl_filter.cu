@@ -16,8 +16,10 @@
 // D_vv < 0.
 // The epilogue also applies the taps (FP64 accumulation), the re-pinning of
 // fixed nodes, the relaxation of Algorithm 1 (FP64) and the clamping.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "pl_bins.cuh"
 #include "pl_internal.h"
@@ -427,55 +429,60 @@ __device__ __forceinline__ void row_groups(const int32_t *col, const void *w, ui
   }
 }
 
+// One pass of a warp over 32 / kRowLanes consecutive short rows from `base`.
 template <int WT, int MODE>
-__global__ void __launch_bounds__(kRowThreads, 6) k_spmm_rows(StepArgs A) {
+__device__ __forceinline__ void rows_group(const StepArgs &A, long long base) {
   const int64_t N = A.nrows;
-  constexpr int L = kRowLanes, RPW = 32 / L;
+  constexpr int L = kRowLanes;
   const int lane = threadIdx.x & 31, m = lane & (L - 1);
-  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
   const bool two = A.hrp != nullptr;
-  for (long long base = gw * RPW; base < N; base += nw * RPW) {
-    const long long v = base + lane / L;
-    bool live = false;
-    uint32_t sa = 0, sb = 0, ha = 0, hb = 0;
-    int hbv = -1;
-    if (v < N) {
-      const uint32_t f0 = A.srp[v], f1 = A.srp[v + 1];
-      if (MODE == MODE_HR && two && v < A.C) hbv = A.hbin[v];  // in flight with the row pointers
-      sa = f0 & kOffMask;
-      sb = f1 & kOffMask;
-      if (two) {
-        const uint32_t h0 = A.hrp[v];
-        ha = h0 & kOffMask;
-        hb = A.hrp[v + 1] & kOffMask;
-        live = !(h0 & kHubFlag);
-      } else {
-        live = !(f0 & kHubFlag);
-      }
-    }
-    float sx = 0.f, sy = 0.f;
-    if (live) {
-      row_groups<WT>(A.scol, A.sw, sa, sb, m, A.x, sx, sy);
-      if (two) {
-        row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
-        if (MODE == MODE_HR) slot_piece<WT, L>(A, v, hbv, m, sx, sy);
-      }
-    }
-#pragma unroll
-    for (int d = 1; d < L; d <<= 1) {
-      sx += __shfl_xor_sync(0xffffffffu, sx, d);
-      sy += __shfl_xor_sync(0xffffffffu, sy, d);
-    }
-    if (live) {
-      // lane m of the pair finishes coordinate m
-      const float av = A.a[v];
-      const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
-      const float xr = reinterpret_cast<const float *>(A.x)[2 * v + m];
-      const double acv = A.tap ? reinterpret_cast<const double *>(A.acc)[2 * v + m] : 0.0;
-      epilogue_c(A, v, A.nkind[v], m, acv, av * xr + bv * (m ? sy : sx));
+  const long long v = base + lane / L;
+  bool live = false;
+  uint32_t sa = 0, sb = 0, ha = 0, hb = 0;
+  int hbv = -1;
+  if (v < N) {
+    const uint32_t f0 = A.srp[v], f1 = A.srp[v + 1];
+    if (MODE == MODE_HR && two && v < A.C) hbv = A.hbin[v];  // in flight with the row pointers
+    sa = f0 & kOffMask;
+    sb = f1 & kOffMask;
+    if (two) {
+      const uint32_t h0 = A.hrp[v];
+      ha = h0 & kOffMask;
+      hb = A.hrp[v + 1] & kOffMask;
+      live = !(h0 & kHubFlag);
+    } else {
+      live = !(f0 & kHubFlag);
     }
   }
+  float sx = 0.f, sy = 0.f;
+  if (live) {
+    row_groups<WT>(A.scol, A.sw, sa, sb, m, A.x, sx, sy);
+    if (two) {
+      row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
+      if (MODE == MODE_HR) slot_piece<WT, L>(A, v, hbv, m, sx, sy);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < L; d <<= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, d);
+    sy += __shfl_xor_sync(0xffffffffu, sy, d);
+  }
+  if (live) {
+    // lane m of the pair finishes coordinate m
+    const float av = A.a[v];
+    const float bv = MODE == MODE_GIFT ? A.b[v] : A.binvf;
+    const float xr = reinterpret_cast<const float *>(A.x)[2 * v + m];
+    const double acv = A.tap ? reinterpret_cast<const double *>(A.acc)[2 * v + m] : 0.0;
+    epilogue_c(A, v, A.nkind[v], m, acv, av * xr + bv * (m ? sy : sx));
+  }
+}
+
+template <int WT, int MODE>
+__global__ void __launch_bounds__(kRowThreads, 6) k_spmm_rows(StepArgs A) {
+  constexpr int RPW = 32 / kRowLanes;
+  const long long gw = ((long long)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kRowThreads) >> 5;
+  for (long long base = gw * RPW; base < A.nrows; base += nw * RPW) rows_group<WT, MODE>(A, base);
 }
 
 // A GiFt chain pair over the short rows of the static matrix: the same
@@ -547,11 +554,12 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm_rows4(StepArgs A) {
 // chunks, then a fixed tree); one warp then does the combines in FP64, a lane
 // per row, so the FP64 work of kHubRows rows shares its instructions.
 constexpr int kHubRows = 8;
+// Row block `blk` (kHubRows rows) by a block of kHubRows warps; sums: the
+// block's shared scratch of kHubRows float4.
 template <int WT, int MODE>
-__global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
-  __shared__ float4 sums[kHubRows];
+__device__ __forceinline__ void hub_rows_block(const StepArgs &A, long long blk, float4 *sums) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long l = (long long)blockIdx.x * kHubRows + w;
+  const long long l = blk * kHubRows + w;
   if (l < A.nlong) {
     const int c0 = A.lchunk[l], nch = A.lchunk[l + 1] - c0;
     dfl px{0.f, 0.f}, py{0.f, 0.f};
@@ -591,7 +599,7 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
     if (lane == 0) sums[w] = make_float4(px.hi, px.lo, py.hi, py.lo);
   }
   __syncthreads();
-  const long long lr = (long long)blockIdx.x * kHubRows + lane;
+  const long long lr = blk * kHubRows + lane;
   if (w != 0 || lane >= kHubRows || lr >= A.nlong) return;
   const float4 q = sums[lane];
   const int64_t v = A.lrow[lr];
@@ -607,6 +615,12 @@ __global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
   const int64_t xi = MODE == MODE_GIFT ? v * A.xs : v;
   const float2 xv = A.x[xi];
   epilogue<double>(A, v, av * (double)xv.x + bv * tx, av * (double)xv.y + bv * ty, xi);
+}
+
+template <int WT, int MODE>
+__global__ void __launch_bounds__(kHubRows * 32) k_hub_rows(StepArgs A) {
+  __shared__ float4 sums[kHubRows];
+  hub_rows_block<WT, MODE>(A, blockIdx.x, sums);
 }
 
 // ------------------------------------------------------------- helpers
@@ -1228,6 +1242,237 @@ pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int
       if (k[i] == t) out[i] = y;
     x = y;
   }
+  return PL_OK;
+}
+
+}  // namespace pl
+
+// ------------------------------------------------ the batched product (NEXT-1)
+// One launch per kernel of a refinement product covers every design of a
+// batch: the designs' work units (short-row groups, hub chunks, bin chunks,
+// (bucket, slot) pairs, hub-row blocks) are concatenated, a block-diagonal
+// union of the designs' matrices with each design's own lambda_up and
+// per-node coefficients.  Unit u belongs to the design d with
+// pre[d] <= u < pre[d + 1]; a warp takes a run of consecutive units and
+// keeps its design's arguments in shared memory.  A design's units compute
+// exactly what its own launch computes, so every result keeps its bits.
+namespace pl {
+
+enum { BK_ROWS = 0, BK_HUB = 1, BK_BINC = 2, BK_PAIR = 3, BK_HROW = 4, BK_KINDS = 5 };
+
+__device__ __forceinline__ int unit_design(const long long *pre, int nd, long long u) {
+  int lo = 0, hi = nd - 1;  // the largest d with pre[d] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void warp_copy_args(StepArgs *dst, const StepArgs *src) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+  for (int i = lane; i < (int)(sizeof(StepArgs) / 4); i += 32) d[i] = s[i];
+  __syncwarp();
+}
+
+// Warp-level units of kind K: the warp's run [u, u1) of pre's units.
+template <int K, int WT, int MODE>
+__device__ __forceinline__ void batch_units(const StepArgs *As, const long long *pre, int nd,
+                                            long long per, StepArgs *sa) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long total = pre[nd];
+  long long u = gw * per;
+  const long long u1 = u + per < total ? u + per : total;
+  if (u >= u1) return;
+  int d = unit_design(pre, nd, u);
+  warp_copy_args(sa, &As[d]);
+  for (; u < u1; ++u) {
+    if (u >= pre[d + 1]) {
+      __syncwarp();
+      d = unit_design(pre, nd, u);
+      warp_copy_args(sa, &As[d]);
+    }
+    const StepArgs &A = *sa;
+    const long long k = u - pre[d];
+    if (K == BK_ROWS) {
+      rows_group<WT, MODE>(A, k * (32 / kRowLanes));
+    } else if (K == BK_HUB) {
+      warp_chunk<WT, MODE>(A, (int)k);
+    } else if (K == BK_BINC) {
+      if (k < A.bchunk[A.B.NB])
+        bin_chunk<WT, false>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart, k);
+    } else {
+      bucket_sum(A.B, A.bchunk, A.bpart, A.bpartb, k);
+    }
+  }
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kRowThreads, 5) k_rows_batch(const StepArgs *As,
+                                                              const long long *pre, int nd,
+                                                              long long per) {
+  __shared__ StepArgs sa[kRowThreads / 32];
+  batch_units<BK_ROWS, WT, MODE_HR>(As, pre, nd, per, &sa[threadIdx.x >> 5]);
+}
+
+template <int K, int WT>
+__global__ void __launch_bounds__(256) k_side_batch(const StepArgs *As, const long long *pre,
+                                                     int nd, long long per) {
+  __shared__ StepArgs sa[8];
+  batch_units<K, WT, MODE_HR>(As, pre, nd, per, &sa[threadIdx.x >> 5]);
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kHubRows * 32) k_hub_rows_batch(const StepArgs *As,
+                                                                  const long long *pre, int nd) {
+  __shared__ StepArgs sa;
+  __shared__ float4 sums[kHubRows];
+  const int d = unit_design(pre, nd, blockIdx.x);
+  {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&As[d]);
+    uint32_t *t = reinterpret_cast<uint32_t *>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / 4); i += blockDim.x) t[i] = s[i];
+  }
+  __syncthreads();
+  hub_rows_block<WT, MODE_HR>(sa, blockIdx.x - pre[d], sums);
+}
+
+size_t batch_ws_bytes(int nd, const pl_params *p) {
+  const int kmax = p->ntaps >= 1 ? p->tap_k[p->ntaps - 1] : 1;
+  return ((size_t)kmax * nd * sizeof(StepArgs) + 255) / 256 * 256 +
+         ((size_t)BK_KINDS * (nd + 1) * sizeof(long long) + 255) / 256 * 256 + 256;
+}
+
+// One round's filter (A4) for every design of a batch, each from in[d] into
+// out[d]: the plain filter's products and epilogues, one launch per kernel
+// and power over all designs (short rows on s, the hub and bin-row kernels on
+// sh, forked and joined with the first graph's events).  rows_ctas: CTAs per
+// SM of the short-row kernel.  ws: batch_ws_bytes(nd, p) device bytes, not in
+// use by another launch.  Does not synchronize.
+pl_status run_filter_batch(pl_graph *const *gs, int nd, const pl_params *p, const float *const *in,
+                           float *const *out, void *ws, size_t ws_bytes, int rows_ctas,
+                           cudaStream_t s, cudaStream_t sh) {
+  if (nd < 1) return PL_OK;
+  if (ws_bytes < batch_ws_bytes(nd, p)) {
+    set_error("batch workspace too small: need %zu bytes", batch_ws_bytes(nd, p));
+    return PL_ERR_WORKSPACE;
+  }
+  if (p->gamma == 0.0) {
+    for (int d = 0; d < nd; ++d) {
+      pl_graph *g = gs[d];
+      k_clamp<<<grid_for(g->N, 256), 256, 0, s>>>(g->N, P<uint8_t>(g->nkind), P<float2>(g->fixedp),
+                                                   P<float4>(g->bounds),
+                                                   reinterpret_cast<const float2 *>(in[d]),
+                                                   reinterpret_cast<float2 *>(out[d]), p->clamp);
+      note_launch();
+    }
+    TRY(cudaGetLastError());
+    return PL_OK;
+  }
+  const int kmax = p->tap_k[p->ntaps - 1];
+  const bool single = p->ntaps == 1 && p->tap_alpha[0] == 1.0;
+  const int wd = gs[0]->wdtype;
+  std::vector<StepArgs> hA((size_t)kmax * nd);
+  std::vector<long long> pre((size_t)BK_KINDS * (nd + 1), 0);
+  for (int d = 0; d < nd; ++d) {
+    pl_graph *g = gs[d];
+    if (g->wdtype != wd) {
+      set_error("designs of a batch need one weight type");
+      return PL_ERR_INVALID_ARG;
+    }
+    if (!single) TRY(cudaMemsetAsync(g->acc.p, 0, (size_t)g->N * 16, s));
+    StepArgs A{};
+    hr_args(g, A);
+    A.g0 = reinterpret_cast<const float2 *>(in[d]);
+    A.gnext = reinterpret_cast<float2 *>(out[d]);
+    A.gamma = p->gamma;
+    A.omg = 1.0 - p->gamma;
+    A.relax = 1;
+    A.clamp = p->clamp;
+    A.single = single ? 1 : 0;
+    A.pin = p->pin_every_step;
+    float2 *bufs[2] = {P<float2>(g->xa), P<float2>(g->xb)};
+    for (int t = 1; t <= kmax; ++t) {
+      StepArgs &B = hA[(size_t)(t - 1) * nd + d];
+      B = A;
+      B.x = t == 1 ? reinterpret_cast<const float2 *>(in[d]) : bufs[(t - 1) & 1];
+      B.y = bufs[t & 1];
+      B.tap = 0;
+      B.alpha = 0.0;
+      if (!single)
+        for (int j = 0; j < p->ntaps; ++j)
+          if (p->tap_k[j] == t) {
+            B.tap = 1;
+            B.alpha = p->tap_alpha[j];
+          }
+      B.fin = t == kmax;
+    }
+    const long long units[BK_KINDS] = {
+        (g->N + 32 / kRowLanes - 1) / (32 / kRowLanes), (long long)A.nchunks,
+        A.bpart ? (long long)g->nbc_max : 0LL, A.bpart ? (long long)g->NB * g->W : 0LL,
+        ((long long)A.nlong + kHubRows - 1) / kHubRows};
+    for (int k = 0; k < BK_KINDS; ++k) pre[(size_t)k * (nd + 1) + d + 1] = units[k];
+  }
+  for (int k = 0; k < BK_KINDS; ++k)
+    for (int d = 0; d < nd; ++d) pre[(size_t)k * (nd + 1) + d + 1] += pre[(size_t)k * (nd + 1) + d];
+  StepArgs *dA = static_cast<StepArgs *>(ws);
+  long long *dpre = reinterpret_cast<long long *>(
+      static_cast<char *>(ws) + ((size_t)kmax * nd * sizeof(StepArgs) + 255) / 256 * 256);
+  TRY(cudaMemcpyAsync(dA, hA.data(), hA.size() * sizeof(StepArgs), cudaMemcpyHostToDevice, s));
+  TRY(cudaMemcpyAsync(dpre, pre.data(), pre.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+  pl_graph *g0 = gs[0];
+  TRY(ensure_side(g0));  // its fork and join events
+  const int nsm = graph_nsm(g0);
+  auto total = [&](int k) { return pre[(size_t)k * (nd + 1) + nd]; };
+  auto per_for = [&](long long U, long long warps) {
+    return std::max(1LL, (U + warps - 1) / warps);
+  };
+  const int rc = std::min(std::max(rows_ctas, 1), 5);
+  const long long rows_per = per_for(total(BK_ROWS), (long long)rc * nsm * (kRowThreads / 32));
+  const int rows_grid = (int)std::max(1LL, (total(BK_ROWS) + rows_per * (kRowThreads / 32) - 1) /
+                                                 (rows_per * (kRowThreads / 32)));
+  long long side_per[BK_KINDS] = {0, 0, 0, 0, 0};
+  int side_grid[BK_KINDS] = {0, 0, 0, 0, 0};
+  for (int k = BK_HUB; k <= BK_PAIR; ++k) {
+    const long long U = total(k);
+    if (!U) continue;
+    side_per[k] = per_for(U, 8LL * nsm * 8);
+    side_grid[k] = (int)((U + side_per[k] * 8 - 1) / (side_per[k] * 8));
+  }
+  const int hrow_grid = (int)total(BK_HROW);
+  for (int t = 1; t <= kmax; ++t) {
+    const StepArgs *dAt = dA + (size_t)(t - 1) * nd;
+    TRY(cudaEventRecord(g0->ev_fork, s));
+    TRY(cudaStreamWaitEvent(sh, g0->ev_fork, 0));
+    if (side_grid[BK_HUB]) {
+      if (wd == PL_W_BF16) k_side_batch<BK_HUB, 1><<<side_grid[BK_HUB], 256, 0, sh>>>(dAt, dpre + 1 * (nd + 1), nd, side_per[BK_HUB]);
+      else k_side_batch<BK_HUB, 0><<<side_grid[BK_HUB], 256, 0, sh>>>(dAt, dpre + 1 * (nd + 1), nd, side_per[BK_HUB]);
+      note_launch();
+    }
+    if (side_grid[BK_BINC]) {
+      if (wd == PL_W_BF16) k_side_batch<BK_BINC, 1><<<side_grid[BK_BINC], 256, 0, sh>>>(dAt, dpre + 2 * (nd + 1), nd, side_per[BK_BINC]);
+      else k_side_batch<BK_BINC, 0><<<side_grid[BK_BINC], 256, 0, sh>>>(dAt, dpre + 2 * (nd + 1), nd, side_per[BK_BINC]);
+      note_launch();
+    }
+    if (side_grid[BK_PAIR]) {
+      k_side_batch<BK_PAIR, 0><<<side_grid[BK_PAIR], 256, 0, sh>>>(dAt, dpre + 3 * (nd + 1), nd, side_per[BK_PAIR]);
+      note_launch();
+    }
+    if (hrow_grid) {
+      if (wd == PL_W_BF16) k_hub_rows_batch<1><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 4 * (nd + 1), nd);
+      else k_hub_rows_batch<0><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 4 * (nd + 1), nd);
+      note_launch();
+    }
+    TRY(cudaEventRecord(g0->ev_join, sh));
+    if (wd == PL_W_BF16) k_rows_batch<1><<<rows_grid, kRowThreads, 0, s>>>(dAt, dpre, nd, rows_per);
+    else k_rows_batch<0><<<rows_grid, kRowThreads, 0, s>>>(dAt, dpre, nd, rows_per);
+    note_launch();
+    TRY(cudaStreamWaitEvent(s, g0->ev_join, 0));
+  }
+  TRY(cudaGetLastError());
   return PL_OK;
 }
 

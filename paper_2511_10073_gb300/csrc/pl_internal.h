@@ -204,6 +204,12 @@ pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int
                      const float2 *out[3], cudaStream_t s);
 pl_status clamp_nodes(pl_graph *g, const pl_params *p, const float *in, float *out, cudaStream_t s);
 pl_status check_model(const pl_learned *m);
+pl_status check_params(const pl_params *p);
+pl_status same_layout(const pl_graph *g, const pl_params *p);
+size_t batch_ws_bytes(int nd, const pl_params *p);
+pl_status run_filter_batch(pl_graph *const *gs, int nd, const pl_params *p, const float *const *in,
+                           float *const *out, void *ws, size_t ws_bytes, int rows_ctas,
+                           cudaStream_t s, cudaStream_t sh);
 pl_status run_learned(pl_graph *g, const pl_params *p, const pl_learned *m, int32_t round,
                       const float *in, float *out, cudaStream_t s);
 pl_status read_status(pl_graph *g, cudaStream_t s);

@@ -27,13 +27,22 @@ def test_batch_equals_single_runs():
         pl.pl_filter_init(g, prm, sd, None, o)
         single.append(o)
     torch.cuda.synchronize()
-    for ns in (1, 3):
+    # both forms, several stream counts and short-row CTA counts: the same bits
+    for union, ns, rc in ((0, 1, 5), (0, 3, 5), (1, 1, 5), (1, 3, 3), (1, 4, 1)):
         outs = [torch.full_like(o, float("nan")) for o in single]
         streams = [torch.cuda.Stream() for _ in range(ns)]
-        pl.pl_filter_init_batch(graphs, prm, seeds, outs, streams)
+        pl.pl_filter_init_batch(graphs, prm, seeds, outs, streams,
+                                pl.batch_opts(union_products=union, rows_ctas_per_sm=rc))
         torch.cuda.synchronize()
         for a, b in zip(single, outs):
-            assert torch.equal(a, b)
+            assert torch.equal(a, b), (union, ns, rc)
+    # the autotuner runs every candidate and leaves the same bits
+    outs = [torch.full_like(o, float("nan")) for o in single]
+    best, ms = pl.pl_batch_autotune(graphs, prm, seeds, outs, [torch.cuda.Stream() for _ in range(4)])
+    torch.cuda.synchronize()
+    assert ms > 0 and best.streams in (1, 2, 4) and best.union_products in (0, 1)
+    for a, b in zip(single, outs):
+        assert torch.equal(a, b)
     # the smallest design against the oracle
     i = int(np.argmin([nl.num_cells for nl in nls]))
     o = oracle.Oracle(nls[i], nbx=16, nby=16, wdtype=oracle.W_BF16, ntaps=3, tap_k=(2, 4, 8, 0),
@@ -52,7 +61,15 @@ def test_batch_reports_the_failing_design():
     prm = pl.params(nbx=4, nby=4)
     g = pl.pl_build_graph(pl.DeviceNetlist(nl), prm)
     out = torch.empty(nl.num_cells * 2, dtype=torch.float32, device="cuda")
-    with pytest.raises(pl.PlError) as e:
+    with pytest.raises(pl.PlError) as e:  # per-design form: the failing design is named
+        pl.pl_filter_init_batch([g, g], pl.params(nbx=8, nby=4), [1, 2], [out, out],
+                                [torch.cuda.Stream()], pl.batch_opts(union_products=0))
+    assert e.value.code == pl.PL_ERR_INVALID_ARG and "design" in str(e.value)
+    with pytest.raises(pl.PlError) as e:  # union form: checked before any work
         pl.pl_filter_init_batch([g, g], pl.params(nbx=8, nby=4), [1, 2], [out, out],
                                 [torch.cuda.Stream()])
-    assert e.value.code == pl.PL_ERR_INVALID_ARG and "design" in str(e.value)
+    assert e.value.code == pl.PL_ERR_INVALID_ARG
+    with pytest.raises(pl.PlError) as e:  # union form: workspace too small
+        pl.pl_filter_init_batch([g, g], prm, [1, 2], [out, out], [torch.cuda.Stream()],
+                                ws=torch.empty(256, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == pl.PL_ERR_WORKSPACE
