@@ -49,9 +49,10 @@ __device__ __forceinline__ float bw_load(const void *bw, size_t k) {
 // A warp per chunk: lane j takes the chunk's cells j, j + 32, ... (all their
 // loads in flight together); per slot, each lane adds its cells in order and
 // a fixed tree adds the lanes, so every partial is a fixed function of the
-// inputs.  bwq: the window blocks in bucket-list order (the block of the cell
-// at list position k at k W), read as consecutive blocks; x: coordinates of
-// every node (the cells' ones are gathered).  The chunk count is bchunk[NB];
+// inputs.  bwq: the chunks' window blocks, slot-major within a chunk (slot t
+// of the chunk's i-th cell at (c W + t) kBinChunk + i), so each slot is read
+// as consecutive weights; x: coordinates of every node (the cells' ones are
+// gathered).  The chunk count is bchunk[NB];
 // the grid may be any size.
 template <int WT, bool DEG>
 __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk,
@@ -77,7 +78,8 @@ __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk
   for (int t = 0; t < B.W; ++t) {
     float w[kBinPer];
 #pragma unroll
-    for (int u = 0; u < kBinPer; ++u) w[u] = cv[u] ? bw_load<WT>(bwq, (size_t)kp[u] * B.W + t) : 0.f;
+    for (int u = 0; u < kBinPer; ++u)
+      w[u] = cv[u] ? bw_load<WT>(bwq, ((size_t)c * B.W + t) * kBinChunk + lane + 32 * u) : 0.f;
     dfl a{0.f, 0.f}, e{0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < kBinPer; ++u) {

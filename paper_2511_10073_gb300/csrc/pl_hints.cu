@@ -823,16 +823,30 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
   if (lane == 0 && hints) atomicAdd(counts + 1, hints);
 }
 
-// The window blocks in bucket-list order: a thread per list position copies
-// the block of the cell there (its W weights, one gathered block) to the
-// position's place.  Positions of non-hint cells copy blocks nobody reads.
+// The window blocks of the bin rows' chunks, slot-major within a chunk: the
+// weight of slot t of the i-th hint cell of chunk c (the cell at list
+// position boff[2b] + (c - bchunk[b]) kBinChunk + i of its bin b) goes to
+// out[(c W + t) kBinChunk + i], so the bin rows read each slot of a chunk as
+// consecutive weights.  A thread per (chunk, cell) gathers the cell's block
+// and writes its W weights; places past a bucket's last hint cell get 0.
 template <typename T>
-__global__ void k_blocks_to_lists(long long n, int W, const uint32_t *blist, const T *blk, T *out) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const T *src = blk + (size_t)blist[k] * W;
-    T *dst = out + (size_t)k * W;
-    for (int s = 0; s < W; ++s) dst[s] = src[s];
+__global__ void k_blocks_to_chunks(long long nthreads, int W, const int32_t *bchunk, int NB,
+                                   const int32_t *cown, const int64_t *boff,
+                                   const uint32_t *blist, const T *blk, T *out) {
+  const int nchunk = bchunk[NB];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nthreads;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = q / kBinChunk;
+    if (c >= nchunk) break;
+    const int i = (int)(q - c * kBinChunk), b = cown[c];
+    const long long k = boff[2 * b] + (long long)(c - bchunk[b]) * kBinChunk + i;
+    T *dst = out + (size_t)c * W * kBinChunk + i;
+    if (k < boff[2 * b + 1]) {
+      const T *src = blk + (size_t)blist[k] * W;
+      for (int t = 0; t < W; ++t) dst[(size_t)t * kBinChunk] = src[t];
+    } else {
+      for (int t = 0; t < W; ++t) dst[(size_t)t * kBinChunk] = (T)0;
+    }
   }
 }
 
@@ -1345,7 +1359,6 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   const int W = (2 * g->hx + 1) * (2 * g->hy + 1);
   g->W = W;
   TRY(ensure(g->hbw, (size_t)C * W * m.wbytes + 64));
-  TRY(ensure(g->hbwq, (size_t)nbl * W * m.wbytes + 64));
   TRY(ensure(g->hbin, (size_t)C * 4 + 16));
   unsigned long long *counts = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 3);
   TRY(cudaMemsetAsync(counts, 0, 16, s));
@@ -1358,14 +1371,6 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       W, cmem_ok ? P<int32_t>(g->cmem) : nullptr, P<float4>(g->mgeo), P<int32_t>(m.col), m.w.p,
       g->hbw.p, P<int32_t>(g->hbin), P<dfl>(m.dsum), P<dfl>(m.psum), P<uint64_t>(g->mac_base),
       counts);
-  note_launch();
-  // the bucket-order copy of the window blocks (read in list order by the bin rows)
-  if (g->wdtype == PL_W_BF16)
-    k_blocks_to_lists<uint16_t><<<grid_for(nbl, 256), 256, 0, s>>>(
-        nbl, W, P<uint32_t>(g->blist), P<uint16_t>(g->hbw), P<uint16_t>(g->hbwq));
-  else
-    k_blocks_to_lists<uint32_t><<<grid_for(nbl, 256), 256, 0, s>>>(
-        nbl, W, P<uint32_t>(g->blist), P<uint32_t>(g->hbw), P<uint32_t>(g->hbwq));
   note_launch();
   // H10: bin rows (degree partials of the window blocks, chunk by chunk) and
   // macro rows (their entries and degree partials)
@@ -1380,6 +1385,20 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->cown, (size_t)nbc_max * 4 + 256));
   k_chunk_bins<<<grid_for(NB, 128), 128, 0, s>>>(NB, P<int32_t>(g->bchunk), P<int32_t>(g->cown));
   note_launch();
+  // the chunks' copy of the window blocks (read slot by slot by the bin rows)
+  TRY(ensure(g->hbwq, (size_t)nbc_max * kBinChunk * W * m.wbytes + 64));
+  {
+    const long long nth = nbc_max * kBinChunk;
+    if (g->wdtype == PL_W_BF16)
+      k_blocks_to_chunks<uint16_t><<<grid_for(nth, 256), 256, 0, s>>>(
+          nth, W, P<int32_t>(g->bchunk), NB, P<int32_t>(g->cown), P<int64_t>(g->boff),
+          P<uint32_t>(g->blist), P<uint16_t>(g->hbw), P<uint16_t>(g->hbwq));
+    else
+      k_blocks_to_chunks<uint32_t><<<grid_for(nth, 256), 256, 0, s>>>(
+          nth, W, P<int32_t>(g->bchunk), NB, P<int32_t>(g->cown), P<int64_t>(g->boff),
+          P<uint32_t>(g->blist), P<uint32_t>(g->hbw), P<uint32_t>(g->hbwq));
+    note_launch();
+  }
   TRY(ensure(g->bdeg, (size_t)nbc_max * W * 16 + 256));
   TRY(ensure(g->bpart, (size_t)nbc_max * W * 16 + 256));
   const long long bwant = (nbc_max + kBinThreads / 32 - 1) / (kBinThreads / 32);

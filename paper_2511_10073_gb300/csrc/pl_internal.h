@@ -117,8 +117,8 @@ struct pl_graph {
   int64_t nhint = 0;   // hint cells (movable, baseWeight > 0)
   long long nbc_max = 0;  // bin-row chunks at most (grid of the chunk kernels)
   pl::Buf hbw;         // storage type [C * W] window-block weights of hint cells
-  pl::Buf hbwq;        // storage type [movable cells * W] the same blocks at each cell's
-                       // place in the bucket lists (read in list order by the bin rows)
+  pl::Buf hbwq;        // storage type [chunks * W * kBinChunk] the blocks of each bin-row
+                       // chunk's hint cells, slot-major (read slot by slot by the bin rows)
   pl::Buf hbin;        // int32 [C] bin of a hint cell, -1 for other cells
   pl::Buf bchunk;      // int32 [NB + 1] first chunk of each bin's hint bucket
   pl::Buf cown;        // int32 [chunks] bin of each chunk

@@ -161,9 +161,6 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, float *v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) {
-  return (uint32_t)lo | ((uint32_t)hi << 16);
-}
 // Two floats rounded to BF16 (nearest even) in one conversion: lo in the low
 // half; with RELU, negative values become 0.
 template <bool RELU>

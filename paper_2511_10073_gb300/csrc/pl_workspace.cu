@@ -185,7 +185,7 @@ double workspace_bound(const pl_netlist *nl, const pl_params *p) {
   h.add((nchunk_h + 1) * 48);
   h.add(C * 8 + 16);                 // macro entry offsets
   h.add(C * W * sw + 64);            // window blocks, cell order
-  h.add(nmov * W * sw + 64);         // window blocks, bucket order
+  h.add((std::floor(nmov / kBinChunk) + NB + 1) * kBinChunk * W * sw + 64);  // chunks' window blocks
   h.add(C * 4 + 16);
   h.add((NB + 1) * 4 + 256);
   h.add((NB + 1) * 4 + 256);
