@@ -838,8 +838,9 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
       // bin rows: chunk partials of the window blocks times the cells' x
       const long long bwant = (g->nbc_max + kBinThreads / 32 - 1) / (kBinThreads / 32);
       const int bgrid = (int)(bwant < 152LL * 16 ? bwant : 152LL * 16);
-      if (wi) k_bin_partials<1, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
-      else k_bin_partials<0, false><<<bgrid, kBinThreads, 0, sh>>>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart);
+      e = launch_bin_partials<false>(wi ? PL_W_BF16 : PL_W_FP32, bgrid, sh, A.B, A.bchunk, A.cown,
+                                     A.boff, A.blist, A.hbwq, A.x, A.bpart);
+      if (e != cudaSuccess) return e;
       k_bin_bucket_sums<<<grid_for((long long)A.B.NB * A.B.W * 32, 256), 256, 0, sh>>>(
           A.B, A.bchunk, A.bpart, A.bpartb);
       note_launch();

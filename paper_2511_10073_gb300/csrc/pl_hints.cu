@@ -1403,14 +1403,9 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->bpart, (size_t)nbc_max * W * 16 + 256));
   const long long bwant = (nbc_max + kBinThreads / 32 - 1) / (kBinThreads / 32);
   const int bgrid = (int)(bwant < 152 * 16 ? bwant : 152 * 16);
-  if (g->wdtype == PL_W_BF16)
-    k_bin_partials<1, true><<<bgrid, kBinThreads, 0, s>>>(B, P<int32_t>(g->bchunk), P<int32_t>(g->cown), P<int64_t>(g->boff),
-                                                         P<uint32_t>(g->blist), g->hbwq.p, nullptr,
-                                                         P<float4>(g->bdeg));
-  else
-    k_bin_partials<0, true><<<bgrid, kBinThreads, 0, s>>>(B, P<int32_t>(g->bchunk), P<int32_t>(g->cown), P<int64_t>(g->boff),
-                                                         P<uint32_t>(g->blist), g->hbwq.p, nullptr,
-                                                         P<float4>(g->bdeg));
+  TRY(launch_bin_partials<true>(g->wdtype, bgrid, s, B, P<int32_t>(g->bchunk), P<int32_t>(g->cown),
+                                 P<int64_t>(g->boff), P<uint32_t>(g->blist), g->hbwq.p, nullptr,
+                                 P<float4>(g->bdeg)));
   note_launch();
   // degree partials per (bucket, slot)
   TRY(ensure(g->bdegb, (size_t)NB * W * 16 + 256));
