@@ -229,10 +229,20 @@ static __global__ void k_bin_chunk_count(int NB, const int64_t *boff, int32_t *c
   }
 }
 
-// Bucket of each chunk.
-static __global__ void k_chunk_bins(int NB, const int32_t *bchunk, int32_t *cown) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x)
-    for (int c = bchunk[b]; c < bchunk[b + 1]; ++c) cown[c] = b;
+// Bucket of each chunk: a thread per chunk finds the last bucket whose first
+// chunk is at or before it (bchunk is nondecreasing).
+static __global__ void k_chunk_bins(int NB, long long ncmax, const int32_t *bchunk, int32_t *cown) {
+  const int nchunk = bchunk[NB];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncmax && c < nchunk;
+       c += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = NB - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bchunk[mid] <= c) lo = mid;
+      else hi = mid - 1;
+    }
+    cown[c] = lo;
+  }
 }
 
 }  // namespace pl

@@ -1335,7 +1335,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       note_launch();
     }
   }
-  k_dens_final<<<grid_for(NB, 128), 128, 0, s2>>>(
+  k_dens_final<<<grid_for(NB, 32), 32, 0, s2>>>(  // a warp per 32 bins: spread over the SMs
       G, nlev, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch), lv,
       P<double>(g->amac), g->abin, p->capacity, p->mu, P<double>(g->Db), P<double>(g->Cb),
       P<double>(g->phi), phif);
@@ -1383,7 +1383,7 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   const long long nbc_max = nbl / kBinChunk + NB + 1;  // chunks at most (the grid size)
   g->nbc_max = nbc_max;
   TRY(ensure(g->cown, (size_t)nbc_max * 4 + 256));
-  k_chunk_bins<<<grid_for(NB, 128), 128, 0, s>>>(NB, P<int32_t>(g->bchunk), P<int32_t>(g->cown));
+  k_chunk_bins<<<grid_for(nbc_max, 256), 256, 0, s>>>(NB, nbc_max, P<int32_t>(g->bchunk), P<int32_t>(g->cown));
   note_launch();
   // the chunks' copy of the window blocks (read slot by slot by the bin rows)
   TRY(ensure(g->hbwq, (size_t)nbc_max * kBinChunk * W * m.wbytes + 64));
