@@ -54,16 +54,12 @@ __device__ __forceinline__ float bw_load(const void *bw, size_t k) {
 // as consecutive weights; x: coordinates of every node (the cells' ones are
 // gathered).  The chunk count is bchunk[NB];
 // the grid may be any size.
-// Chunk c's partials.  With wsm (the warp's shared memory, at least
-// W kBinChunk weights), the chunk's weights are first copied there with
-// 16-byte loads, all in flight together, so the slots read no global memory;
-// without it, each slot's weights are loaded from global memory in turn.
+// Chunk c's partials (a warp).
 template <int WT, bool DEG>
 __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk,
                                           const int32_t *cown, const int64_t *boff,
                                           const uint32_t *blist, const void *bwq,
-                                          const float2 *x, float4 *part, long long c,
-                                          void *wsm = nullptr) {
+                                          const float2 *x, float4 *part, long long c) {
   const int lane = threadIdx.x & 31;
   const int b = cown[c];
   const long long k0 = boff[2 * b] + (long long)(c - bchunk[b]) * kBinChunk;
@@ -77,25 +73,15 @@ __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk
     cv[u] = k0 + lane + 32LL * u < k1;
     ci[u] = (!DEG && cv[u]) ? blist[kp[u]] : 0u;
   }
-  const void *wsrc = bwq;
-  size_t wbase = (size_t)c * B.W * kBinChunk;
-  if (wsm) {
-    const int nvec = B.W * kBinChunk * (WT == 0 ? 4 : 2) / 16;
-    const uint4 *src = reinterpret_cast<const uint4 *>(bwq) + (size_t)c * nvec;
-    uint4 *dst = reinterpret_cast<uint4 *>(wsm);
-    for (int i = lane; i < nvec; i += 32) dst[i] = __ldcs(src + i);
-    __syncwarp();
-    wsrc = wsm;
-    wbase = 0;
-  }
   float2 xi[kBinPer];
 #pragma unroll
   for (int u = 0; u < kBinPer; ++u) xi[u] = (!DEG && cv[u]) ? x[ci[u]] : make_float2(0.f, 0.f);
+  const size_t wbase = (size_t)c * B.W * kBinChunk;
   for (int t = 0; t < B.W; ++t) {
     float w[kBinPer];
 #pragma unroll
     for (int u = 0; u < kBinPer; ++u)
-      w[u] = cv[u] ? bw_load<WT>(wsrc, wbase + (size_t)t * kBinChunk + lane + 32 * u) : 0.f;
+      w[u] = cv[u] ? bw_load<WT>(bwq, wbase + (size_t)t * kBinChunk + lane + 32 * u) : 0.f;
     dfl a{0.f, 0.f}, e{0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < kBinPer; ++u) {
@@ -111,59 +97,28 @@ __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk
     e = warp_sum_df(e);
     if (lane == 0) part[(size_t)c * B.W + t] = make_float4(a.hi, a.lo, e.hi, e.lo);
   }
-  if (wsm) __syncwarp();  // the next chunk overwrites the staged weights
 }
 
-// Shared memory of the staged k_bin_partials: a chunk's weights per warp.
-inline size_t bin_stage_bytes(int W, int wt) {
-  return (size_t)(kBinThreads / 32) * W * kBinChunk * (wt == 0 ? 4 : 2);
-}
-constexpr size_t kBinStageMax = 100 * 1024;  // beyond this the slots load from global memory
-
-template <int WT, bool DEG, bool STAGE>
+template <int WT, bool DEG>
 __global__ void __launch_bounds__(kBinThreads, 4) k_bin_partials(BinGeo B, const int32_t *bchunk,
                                                               const int32_t *cown,
                                                               const int64_t *boff,
                                                               const uint32_t *blist,
                                                               const void *bwq, const float2 *x,
                                                               float4 *part) {
-  extern __shared__ __align__(16) unsigned char bin_smem[];
-  void *wsm = STAGE ? bin_smem + (size_t)(threadIdx.x >> 5) * B.W * kBinChunk * (WT == 0 ? 4 : 2)
-                    : nullptr;
   const int nchunk = bchunk[B.NB];
   for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nchunk;
        c += ((long long)gridDim.x * blockDim.x) >> 5)
-    bin_chunk<WT, DEG>(B, bchunk, cown, boff, blist, bwq, x, part, c, wsm);
+    bin_chunk<WT, DEG>(B, bchunk, cown, boff, blist, bwq, x, part, c);
 }
 
-// Launches k_bin_partials, staged in shared memory when the chunk's weights
-// fit (the same sums either way).
 template <bool DEG>
 inline cudaError_t launch_bin_partials(int wt, int grid, cudaStream_t s, const BinGeo &B,
                                        const int32_t *bchunk, const int32_t *cown,
                                        const int64_t *boff, const uint32_t *blist,
                                        const void *bwq, const float2 *x, float4 *part) {
-  const size_t sm = bin_stage_bytes(B.W, wt == 2 ? 1 : 0);
-  const bool stage = sm <= kBinStageMax;
-  if (wt == 2) {
-    if (stage) {
-      cudaError_t e = cudaFuncSetAttribute(k_bin_partials<1, DEG, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_bin_partials<1, DEG, true><<<grid, kBinThreads, sm, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
-    } else {
-      k_bin_partials<1, DEG, false><<<grid, kBinThreads, 0, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
-    }
-  } else {
-    if (stage) {
-      cudaError_t e = cudaFuncSetAttribute(k_bin_partials<0, DEG, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      k_bin_partials<0, DEG, true><<<grid, kBinThreads, sm, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
-    } else {
-      k_bin_partials<0, DEG, false><<<grid, kBinThreads, 0, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
-    }
-  }
+  if (wt == 2) k_bin_partials<1, DEG><<<grid, kBinThreads, 0, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
+  else k_bin_partials<0, DEG><<<grid, kBinThreads, 0, s>>>(B, bchunk, cown, boff, blist, bwq, x, part);
   return cudaGetLastError();
 }
 

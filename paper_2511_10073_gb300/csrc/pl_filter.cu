@@ -100,6 +100,10 @@ struct StepArgs {
   const uint32_t *blist;
   float4 *bpart;
   float4 *bpartb;  // bpart summed per (bucket, slot)
+  // windows of at most kSlotUnroll * kRowLanes slots: lane m's slot
+  // m + u kRowLanes is at bin offset soff[m][u] from the cell's bin
+  int sfast;
+  int soff[2][5];
 };
 
 // Epilogue of node v with its kind kd and (tap steps) accumulator ac loaded
@@ -342,6 +346,7 @@ __device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uin
 // 0, so their bin index is clamped into the grid instead of tested (a finite
 // coordinate times 0).  The weights are loaded before their gathers of x.
 constexpr int kSlotUnroll = 5;  // slots a lane loads at once (a 3 x 3 window over 2 lanes)
+static_assert(kRowLanes == 2 && kSlotUnroll == 5, "StepArgs::soff is [kRowLanes][kSlotUnroll]");
 template <int WT, int L>
 __device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int hb, int m, float &sx,
                                            float &sy) {
@@ -372,6 +377,39 @@ __device__ __forceinline__ void slot_piece(const StepArgs &A, long long v, int h
         sx = fmaf(wv[u], xv.x, sx);
         sy = fmaf(wv[u], xv.y, sy);
       }
+    }
+  }
+}
+
+// The same slots as slot_piece when the window has at most
+// kSlotUnroll * kRowLanes of them (the 3 x 3 window of 32 x 32 bins has 9):
+// lane m's slots m + u kRowLanes have the bin offsets A.soff[m][u] (dy nbx +
+// dx, computed on the host), and the bin of a slot is the cell's bin plus its
+// offset, clamped into the grid as a linear index (slots outside the grid
+// hold weight 0, so any bin there adds 0).
+template <int WT>
+__device__ __forceinline__ void slot_piece_fast(const StepArgs &A, long long v, int hb, int m,
+                                                float &sx, float &sy) {
+  if (hb < 0) return;
+  const float *wf = reinterpret_cast<const float *>(A.hbw) + (size_t)v * A.B.W;
+  const unsigned short *wh = reinterpret_cast<const unsigned short *>(A.hbw) + (size_t)v * A.B.W;
+  const float2 *xb = A.x + A.bn0;
+  const int nb1 = A.B.NB - 1;
+  float wv[kSlotUnroll];
+  int cb[kSlotUnroll];
+#pragma unroll
+  for (int u = 0; u < kSlotUnroll; ++u) {
+    const int sl = m + u * kRowLanes;
+    const bool on = sl < A.B.W;
+    wv[u] = on ? (WT == 0 ? __ldcs(wf + sl) : __uint_as_float((uint32_t)__ldcs(wh + sl) << 16)) : 0.f;
+    cb[u] = on ? min(max(hb + (m ? A.soff[1][u] : A.soff[0][u]), 0), nb1) : -1;
+  }
+#pragma unroll
+  for (int u = 0; u < kSlotUnroll; ++u) {
+    if (cb[u] >= 0) {
+      const float2 xv = __ldg(xb + cb[u]);
+      sx = fmaf(wv[u], xv.x, sx);
+      sy = fmaf(wv[u], xv.y, sy);
     }
   }
 }
@@ -459,7 +497,10 @@ __device__ __forceinline__ void rows_group(const StepArgs &A, long long base) {
     row_groups<WT>(A.scol, A.sw, sa, sb, m, A.x, sx, sy);
     if (two) {
       row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
-      if (MODE == MODE_HR) slot_piece<WT, L>(A, v, hbv, m, sx, sy);
+      if (MODE == MODE_HR) {
+        if (A.sfast) slot_piece_fast<WT>(A, v, hbv, m, sx, sy);
+        else slot_piece<WT, L>(A, v, hbv, m, sx, sy);
+      }
     }
   }
 #pragma unroll
@@ -1148,6 +1189,12 @@ static void hr_args(pl_graph *g, StepArgs &A) {
   A.B.hy = g->hy;
   A.B.W = g->W;
   A.B.NB = g->NB;
+  A.sfast = g->W <= kSlotUnroll * kRowLanes ? 1 : 0;
+  for (int mm = 0; mm < kRowLanes; ++mm)
+    for (int u = 0; u < kSlotUnroll; ++u) {
+      const int sl = mm + u * kRowLanes, wx = 2 * g->hx + 1;
+      A.soff[mm][u] = (sl / wx - g->hy) * g->nbx + (sl % wx - g->hx);
+    }
   A.bchunk = P<int32_t>(g->bchunk);
   A.cown = P<int32_t>(g->cown);
   A.boff = P<int64_t>(g->boff);

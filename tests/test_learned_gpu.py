@@ -160,7 +160,11 @@ def test_collect_matches_oracle(cfg, seed, kw, k, rnd):
     ("tiny", 2, dict(nbx=16, nby=16), (0, 2, 4), 1),
     ("tiny", 5, dict(nbx=16, nby=16, wdtype=2, gamma=0.7), (0, 1, 2), 0),
     ("medium", 1, dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
-                       tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0)), (0, 2, 4), 2)])
+                       tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0)), (0, 2, 4), 2),
+    # the 2.2M-cell workload with a committed model's parameters and powers
+    pytest.param("large", 1, dict(nbx=32, nby=32, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+                                  tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0), pin_every_step=1),
+                 (0, 1, 2), 1, marks=pytest.mark.slow)])
 def test_learned_round_matches_oracle(cfg, seed, kw, k, rnd):
     m = pl()
     s = Round(cfg, seed, **kw)
