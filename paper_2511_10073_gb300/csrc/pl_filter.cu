@@ -309,28 +309,33 @@ __global__ void __launch_bounds__(256) k_spmm_hub(StepArgs A) {
 
 // Short rows, row-split: a group of kRowLanes lanes per row reads the row's
 // st and hm pieces straight from global memory (lane m takes entries m,
-// m + kRowLanes, ...; kRowUnroll index and weight loads in flight, then their
+// m + kRowLanes, ...; several index and weight loads in flight, then their
 // gathers of x), a butterfly over the group sums them, and the group's first
 // lane applies the epilogue.  Hub rows are skipped (their own launches).
 constexpr int kRowLanes = 2;  // the epilogue takes one coordinate per lane
 static_assert(kRowLanes == 2, "the row epilogue splits x and y over the row's two lanes");
-constexpr int kRowUnroll = 8;
+constexpr int kRowUnroll = 8;  // entries per lane and pass of a GiFt pair's static row
+// A short row's hm piece holds only its macro entries (the bin hints have no
+// stored columns), in nearly every warp pass but rarely more than one per
+// row: kHmUnroll entries per lane and pass keep that piece to a few
+// instructions.
+constexpr int kHmUnroll = 2;
 constexpr int kRowThreads = 256;
 
-template <int WT, int L>
+template <int WT, int L, int U>
 __device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uint32_t k,
                                           uint32_t e, const float2 *x, float &sx, float &sy) {
-  for (; k < e; k += kRowUnroll * L) {
-    int c[kRowUnroll];
-    float wv[kRowUnroll];
+  for (; k < e; k += U * L) {
+    int c[U];
+    float wv[U];
 #pragma unroll
-    for (int u = 0; u < kRowUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint32_t kk = k + u * L;
       c[u] = kk < e ? __ldcs(col + kk) : -1;
       wv[u] = kk < e ? wload<WT>(w, kk) : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < kRowUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       if (c[u] >= 0) {
         const float2 xv = __ldg(x + c[u]);
         sx = fmaf(wv[u], xv.x, sx);
@@ -496,7 +501,7 @@ __device__ __forceinline__ void rows_group(const StepArgs &A, long long base) {
   if (live) {
     row_groups<WT>(A.scol, A.sw, sa, sb, m, A.x, sx, sy);
     if (two) {
-      row_piece<WT, L>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
+      row_piece<WT, L, kHmUnroll>(A.hcol, A.hw, ha + m, hb, A.x, sx, sy);
       if (MODE == MODE_HR) {
         if (A.sfast) slot_piece_fast<WT>(A, v, hbv, m, sx, sy);
         else slot_piece<WT, L>(A, v, hbv, m, sx, sy);
