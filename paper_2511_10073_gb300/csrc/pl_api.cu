@@ -134,8 +134,13 @@ static void destroy(pl_graph *g) {
     cudaStreamSynchronize(g->side);
     cudaStreamDestroy(g->side);
   }
+  if (g->side2) {
+    cudaStreamSynchronize(g->side2);
+    cudaStreamDestroy(g->side2);
+  }
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->ev_join2) cudaEventDestroy(g->ev_join2);
   delete g;  // its device memory is the caller's workspace
 }
 

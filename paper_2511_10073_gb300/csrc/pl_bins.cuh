@@ -54,6 +54,43 @@ __device__ __forceinline__ float bw_load(const void *bw, size_t k) {
 // as consecutive weights; x: coordinates of every node (the cells' ones are
 // gathered).  The chunk count is bchunk[NB];
 // the grid may be any size.
+// Slots T0 .. T0 + NT - 1 of chunk c with the partials of all of them
+// reduced over the warp at once (warp_rs_df): value 2 t of the slot group is
+// the first double-float of slot T0 + t, value 2 t + 1 the second.  The same
+// sums, bit for bit, as a warp_sum_df per slot and value.
+template <int WT, bool DEG, int T0, int NT>
+__device__ __forceinline__ void bin_slot_group(const void *bwq, size_t wbase, const bool *cv,
+                                               const float2 *xi, float4 *part, size_t pbase) {
+  const int lane = threadIdx.x & 31;
+  dfl v[2 * NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    float w[kBinPer];
+#pragma unroll
+    for (int u = 0; u < kBinPer; ++u)
+      w[u] = cv[u] ? bw_load<WT>(bwq, wbase + (size_t)(T0 + t) * kBinChunk + lane + 32 * u) : 0.f;
+    dfl a{0.f, 0.f}, e{0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kBinPer; ++u) {
+      if (DEG) {
+        df_add(a, w[u]);
+        if (w[u] > 0.f) df_add(e, w[u]);
+      } else {
+        df_add_prod(a, w[u], xi[u].x);
+        df_add_prod(e, w[u], xi[u].y);
+      }
+    }
+    v[2 * t] = a;
+    v[2 * t + 1] = e;
+  }
+  int pos = 0, cnt = 2 * NT;
+  warp_rs_df<2 * NT, 16>(v, pos, cnt);
+  if (cnt == 1) {
+    const dfl r = df_norm(v[0]);
+    reinterpret_cast<float2 *>(part)[(pbase + T0 + (pos >> 1)) * 2 + (pos & 1)] = make_float2(r.hi, r.lo);
+  }
+}
+
 // Chunk c's partials (a warp).
 template <int WT, bool DEG>
 __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk,
@@ -77,6 +114,11 @@ __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk
 #pragma unroll
   for (int u = 0; u < kBinPer; ++u) xi[u] = (!DEG && cv[u]) ? x[ci[u]] : make_float2(0.f, 0.f);
   const size_t wbase = (size_t)c * B.W * kBinChunk;
+  if (B.W == 9) {  // the 3 x 3 window: two slot groups, each reduced at once
+    bin_slot_group<WT, DEG, 0, 5>(bwq, wbase, cv, xi, part, (size_t)c * 9);
+    bin_slot_group<WT, DEG, 5, 4>(bwq, wbase, cv, xi, part, (size_t)c * 9);
+    return;
+  }
   for (int t = 0; t < B.W; ++t) {
     float w[kBinPer];
 #pragma unroll

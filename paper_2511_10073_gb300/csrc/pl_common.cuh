@@ -138,6 +138,37 @@ __device__ __forceinline__ dfl warp_sum_df(dfl s) {
   return df_norm(s);
 }
 
+// Reduce-scatter of the N double-floats v over the warp (level M = 16, 8, ...,
+// 1): at each level a lane keeps one half of its values (the upper half when
+// its bit M is set), sends the other half to lane ^ M and adds what it
+// receives, the lower lane's partial first.  On return exactly one lane holds
+// the warp sum of value j, in v[0], with pos = j and cnt = 1; the others have
+// cnt = 0.  Every sum follows the tree of warp_sum_df's lane 0 (the group of
+// lanes with the bit clear plus the group with it set, level by level), so
+// before df_norm it is bit-identical to it, for far fewer shuffles and adds
+// when N is large.  Call with pos = 0, cnt = N.
+template <int N, int M>
+__device__ __forceinline__ void warp_rs_df(dfl *v, int &pos, int &cnt) {
+  constexpr int H = (N + 1) / 2;
+  const bool hi = (threadIdx.x & M) != 0;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const dfl a = v[i];
+    const dfl b = i + H < N ? v[i + H] : dfl{0.f, 0.f};
+    const dfl r = df_shfl_xor(hi ? a : b, M);
+    dfl s = hi ? r : a;
+    df_add_df(s, hi ? b : r);
+    v[i] = s;
+  }
+  if (hi) {
+    pos += H;
+    cnt = cnt > H ? cnt - H : 0;
+  } else {
+    cnt = cnt < H ? cnt : H;
+  }
+  if constexpr (M > 1) warp_rs_df<H, M / 2>(v, pos, cnt);
+}
+
 // Monotone 64-bit key of a non-negative double-float value (hi >= 0), for
 // atomicMax: hi's bits above lo's order-preserving bits.
 __device__ __forceinline__ unsigned long long df_maxkey(dfl s) {

@@ -1085,6 +1085,12 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
                                                  C, P<float2>(g->fixedp));
     note_launch();
   }
+  TRY(ensure(g->carea, (size_t)C * 8 + 16));
+  if (C) {
+    k_cell_area<<<grid_for(C, 256), 256, 0, s2>>>(C, P<float>(g->cw), P<float>(g->ch),
+                                                  P<double>(g->carea));
+    note_launch();
+  }
   TRY(ensure(g->amac, (size_t)g->NB * 8 + 16));
   TRY(ensure(g->Cb, (size_t)g->NB * 8 + 16));
   TRY(ensure(g->mgeo, (size_t)g->Mm * 16 + 16));

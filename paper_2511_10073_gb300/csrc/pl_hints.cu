@@ -368,8 +368,11 @@ struct LevelBufs {
   double *base[kMaxLevels];
 };
 
-__device__ __forceinline__ double cell_area(const float *cw, const float *ch, uint32_t i) {
-  return __dmul_rn((double)cw[i], (double)ch[i]);
+// Cell areas w h in FP64 (exact: a product of two floats fits a double), once
+// per netlist, so that the density sums take one FP64 operation per cell.
+__global__ void k_cell_area(int32_t C, const float *cw, const float *ch, double *area) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x)
+    area[i] = __dmul_rn((double)cw[i], (double)ch[i]);
 }
 
 // A_mov(b) as a blocked FP64 sum: the bin's cells (hint cells ascending,
@@ -396,9 +399,9 @@ __device__ __forceinline__ DensLevel dens_level(const int64_t *boff, int b, int 
 }
 
 __global__ void __launch_bounds__(256) k_dens_level(int NB, int L, const int64_t *boff,
-                                                    const uint32_t *blist, const float *cw,
-                                                    const float *ch, const double *prev,
-                                                    double *out, long long nidx) {
+                                                    const uint32_t *blist, const double *area,
+                                                    const double *prev, double *out,
+                                                    long long nidx) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nidx;
        idx += (long long)gridDim.x * blockDim.x) {
     int lo = 0, hi = NB - 1;  // last bin with out_L(b) <= idx
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(256) k_dens_level(int NB, int L, const int64_t
       for (int64_t k = k0; k < k1; k += 16) {
         double a[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] = k + q < k1 ? cell_area(cw, ch, blist[k + q]) : 0.0;
+        for (int q = 0; q < 16; ++q) a[q] = k + q < k1 ? area[blist[k + q]] : 0.0;
 #pragma unroll
         for (int q = 0; q < 16; ++q)
           if (k + q < k1) acc = __dadd_rn(acc, a[q]);
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(256) k_dens_level(int NB, int L, const int64_t
 // Per bin: the last (at most 64-value) sum, D_b, C_b, phi_b and the hub row
 // length (hint cells of the window bins).
 __global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uint32_t *blist,
-                             const float *cw, const float *ch, LevelBufs lv, const double *amac,
+                             const double *area, LevelBufs lv, const double *amac,
                              double abin, double cap, double mu, double *Db, double *Cb,
                              double *phi, float *phif) {
   const int NB = G.nbx * G.nby;
@@ -447,7 +450,7 @@ __global__ void k_dens_final(HintGeo G, int nlev, const int64_t *boff, const uin
       double a[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q)
-        a[q] = k + q < d.len ? (L == 0 ? cell_area(cw, ch, blist[d.st + k + q]) : src[d.st + k + q])
+        a[q] = k + q < d.len ? (L == 0 ? area[blist[d.st + k + q]] : src[d.st + k + q])
                              : 0.0;
 #pragma unroll
       for (int q = 0; q < 16; ++q)
@@ -1285,23 +1288,25 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
     TRY((segmented_sort<uint32_t, MODE_SORT>(P<uint32_t>(g->mlist), P<int64_t>(g->moff), Mm, nml,
                                              nullptr, nullptr, nullptr, g->tmp[3].p, s)));
   }
-  // H5: densities and phi, and the tiled macro lists, on the side stream
-  // while the row lengths and the layout go on (joined before the assembly)
-  TRY(ensure_side(g));
-  cudaStream_t s2 = g->side;
+  // H5: densities and phi on the side stream, the tiled macro lists on a
+  // third one, while the row lengths and the layout go on (both joined
+  // before the assembly)
+  TRY(ensure_side2(g));
+  cudaStream_t s2 = g->side, s3 = g->side2;
   TRY(ensure(g->Db, (size_t)NB * 8 + 16));
   TRY(ensure(g->phi, (size_t)NB * 8 + 16));
   TRY(ensure(g->tmp[4], (size_t)NB * 4 + 256));
   float *phif = P<float>(g->tmp[4]);
   TRY(cudaEventRecord(g->ev_fork, s));
   TRY(cudaStreamWaitEvent(s2, g->ev_fork, 0));
+  TRY(cudaStreamWaitEvent(s3, g->ev_fork, 0));
   if (cmem_ok) {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
       cudaFuncSetAttribute(k_macro_tile_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kMaxSmemMacros * 6);
     });
-    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s2>>>(C, P<int32_t>(g->n_ovl),
+    k_macro_tile_scatter<<<ntile, 256, (size_t)Mm * 6, s3>>>(C, P<int32_t>(g->n_ovl),
                                                             P<int32_t>(g->cmem), Mm, ntile,
                                                             P<int64_t>(g->mtoff),
                                                             P<uint32_t>(g->mlist));
@@ -1329,18 +1334,20 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
       span *= 64.0;
     }
     for (int L = 0; L < nlev; ++L) {
-      k_dens_level<<<grid_for((long long)sizes[L], 256, 152 * 16), 256, 0, s2>>>(
-          NB, L, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch),
+      // blocks of 64 threads, so that the first level's FP64 sums spread over every SM
+      k_dens_level<<<grid_for((long long)sizes[L], 64, 152 * 64), 64, 0, s2>>>(
+          NB, L, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<double>(g->carea),
           L ? lv.base[L - 1] : nullptr, lv.base[L], (long long)sizes[L]);
       note_launch();
     }
   }
   k_dens_final<<<grid_for(NB, 32), 32, 0, s2>>>(  // a warp per 32 bins: spread over the SMs
-      G, nlev, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<float>(g->cw), P<float>(g->ch), lv,
+      G, nlev, P<int64_t>(g->boff), P<uint32_t>(g->blist), P<double>(g->carea), lv,
       P<double>(g->amac), g->abin, p->capacity, p->mu, P<double>(g->Db), P<double>(g->Cb),
       P<double>(g->phi), phif);
   note_launch();
   TRY(cudaEventRecord(g->ev_join, s2));
+  TRY(cudaEventRecord(g->ev_join2, s3));
   // H6-H7: row lengths and layout
   pl_status st = ensure_row_arrays(g);
   if (st != PL_OK) return st;
@@ -1362,7 +1369,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->hbin, (size_t)C * 4 + 16));
   unsigned long long *counts = reinterpret_cast<unsigned long long *>(P<double>(m.lam) + 3);
   TRY(cudaMemsetAsync(counts, 0, 16, s));
-  TRY(cudaStreamWaitEvent(s, g->ev_join, 0));  // phi and the macro lists
+  TRY(cudaStreamWaitEvent(s, g->ev_join, 0));   // phi
+  TRY(cudaStreamWaitEvent(s, g->ev_join2, 0));  // the macro lists
   k_assemble_hints<<<grid_for(g->Nst, 256), 256, 0, s>>>(
       G, g->wdtype, P<uint32_t>(m.rp_s), P<int32_t>(m.longidx), P<uint64_t>(m.lptr),
       P<dfl>(g->st.dsum), P<dfl>(g->st.psum), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin),

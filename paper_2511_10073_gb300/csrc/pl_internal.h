@@ -91,6 +91,7 @@ struct pl_graph {
   pl::Buf fixedp;      // float2 [N]
   pl::Buf bounds;      // float4 [N] clamp box of the centre
   pl::Buf amac, Cb;    // double [NB]
+  pl::Buf carea;       // double [C] cell areas w h
   // macro lookup grid
   int32_t gnx = 1, gny = 1;
   double gsz = 1.0, gsx = 1.0, gsy = 1.0;
@@ -144,6 +145,8 @@ struct pl_graph {
   size_t hint_mark = 0;
   cudaStream_t side = nullptr;  // the hint build's second stream (forked from and joined
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // back to the caller's stream)
+  cudaStream_t side2 = nullptr;  // a third stream of the hint build, joined by ev_join2
+  cudaEvent_t ev_join2 = nullptr;
   bool star_w_ok = false;
   // launch shapes of the sparse products on the graph's device (0 = not yet
   // looked up): SM count, resident blocks per SM of the short-row kernels by
@@ -157,6 +160,8 @@ struct pl_graph {
 };
 
 namespace pl {
+
+__global__ void k_cell_area(int32_t C, const float *cw, const float *ch, double *area);
 
 // Every device buffer of a graph.  kind 0: all; kind 1: those a hint build
 // takes anew (its own results and the scratch buffers every phase shares).
@@ -182,7 +187,7 @@ void for_each_buf(pl_graph *g, int kind, F f) {
   Buf *rest[] = {&g->cw, &g->ch, &g->ckind, &g->cfx, &g->cfy, &g->net_ptr, &g->pin_node,
                  &g->nd, &g->net_p, &g->star_of, &g->star_net, &g->star_p, &g->macro_cell,
                  &g->cell_macro, &g->srp, &g->base_w, &g->hflag, &g->nkind, &g->fixedp,
-                 &g->bounds, &g->amac, &g->Cb, &g->gptr, &g->glist, &g->ggeo, &g->mgeo,
+                 &g->bounds, &g->amac, &g->Cb, &g->carea, &g->gptr, &g->glist, &g->ggeo, &g->mgeo,
                  &g->xa, &g->xb, &g->xc, &g->g0, &g->ua, &g->ub, &g->acc, &g->gsc, &g->q4a,
                  &g->q4b, &g->status, &g->stage, &g->star_w, &g->lscr};
   for (Buf *b : rest) f(*b);
@@ -223,6 +228,14 @@ inline cudaError_t ensure_side(pl_graph *g) {
   cudaError_t e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
+  return e;
+}
+// The third stream and its join event, created on first use.
+inline cudaError_t ensure_side2(pl_graph *g) {
+  cudaError_t e = ensure_side(g);
+  if (e != cudaSuccess || g->side2) return e;
+  e = cudaStreamCreateWithFlags(&g->side2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join2, cudaEventDisableTiming);
   return e;
 }
 }  // namespace pl

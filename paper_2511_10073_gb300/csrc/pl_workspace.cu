@@ -104,6 +104,7 @@ double workspace_bound(const pl_netlist *nl, const pl_params *p) {
   st.add(N + 16);
   st.add(N * 8 + 16);
   st.add(N * 16 + 16);
+  st.add(C * 8 + 16);  // cell areas
   st.add(NB * 8 + 16);
   st.add(NB * 8 + 16);
   st.add(Mm * 16 + 16);
