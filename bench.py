@@ -544,11 +544,11 @@ def main():
         "config": {"workload": args.config, "netlist": DESCR[args.config],
                    "movable_cells": movable, "nodes": info["N"], "static_nnz": info["static_nnz"],
                    "augmented_nnz": info["nnz"], "hub_rows": info["hub_rows"],
-                   "l2": "inputs larger than L2 (each sparse product streams >400 MB)",
+                   "l2": "inputs larger than L2 (each sparse product streams >300 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"kernel": "one sparse product of the refinement filter (A4): k_spmm_rows (short rows, "
-                               "window slots) + k_spmm_hub, k_bin_partials, k_bin_bucket_sums, "
-                               "k_hub_rows (second stream)",
+                               "window slots) + k_spmm_hub, k_bin_partials, k_hub_rows (second "
+                               "stream)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

@@ -13,8 +13,8 @@
 // kBinChunk; a CTA per chunk forms, for every slot, the chunk's double-float
 // sum (exact products for the filter, weights and positive weights for the
 // degrees), warps first and then the warps in order, so every partial is a
-// fixed function of the inputs.  The row of bin b adds its slots' chunk
-// partials in slot order, each slot's chunks in order.
+// fixed function of the inputs.  The row of bin b adds, slot by slot, the
+// partials of that slot's source-bucket chunks (bin_row_chunks).
 #pragma once
 
 #include "pl_common.cuh"
@@ -164,55 +164,52 @@ inline cudaError_t launch_bin_partials(int wt, int grid, cudaStream_t s, const B
   return cudaGetLastError();
 }
 
-// Sums of each (bucket, slot) over the bucket's chunks: a warp per pair, the
-// lanes strided over the chunks in order, then a fixed tree (a hot bucket's
-// hundreds of chunks spread over the warp).
-__device__ __forceinline__ void bucket_sum(const BinGeo &B, const int32_t *bchunk,
-                                           const float4 *part, float4 *bsum, long long q) {
-  const int lane = threadIdx.x & 31;
-  const int b = (int)(q / B.W), s = (int)(q - (long long)b * B.W);
-  dfl a{0.f, 0.f}, e{0.f, 0.f};
-  const int c1 = bchunk[b + 1];
-  for (int c0 = bchunk[b] + lane; c0 < c1; c0 += 32 * 4) {
-    float4 v[4];  // four partials in flight, added in order
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      v[u] = c0 + 32 * u < c1 ? __ldcg(&part[(size_t)(c0 + 32 * u) * B.W + s])
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      df_add_df(a, dfl{v[u].x, v[u].y});
-      df_add_df(e, dfl{v[u].z, v[u].w});
-    }
-  }
-  a = warp_sum_df(a);
-  e = warp_sum_df(e);
-  if (lane == 0) bsum[q] = make_float4(a.hi, a.lo, e.hi, e.lo);
-}
-
-static __global__ void k_bin_bucket_sums(BinGeo B, const int32_t *bchunk, const float4 *part,
-                                  float4 *bsum) {
-  const long long npair = (long long)B.NB * B.W;
-  for (long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; q < npair;
-       q += ((long long)gridDim.x * blockDim.x) >> 5)
-    bucket_sum(B, bchunk, part, bsum, q);
-}
-
-// Sums of bin b's row by the lanes of one warp: for every slot s whose source
-// bucket b - offset(s) lies in the grid, that bucket's sum for s; lanes
-// strided over the slots, then a fixed tree.  Returns the two double-floats of
-// the partials' layout.
-__device__ __forceinline__ void bin_row_sums(const BinGeo &B, int b, const float4 *bsum, dfl *a,
-                                             dfl *e) {
+// Sums of bin b's row by the lanes of one warp, straight from the chunk
+// partials: for every slot s whose source bucket b - offset(s) lies in the
+// grid, the partials of slot s of that bucket's chunks.  The items (slot by
+// slot, each bucket's chunks in order; slots in groups of 32) are dealt to
+// the lanes in turn, then a fixed tree adds the lanes, so the sums are a fixed
+// function of the partials.  Returns the two double-floats of the partials'
+// layout.
+__device__ __forceinline__ void bin_row_chunks(const BinGeo &B, int b, const int32_t *bchunk,
+                                               const float4 *part, dfl *a, dfl *e) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int bx = b % B.nbx, by = b / B.nbx, wx = 2 * B.hx + 1;
   dfl sa{0.f, 0.f}, se{0.f, 0.f};
-  for (int s = lane; s < B.W; s += 32) {
-    const int sx = bx - (s % wx - B.hx), sy = by - (s / wx - B.hy);
-    if (sx < 0 || sy < 0 || sx >= B.nbx || sy >= B.nby) continue;
-    const float4 q = __ldcg(&bsum[(size_t)(sy * B.nbx + sx) * B.W + s]);
-    df_add_df(sa, dfl{q.x, q.y});
-    df_add_df(se, dfl{q.z, q.w});
+  for (int s0 = 0; s0 < B.W; s0 += 32) {
+    // lane j: the chunk range of slot s0 + j's source bucket
+    const int s = s0 + lane;
+    int c0 = 0, n = 0;
+    if (s < B.W) {
+      const int sx = bx - (s % wx - B.hx), sy = by - (s / wx - B.hy);
+      if (sx >= 0 && sy >= 0 && sx < B.nbx && sy < B.nby) {
+        const int bb = sy * B.nbx + sx;
+        c0 = bchunk[bb];
+        n = bchunk[bb + 1] - c0;
+      }
+    }
+    int inc = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(full, inc, d);
+      if (lane >= d) inc += t;
+    }
+    const int exc = inc - n, tot = __shfl_sync(full, inc, 31);
+    for (int i0 = 0; i0 < tot; i0 += 32) {
+      const int i = i0 + lane;
+      // the lane whose range holds item i: the last one starting at or before it
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(full, exc, lo + step) <= i) lo += step;
+      const int cj = __shfl_sync(full, c0, lo), ej = __shfl_sync(full, exc, lo);
+      if (i < tot) {
+        const float4 q = __ldcg(&part[(size_t)(cj + i - ej) * B.W + s0 + lo]);
+        df_add_df(sa, dfl{q.x, q.y});
+        df_add_df(se, dfl{q.z, q.w});
+      }
+    }
   }
   *a = warp_sum_df(sa);
   *e = warp_sum_df(se);

@@ -99,7 +99,6 @@ struct StepArgs {
   const int64_t *boff;
   const uint32_t *blist;
   float4 *bpart;
-  float4 *bpartb;  // bpart summed per (bucket, slot)
   // windows of at most kSlotUnroll * kRowLanes slots: lane m's slot
   // m + u kRowLanes is at bin offset soff[m][u] from the cell's bin
   int sfast;
@@ -621,7 +620,7 @@ __device__ __forceinline__ void hub_rows_block(const StepArgs &A, long long blk,
       if (v >= A.bn0) {
         // a bin row: its window-slot partials over the source buckets
         dfl bx, by;
-        bin_row_sums(A.B, (int)(v - A.bn0), A.bpartb, &bx, &by);
+        bin_row_chunks(A.B, (int)(v - A.bn0), A.bchunk, A.bpart, &bx, &by);
         df_add_df(px, bx);
         df_add_df(py, by);
       } else if (v < A.C && A.hbin[v] >= 0) {
@@ -887,9 +886,6 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
       e = launch_bin_partials<false>(wi ? PL_W_BF16 : PL_W_FP32, bgrid, sh, A.B, A.bchunk, A.cown,
                                      A.boff, A.blist, A.hbwq, A.x, A.bpart);
       if (e != cudaSuccess) return e;
-      k_bin_bucket_sums<<<grid_for((long long)A.B.NB * A.B.W * 32, 256), 256, 0, sh>>>(
-          A.B, A.bchunk, A.bpart, A.bpartb);
-      note_launch();
       note_launch();
     }
     const int rgrid = (int)(((long long)A.nlong + kHubRows - 1) / kHubRows);
@@ -1205,7 +1201,6 @@ static void hr_args(pl_graph *g, StepArgs &A) {
   A.boff = P<int64_t>(g->boff);
   A.blist = P<uint32_t>(g->blist);
   A.bpart = P<float4>(g->bpart);
-  A.bpartb = P<float4>(g->bpartb);
   fill_nodes(A, g);
   A.a = P<float>(m.c32);
   A.b = nullptr;
@@ -1311,7 +1306,7 @@ pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int
 // exactly what its own launch computes, so every result keeps its bits.
 namespace pl {
 
-enum { BK_ROWS = 0, BK_HUB = 1, BK_BINC = 2, BK_PAIR = 3, BK_HROW = 4, BK_KINDS = 5 };
+enum { BK_ROWS = 0, BK_HUB = 1, BK_BINC = 2, BK_HROW = 3, BK_KINDS = 4 };
 
 __device__ __forceinline__ int unit_design(const long long *pre, int nd, long long u) {
   int lo = 0, hi = nd - 1;  // the largest d with pre[d] <= u
@@ -1354,11 +1349,9 @@ __device__ __forceinline__ void batch_units(const StepArgs *As, const long long 
       rows_group<WT, MODE>(A, k * (32 / kRowLanes));
     } else if (K == BK_HUB) {
       warp_chunk<WT, MODE>(A, (int)k);
-    } else if (K == BK_BINC) {
+    } else {
       if (k < A.bchunk[A.B.NB])
         bin_chunk<WT, false>(A.B, A.bchunk, A.cown, A.boff, A.blist, A.hbwq, A.x, A.bpart, k);
-    } else {
-      bucket_sum(A.B, A.bchunk, A.bpart, A.bpartb, k);
     }
   }
 }
@@ -1465,8 +1458,7 @@ pl_status run_filter_batch(pl_graph *const *gs, int nd, const pl_params *p, cons
     }
     const long long units[BK_KINDS] = {
         (g->N + 32 / kRowLanes - 1) / (32 / kRowLanes), (long long)A.nchunks,
-        A.bpart ? (long long)g->nbc_max : 0LL, A.bpart ? (long long)g->NB * g->W : 0LL,
-        ((long long)A.nlong + kHubRows - 1) / kHubRows};
+        A.bpart ? (long long)g->nbc_max : 0LL, ((long long)A.nlong + kHubRows - 1) / kHubRows};
     for (int k = 0; k < BK_KINDS; ++k) pre[(size_t)k * (nd + 1) + d + 1] = units[k];
   }
   for (int k = 0; k < BK_KINDS; ++k)
@@ -1487,9 +1479,9 @@ pl_status run_filter_batch(pl_graph *const *gs, int nd, const pl_params *p, cons
   const long long rows_per = per_for(total(BK_ROWS), (long long)rc * nsm * (kRowThreads / 32));
   const int rows_grid = (int)std::max(1LL, (total(BK_ROWS) + rows_per * (kRowThreads / 32) - 1) /
                                                  (rows_per * (kRowThreads / 32)));
-  long long side_per[BK_KINDS] = {0, 0, 0, 0, 0};
-  int side_grid[BK_KINDS] = {0, 0, 0, 0, 0};
-  for (int k = BK_HUB; k <= BK_PAIR; ++k) {
+  long long side_per[BK_KINDS] = {0, 0, 0, 0};
+  int side_grid[BK_KINDS] = {0, 0, 0, 0};
+  for (int k = BK_HUB; k <= BK_BINC; ++k) {
     const long long U = total(k);
     if (!U) continue;
     side_per[k] = per_for(U, 8LL * nsm * 8);
@@ -1510,13 +1502,9 @@ pl_status run_filter_batch(pl_graph *const *gs, int nd, const pl_params *p, cons
       else k_side_batch<BK_BINC, 0><<<side_grid[BK_BINC], 256, 0, sh>>>(dAt, dpre + 2 * (nd + 1), nd, side_per[BK_BINC]);
       note_launch();
     }
-    if (side_grid[BK_PAIR]) {
-      k_side_batch<BK_PAIR, 0><<<side_grid[BK_PAIR], 256, 0, sh>>>(dAt, dpre + 3 * (nd + 1), nd, side_per[BK_PAIR]);
-      note_launch();
-    }
     if (hrow_grid) {
-      if (wd == PL_W_BF16) k_hub_rows_batch<1><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 4 * (nd + 1), nd);
-      else k_hub_rows_batch<0><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 4 * (nd + 1), nd);
+      if (wd == PL_W_BF16) k_hub_rows_batch<1><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 3 * (nd + 1), nd);
+      else k_hub_rows_batch<0><<<hrow_grid, kHubRows * 32, 0, sh>>>(dAt, dpre + 3 * (nd + 1), nd);
       note_launch();
     }
     TRY(cudaEventRecord(g0->ev_join, sh));

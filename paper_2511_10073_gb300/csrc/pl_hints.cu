@@ -905,9 +905,10 @@ __global__ void __launch_bounds__(256) k_hub_chunks(
 }
 
 // Degrees of virtual rows (warp per row): a macro row from its chunk
-// partials, a bin row from the window blocks' degree partials.
+// partials, a bin row from the window blocks' degree partials per chunk.
 __global__ void k_hub_finalize(HintGeo G, BinGeo B, int32_t nlong, const int32_t *lrow,
-                               const int32_t *lchunk, const dfl *cpart, const float4 *bdeg,
+                               const int32_t *lchunk, const dfl *cpart, const int32_t *bchunk,
+                               const float4 *bdeg,
                                dfl *dsum, dfl *psum) {
   const int lane = threadIdx.x & 31;
   for (long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; l < nlong;
@@ -916,7 +917,7 @@ __global__ void k_hub_finalize(HintGeo G, BinGeo B, int32_t nlong, const int32_t
     if (v < G.mv0) continue;
     dfl D{0.f, 0.f}, Pp{0.f, 0.f};
     if (v >= G.bn0) {
-      bin_row_sums(B, (int)(v - G.bn0), bdeg, &D, &Pp);
+      bin_row_chunks(B, (int)(v - G.bn0), bchunk, bdeg, &D, &Pp);
     } else {
       for (int c = lchunk[l] + lane; c < lchunk[l + 1]; c += 32) {
         df_add_df(D, cpart[2 * (long long)c]);
@@ -1415,12 +1416,6 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
                                  P<int64_t>(g->boff), P<uint32_t>(g->blist), g->hbwq.p, nullptr,
                                  P<float4>(g->bdeg)));
   note_launch();
-  // degree partials per (bucket, slot)
-  TRY(ensure(g->bdegb, (size_t)NB * W * 16 + 256));
-  k_bin_bucket_sums<<<grid_for((long long)NB * W * 32, 256), 256, 0, s>>>(
-      B, P<int32_t>(g->bchunk), P<float4>(g->bdeg), P<float4>(g->bdegb));
-  note_launch();
-  TRY(ensure(g->bpartb, (size_t)NB * W * 16 + 256));
   TRY(ensure(g->tmp[5], (size_t)(m.nchunks + 1) * 2 * sizeof(dfl) + 256));
   dfl *cpart = P<dfl>(g->tmp[5]);
   if (m.nchunks) {
@@ -1430,7 +1425,8 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
         P<uint64_t>(g->mac_base), P<int32_t>(m.col), m.w.p, cpart);
     note_launch();
     k_hub_finalize<<<grid_for((long long)m.nlong * 32, 256), 256, 0, s>>>(
-        G, B, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<float4>(g->bdegb),
+        G, B, m.nlong, P<int32_t>(m.lrow), P<int32_t>(m.lchunk), cpart, P<int32_t>(g->bchunk),
+        P<float4>(g->bdeg),
         P<dfl>(m.dsum), P<dfl>(m.psum));
     note_launch();
   }

@@ -125,7 +125,6 @@ struct pl_graph {
   pl::Buf cown;        // int32 [chunks] bin of each chunk
   pl::Buf bdeg;        // float4 [chunks * W] degree partials of the bin rows
   pl::Buf bpart;       // float4 [chunks * W] product partials of the bin rows
-  pl::Buf bdegb, bpartb;  // float4 [NB * W] the same summed per (bucket, slot)
   pl::Buf hubtmp;      // int32 scratch for merging bin rows
   pl::SpMat st;        // static matrix (A0)
   pl::SpMat hm;        // augmented matrix (A2-A4)
@@ -173,7 +172,7 @@ void for_each_buf(pl_graph *g, int kind, F f) {
                  &g->n_ovl, &g->bcnt, &g->boff, &g->blist, &g->bcur, &g->mcnt, &g->moff,
                  &g->mlist, &g->mcur, &g->mtc, &g->mtoff, &g->cmem, &g->Db, &g->phi,
                  &g->mac_base, &g->hbw, &g->hbwq, &g->hbin, &g->bchunk, &g->cown, &g->bdeg,
-                 &g->bpart, &g->bdegb, &g->bpartb};
+                 &g->bpart};
   for (Buf *b : hint) f(*b);
   SpMat *ms[] = {&g->hm, &g->st};
   for (int i = 0; i < (kind == 0 ? 2 : 1); ++i) {

@@ -193,8 +193,6 @@ double workspace_bound(const pl_netlist *nl, const pl_params *p) {
   const double nbc = std::floor(nmov / kBinChunk) + NB + 1;
   h.add(nbc * 4 + 256);
   h.add(nbc * W * 16 + 256);
-  h.add(NB * W * 16 + 256);
-  h.add(NB * W * 16 + 256);
   h.add(nbc * W * 16 + 256);
   h.add((nchunk_h + 1) * 2 * 8 + 256);
   return st.b + h.b + 4096.0;
