@@ -760,6 +760,44 @@ __global__ void __launch_bounds__(256, 3) k_assemble_hints(
       uint16_t *wb16 = reinterpret_cast<uint16_t *>(bwin) + (size_t)v * W;
       uint32_t *wb32 = reinterpret_cast<uint32_t *>(bwin) + (size_t)v * W;
       int sidx = 0;
+      if (bf && G.hx == 1) {
+        // three window columns: their ratios and e^{-rx} once per cell, not
+        // once per window row (the same values, so the same weights)
+        dfl rxs[3];
+        float exs[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int xx = bx - 1 + c;
+          rxs[c] = df_absdiff(ux.hi, ux.lo, (float)(2 * xx + 1));
+          exs[c] = (xx >= 0 && xx < G.nbx) ? exp_neg_df(rxs[c]) : 0.f;
+        }
+        for (int yy = by - G.hy; yy <= by + G.hy; ++yy) {
+          const bool yin = yy >= 0 && yy < G.nby;
+          const dfl ry = df_absdiff(uy.hi, uy.lo, (float)(2 * yy + 1));
+          const float ey = yin ? exp_neg_df(ry) : 0.f;
+          float ph[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int xx = bx - 1 + c;
+            ph[c] = (yin && xx >= 0 && xx < G.nbx) ? phif[yy * G.nbx + xx] : 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int xx = bx - 1 + c;
+            uint16_t h = 0;
+            if (yin && xx >= 0 && xx < G.nbx) {
+              const float e = df_ge(rxs[c], ry) ? exs[c] : ey;
+              const float wv = -((e * ph[c]) * bwf);
+              h = near_bf16_tie(wv)
+                      ? d2bf16(bin_w_exact(p.x, p.y, xx, yy, G, phid[yy * G.nbx + xx], bw))
+                      : f2bf16(wv);
+              acc_deg(Dl, Pl, bf16_to_f(h));
+              ++slots;
+            }
+            wb16[sidx++] = h;
+          }
+        }
+      } else
       for (int yy = by - G.hy; yy <= by + G.hy; ++yy) {
         const bool yin = yy >= 0 && yy < G.nby;
         // e^{-max(rx, ry)} is e^{-rx} or e^{-ry}
