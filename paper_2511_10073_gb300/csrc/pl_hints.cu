@@ -221,7 +221,7 @@ __global__ void k_macro_scatter(HintGeo G, const float2 *xy, const uint8_t *ckin
 // turns; inside a turn the lanes mark their macros in a per-macro lane mask,
 // and a membership's place is its macro's tile start (loaded before the
 // turns), the macro's run so far and the number of lower lanes marked.
-__global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int32_t *n_ovl,
+__global__ void __launch_bounds__(256, 4) k_macro_tile_scatter(int32_t C, const int32_t *n_ovl,
                                                             const int32_t *cmem, int Mm,
                                                             int ntile, const int64_t *off,
                                                             uint32_t *mlist) {
@@ -257,6 +257,9 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
 #pragma unroll
     for (int j = 0; j < kMacroSlots; ++j)
       mn[j] = j < nn ? cmem[(long long)inext * kMacroSlots + j] : 0;
+    // places within the tile's runs, by turns in shared memory; the stores
+    // wait for the tile starts only after the turns
+    int rel[kMacroSlots];
     for (int w = 0; w < nw; ++w) {
       if (wid == w) {
 #pragma unroll
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < kMacroSlots; ++j)
-          if (j < n) mlist[tst[j] + run[mk[j]] + __popc(lmask[mk[j]] & lt)] = (uint32_t)i;
+          rel[j] = j < n ? (int)run[mk[j]] + __popc(lmask[mk[j]] & lt) : 0;
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < kMacroSlots; ++j) {
@@ -281,6 +284,9 @@ __global__ void __launch_bounds__(256) k_macro_tile_scatter(int32_t C, const int
       }
       __syncthreads();
     }
+#pragma unroll
+    for (int j = 0; j < kMacroSlots; ++j)
+      if (j < n) mlist[tst[j] + rel[j]] = (uint32_t)i;
   }
 }
 
@@ -324,6 +330,7 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
     const bool mv = i < i1 && ckind[i] == 0;
     const int key = mv ? bucket_of(hflag, cell_bin, i) : -1 - lane;
     const long long tst = mv ? off[(long long)key * ntile + t] : 0;  // loaded before the turns
+    int rel = 0;  // place within the tile's run of the bucket (the store waits for tst after the turns)
     for (int w = 0; w < nw; ++w) {
       if (wid == w) {
         unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -334,13 +341,11 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
           run[key] = before + __popc(grp);
         }
         before = __shfl_sync(0xffffffffu, before, leader);
-        if (mv) {
-          const long long pos = tst + before + __popc(grp & lt);
-          blist[pos] = (uint32_t)i;
-        }
+        rel = before + __popc(grp & lt);
       }
       __syncthreads();
     }
+    if (mv) blist[tst + rel] = (uint32_t)i;
   }
 }
 
