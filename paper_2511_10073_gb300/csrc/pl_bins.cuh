@@ -196,18 +196,27 @@ __device__ __forceinline__ void bin_row_chunks(const BinGeo &B, int b, const int
       if (lane >= d) inc += t;
     }
     const int exc = inc - n, tot = __shfl_sync(full, inc, 31);
-    for (int i0 = 0; i0 < tot; i0 += 32) {
-      const int i = i0 + lane;
-      // the lane whose range holds item i: the last one starting at or before it
-      int lo = 0;
+    constexpr int kU = 4;  // items a lane loads at once
+    for (int i0 = 0; i0 < tot; i0 += 32 * kU) {
+      float4 q[kU];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (__shfl_sync(full, exc, lo + step) <= i) lo += step;
-      const int cj = __shfl_sync(full, c0, lo), ej = __shfl_sync(full, exc, lo);
-      if (i < tot) {
-        const float4 q = __ldcg(&part[(size_t)(cj + i - ej) * B.W + s0 + lo]);
-        df_add_df(sa, dfl{q.x, q.y});
-        df_add_df(se, dfl{q.z, q.w});
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + 32 * u + lane;
+        // the lane whose range holds item i: the last one starting at or before it
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (__shfl_sync(full, exc, lo + step) <= i) lo += step;
+        const int cj = __shfl_sync(full, c0, lo), ej = __shfl_sync(full, exc, lo);
+        q[u] = i < tot ? __ldcg(&part[(size_t)(cj + i - ej) * B.W + s0 + lo])
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (i0 + 32 * u + lane < tot) {
+          df_add_df(sa, dfl{q[u].x, q[u].y});
+          df_add_df(se, dfl{q[u].z, q[u].w});
+        }
       }
     }
   }
