@@ -150,6 +150,8 @@ def _compare_hints(s, ge, oe):
 @pytest.mark.parametrize("cfg,seed,kw", [
     ("micro", 1, {}), ("small", 1, {}), ("small", 3, dict(wdtype=2)), ("tiny", 1, {}),
     ("tiny", 2, dict(nbx=32, nby=32)), ("tiny", 4, dict(nbx=20, nby=12, det_ratio=0.3, wdtype=2)),
+    # a 7 x 7 window (49 slots): the bin rows' degree sums take two groups of 32 slots
+    ("tiny", 7, dict(nbx=32, nby=32, det_ratio=0.25, wdtype=2)),
     ("medium", 2, {}),
     # more bin buckets than the tiled counting sort takes: atomic bucket
     # counts, sorted buckets, bin rows gathered by the hub-chunk kernel
@@ -237,7 +239,12 @@ def test_init_and_gift_crossfed(cfg, seed, kw):
     ("tiny", 4, dict(pin_every_step=1, gamma=0.7)), ("tiny", 5, dict(nbx=32, nby=32)),
     ("medium", 3, {}), ("medium", 1, dict(wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
                                          tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0))),
-    ("tiny", 6, dict(nbx=96, nby=80, wdtype=2))])
+    ("tiny", 6, dict(nbx=96, nby=80, wdtype=2)),
+    # windows other than 3 x 3: 5 x 3 (15 slots) and 7 x 7 (49 slots, two groups
+    # of 32 in the bin rows' sums), the chunk partials slot by slot
+    ("tiny", 7, dict(nbx=20, nby=12, det_ratio=0.3, wdtype=2)),
+    ("tiny", 8, dict(nbx=32, nby=32, det_ratio=0.25, wdtype=2, ntaps=3, tap_k=(2, 4, 8, 0),
+                     tap_alpha=(1 / 3, 1 / 3, 1 / 3, 0)))])
 def test_filter_step_crossfed(cfg, seed, kw):
     nl = netgen.make_netlist(cfg, seed)
     s = Side(nl, **cfg_params(cfg, **kw))
