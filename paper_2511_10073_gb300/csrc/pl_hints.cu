@@ -349,6 +349,49 @@ __global__ void __launch_bounds__(256) k_bin_tile_scatter(int32_t C, int nbk, in
   }
 }
 
+// The same lists without turns, for grids whose per-warp counters fit shared
+// memory (20 nbk bytes): in each round every warp ranks its lanes by key with
+// match_any and writes its group sizes to its own row of counters; after a
+// barrier a cell's place is the key's run so far, plus the same key's cells in
+// the round's lower warps, plus its lower lanes of the same key, which is its
+// place in cell order.  Two barriers per round instead of one per warp.
+__global__ void __launch_bounds__(256) k_bin_tile_scatter_wc(int32_t C, int nbk, int ntile,
+                                                             const uint8_t *ckind,
+                                                             const uint8_t *hflag,
+                                                             const int32_t *cell_bin,
+                                                             const int64_t *off, uint32_t *blist) {
+  extern __shared__ int32_t run[];  // [nbk] runs, then uint16 [8][nbk] counts of the round
+  uint16_t *wc = reinterpret_cast<uint16_t *>(run + nbk);
+  for (int k = threadIdx.x; k < nbk; k += blockDim.x) run[k] = 0;
+  for (int k = threadIdx.x; k < 8 * nbk; k += blockDim.x) wc[k] = 0;
+  __syncthreads();
+  const int t = blockIdx.x, i0 = t * kBinTile, i1 = min(C, i0 + kBinTile);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = i0; base < i1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool mv = i < i1 && ckind[i] == 0;
+    const int key = mv ? bucket_of(hflag, cell_bin, i) : -1 - lane;
+    const long long tst = mv ? off[(long long)key * ntile + t] : 0;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const bool lead = mv && lane == __ffs(grp) - 1;
+    if (lead) wc[wid * nbk + key] = (uint16_t)__popc(grp);
+    __syncthreads();
+    int rel = 0;
+    if (mv) {
+      rel = run[key] + __popc(grp & lt);
+      for (int w = 0; w < wid; ++w) rel += wc[w * nbk + key];
+    }
+    __syncthreads();  // the round's counters are read
+    if (lead) {
+      atomicAdd(&run[key], __popc(grp));  // warps of the round may share a key
+      wc[wid * nbk + key] = 0;
+    }
+    __syncwarp();
+    if (mv) blist[tst + rel] = (uint32_t)i;
+  }
+}
+
 __global__ void k_bucket_starts(int nbk, int ntile, const int64_t *off, int64_t *boff) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nbk; k += gridDim.x * blockDim.x)
     boff[k] = off[(long long)k * ntile];
@@ -1301,10 +1344,15 @@ pl_status build_hints(pl_graph *g, const pl_params *p, const float *xy_in, cudaS
   TRY(ensure(g->blist, (size_t)nbl * 4 + 16));
   TRY(ensure(g->mlist, (size_t)nml * 4 + 16));
   if (tiled) {
-    k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
-                                                          P<uint8_t>(g->hflag),
-                                                          P<int32_t>(g->cell_bin), cmo,
-                                                          P<uint32_t>(g->blist));
+    if ((size_t)nbk * 20 <= 48 * 1024)
+      k_bin_tile_scatter_wc<<<ntile, 256, (size_t)nbk * 20, s>>>(
+          C, nbk, ntile, P<uint8_t>(g->ckind), P<uint8_t>(g->hflag), P<int32_t>(g->cell_bin), cmo,
+          P<uint32_t>(g->blist));
+    else
+      k_bin_tile_scatter<<<ntile, 256, (size_t)nbk * 4, s>>>(C, nbk, ntile, P<uint8_t>(g->ckind),
+                                                            P<uint8_t>(g->hflag),
+                                                            P<int32_t>(g->cell_bin), cmo,
+                                                            P<uint32_t>(g->blist));
     note_launch();
   } else {
     TRY(ensure(g->bcur, (size_t)(nbk + 1) * 4));

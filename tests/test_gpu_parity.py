@@ -152,6 +152,8 @@ def _compare_hints(s, ge, oe):
     ("tiny", 2, dict(nbx=32, nby=32)), ("tiny", 4, dict(nbx=20, nby=12, det_ratio=0.3, wdtype=2)),
     # a 7 x 7 window (49 slots): the bin rows' degree sums take two groups of 32 slots
     ("tiny", 7, dict(nbx=32, nby=32, det_ratio=0.25, wdtype=2)),
+    # 4608 buckets: too many for the per-warp counters, the bucket lists by warp turns
+    ("tiny", 8, dict(nbx=48, nby=48)),
     ("medium", 2, {}),
     # more bin buckets than the tiled counting sort takes: atomic bucket
     # counts, sorted buckets, bin rows gathered by the hub-chunk kernel
