@@ -10,10 +10,10 @@
 // formed from the bucket lists and the window blocks.
 //
 // The hint cells of each bucket (ascending id) are cut into chunks of
-// kBinChunk; a CTA per chunk forms, for every slot, the chunk's double-float
+// kBinChunk; a warp per chunk forms, for every slot, the chunk's double-float
 // sum (exact products for the filter, weights and positive weights for the
-// degrees), warps first and then the warps in order, so every partial is a
-// fixed function of the inputs.  The row of bin b adds, slot by slot, the
+// degrees), each lane over its cells in order and then a fixed tree over the
+// lanes, so every partial is a fixed function of the inputs.  The row of bin b adds, slot by slot, the
 // partials of that slot's source-bucket chunks (bin_row_chunks).
 #pragma once
 

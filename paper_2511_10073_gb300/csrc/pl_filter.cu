@@ -1298,7 +1298,7 @@ pl_status run_powers(pl_graph *g, const pl_params *p, const float *in, const int
 // ------------------------------------------------ the batched product (NEXT-1)
 // One launch per kernel of a refinement product covers every design of a
 // batch: the designs' work units (short-row groups, hub chunks, bin chunks,
-// (bucket, slot) pairs, hub-row blocks) are concatenated, a block-diagonal
+// hub-row blocks) are concatenated, a block-diagonal
 // union of the designs' matrices with each design's own lambda_up and
 // per-node coefficients.  Unit u belongs to the design d with
 // pre[d] <= u < pre[d + 1]; a warp takes a run of consecutive units and
