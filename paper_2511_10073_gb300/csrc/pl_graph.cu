@@ -122,10 +122,13 @@ __global__ void k_macro_list(const uint8_t *is_macro, const int32_t *scan, int32
 }
 
 __global__ void k_pin_macro_flag(const int32_t *pin_cell, const uint8_t *is_macro, int64_t P,
-                                 uint8_t *f) {
+                                 int32_t C, uint8_t *f) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
        p += (long long)gridDim.x * blockDim.x)
-    f[p] = is_macro[pin_cell[p]];
+  {
+    const int32_t c = pin_cell[p];  // checked by the validation, read before its result
+    f[p] = (c >= 0 && c < C) ? is_macro[c] : (uint8_t)0;
+  }
 }
 
 __global__ void k_pin_node(const int32_t *pin_cell, const uint8_t *f, const int32_t *scan,
@@ -862,8 +865,30 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
     note_launch();
   }
   TRY(cudaGetLastError());
+
+  // macros and macro pin nodes (their counts read with the validation's
+  // result: the pin flags skip pins out of range)
+  void *stmp;
+  TRY(ensure(g->cell_macro, (size_t)(C + 1) * 4));
+  TRY(scan_tmp(g, C > NP ? C : NP, &stmp));
+  TRY((exclusive_scan<uint8_t, int32_t>(is_macro, P<int32_t>(g->cell_macro), C, stmp, s)));
+  TRY(ensure(g->tmp[1], (size_t)(NP > M ? NP : M) + 256));  // pin flags, later net flags
+  uint8_t *pflag = P<uint8_t>(g->tmp[1]);
+  TRY(ensure(g->tmp[2], (size_t)(NP + 1) * 4 + 256));
+  int32_t *pscan = P<int32_t>(g->tmp[2]);
+  if (NP) {
+    k_pin_macro_flag<<<grid_for(NP, 256), 256, 0, s>>>(nl->pin_cell, is_macro, NP, C, pflag);
+    note_launch();
+  }
+  TRY((exclusive_scan<uint8_t, int32_t>(pflag, pscan, NP, stmp, s)));
   int hst[16];
-  TRY(d2h(hst, g->status.p, 16, s));
+  int32_t sizes2[2];
+  {
+    const D2H it[3] = {{hst, g->status.p, 64},
+                       {&sizes2[0], P<int32_t>(g->cell_macro) + C, 4},
+                       {&sizes2[1], pscan + NP, 4}};
+    TRY(d2h_many(g->stage, it, 3, s));
+  }
   if (hst[0] & (ST_BAD_CELL | ST_BAD_NET | ST_BAD_INDEX)) {
     set_error("invalid netlist:%s%s%s", (hst[0] & ST_BAD_CELL) ? " cell size/kind/position" : "",
               (hst[0] & ST_BAD_NET) ? " net_ptr" : "",
@@ -881,26 +906,6 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   memcpy(&hmax, &hst[9], 4);
   memcpy(&mwmax, &hst[10], 4);
   memcpy(&mhmax, &hst[11], 4);
-
-  // macros and macro pin nodes
-  void *stmp;
-  TRY(ensure(g->cell_macro, (size_t)(C + 1) * 4));
-  TRY(scan_tmp(g, C > NP ? C : NP, &stmp));
-  TRY((exclusive_scan<uint8_t, int32_t>(is_macro, P<int32_t>(g->cell_macro), C, stmp, s)));
-  TRY(ensure(g->tmp[1], (size_t)(NP > M ? NP : M) + 256));  // pin flags, later net flags
-  uint8_t *pflag = P<uint8_t>(g->tmp[1]);
-  TRY(ensure(g->tmp[2], (size_t)(NP + 1) * 4 + 256));
-  int32_t *pscan = P<int32_t>(g->tmp[2]);
-  if (NP) {
-    k_pin_macro_flag<<<grid_for(NP, 256), 256, 0, s>>>(nl->pin_cell, is_macro, NP, pflag);
-    note_launch();
-  }
-  TRY((exclusive_scan<uint8_t, int32_t>(pflag, pscan, NP, stmp, s)));
-  int32_t sizes2[2];
-  {
-    const D2H it[2] = {{&sizes2[0], P<int32_t>(g->cell_macro) + C, 4}, {&sizes2[1], pscan + NP, 4}};
-    TRY(d2h_many(g->stage, it, 2, s));
-  }
   g->Mm = sizes2[0];
   g->Pm = sizes2[1];
   TRY(ensure(g->macro_cell, (size_t)g->Mm * 4 + 16));
@@ -1003,9 +1008,6 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
                                             g->tmp[3].p, s, maxrow)));
   TRY(ensure(g->srp, (size_t)(Nst + 1) * 8));
   TRY((exclusive_scan<int32_t, int64_t>(cnt, P<int64_t>(g->srp), Nst, stmp, s)));
-  int64_t nnz;
-  TRY(d2h(&nnz, P<int64_t>(g->srp) + Nst, 1, s));
-  g->nnz_static = (uint64_t)nnz;
   {
     pl_status ls = prepare_static_layout(g, s);
     if (ls != PL_OK) return ls;
@@ -1166,7 +1168,11 @@ pl_status build_static(pl_graph *g, const pl_netlist *nl, const pl_params *p, cu
   TRY(cudaEventRecord(g->ev_join, s2));
   TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
   TRY(cudaGetLastError());
-  TRY(cudaStreamSynchronize(s));
+  {
+    int64_t nnz;  // read with the build's final synchronisation
+    TRY(d2h(&nnz, P<int64_t>(g->srp) + Nst, 1, s));
+    g->nnz_static = (uint64_t)nnz;
+  }
   (void)kMaxNetPins;
   {
     pl_status fs = take_filter_buffers(g);
