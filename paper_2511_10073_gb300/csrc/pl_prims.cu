@@ -27,17 +27,33 @@ cudaError_t ensure(Buf &b, size_t bytes) {
   return cudaSuccess;
 }
 
+// The device values of a d2h_many call: item i's n[i] bytes (at most 64) go
+// to slot i of the staging buffer.
+struct GatherItems {
+  const unsigned char *src[8];
+  int n[8];
+};
+__global__ void k_gather_items(GatherItems it, int count, unsigned char *stage) {
+  const int i = threadIdx.x >> 6, b = threadIdx.x & 63;  // a thread per byte of a slot
+  if (i < count && b < it.n[i]) stage[i * 64 + b] = it.src[i][b];
+}
+
 cudaError_t d2h_many(Buf &stage, const D2H *items, int count, cudaStream_t s) {
   constexpr int kMax = 8, kSlot = 64;
   if (count < 1 || count > kMax) return cudaErrorInvalidValue;
   cudaError_t e = ensure(stage, (size_t)kMax * kSlot);
   if (e != cudaSuccess) return e;
+  GatherItems g{};
   for (int i = 0; i < count; ++i) {
     if (items[i].n > (size_t)kSlot) return cudaErrorInvalidValue;
-    e = cudaMemcpyAsync(static_cast<char *>(stage.p) + i * kSlot, items[i].d, items[i].n,
-                        cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+    g.src[i] = static_cast<const unsigned char *>(items[i].d);
+    g.n[i] = (int)items[i].n;
   }
+  // one gather kernel instead of a copy per item
+  k_gather_items<<<1, kMax * kSlot, 0, s>>>(g, count, static_cast<unsigned char *>(stage.p));
+  note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   unsigned char host[kMax * kSlot];
   e = cudaMemcpyAsync(host, stage.p, (size_t)count * kSlot, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
