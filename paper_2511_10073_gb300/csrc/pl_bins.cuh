@@ -21,7 +21,10 @@
 
 namespace pl {
 
-constexpr int kBinThreads = 256;   // 8 warps a CTA, each on its own chunks
+// 4 warps a CTA, each on its own chunks: a CTA of 8 K registers fits beside
+// the refinement product's short-row kernel held to 5 CTAs per SM, so the bin
+// rows run beside the short rows instead of after them
+constexpr int kBinThreads = 128;
 constexpr int kBinPer = 8;         // hint cells per lane
 constexpr int kBinChunk = 32 * kBinPer;  // hint cells per chunk (one warp)
 
@@ -142,7 +145,7 @@ __device__ __forceinline__ void bin_chunk(const BinGeo &B, const int32_t *bchunk
 }
 
 template <int WT, bool DEG>
-__global__ void __launch_bounds__(kBinThreads, 4) k_bin_partials(BinGeo B, const int32_t *bchunk,
+__global__ void __launch_bounds__(kBinThreads, 8) k_bin_partials(BinGeo B, const int32_t *bchunk,
                                                               const int32_t *cown,
                                                               const int64_t *boff,
                                                               const uint32_t *blist,

@@ -320,6 +320,7 @@ constexpr int kRowUnroll = 8;  // entries per lane and pass of a GiFt pair's sta
 // instructions.
 constexpr int kHmUnroll = 2;
 constexpr int kRowThreads = 256;
+constexpr int kRowCtasSide = 5;  // short-row CTAs per SM beside the hub and bin-row kernels
 
 template <int WT, int L, int U>
 __device__ __forceinline__ void row_piece(const int32_t *col, const void *w, uint32_t k,
@@ -897,7 +898,11 @@ static cudaError_t launch_step(const StepArgs &A, double bytes, int wdtype, cuda
   }
   const long long rows_per_block = (long long)(kRowThreads / 32) * (32 / kRowLanes);
   const long long want = (A.nrows + rows_per_block - 1) / rows_per_block;
-  const long long cap = (long long)occ[wi] * nsm;
+  // refinement products with a second stream: at most kRowCtasSide CTAs per
+  // SM, so the registers they leave free hold the second stream's CTAs, which
+  // then run beside the short rows rather than after them
+  const int per_sm = MODE == MODE_HR && fork && occ[wi] > kRowCtasSide ? kRowCtasSide : occ[wi];
+  const long long cap = (long long)per_sm * nsm;
   const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   if (wi) k_spmm_rows<1, MODE><<<grid, kRowThreads, 0, s>>>(A);
   else k_spmm_rows<0, MODE><<<grid, kRowThreads, 0, s>>>(A);
